@@ -1,0 +1,415 @@
+"""Benchmark of the GB300 per-day GradABM step (forward + MSE + hand-written backward).
+
+Workload: 1,000,000 agents on the four-interaction-type synthetic contact graph
+(households, schools, workplaces, random contacts; ~22.4M directed edges),
+60 days, R = 2.5, 20 seed infections, MSE on daily deaths against a seeded
+synthetic curve, gradients for R_t, m_t and S_a.  One step = one forward over
+the horizon + the loss + the reverse sweep, all in the library's kernels.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
+oracle instead (on a bounded sample of the same workload).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "agent-days/s fwd and fwd+bwd at 1M agents; HBM GB/s fraction; batched vs plain"
+N_AGENTS = 1_000_000
+DAYS = 60
+R0 = 2.5
+MORTALITY = 0.01
+N_SEED = 20
+TAU_EI, TAU_IR = 4, 7
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def _kernel_source_sha(names):
+    h = hashlib.sha256()
+    for n in names:
+        with open(os.path.join(ROOT, "paper_2207_09714_gb300", "csrc", n), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def _ncu_traffic(kernel: str, sha: str, workload: str):
+    """Per-launch DRAM bytes of ``kernel`` from the committed ncu summary, if it was taken
+    on the current kernel source and this workload; else None."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    for line in open(path):
+        if line.startswith("#") or not line.strip():
+            continue
+        kv = dict(tok.split("=", 1) for tok in line.split() if "=" in tok)
+        if kv.get("kernel") == kernel and kv.get("src_sha") == sha and kv.get("workload") == workload:
+            return float(kv["bytes_per_launch"])
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            p = [x.strip() for x in l.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx.append(float(p[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def trajectory_bytes(E, deg, T, L, n_rows, policy_store):
+    """Algorithmic (compulsory) HBM bytes of every forward and backward day launch, from
+    the final exposure days E (which determine each day's state)."""
+    E = E.astype(np.int64)
+    NEVER = 32767
+    seed = (E != NEVER) & (E < 0)
+    live = ~seed
+    never = E == NEVER
+    Ec = np.where(never, T, E)          # never infected counts as susceptible every day
+    Ec = np.where(seed, -1, Ec)
+    # rows susceptible on day t: Ec >= t ; edges of those rows
+    hist_n = np.bincount(np.clip(Ec[live], 0, T), minlength=T + 1)
+    hist_e = np.bincount(np.clip(Ec[live], 0, T), weights=deg[live], minlength=T + 1)
+    S_cnt = np.cumsum(hist_n[::-1])[::-1][:T]
+    S_nnz = np.cumsum(hist_e[::-1])[::-1][:T]
+    new = np.bincount(E[live & ~never], minlength=T)[:T]
+    fwd = 8.0 * S_nnz + 4.0 * S_cnt + 1.0 * S_cnt + 2.0 * n_rows + 2.0 * new
+    if policy_store:
+        fwd += 4.0 * S_cnt
+    # backward: rows needing the transpose gather on day t are live with Ec >= t + 2 - L
+    def ge(thr):
+        thr = np.clip(thr, 0, T)
+        return S_cnt_full[thr], S_nnz_full[thr]
+    S_cnt_full = np.concatenate([np.cumsum(hist_n[::-1])[::-1], [0]])
+    S_nnz_full = np.concatenate([np.cumsum(hist_e[::-1])[::-1], [0]])
+    bwd = np.zeros(T)
+    for t in range(T):
+        nS, eS = S_cnt[t], S_nnz[t]
+        if t + 1 < T:
+            nA, eA = ge(max(t + 2 - L, 0))
+        else:
+            nA, eA = nS, eS
+        ring_reads = max(0, min(L - 1, T - 1 - t) - 1)      # slots k = 2..L-1 inside the horizon
+        b = 8.0 * eA + 4.0 * nA + 2.0 * n_rows + 1.0 * nS
+        b += 4.0 * ring_reads * nS + (4.0 * nA if t + 1 < T else 0.0)   # ring reads and write
+        b += 4.0 * nS + 4.0 * nS                                     # A read/write, r write
+        if policy_store:
+            b += 4.0 * nS
+        b += 72.0 * (n_rows // 32)                                   # per-tile partial sums
+        bwd[t] = b
+    return fwd, bwd, S_cnt, S_nnz
+
+
+def run_reference(args, world, rank):
+    """The FP64 CPU oracle as it stands, on a bounded sample of the workload."""
+    if rank != 0:
+        return
+    import oracle as O
+    from paper_2207_09714_gb300 import synth
+    n_sample = 250_000
+    pop = synth.population_typed(n_sample, seed=0)
+    c = synth.infectiousness_table(TAU_EI, TAU_IR)
+    R = np.full(DAYS, R0, np.float32)
+    m = np.full(DAYS, MORTALITY, np.float32)
+    S = synth.SUSCEPTIBILITY.astype(np.float32)
+    y = synth.target_curve(DAYS, pop.n)
+    md = O.Model(TAU_EI, TAU_IR, c, seed=0)
+
+    def step():
+        f = O.forward_hard(pop, md, R, m, S, n_seed=N_SEED)
+        _, gD = O.mse(f["D"], y)
+        O.backward_hard(pop, md, R, m, S, f["e_final"], gD)
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = (time.perf_counter() - t0) / max(args.steps, 1)
+    value = pop.n * DAYS / dt
+    sample = (f"{pop.n} agents of the same generator ({pop.nnz} directed edges), {DAYS} days, "
+              f"forward + MSE + backward per step")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "agent-days/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"typed contact graph, {DAYS} days, fwd+bwd (CPU oracle sample)",
+                   "n_agents": pop.n, "nnz": pop.nnz, "days": DAYS},
+        "cpu_baseline": {"value": value, "unit": "agent-days/s", "cores": O.num_threads(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "agent-days/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(pop, c, y):
+    """Oracle timing on the host cores: one forward + MSE + backward on a 250k-agent sample."""
+    import oracle as O
+    from paper_2207_09714_gb300 import synth
+    n_sample = 250_000
+    sub = synth.population_typed(n_sample, seed=0)
+    R = np.full(DAYS, R0, np.float32)
+    m = np.full(DAYS, MORTALITY, np.float32)
+    S = synth.SUSCEPTIBILITY.astype(np.float32)
+    ys = synth.target_curve(DAYS, sub.n)
+    md = O.Model(TAU_EI, TAU_IR, c, seed=0)
+    O.build()
+    t0 = time.perf_counter()
+    f = O.forward_hard(sub, md, R, m, S, n_seed=N_SEED)
+    _, gD = O.mse(f["D"], ys)
+    O.backward_hard(sub, md, R, m, S, f["e_final"], gD)
+    dt = time.perf_counter() - t0
+    return {"value": sub.n * DAYS / dt, "unit": "agent-days/s", "cores": O.num_threads(), "kind": "oracle",
+            "sample": f"one forward + MSE + backward of a {sub.n}-agent graph from the same generator "
+                      f"({sub.nnz} directed edges), {DAYS} days, FP64 ({dt:.1f} s)"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--policy", default="recompute", choices=["store", "recompute"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        if world > 1:
+            import torch.distributed as dist
+            dist.init_process_group("gloo")
+        run_reference(args, world, rank)
+        return
+
+    import torch
+    from paper_2207_09714_gb300 import build as gbuild
+    from paper_2207_09714_gb300 import capi, synth
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    gbuild.build()
+
+    pop = synth.population_typed(N_AGENTS, seed=0)
+    c = synth.infectiousness_table(TAU_EI, TAU_IR)
+    policy = capi.GABM_STORE_LAMBDA if args.policy == "store" else capi.GABM_RECOMPUTE
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        ctx = capi.gabm_create([pop], capi.ModelDesc(TAU_EI, TAU_IR, c, seed=rank, lambda_policy=policy),
+                               stream=stream)
+    R = torch.full((1, DAYS), R0, dtype=torch.float32, device="cuda")
+    m = torch.full((1, DAYS), MORTALITY, dtype=torch.float32, device="cuda")
+    S = torch.from_numpy(synth.SUSCEPTIBILITY[None, :].copy()).cuda()
+    y_np = synth.target_curve(DAYS, pop.n)[None, :]
+    y = torch.from_numpy(y_np).cuda()
+    D = torch.empty((1, DAYS), dtype=torch.float64, device="cuda")
+    loss = torch.empty((1,), dtype=torch.float64, device="cuda")
+    gD = torch.empty((1, DAYS), dtype=torch.float64, device="cuda")
+    dR = torch.empty((1, DAYS), dtype=torch.float64, device="cuda")
+    dm = torch.empty((1, DAYS), dtype=torch.float64, device="cuda")
+    dS = torch.empty((1, 9), dtype=torch.float64, device="cuda")
+
+    def step(ev_mid=None):
+        capi.gabm_forward(ctx, DAYS, R, m, S, [N_SEED], D=D)
+        if ev_mid is not None:
+            ev_mid.record(stream)
+        capi.gabm_mse_loss(ctx, y, loss=loss, gD=gD)
+        capi.gabm_backward(ctx, gD, dR=dR, dm=dm, dS_age=dS)
+
+    torch.cuda.synchronize()
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+
+    # ---- timed region (device-resident inputs) ----
+    capi.gabm_set_profiling(ctx, True)
+    launches0 = capi.gabm_launch_count(ctx)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    mids = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            starts[k].record(stream)
+            step(mids[k])
+            ends[k].record(stream)
+        torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    launches = capi.gabm_launch_count(ctx) - launches0
+    fwd_ms_k, fwd_n = capi.gabm_get_profile(ctx, 0)
+    bwd_ms_k, bwd_n = capi.gabm_get_profile(ctx, 1)
+    capi.gabm_set_profiling(ctx, False)
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    fwd_ms = [s.elapsed_time(e) for s, e in zip(starts, mids)]
+    total_ms = sum(step_ms)
+    if dist is not None:
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    units = world * pop.n * DAYS
+    value = units / (ms_per_step / 1e3)
+    fwd_value = world * pop.n * DAYS / (statistics.median(fwd_ms) / 1e3)
+
+    # ---- algorithmic bytes of the day kernels, from this trajectory ----
+    E = capi.gabm_get_state(ctx)[0]
+    deg = pop.degrees().astype(np.float64)
+    n_rows = ((pop.n + 31) // 32) * 32
+    fwd_b, bwd_b, S_cnt, S_nnz = trajectory_bytes(E, deg, DAYS, TAU_EI + TAU_IR, n_rows,
+                                                  policy == capi.GABM_STORE_LAMBDA)
+    fwd_gbs = fwd_b.sum() * args.steps / (fwd_ms_k / 1e3) / 1e9 if fwd_ms_k > 0 else None
+    bwd_gbs = bwd_b.sum() * args.steps / (bwd_ms_k / 1e3) / 1e9 if bwd_ms_k > 0 else None
+    peak, peak_kind = _peaks()
+    dominant = "k_bwd_day" if bwd_ms_k >= fwd_ms_k else "k_fwd_day"
+    src = ["backward.cu", "rowsum.cuh", "gabm_internal.cuh"] if dominant == "k_bwd_day" else \
+          ["forward.cu", "rowsum.cuh", "gabm_internal.cuh"]
+    workload_tag = f"typed1M_T{DAYS}_{args.policy}"
+    traffic = _ncu_traffic(dominant, _kernel_source_sha(src), workload_tag)
+    dom_gbs = bwd_gbs if dominant == "k_bwd_day" else fwd_gbs
+    dom_bytes = (bwd_b.sum() if dominant == "k_bwd_day" else fwd_b.sum()) / DAYS
+    dom_ms = (bwd_ms_k / bwd_n) if dominant == "k_bwd_day" else (fwd_ms_k / fwd_n)
+
+    # ---- end to end through the C ABI with pinned host buffers ----
+    Rh = torch.full((1, DAYS), R0, dtype=torch.float32).pin_memory()
+    mh = torch.full((1, DAYS), MORTALITY, dtype=torch.float32).pin_memory()
+    Sh = torch.from_numpy(synth.SUSCEPTIBILITY[None, :].copy()).pin_memory()
+    yh = torch.from_numpy(y_np.copy()).pin_memory()
+    Dh = torch.empty((1, DAYS), dtype=torch.float64).pin_memory()
+    lh = torch.empty((1,), dtype=torch.float64).pin_memory()
+    gDh = torch.empty((1, DAYS), dtype=torch.float64).pin_memory()
+    dRh = torch.empty((1, DAYS), dtype=torch.float64).pin_memory()
+    dmh = torch.empty((1, DAYS), dtype=torch.float64).pin_memory()
+    dSh = torch.empty((1, 9), dtype=torch.float64).pin_memory()
+
+    def e2e_step():
+        capi.gabm_forward(ctx, DAYS, Rh, mh, Sh, [N_SEED], D=Dh)
+        capi.gabm_mse_loss(ctx, yh, loss=lh, gD=gDh)
+        capi.gabm_backward(ctx, gDh, dR=dRh, dm=dmh, dS_age=dSh)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1)
+    if dist is not None:
+        t = torch.tensor([e2e_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e_value = units / (e2e_ms / args.steps / 1e3)
+    h2d = (Rh.numel() * 4 + mh.numel() * 4 + Sh.numel() * 4 + yh.numel() * 8 + gDh.numel() * 8)
+    d2h = (Dh.numel() * 8 + lh.numel() * 8 + gDh.numel() * 8 + dRh.numel() * 8 + dmh.numel() * 8 + dSh.numel() * 8)
+
+    cur, peak_mem = capi.gabm_mem_stats(ctx)
+    if rank != 0:
+        return
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        cpu = cpu_baseline(pop, c, y_np[0])
+    line = {
+        "metric": METRIC, "value": value, "unit": "agent-days/s", "n_gpus": world, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"1M-agent typed contact graph (households, schools, workplaces, random), "
+                               f"{DAYS} days, forward + MSE + hand-written backward",
+                   "n_agents": pop.n, "nnz": pop.nnz, "days": DAYS, "instances_per_gpu": 1,
+                   "lambda_policy": args.policy, "R": R0, "n_seed": N_SEED,
+                   "l2": f"inputs larger than L2 (edge arrays {pop.nnz * 8 / 1e6:.0f} MB > 129 MB), no flush"},
+        "fwd_agent_days_per_s": fwd_value,
+        "edge_updates_per_s": world * pop.nnz * DAYS / (ms_per_step / 1e3),
+        "sus_edges_per_day_mean": float(S_nnz.mean()),
+        "roofline": {"bound": "hbm", "kernel": dominant, "achieved": dom_gbs, "peak": peak, "unit": "GB/s",
+                     "frac": (dom_gbs / peak) if dom_gbs else None, "traffic": traffic,
+                     "peak_source": peak_kind,
+                     "alg_bytes_per_launch": dom_bytes, "avg_launch_ms": dom_ms,
+                     "fwd_day": {"achieved": fwd_gbs, "launches": fwd_n, "ms_total": fwd_ms_k},
+                     "bwd_day": {"achieved": bwd_gbs, "launches": bwd_n, "ms_total": bwd_ms_k}},
+        "e2e": {"value": e2e_value, "unit": "agent-days/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+        "peak_hbm_bytes": peak_mem,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

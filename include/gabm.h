@@ -1,0 +1,188 @@
+/*
+ * gabm.h -- C ABI of the GB300 library for the per-day step of GradABM
+ * ("Differentiable Agent-based Epidemiology", arXiv 2207.09714).
+ *
+ * The library simulates the hard (sampled) epidemic model of Sec. 3.1 over T
+ * days on a contact graph and computes the straight-through adjoint of an MSE
+ * loss on daily deaths with respect to the per-day transmissibility R_t, the
+ * per-day mortality m_t and the per-age susceptibility S_a (Sec. 3.2, App. B).
+ *
+ * Model (Sec. 3.1, Eq. 1-3; assumptions A1-A6 of App. A):
+ *   agent state: age bin a_i in 0..8, exposure day e_i (GABM_NEVER = susceptible);
+ *   stage on day t from k = t - e_i: E if k < tau_EI, I if k < L, RM otherwise,
+ *     L = tau_EI + tau_IR (Progress is deterministic, Sec. 3.1 and App. B);
+ *   Transmit for susceptible i:
+ *     lambda_i(t) = R_t * S[a_i] * (1/Dbar) * sum_{j in N_in(i)} w_ji * c[t - e_j],
+ *     Dbar = (sum of all weights) / n, c[0] = 0 (A2), c[k] = 0 for k >= L;
+ *     p_i = 1 - exp(-lambda_i)  (Eq. 3, one-day step A1);
+ *     infected iff u_i < p_i, u_i from Philox4x32-10 keyed (seed; agent, day,
+ *     instance, 0), u = ((x0 >> 9) + 0.5) * 2^-23; newly infected get e_i = t;
+ *   Aggregate: daily new deaths D_t = m_t * #{i : t - e_i = L};
+ *   initial infections: the n_seed agents with the smallest Philox key at
+ *     (agent, 0, instance, 1), placed at e = -tau_EI (they start in I on day 0);
+ *   backward: Gumbel-softmax relaxation y = sigmoid(logit p - logit u) used
+ *     straight-through, adjoint of the unrolled day loop (App. B).
+ *
+ * Conventions
+ *   - Status codes are returned by every call; no exception crosses the ABI.
+ *     gabm_last_error() gives a message for the last failing call on a ctx.
+ *   - "Instances": num_graphs graphs x sets_per_graph parameter sets; instance
+ *     index = graph * sets_per_graph + set.  Per-instance arrays are laid out
+ *     [instance][...] row-major.
+ *   - Agent ids in and out are the caller's ids within each graph.
+ *   - A mem_space argument (GABM_DEVICE / GABM_HOST) says where every array
+ *     argument of that call lives.  Device work is enqueued on the ctx stream;
+ *     with GABM_DEVICE the call returns without waiting for it, with GABM_HOST
+ *     the call copies through ctx-owned device buffers and synchronises the
+ *     stream before it returns.
+ *   - A ctx owns all of its device memory and is not thread-safe.
+ */
+#ifndef GABM_H
+#define GABM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GABM_OK = 0,
+    GABM_EINVAL = 1,       /* invalid argument or input data (nothing was changed) */
+    GABM_ENOMEM = 2,       /* device allocation failed (ctx left usable, or not created) */
+    GABM_ECUDA = 3,        /* a CUDA runtime call failed */
+    GABM_ESTATE = 4,       /* call out of order (e.g. backward without a matching forward) */
+    GABM_ETIMEOUT = 5,     /* reserved: a bounded device wait gave up */
+    GABM_ECANCELLED = 6,   /* reserved: cancelled between days */
+    GABM_EUNSUPPORTED = 7  /* valid request this build does not implement */
+} gabm_status;
+
+enum { GABM_DEVICE = 0, GABM_HOST = 1 };
+enum { GABM_HARD_ST = 0, GABM_SOFT = 1 };
+/* Where the backward gets lambda_i(t): stored by the forward (4 bytes per
+ * susceptible agent-day), or recomputed from the final state.  In the hard
+ * model the final exposure-day vector determines every day's state (A3/A4: no
+ * reinfection), so recomputation needs no intermediate checkpoints. */
+enum { GABM_STORE_LAMBDA = 0, GABM_RECOMPUTE = 1 };
+
+#define GABM_NEVER 32767     /* exposure day of a susceptible agent */
+#define GABM_NUM_AGES 9      /* age bins 0-10, 11-20, ..., 71-80, 80+ (Sec. 3.1) */
+#define GABM_MAX_L 32        /* upper bound on tau_EI + tau_IR */
+#define GABM_MAX_DAYS 16384  /* upper bound on T (exposure days are int16) */
+
+typedef struct gabm_ctx gabm_ctx;
+
+/* One contact graph in destination-sorted CSR form (Sec. 3.1: interaction
+ * network as a sparse adjacency matrix; App. A: sparse, small-world).
+ * Row i lists the in-neighbours j of agent i; w[p] is the weight of the
+ * interaction from j into i.  Requirements (checked, GABM_EINVAL otherwise):
+ * rowptr[0] = 0, non-decreasing, rowptr[n] = nnz; col < n; w finite and >= 0;
+ * age <= 8.  Self loops and repeated pairs are allowed and harmless (an agent
+ * is never infectious while susceptible; repeated pairs add).  n < 2^31 and
+ * nnz < 2^32 per graph.  Arrays are read during gabm_create only. */
+typedef struct {
+    int64_t n, nnz;
+    const uint64_t *rowptr;  /* [n+1] */
+    const uint32_t *col;     /* [nnz] */
+    const float *w;          /* [nnz] */
+    const uint8_t *age;      /* [n]   */
+    int mem_space;           /* GABM_HOST or GABM_DEVICE */
+} gabm_graph_desc;
+
+/* Model constants fixed for the life of a ctx (Sec. 3.1: theta_P stage times,
+ * T_s stage transmissibility folded into c; App. D: infectiousness profile). */
+typedef struct {
+    int tau_EI, tau_IR;   /* days E->I and I->RM; 1 <= each, L = sum <= GABM_MAX_L */
+    const float *c;       /* host [L]: infectiousness by days since exposure, c[0] = 0, c >= 0 */
+    float gumbel_tau;     /* relaxation temperature; this build supports 1.0 */
+    int relax_mode;       /* GABM_HARD_ST (GABM_SOFT: GABM_EUNSUPPORTED in this build) */
+    int lambda_policy;    /* GABM_STORE_LAMBDA or GABM_RECOMPUTE */
+    uint64_t seed;        /* Philox key */
+} gabm_model_desc;
+
+/* Build a ctx: validates and copies the graphs (GABM_EINVAL on bad data, before
+ * any CUDA call), builds the device CSR and its transpose (aliased when the
+ * weights are symmetric), and allocates the per-agent state.  cuda_stream is a
+ * cudaStream_t (NULL = legacy default stream).  num_graphs >= 1 graphs are
+ * concatenated block-diagonally (uneven batch); sets_per_graph must be 1 in
+ * this build.  On success *out owns everything; release with gabm_destroy. */
+gabm_status gabm_create(const gabm_graph_desc *graphs, int num_graphs, int sets_per_graph,
+                        const gabm_model_desc *model, void *cuda_stream, gabm_ctx **out);
+
+/* Forward over days t0..T-1 (Sec. 3.1, Eq. 1-3, K = T steps).  t0 = 0 after
+ * create (seeding from n_seed), or the day given to the last gabm_set_state.
+ *   R      [I][T] float  transmissibility R_t per instance
+ *   m      [I][T] float  mortality m_t per instance
+ *   S_age  [I][9] float  susceptibility per age bin
+ *   n_seed [I]    int32  initial infections per instance (HOST memory always;
+ *                        ignored when resuming from gabm_set_state)
+ *   D      [I][T] double out: daily new deaths D_t = m_t * newRM(t) (days >= t0)
+ *   counts [I][T][4] int32 out or NULL: S, E, I, RM at the start of each day
+ * 1 <= T <= GABM_MAX_DAYS.  The first call with a larger T grows the per-day
+ * buffers (an allocation). */
+gabm_status gabm_forward(gabm_ctx *ctx, int T, const float *R, const float *m, const float *S_age,
+                         const int32_t *n_seed, double *D, int32_t *counts, int mem_space);
+
+/* MSE on daily deaths of the last forward (Sec. 3.2, Stage 3):
+ *   loss[i] = (1/T) sum_t (D[i][t] - y[i][t])^2,  gD[i][t] = 2 (D[i][t] - y[i][t]) / T.
+ *   y [I][T] double in; loss [I] double out; gD [I][T] double out.
+ * GABM_ESTATE if no forward has run. */
+gabm_status gabm_mse_loss(gabm_ctx *ctx, const double *y, double *loss, double *gD, int mem_space);
+
+/* Straight-through adjoint of the last forward (App. B): given gD = dL/dD_t
+ * [I][T] (double), writes dR [I][T], dm [I][T] and dS_age [I][9] (double).
+ * Cross-agent and cross-day sums are FP64 in a fixed order (bitwise
+ * reproducible).  GABM_ESTATE without a forward (or set_state) of the same T,
+ * or with GABM_STORE_LAMBDA when the stored lambdas do not cover days 0..T-1. */
+gabm_status gabm_backward(gabm_ctx *ctx, const double *gD, double *dR, double *dm,
+                          double *dS_age, int mem_space);
+
+/* Current exposure-day vector e [sets_per_graph][n_total] (int16; per set, the
+ * graphs' agents concatenated in graph order, caller ids within each graph).
+ * After a forward over T days this is the final state. */
+gabm_status gabm_get_state(gabm_ctx *ctx, int16_t *e_out, int mem_space);
+
+/* Replace the state with e [sets_per_graph][n_total] as the start of day `day` (0 <= day <=
+ * GABM_MAX_DAYS).  The next gabm_forward then runs days day..T-1 without
+ * seeding; a gabm_forward with T == day only records its parameters, after
+ * which gabm_backward (GABM_RECOMPUTE) replays the trajectory e encodes.
+ * Values must be GABM_NEVER or in [-GABM_MAX_L, day). */
+gabm_status gabm_set_state(gabm_ctx *ctx, int day, const int16_t *e_in, int mem_space);
+
+/* lambda_i(t) of the last forward for day t, [sets_per_graph][n_total] float, 0 for agents
+ * not susceptible on day t.  Needs GABM_STORE_LAMBDA and t run by the forward. */
+gabm_status gabm_get_lambda(gabm_ctx *ctx, int t, float *lam_out, int mem_space);
+
+/* Device bytes the ctx holds now and at most so far. */
+gabm_status gabm_mem_stats(const gabm_ctx *ctx, size_t *current, size_t *peak);
+
+/* Kernel launches this ctx has issued since creation. */
+uint64_t gabm_launch_count(const gabm_ctx *ctx);
+
+/* Per-kind kernel timing with CUDA events recorded on the ctx stream around
+ * each launch of that kind (kind 0: forward day, 1: backward day).  Enable,
+ * run, then read the summed milliseconds and launch count (syncs the stream). */
+gabm_status gabm_set_profiling(gabm_ctx *ctx, int enable);
+gabm_status gabm_get_profile(gabm_ctx *ctx, int kind, double *total_ms, int64_t *launches);
+
+/* Evaluate the device Philox4x32-10 (Salmon et al., SC'11) for test use:
+ * ctr [count][4] uint32 and out [count][4] uint32, both device memory. */
+gabm_status gabm_philox(uint64_t seed, const uint32_t *ctr, uint32_t *out, int64_t count,
+                        void *cuda_stream);
+
+/* Message for the last failing call on ctx (or for the last failing
+ * gabm_create when ctx is NULL).  Valid until the next call on that ctx. */
+const char *gabm_last_error(const gabm_ctx *ctx);
+
+/* Release everything a ctx owns (waits for its stream).  NULL-safe. */
+void gabm_destroy(gabm_ctx *ctx);
+
+/* Library version string. */
+const char *gabm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GABM_H */

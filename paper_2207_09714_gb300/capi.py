@@ -1,0 +1,340 @@
+"""Thin Python binding of the C ABI in ``include/gabm.h`` (same function names).
+
+Argument marshalling only: every step of the simulation and of its adjoint
+runs in the CUDA library ``_build/libgabm.so``.  Arrays may be CUDA tensors
+(the call runs with GABM_DEVICE) or numpy arrays / CPU tensors (GABM_HOST);
+one call takes all of its arrays from the same side.  PyTorch is used for
+device memory and the CUDA stream.  There is no CPU fallback: if the library
+has not been built, loading it raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import os
+import re
+import threading
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libgabm.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "gabm.h")
+
+GABM_OK, GABM_EINVAL, GABM_ENOMEM, GABM_ECUDA, GABM_ESTATE = 0, 1, 2, 3, 4
+GABM_ETIMEOUT, GABM_ECANCELLED, GABM_EUNSUPPORTED = 5, 6, 7
+GABM_DEVICE, GABM_HOST = 0, 1
+GABM_HARD_ST, GABM_SOFT = 0, 1
+GABM_STORE_LAMBDA, GABM_RECOMPUTE = 0, 1
+GABM_NEVER = 32767
+GABM_NUM_AGES = 9
+STATUS_NAMES = {0: "GABM_OK", 1: "GABM_EINVAL", 2: "GABM_ENOMEM", 3: "GABM_ECUDA", 4: "GABM_ESTATE",
+                5: "GABM_ETIMEOUT", 6: "GABM_ECANCELLED", 7: "GABM_EUNSUPPORTED"}
+
+
+class GabmError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class _GraphDesc(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("nnz", ctypes.c_int64), ("rowptr", ctypes.c_void_p),
+                ("col", ctypes.c_void_p), ("w", ctypes.c_void_p), ("age", ctypes.c_void_p),
+                ("mem_space", ctypes.c_int)]
+
+
+class _ModelDesc(ctypes.Structure):
+    _fields_ = [("tau_EI", ctypes.c_int), ("tau_IR", ctypes.c_int), ("c", ctypes.c_void_p),
+                ("gumbel_tau", ctypes.c_float), ("relax_mode", ctypes.c_int),
+                ("lambda_policy", ctypes.c_int), ("seed", ctypes.c_uint64)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load libgabm.so (built by ``paper_2207_09714_gb300.build``); raises if it is missing."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise RuntimeError(f"CUDA library not built: {path} is missing "
+                               "(run `python -m paper_2207_09714_gb300.build`)")
+        L = ctypes.CDLL(path)
+        P, i32, i64, u64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_uint64
+        L.gabm_create.argtypes = [ctypes.POINTER(_GraphDesc), i32, i32, ctypes.POINTER(_ModelDesc), P,
+                                  ctypes.POINTER(P)]
+        L.gabm_forward.argtypes = [P, i32, P, P, P, P, P, P, i32]
+        L.gabm_mse_loss.argtypes = [P, P, P, P, i32]
+        L.gabm_backward.argtypes = [P, P, P, P, P, i32]
+        L.gabm_get_state.argtypes = [P, P, i32]
+        L.gabm_set_state.argtypes = [P, i32, P, i32]
+        L.gabm_get_lambda.argtypes = [P, i32, P, i32]
+        L.gabm_mem_stats.argtypes = [P, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t)]
+        L.gabm_launch_count.argtypes = [P]
+        L.gabm_launch_count.restype = u64
+        L.gabm_set_profiling.argtypes = [P, i32]
+        L.gabm_get_profile.argtypes = [P, i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)]
+        L.gabm_philox.argtypes = [u64, P, P, i64, P]
+        L.gabm_last_error.argtypes = [P]
+        L.gabm_last_error.restype = ctypes.c_char_p
+        L.gabm_destroy.argtypes = [P]
+        L.gabm_destroy.restype = None
+        L.gabm_version.restype = ctypes.c_char_p
+        for name in ("gabm_create", "gabm_forward", "gabm_mse_loss", "gabm_backward", "gabm_get_state",
+                     "gabm_set_state", "gabm_get_lambda", "gabm_mem_stats", "gabm_set_profiling",
+                     "gabm_get_profile", "gabm_philox"):
+            getattr(L, name).restype = ctypes.c_int
+        _lib = L
+        return L
+
+
+def header_functions(path: str = HEADER):
+    """Names of the functions include/gabm.h declares."""
+    src = open(path).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(gabm_[a-z_0-9]+)\s*\(", src)))
+
+
+# --------------------------------------------------------------------------- marshalling
+def _is_cuda(x) -> bool:
+    return hasattr(x, "is_cuda") and bool(x.is_cuda)
+
+
+def _space(*arrays) -> int:
+    present = [a for a in arrays if a is not None]
+    kinds = {_is_cuda(a) for a in present}
+    if len(kinds) > 1:
+        raise ValueError("all arrays of one call must be CUDA tensors, or all host arrays")
+    return GABM_DEVICE if kinds == {True} else GABM_HOST
+
+
+def _ptr(x, dtype=None):
+    """Pointer to a contiguous array of the given numpy dtype (validated, never converted)."""
+    if x is None:
+        return None
+    if _is_cuda(x) or hasattr(x, "data_ptr"):
+        import torch
+        want = {np.float32: torch.float32, np.float64: torch.float64, np.int32: torch.int32,
+                np.int16: torch.int16, np.uint8: torch.uint8, np.uint32: torch.uint32,
+                np.uint64: torch.uint64}.get(dtype)
+        if want is not None and x.dtype != want:
+            raise TypeError(f"expected {want}, got {x.dtype}")
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return ctypes.c_void_p(x.data_ptr())
+    if not isinstance(x, np.ndarray):
+        raise TypeError(f"unsupported array type {type(x)}")
+    if dtype is not None and x.dtype != np.dtype(dtype):
+        raise TypeError(f"expected {np.dtype(dtype)}, got {x.dtype}")
+    if not x.flags["C_CONTIGUOUS"]:
+        raise ValueError("array must be C-contiguous")
+    return ctypes.c_void_p(x.ctypes.data)
+
+
+def _check(status: int, handle=None):
+    if status != GABM_OK:
+        msg = load_library().gabm_last_error(handle).decode(errors="replace")
+        raise GabmError(status, msg)
+
+
+def _empty(shape, np_dtype, cuda: bool, device=None):
+    if cuda:
+        import torch
+        tdt = {np.float64: torch.float64, np.float32: torch.float32, np.int32: torch.int32,
+               np.int16: torch.int16}[np_dtype]
+        return torch.empty(shape, dtype=tdt, device=device)
+    return np.empty(shape, dtype=np_dtype)
+
+
+@dataclasses.dataclass
+class ModelDesc:
+    """Model constants of a ctx (mirrors gabm_model_desc)."""
+    tau_EI: int
+    tau_IR: int
+    c: np.ndarray
+    seed: int = 0
+    lambda_policy: int = GABM_STORE_LAMBDA
+    gumbel_tau: float = 1.0
+    relax_mode: int = GABM_HARD_ST
+
+
+class GabmCtx:
+    """Owning handle of a gabm_ctx (destroyed with the object)."""
+
+    def __init__(self, handle, graphs, sets, model, device, stream):
+        self.handle = handle
+        self.num_graphs = len(graphs)
+        self.sets = sets
+        self.instances = len(graphs) * sets
+        self.n_per_graph = [int(g.n) for g in graphs]
+        self.n_total = sum(self.n_per_graph)
+        self.model = model
+        self.device = device
+        self.stream = stream
+        self.T = None
+        self._lib = load_library()
+
+    def close(self):
+        if self.handle:
+            self._lib.gabm_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# --------------------------------------------------------------------------- ABI
+def gabm_version() -> str:
+    return load_library().gabm_version().decode()
+
+
+def gabm_create(graphs, model: ModelDesc, sets_per_graph: int = 1, stream=None) -> GabmCtx:
+    """Create a ctx from graphs (objects with n, rowptr, col, w, age) and a ModelDesc."""
+    L = load_library()
+    keep = []
+    descs = (_GraphDesc * max(len(graphs), 1))()
+    device = None
+    for i, g in enumerate(graphs):
+        ms = _space(g.rowptr, g.col, g.w, g.age)
+        if ms == GABM_DEVICE:
+            device = g.rowptr.device
+        descs[i] = _GraphDesc(int(g.n), int(g.col.shape[0]), _ptr(g.rowptr, np.uint64), _ptr(g.col, np.uint32),
+                              _ptr(g.w, np.float32), _ptr(g.age, np.uint8), ms)
+        keep.append(g)
+    c = np.ascontiguousarray(model.c, dtype=np.float32)
+    md = _ModelDesc(int(model.tau_EI), int(model.tau_IR), _ptr(c, np.float32), float(model.gumbel_tau),
+                    int(model.relax_mode), int(model.lambda_policy), int(model.seed))
+    s = None
+    if stream is not None:
+        s = ctypes.c_void_p(int(getattr(stream, "cuda_stream", stream)))
+    else:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                stream = torch.cuda.current_stream()
+                s = ctypes.c_void_p(stream.cuda_stream)
+                device = device or torch.device("cuda", torch.cuda.current_device())
+        except ImportError:
+            pass
+    out = ctypes.c_void_p()
+    st = L.gabm_create(descs, len(graphs), int(sets_per_graph), ctypes.byref(md), s, ctypes.byref(out))
+    _check(st, None)
+    return GabmCtx(out, graphs, int(sets_per_graph), model, device, stream)
+
+
+def gabm_forward(ctx: GabmCtx, T: int, R, m, S_age, n_seed=None, D=None, counts=None, want_counts=False):
+    """Run the forward over T days; returns (D [I,T] float64, counts [I,T,4] int32 or None)."""
+    ms = _space(R, m, S_age, D, counts)
+    cuda = ms == GABM_DEVICE
+    I = ctx.instances
+    if D is None:
+        D = _empty((I, T), np.float64, cuda, ctx.device)
+    if counts is None and want_counts:
+        counts = _empty((I, T, 4), np.int32, cuda, ctx.device)
+    seeds = None
+    if n_seed is not None:
+        seeds = np.ascontiguousarray(np.broadcast_to(np.asarray(n_seed, dtype=np.int32), (I,)))
+    st = load_library().gabm_forward(ctx.handle, int(T), _ptr(R, np.float32), _ptr(m, np.float32),
+                                     _ptr(S_age, np.float32), _ptr(seeds, np.int32), _ptr(D, np.float64),
+                                     _ptr(counts, np.int32), ms)
+    _check(st, ctx.handle)
+    ctx.T = int(T)
+    return D, counts
+
+
+def gabm_mse_loss(ctx: GabmCtx, y, loss=None, gD=None):
+    """MSE of the last forward's daily deaths against y [I,T]; returns (loss [I], gD [I,T])."""
+    ms = _space(y, loss, gD)
+    cuda = ms == GABM_DEVICE
+    I, T = ctx.instances, (ctx.T if ctx.T is not None else int(y.shape[-1]))
+    if loss is None:
+        loss = _empty((I,), np.float64, cuda, ctx.device)
+    if gD is None:
+        gD = _empty((I, T), np.float64, cuda, ctx.device)
+    st = load_library().gabm_mse_loss(ctx.handle, _ptr(y, np.float64), _ptr(loss, np.float64),
+                                      _ptr(gD, np.float64), ms)
+    _check(st, ctx.handle)
+    return loss, gD
+
+
+def gabm_backward(ctx: GabmCtx, gD, dR=None, dm=None, dS_age=None):
+    """Straight-through adjoint; returns (dR [I,T], dm [I,T], dS_age [I,9]) in float64."""
+    ms = _space(gD, dR, dm, dS_age)
+    cuda = ms == GABM_DEVICE
+    I, T = ctx.instances, (ctx.T if ctx.T is not None else int(gD.shape[-1]))
+    if dR is None:
+        dR = _empty((I, T), np.float64, cuda, ctx.device)
+    if dm is None:
+        dm = _empty((I, T), np.float64, cuda, ctx.device)
+    if dS_age is None:
+        dS_age = _empty((I, GABM_NUM_AGES), np.float64, cuda, ctx.device)
+    st = load_library().gabm_backward(ctx.handle, _ptr(gD, np.float64), _ptr(dR, np.float64),
+                                      _ptr(dm, np.float64), _ptr(dS_age, np.float64), ms)
+    _check(st, ctx.handle)
+    return dR, dm, dS_age
+
+
+def gabm_get_state(ctx: GabmCtx, out=None, device: bool = False):
+    """Exposure days [sets, n_total] int16 (host numpy unless device=True or out is a CUDA tensor)."""
+    cuda = _is_cuda(out) if out is not None else device
+    if out is None:
+        out = _empty((ctx.sets, ctx.n_total), np.int16, cuda, ctx.device)
+    st = load_library().gabm_get_state(ctx.handle, _ptr(out, np.int16), GABM_DEVICE if cuda else GABM_HOST)
+    _check(st, ctx.handle)
+    return out
+
+
+def gabm_set_state(ctx: GabmCtx, day: int, e):
+    st = load_library().gabm_set_state(ctx.handle, int(day), _ptr(e, np.int16), _space(e))
+    _check(st, ctx.handle)
+
+
+def gabm_get_lambda(ctx: GabmCtx, t: int, out=None, device: bool = False):
+    cuda = _is_cuda(out) if out is not None else device
+    if out is None:
+        out = _empty((ctx.sets, ctx.n_total), np.float32, cuda, ctx.device)
+    st = load_library().gabm_get_lambda(ctx.handle, int(t), _ptr(out, np.float32), GABM_DEVICE if cuda else GABM_HOST)
+    _check(st, ctx.handle)
+    return out
+
+
+def gabm_mem_stats(ctx: GabmCtx):
+    cur, peak = ctypes.c_size_t(), ctypes.c_size_t()
+    _check(load_library().gabm_mem_stats(ctx.handle, ctypes.byref(cur), ctypes.byref(peak)), ctx.handle)
+    return int(cur.value), int(peak.value)
+
+
+def gabm_launch_count(ctx: GabmCtx) -> int:
+    return int(load_library().gabm_launch_count(ctx.handle))
+
+
+def gabm_set_profiling(ctx: GabmCtx, enable: bool):
+    _check(load_library().gabm_set_profiling(ctx.handle, int(bool(enable))), ctx.handle)
+
+
+def gabm_get_profile(ctx: GabmCtx, kind: int):
+    ms, n = ctypes.c_double(), ctypes.c_int64()
+    _check(load_library().gabm_get_profile(ctx.handle, int(kind), ctypes.byref(ms), ctypes.byref(n)), ctx.handle)
+    return float(ms.value), int(n.value)
+
+
+def gabm_philox(seed: int, ctr, out=None, stream=None):
+    """Device Philox4x32-10 on counters ctr [count, 4] (uint32 CUDA tensor)."""
+    import torch
+    if out is None:
+        out = torch.empty_like(ctr)
+    s = ctypes.c_void_p((stream or torch.cuda.current_stream()).cuda_stream)
+    st = load_library().gabm_philox(int(seed), _ptr(ctr, np.uint32), _ptr(out, np.uint32), int(ctr.shape[0]), s)
+    _check(st, None)
+    return out
+
+
+def gabm_destroy(ctx: GabmCtx):
+    ctx.close()

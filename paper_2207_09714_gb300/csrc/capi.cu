@@ -1,0 +1,818 @@
+// capi.cu -- the C ABI (include/gabm.h) and the host runtime behind it:
+// input validation, the device memory plan of a ctx, CSR concatenation and
+// transpose, the per-day launch sequences of the forward and the reverse
+// sweep, and the host/device staging of arguments.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "gabm_internal.cuh"
+
+using namespace gabm;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+size_t round_up(size_t x, size_t m) { return (x + m - 1) / m * m; }
+
+}  // namespace
+
+struct gabm_ctx {
+    cudaStream_t stream = nullptr;
+    int device = 0, num_sms = 0;
+    int G = 0, B = 1, I = 0;
+    int tau_EI = 0, tau_IR = 0, L = 0;
+    float c[kMaxL] = {0};
+    uint64_t seed = 0;
+    int policy = GABM_STORE_LAMBDA;
+
+    int64_t n_total = 0, n_rows = 0, nnz = 0, nnz_pad = 0;
+    int ntiles = 0;
+    std::vector<int32_t> h_row0, h_rows, h_tile0, h_ntiles;
+    std::vector<double> h_Dbar;
+    bool symmetric = false;
+
+    uint32_t *rowptr = nullptr, *col = nullptr;
+    float *w = nullptr;
+    uint8_t *age = nullptr;
+    uint32_t *t_rowptr = nullptr, *t_col = nullptr;
+    float *t_w = nullptr;
+    int32_t *d_row0 = nullptr, *d_rows = nullptr, *d_tile0 = nullptr, *d_ntiles = nullptr;
+    uint16_t *d_tile_graph = nullptr;
+    float *d_inv_Dbar = nullptr;
+    int16_t *e = nullptr;
+
+    int Tcap = 0;
+    float *lam = nullptr;
+    int32_t *counts = nullptr, *newRM = nullptr, *newRM_b = nullptr;
+    double *D = nullptr, *gD = nullptr, *y = nullptr, *P = nullptr, *Q = nullptr;
+    float *R = nullptr, *m = nullptr, *S = nullptr;
+    double *dR_s = nullptr, *dm_s = nullptr, *dS_s = nullptr, *loss_s = nullptr;
+
+    SeedState *seedst = nullptr;
+    uint32_t *hist = nullptr, *ties = nullptr;
+    int32_t *d_nseed = nullptr;
+
+    float *ring = nullptr, *A = nullptr, *r = nullptr, *rows_f = nullptr;
+    int16_t *rows_e = nullptr;
+
+    int t0_next = 0;
+    bool resumed = false;
+    int T_last = -1;
+    int lam_from = -1;
+
+    int lanes_fwd = 8, lanes_bwd = 8, grid_fwd = 0, grid_bwd = 0;
+
+    size_t mem_cur = 0, mem_peak = 0;
+    std::unordered_map<void *, size_t> sizes;
+    long fail_alloc_after = -1, alloc_calls = 0;
+    uint64_t launches = 0;
+
+    bool profiling = false;
+    std::vector<cudaEvent_t> ev[2];
+    size_t ev_used[2] = {0, 0};
+    double prof_ms[2] = {0, 0};
+    int64_t prof_n[2] = {0, 0};
+
+    std::string err;
+};
+
+namespace {
+
+gabm_status fail(gabm_ctx *c, gabm_status st, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf; else g_create_error = buf;
+    return st;
+}
+
+#define CK(call)                                                                              \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess) return fail(c, GABM_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+#define LAUNCH(call)                                                                          \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        c->launches++;                                                                        \
+        if (e_ != cudaSuccess) return fail(c, GABM_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+#define TRY(call)                        \
+    do {                                 \
+        gabm_status s_ = (call);         \
+        if (s_ != GABM_OK) return s_;    \
+    } while (0)
+
+template <typename T>
+gabm_status dalloc(gabm_ctx *c, T **p, size_t count) {
+    c->alloc_calls++;
+    if (c->fail_alloc_after >= 0 && c->alloc_calls > c->fail_alloc_after)
+        return fail(c, GABM_ENOMEM, "device allocation %ld refused (injected allocation failure)", c->alloc_calls);
+    size_t bytes = count * sizeof(T);
+    if (bytes == 0) bytes = 16;
+    void *q = nullptr;
+    cudaError_t e = cudaMalloc(&q, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, GABM_ENOMEM, "cudaMalloc(%zu bytes): %s", bytes, cudaGetErrorString(e));
+    }
+    c->sizes[q] = bytes;
+    c->mem_cur += bytes;
+    if (c->mem_cur > c->mem_peak) c->mem_peak = c->mem_cur;
+    *p = (T *)q;
+    return GABM_OK;
+}
+
+template <typename T>
+void dfree(gabm_ctx *c, T *&p) {
+    if (!p) return;
+    auto it = c->sizes.find((void *)p);
+    if (it != c->sizes.end()) {
+        c->mem_cur -= it->second;
+        c->sizes.erase(it);
+        cudaFree((void *)p);
+    }
+    p = nullptr;
+}
+
+cudaMemcpyKind h2d_kind(int ms) { return ms == GABM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice; }
+cudaMemcpyKind d2h_kind(int ms) { return ms == GABM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice; }
+
+// ---------------------------------------------------------------------------
+// Host-side validation (runs before any CUDA call for host-resident inputs)
+// ---------------------------------------------------------------------------
+struct HostGraph {
+    int64_t n = 0, nnz = 0;
+    std::vector<uint64_t> rowptr;
+    std::vector<uint32_t> col;
+    std::vector<float> w;
+    std::vector<uint8_t> age;
+};
+
+gabm_status validate_model(const gabm_model_desc *md) {
+    if (!md) return fail(nullptr, GABM_EINVAL, "model descriptor is NULL");
+    if (md->tau_EI < 1 || md->tau_IR < 1) return fail(nullptr, GABM_EINVAL, "tau_EI and tau_IR must be >= 1");
+    const int L = md->tau_EI + md->tau_IR;
+    if (L > kMaxL) return fail(nullptr, GABM_EINVAL, "tau_EI + tau_IR = %d exceeds %d", L, kMaxL);
+    if (!md->c) return fail(nullptr, GABM_EINVAL, "infectiousness table c is NULL");
+    if (md->c[0] != 0.0f) return fail(nullptr, GABM_EINVAL, "c[0] must be 0 (no onward infection on the day of exposure)");
+    for (int k = 0; k < L; ++k)
+        if (!std::isfinite(md->c[k]) || md->c[k] < 0.0f)
+            return fail(nullptr, GABM_EINVAL, "c[%d] must be finite and >= 0", k);
+    if (md->relax_mode != GABM_HARD_ST && md->relax_mode != GABM_SOFT)
+        return fail(nullptr, GABM_EINVAL, "unknown relax_mode %d", md->relax_mode);
+    if (md->relax_mode == GABM_SOFT) return fail(nullptr, GABM_EUNSUPPORTED, "GABM_SOFT is not implemented in this build");
+    if (!(md->gumbel_tau == 1.0f)) return fail(nullptr, GABM_EUNSUPPORTED, "only gumbel_tau = 1 is implemented");
+    if (md->lambda_policy != GABM_STORE_LAMBDA && md->lambda_policy != GABM_RECOMPUTE)
+        return fail(nullptr, GABM_EINVAL, "unknown lambda_policy %d", md->lambda_policy);
+    return GABM_OK;
+}
+
+gabm_status fetch_graph(const gabm_graph_desc &d, int g, HostGraph &h) {
+    if (d.n < 0 || d.nnz < 0) return fail(nullptr, GABM_EINVAL, "graph %d: negative n or nnz", g);
+    if (d.n >= ((int64_t)1 << 31) - 64) return fail(nullptr, GABM_EUNSUPPORTED, "graph %d: n >= 2^31", g);
+    if (d.nnz >= ((int64_t)1 << 32) - 64) return fail(nullptr, GABM_EUNSUPPORTED, "graph %d: nnz >= 2^32", g);
+    if (!d.rowptr || (d.nnz > 0 && (!d.col || !d.w)) || (d.n > 0 && !d.age))
+        return fail(nullptr, GABM_EINVAL, "graph %d: NULL array", g);
+    if (d.mem_space != GABM_HOST && d.mem_space != GABM_DEVICE)
+        return fail(nullptr, GABM_EINVAL, "graph %d: bad mem_space", g);
+    h.n = d.n;
+    h.nnz = d.nnz;
+    h.rowptr.resize((size_t)d.n + 1);
+    h.col.resize((size_t)d.nnz);
+    h.w.resize((size_t)d.nnz);
+    h.age.resize((size_t)d.n);
+    if (d.mem_space == GABM_HOST) {
+        memcpy(h.rowptr.data(), d.rowptr, sizeof(uint64_t) * h.rowptr.size());
+        if (d.nnz) memcpy(h.col.data(), d.col, sizeof(uint32_t) * h.col.size());
+        if (d.nnz) memcpy(h.w.data(), d.w, sizeof(float) * h.w.size());
+        if (d.n) memcpy(h.age.data(), d.age, h.age.size());
+    } else {
+        cudaError_t e = cudaMemcpy(h.rowptr.data(), d.rowptr, sizeof(uint64_t) * h.rowptr.size(), cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess && d.nnz) e = cudaMemcpy(h.col.data(), d.col, sizeof(uint32_t) * h.col.size(), cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess && d.nnz) e = cudaMemcpy(h.w.data(), d.w, sizeof(float) * h.w.size(), cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess && d.n) e = cudaMemcpy(h.age.data(), d.age, h.age.size(), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return fail(nullptr, GABM_ECUDA, "graph %d: copy to host: %s", g, cudaGetErrorString(e));
+    }
+    if (h.rowptr[0] != 0) return fail(nullptr, GABM_EINVAL, "graph %d: rowptr[0] != 0", g);
+    for (int64_t i = 0; i < h.n; ++i)
+        if (h.rowptr[i + 1] < h.rowptr[i]) return fail(nullptr, GABM_EINVAL, "graph %d: rowptr decreases at row %lld", g, (long long)i);
+    if ((int64_t)h.rowptr[h.n] != h.nnz) return fail(nullptr, GABM_EINVAL, "graph %d: rowptr[n] != nnz", g);
+    for (int64_t p = 0; p < h.nnz; ++p) {
+        if ((int64_t)h.col[p] >= h.n) return fail(nullptr, GABM_EINVAL, "graph %d: col[%lld] = %u out of range", g, (long long)p, h.col[p]);
+        if (!std::isfinite(h.w[p]) || h.w[p] < 0.0f) return fail(nullptr, GABM_EINVAL, "graph %d: w[%lld] not finite and >= 0", g, (long long)p);
+    }
+    for (int64_t i = 0; i < h.n; ++i)
+        if (h.age[i] >= kAges) return fail(nullptr, GABM_EINVAL, "graph %d: age[%lld] = %u > 8", g, (long long)i, h.age[i]);
+    return GABM_OK;
+}
+
+// Source-sorted CSR of one graph (rows of the transpose in ascending source order).
+void transpose_graph(const HostGraph &h, std::vector<uint64_t> &trp, std::vector<uint32_t> &tcol,
+                     std::vector<float> &tw) {
+    trp.assign((size_t)h.n + 1, 0);
+    tcol.resize((size_t)h.nnz);
+    tw.resize((size_t)h.nnz);
+    for (int64_t p = 0; p < h.nnz; ++p) trp[(size_t)h.col[p] + 1]++;
+    for (int64_t i = 0; i < h.n; ++i) trp[i + 1] += trp[i];
+    std::vector<uint64_t> pos(trp.begin(), trp.end() - 1);
+    for (int64_t i = 0; i < h.n; ++i)
+        for (uint64_t p = h.rowptr[i]; p < h.rowptr[i + 1]; ++p) {
+            const uint64_t q = pos[h.col[p]]++;
+            tcol[q] = (uint32_t)i;
+            tw[q] = h.w[p];
+        }
+}
+
+gabm_status ensure_days(gabm_ctx *c, int T) {
+    if (T <= c->Tcap) return GABM_OK;
+    int cap = c->Tcap > 0 ? c->Tcap : 8;
+    while (cap < T) cap *= 2;
+    if (cap > GABM_MAX_DAYS) cap = GABM_MAX_DAYS;
+    CK(cudaStreamSynchronize(c->stream));
+    dfree(c, c->lam); dfree(c, c->counts); dfree(c, c->newRM); dfree(c, c->newRM_b);
+    dfree(c, c->D); dfree(c, c->gD); dfree(c, c->y); dfree(c, c->P); dfree(c, c->Q);
+    dfree(c, c->R); dfree(c, c->m);
+    dfree(c, c->dR_s); dfree(c, c->dm_s);
+    c->Tcap = 0;
+    const size_t IT = (size_t)c->I * cap;
+    if (c->policy == GABM_STORE_LAMBDA) TRY(dalloc(c, &c->lam, (size_t)cap * c->n_rows));
+    TRY(dalloc(c, &c->counts, IT * 4));
+    TRY(dalloc(c, &c->newRM, IT));
+    TRY(dalloc(c, &c->newRM_b, IT));
+    TRY(dalloc(c, &c->D, IT));
+    TRY(dalloc(c, &c->gD, IT));
+    TRY(dalloc(c, &c->y, IT));
+    TRY(dalloc(c, &c->P, (size_t)cap * c->ntiles * kAges));
+    TRY(dalloc(c, &c->Q, IT * kAges));
+    TRY(dalloc(c, &c->R, IT));
+    TRY(dalloc(c, &c->m, IT));
+    TRY(dalloc(c, &c->dR_s, IT));
+    TRY(dalloc(c, &c->dm_s, IT));
+    CK(cudaMemsetAsync(c->D, 0, IT * sizeof(double), c->stream));
+    c->Tcap = cap;
+    c->T_last = -1;
+    c->lam_from = -1;
+    return GABM_OK;
+}
+
+void prof_begin(gabm_ctx *c, int kind) {
+    if (!c->profiling) return;
+    auto &v = c->ev[kind];
+    if (c->ev_used[kind] + 2 > v.size()) {
+        cudaEvent_t a, b;
+        cudaEventCreate(&a);
+        cudaEventCreate(&b);
+        v.push_back(a);
+        v.push_back(b);
+    }
+    cudaEventRecord(v[c->ev_used[kind]], c->stream);
+}
+
+void prof_end(gabm_ctx *c, int kind) {
+    if (!c->profiling) return;
+    cudaEventRecord(c->ev[kind][c->ev_used[kind] + 1], c->stream);
+    c->ev_used[kind] += 2;
+}
+
+gabm_status prof_collect(gabm_ctx *c) {
+    CK(cudaStreamSynchronize(c->stream));
+    for (int k = 0; k < 2; ++k) {
+        for (size_t i = 0; i + 1 < c->ev_used[k]; i += 2) {
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, c->ev[k][i], c->ev[k][i + 1]));
+            c->prof_ms[k] += ms;
+            c->prof_n[k] += 1;
+        }
+        c->ev_used[k] = 0;
+    }
+    return GABM_OK;
+}
+
+GraphRef graph_ref(const gabm_ctx *c) {
+    GraphRef gr;
+    gr.row0 = c->d_row0;
+    gr.tile_graph = c->G > 1 ? c->d_tile_graph : nullptr;
+    gr.inv_Dbar = c->d_inv_Dbar;
+    return gr;
+}
+
+gabm_status check_ms(gabm_ctx *c, int ms) {
+    if (ms != GABM_HOST && ms != GABM_DEVICE) return fail(c, GABM_EINVAL, "mem_space must be GABM_DEVICE or GABM_HOST");
+    return GABM_OK;
+}
+
+void destroy_all(gabm_ctx *c) {
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    for (auto &kv : c->sizes) cudaFree(kv.first);
+    c->sizes.clear();
+    for (int k = 0; k < 2; ++k)
+        for (auto ev : c->ev[k]) cudaEventDestroy(ev);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *gabm_version(void) { return "gabm-gb300 0.1 (sm_103a)"; }
+
+const char *gabm_last_error(const gabm_ctx *ctx) { return ctx ? ctx->err.c_str() : g_create_error.c_str(); }
+
+gabm_status gabm_create(const gabm_graph_desc *graphs, int num_graphs, int sets_per_graph,
+                        const gabm_model_desc *model, void *cuda_stream, gabm_ctx **out) {
+    g_create_error.clear();
+    if (!out) return fail(nullptr, GABM_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!graphs || num_graphs < 1 || num_graphs > 65535) return fail(nullptr, GABM_EINVAL, "need 1..65535 graphs");
+    if (sets_per_graph < 1) return fail(nullptr, GABM_EINVAL, "sets_per_graph must be >= 1");
+    if (sets_per_graph != 1) return fail(nullptr, GABM_EUNSUPPORTED, "sets_per_graph > 1 is not implemented in this build");
+    TRY(validate_model(model));
+
+    // ---- host side: validate, concatenate, transpose ----
+    std::vector<HostGraph> hg((size_t)num_graphs);
+    bool any_device = false;
+    for (int g = 0; g < num_graphs; ++g) any_device |= (graphs[g].mem_space == GABM_DEVICE);
+    for (int g = 0; g < num_graphs; ++g) TRY(fetch_graph(graphs[g], g, hg[g]));
+    (void)any_device;
+
+    std::vector<int32_t> row0(num_graphs), rows(num_graphs), tile0(num_graphs), ntl(num_graphs);
+    std::vector<double> Dbar(num_graphs);
+    int64_t n_rows = 0, nnz = 0, n_total = 0;
+    for (int g = 0; g < num_graphs; ++g) {
+        row0[g] = (int32_t)n_rows;
+        rows[g] = (int32_t)hg[g].n;
+        tile0[g] = (int32_t)(n_rows / kTile);
+        const int64_t padded = (int64_t)round_up((size_t)hg[g].n, kTile);
+        ntl[g] = (int32_t)(padded / kTile);
+        n_rows += padded;
+        nnz += hg[g].nnz;
+        n_total += hg[g].n;
+        double s = 0.0;
+        for (int64_t p = 0; p < hg[g].nnz; ++p) s += (double)hg[g].w[p];
+        Dbar[g] = hg[g].n > 0 ? s / (double)hg[g].n : 0.0;
+    }
+    if (n_rows >= ((int64_t)1 << 31) - 64) return fail(nullptr, GABM_EUNSUPPORTED, "total rows >= 2^31");
+    if (nnz >= ((int64_t)1 << 32) - 64) return fail(nullptr, GABM_EUNSUPPORTED, "total nnz >= 2^32");
+    if (n_rows == 0) n_rows = kTile;  // keep one (padding) tile so every buffer is non-empty
+    const int64_t nnz_pad = (int64_t)round_up((size_t)(nnz > 0 ? nnz : 1), 4);
+    const int ntiles = (int)(n_rows / kTile);
+
+    std::vector<uint32_t> h_rowptr((size_t)n_rows + 1), h_col((size_t)nnz_pad, 0u);
+    std::vector<float> h_w((size_t)nnz_pad, 0.f);
+    std::vector<uint8_t> h_age((size_t)n_rows, 0);
+    std::vector<uint32_t> t_rowptr((size_t)n_rows + 1), t_col((size_t)nnz_pad, 0u);
+    std::vector<float> t_w((size_t)nnz_pad, 0.f);
+    std::vector<uint16_t> tile_graph((size_t)ntiles, 0);
+    bool symmetric = true;
+    {
+        int64_t e0 = 0;
+        for (int g = 0; g < num_graphs; ++g) {
+            const HostGraph &h = hg[g];
+            std::vector<uint64_t> trp;
+            std::vector<uint32_t> tc;
+            std::vector<float> tw;
+            transpose_graph(h, trp, tc, tw);
+            const int64_t padded = (int64_t)ntl[g] * kTile;
+            for (int64_t i = 0; i < padded; ++i) {
+                const int64_t r = row0[g] + i;
+                h_rowptr[r] = (uint32_t)(e0 + (int64_t)h.rowptr[i < h.n ? i : h.n]);
+                t_rowptr[r] = (uint32_t)(e0 + (int64_t)trp[i < h.n ? i : h.n]);
+                if (i < h.n) h_age[r] = h.age[i];
+            }
+            for (int64_t p = 0; p < h.nnz; ++p) {
+                h_col[e0 + p] = h.col[p] + (uint32_t)row0[g];
+                h_w[e0 + p] = h.w[p];
+                t_col[e0 + p] = tc[p] + (uint32_t)row0[g];
+                t_w[e0 + p] = tw[p];
+            }
+            for (int k = 0; k < ntl[g]; ++k) tile_graph[tile0[g] + k] = (uint16_t)g;
+            e0 += h.nnz;
+        }
+        h_rowptr[n_rows] = (uint32_t)e0;
+        t_rowptr[n_rows] = (uint32_t)e0;
+        symmetric = (h_rowptr == t_rowptr) && (h_col == t_col) &&
+                    (memcmp(h_w.data(), t_w.data(), sizeof(float) * h_w.size()) == 0);
+    }
+
+    // ---- device side ----
+    gabm_ctx *c = new gabm_ctx();
+    c->stream = (cudaStream_t)cuda_stream;
+    c->G = num_graphs;
+    c->B = sets_per_graph;
+    c->I = num_graphs * sets_per_graph;
+    c->tau_EI = model->tau_EI;
+    c->tau_IR = model->tau_IR;
+    c->L = model->tau_EI + model->tau_IR;
+    for (int k = 0; k < c->L; ++k) c->c[k] = model->c[k];
+    c->seed = model->seed;
+    c->policy = model->lambda_policy;
+    c->n_total = n_total;
+    c->n_rows = n_rows;
+    c->nnz = nnz;
+    c->nnz_pad = nnz_pad;
+    c->ntiles = ntiles;
+    c->h_row0 = row0;
+    c->h_rows = rows;
+    c->h_tile0 = tile0;
+    c->h_ntiles = ntl;
+    c->h_Dbar = Dbar;
+    c->symmetric = symmetric;
+    if (const char *f = getenv("GABM_FAIL_ALLOC_AFTER")) c->fail_alloc_after = atol(f);
+    if (const char *f = getenv("GABM_LANES_FWD")) c->lanes_fwd = atoi(f);
+    if (const char *f = getenv("GABM_LANES_BWD")) c->lanes_bwd = atoi(f);
+
+    auto bail = [&](gabm_status st) {
+        g_create_error = c->err;
+        destroy_all(c);
+        delete c;
+        return st;
+    };
+#define CTRY(call)                              \
+    do {                                        \
+        gabm_status s_ = (call);                \
+        if (s_ != GABM_OK) return bail(s_);     \
+    } while (0)
+#define CCK(call)                                                                                       \
+    do {                                                                                                \
+        cudaError_t e_ = (call);                                                                        \
+        if (e_ != cudaSuccess) return bail(fail(c, GABM_ECUDA, "%s: %s", #call, cudaGetErrorString(e_))); \
+    } while (0)
+
+    CCK(cudaGetDevice(&c->device));
+    CCK(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device));
+    if (c->lanes_fwd != 4 && c->lanes_fwd != 8 && c->lanes_fwd != 16 && c->lanes_fwd != 32) c->lanes_fwd = 8;
+    if (c->lanes_bwd != 4 && c->lanes_bwd != 8 && c->lanes_bwd != 16 && c->lanes_bwd != 32) c->lanes_bwd = 8;
+
+    CTRY(dalloc(c, &c->rowptr, (size_t)n_rows + 1));
+    CTRY(dalloc(c, &c->col, (size_t)nnz_pad));
+    CTRY(dalloc(c, &c->w, (size_t)nnz_pad));
+    CTRY(dalloc(c, &c->age, (size_t)n_rows));
+    CCK(cudaMemcpyAsync(c->rowptr, h_rowptr.data(), sizeof(uint32_t) * h_rowptr.size(), cudaMemcpyHostToDevice, c->stream));
+    CCK(cudaMemcpyAsync(c->col, h_col.data(), sizeof(uint32_t) * h_col.size(), cudaMemcpyHostToDevice, c->stream));
+    CCK(cudaMemcpyAsync(c->w, h_w.data(), sizeof(float) * h_w.size(), cudaMemcpyHostToDevice, c->stream));
+    CCK(cudaMemcpyAsync(c->age, h_age.data(), h_age.size(), cudaMemcpyHostToDevice, c->stream));
+    if (symmetric) {
+        c->t_rowptr = c->rowptr;
+        c->t_col = c->col;
+        c->t_w = c->w;
+    } else {
+        CTRY(dalloc(c, &c->t_rowptr, (size_t)n_rows + 1));
+        CTRY(dalloc(c, &c->t_col, (size_t)nnz_pad));
+        CTRY(dalloc(c, &c->t_w, (size_t)nnz_pad));
+        CCK(cudaMemcpyAsync(c->t_rowptr, t_rowptr.data(), sizeof(uint32_t) * t_rowptr.size(), cudaMemcpyHostToDevice, c->stream));
+        CCK(cudaMemcpyAsync(c->t_col, t_col.data(), sizeof(uint32_t) * t_col.size(), cudaMemcpyHostToDevice, c->stream));
+        CCK(cudaMemcpyAsync(c->t_w, t_w.data(), sizeof(float) * t_w.size(), cudaMemcpyHostToDevice, c->stream));
+    }
+    std::vector<float> inv((size_t)num_graphs);
+    for (int g = 0; g < num_graphs; ++g) inv[g] = Dbar[g] > 0.0 ? (float)(1.0 / Dbar[g]) : 0.0f;
+    CTRY(dalloc(c, &c->d_row0, (size_t)num_graphs));
+    CTRY(dalloc(c, &c->d_rows, (size_t)num_graphs));
+    CTRY(dalloc(c, &c->d_tile0, (size_t)num_graphs));
+    CTRY(dalloc(c, &c->d_ntiles, (size_t)num_graphs));
+    CTRY(dalloc(c, &c->d_inv_Dbar, (size_t)num_graphs));
+    CTRY(dalloc(c, &c->d_tile_graph, (size_t)ntiles));
+    CCK(cudaMemcpyAsync(c->d_row0, row0.data(), sizeof(int32_t) * num_graphs, cudaMemcpyHostToDevice, c->stream));
+    CCK(cudaMemcpyAsync(c->d_rows, rows.data(), sizeof(int32_t) * num_graphs, cudaMemcpyHostToDevice, c->stream));
+    CCK(cudaMemcpyAsync(c->d_tile0, tile0.data(), sizeof(int32_t) * num_graphs, cudaMemcpyHostToDevice, c->stream));
+    CCK(cudaMemcpyAsync(c->d_ntiles, ntl.data(), sizeof(int32_t) * num_graphs, cudaMemcpyHostToDevice, c->stream));
+    CCK(cudaMemcpyAsync(c->d_inv_Dbar, inv.data(), sizeof(float) * num_graphs, cudaMemcpyHostToDevice, c->stream));
+    CCK(cudaMemcpyAsync(c->d_tile_graph, tile_graph.data(), sizeof(uint16_t) * ntiles, cudaMemcpyHostToDevice, c->stream));
+
+    CTRY(dalloc(c, &c->e, (size_t)n_rows));
+    CTRY(dalloc(c, &c->ring, (size_t)(c->L - 1) * n_rows));
+    CTRY(dalloc(c, &c->A, (size_t)n_rows));
+    CTRY(dalloc(c, &c->r, (size_t)2 * n_rows));
+    CTRY(dalloc(c, &c->rows_f, (size_t)n_rows));
+    CTRY(dalloc(c, &c->rows_e, (size_t)n_rows));
+    CTRY(dalloc(c, &c->S, (size_t)c->I * kAges));
+    CTRY(dalloc(c, &c->dS_s, (size_t)c->I * kAges));
+    CTRY(dalloc(c, &c->loss_s, (size_t)c->I));
+    CTRY(dalloc(c, &c->seedst, (size_t)c->I));
+    CTRY(dalloc(c, &c->hist, (size_t)c->I * kHistBins));
+    CTRY(dalloc(c, &c->ties, (size_t)c->I * kTieCap));
+    CTRY(dalloc(c, &c->d_nseed, (size_t)c->I));
+    CCK(cudaMemsetAsync(c->hist, 0, sizeof(uint32_t) * (size_t)c->I * kHistBins, c->stream));
+    {
+        int grid = (int)std::min<int64_t>((n_rows + 255) / 256, 65535);
+        cudaError_t e = launch_init_state(c->e, c->d_row0, c->d_rows, c->G, n_rows, grid, c->stream);
+        c->launches++;
+        if (e != cudaSuccess) return bail(fail(c, GABM_ECUDA, "init state: %s", cudaGetErrorString(e)));
+    }
+    c->grid_fwd = c->num_sms * occupancy_fwd(c->lanes_fwd);
+    const int mode = c->policy == GABM_STORE_LAMBDA ? kBwdStore : (symmetric ? kBwdFused : kBwdSplit);
+    c->grid_bwd = c->num_sms * occupancy_bwd(c->lanes_bwd, mode);
+    const int max_grid = (ntiles + kBlock / 32 - 1) / (kBlock / 32);
+    if (c->grid_fwd > max_grid) c->grid_fwd = max_grid;
+    if (c->grid_bwd > max_grid) c->grid_bwd = max_grid;
+    CTRY(ensure_days(c, 8));
+    CCK(cudaStreamSynchronize(c->stream));
+#undef CTRY
+#undef CCK
+    *out = c;
+    return GABM_OK;
+}
+
+void gabm_destroy(gabm_ctx *ctx) {
+    if (!ctx) return;
+    destroy_all(ctx);
+    delete ctx;
+}
+
+gabm_status gabm_forward(gabm_ctx *ctx, int T, const float *R, const float *m, const float *S_age,
+                         const int32_t *n_seed, double *D, int32_t *counts, int mem_space) {
+    gabm_ctx *c = ctx;
+    if (!c) return fail(nullptr, GABM_EINVAL, "ctx is NULL");
+    TRY(check_ms(c, mem_space));
+    if (T < 1 || T > GABM_MAX_DAYS) return fail(c, GABM_EINVAL, "T = %d outside 1..%d", T, GABM_MAX_DAYS);
+    if (!R || !m || !S_age) return fail(c, GABM_EINVAL, "R, m and S_age are required");
+    const int t0 = c->resumed ? c->t0_next : 0;
+    if (t0 > T) return fail(c, GABM_EINVAL, "state was set for day %d > T = %d", t0, T);
+    if (!c->resumed) {
+        if (!n_seed) return fail(c, GABM_EINVAL, "n_seed is required when not resuming");
+        for (int i = 0; i < c->I; ++i) {
+            const int g = i / c->B;
+            if (n_seed[i] < 0 || n_seed[i] > c->h_rows[g])
+                return fail(c, GABM_EINVAL, "n_seed[%d] = %d outside 0..%d", i, n_seed[i], c->h_rows[g]);
+        }
+    }
+    TRY(ensure_days(c, T));
+    const int ld = c->Tcap;
+    cudaStream_t s = c->stream;
+    CK(cudaMemcpy2DAsync(c->R, ld * sizeof(float), R, T * sizeof(float), T * sizeof(float), c->I, h2d_kind(mem_space), s));
+    CK(cudaMemcpy2DAsync(c->m, ld * sizeof(float), m, T * sizeof(float), T * sizeof(float), c->I, h2d_kind(mem_space), s));
+    CK(cudaMemcpyAsync(c->S, S_age, sizeof(float) * c->I * kAges, h2d_kind(mem_space), s));
+    CK(cudaMemsetAsync(c->counts, 0, sizeof(int32_t) * 4 * (size_t)c->I * ld, s));
+    CK(cudaMemsetAsync(c->newRM, 0, sizeof(int32_t) * (size_t)c->I * ld, s));
+    CK(cudaMemsetAsync(c->D, 0, sizeof(double) * (size_t)c->I * ld, s));
+
+    if (!c->resumed) {
+        CK(cudaMemcpyAsync(c->d_nseed, n_seed, sizeof(int32_t) * c->I, cudaMemcpyHostToDevice, s));
+        const int grid = (int)std::min<int64_t>((c->n_rows + 255) / 256, 65535);
+        LAUNCH(launch_init_state(c->e, c->d_row0, c->d_rows, c->G, c->n_rows, grid, s));
+        SeedArgs sa;
+        sa.row0 = c->d_row0;
+        sa.rows = c->d_rows;
+        sa.e = c->e;
+        sa.st = c->seedst;
+        sa.hist = c->hist;
+        sa.ties = c->ties;
+        sa.seed = c->seed;
+        sa.tau_EI = c->tau_EI;
+        int max_rows = 1;
+        for (int g = 0; g < c->G; ++g) max_rows = std::max(max_rows, c->h_rows[g]);
+        const int gx = std::max(1, std::min((max_rows + 255) / 256, 4 * c->num_sms / std::max(1, c->G) + 1));
+        LAUNCH(launch_seed_reset(c->seedst, c->d_nseed, c->I, s));
+        for (int pass = 0; pass < 3; ++pass) {
+            sa.pass = pass;
+            LAUNCH(launch_seed_hist(sa, c->G, gx, s));
+            LAUNCH(launch_seed_scan(sa, c->I, s));
+        }
+        LAUNCH(launch_seed_mark(sa, c->G, gx, s));
+        LAUNCH(launch_seed_ties(sa, c->I, s));
+    }
+
+    FwdDayArgs a;
+    a.rowptr = c->rowptr;
+    a.col4 = (const uint4 *)c->col;
+    a.w4 = (const float4 *)c->w;
+    a.age = c->age;
+    a.gr = graph_ref(c);
+    a.e = c->e;
+    a.R = c->R;
+    a.S = c->S;
+    a.ldP = ld;
+    a.counts = c->counts;
+    a.newRM = c->newRM;
+    a.ntiles = c->ntiles;
+    a.tau_EI = c->tau_EI;
+    a.L = c->L;
+    a.seed = c->seed;
+    for (int k = 0; k < kMaxL; ++k) a.c[k] = k < c->L ? c->c[k] : 0.f;
+    for (int t = t0; t < T; ++t) {
+        a.t = t;
+        a.lam_out = c->policy == GABM_STORE_LAMBDA ? c->lam + (size_t)t * c->n_rows : nullptr;
+        prof_begin(c, 0);
+        LAUNCH(launch_fwd_day(a, c->lanes_fwd, c->grid_fwd, s));
+        prof_end(c, 0);
+    }
+    const bool dev = mem_space == GABM_DEVICE;
+    LAUNCH(launch_fwd_finalize(c->newRM, c->counts, c->m, ld, t0, T, c->I, c->D, dev ? D : nullptr,
+                               dev ? counts : nullptr, s));
+    c->T_last = T;
+    c->lam_from = c->policy == GABM_STORE_LAMBDA ? t0 : -1;
+    c->resumed = false;
+    c->t0_next = 0;
+    if (!dev) {
+        if (D) CK(cudaMemcpy2DAsync(D, T * sizeof(double), c->D, ld * sizeof(double), T * sizeof(double), c->I, cudaMemcpyDeviceToHost, s));
+        if (counts) CK(cudaMemcpy2DAsync(counts, T * 4 * sizeof(int32_t), c->counts, ld * 4 * sizeof(int32_t), T * 4 * sizeof(int32_t), c->I, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+    }
+    return GABM_OK;
+}
+
+gabm_status gabm_mse_loss(gabm_ctx *ctx, const double *y, double *loss, double *gD, int mem_space) {
+    gabm_ctx *c = ctx;
+    if (!c) return fail(nullptr, GABM_EINVAL, "ctx is NULL");
+    TRY(check_ms(c, mem_space));
+    if (c->T_last < 1) return fail(c, GABM_ESTATE, "no forward has run");
+    if (!y) return fail(c, GABM_EINVAL, "y is required");
+    const int T = c->T_last, ld = c->Tcap;
+    cudaStream_t s = c->stream;
+    const double *y_dev = y;
+    if (mem_space == GABM_HOST) {
+        CK(cudaMemcpyAsync(c->y, y, sizeof(double) * (size_t)c->I * T, cudaMemcpyHostToDevice, s));
+        y_dev = c->y;
+    }
+    const bool dev = mem_space == GABM_DEVICE;
+    LAUNCH(launch_mse(c->D, ld, y_dev, T, c->I, dev && loss ? loss : c->loss_s, c->gD, dev ? gD : nullptr, s));
+    if (!dev) {
+        if (loss) CK(cudaMemcpyAsync(loss, c->loss_s, sizeof(double) * c->I, cudaMemcpyDeviceToHost, s));
+        if (gD) CK(cudaMemcpy2DAsync(gD, T * sizeof(double), c->gD, ld * sizeof(double), T * sizeof(double), c->I, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+    }
+    return GABM_OK;
+}
+
+gabm_status gabm_backward(gabm_ctx *ctx, const double *gD, double *dR, double *dm, double *dS_age,
+                          int mem_space) {
+    gabm_ctx *c = ctx;
+    if (!c) return fail(nullptr, GABM_EINVAL, "ctx is NULL");
+    TRY(check_ms(c, mem_space));
+    if (c->T_last < 1) return fail(c, GABM_ESTATE, "backward needs a forward first");
+    if (c->policy == GABM_STORE_LAMBDA && c->lam_from != 0)
+        return fail(c, GABM_ESTATE, "stored lambdas do not cover days 0..T-1 (use GABM_RECOMPUTE to replay a set state)");
+    if (!gD || !dR || !dm || !dS_age) return fail(c, GABM_EINVAL, "gD, dR, dm and dS_age are required");
+    const int T = c->T_last, ld = c->Tcap;
+    cudaStream_t s = c->stream;
+    CK(cudaMemcpy2DAsync(c->gD, ld * sizeof(double), gD, T * sizeof(double), T * sizeof(double), c->I, h2d_kind(mem_space), s));
+    CK(cudaMemsetAsync(c->r, 0, sizeof(float) * 2 * (size_t)c->n_rows, s));
+    CK(cudaMemsetAsync(c->newRM_b, 0, sizeof(int32_t) * (size_t)c->I * ld, s));
+
+    BwdDayArgs a;
+    const int mode = c->policy == GABM_STORE_LAMBDA ? kBwdStore : (c->symmetric ? kBwdFused : kBwdSplit);
+    a.mode = mode;
+    a.rowptr = c->t_rowptr;
+    a.col4 = (const uint4 *)c->t_col;
+    a.w4 = (const float4 *)c->t_w;
+    a.in_rowptr = mode == kBwdSplit ? c->rowptr : nullptr;
+    a.in_col4 = mode == kBwdSplit ? (const uint4 *)c->col : nullptr;
+    a.in_w4 = mode == kBwdSplit ? (const float4 *)c->w : nullptr;
+    a.age = c->age;
+    a.gr = graph_ref(c);
+    a.E = c->e;
+    a.ring = c->ring;
+    a.ring_stride = (size_t)c->n_rows;
+    a.A = c->A;
+    a.R = c->R;
+    a.m = c->m;
+    a.S = c->S;
+    a.gD = c->gD;
+    a.ldP = ld;
+    a.newRM = c->newRM_b;
+    a.ntiles = c->ntiles;
+    a.T = T;
+    a.tau_EI = c->tau_EI;
+    a.L = c->L;
+    a.seed = c->seed;
+    for (int k = 0; k < kMaxL; ++k) a.c[k] = k < c->L ? c->c[k] : 0.f;
+    const int Lm1 = c->L - 1;
+    for (int t = T - 1; t >= 0; --t) {
+        a.t = t;
+        a.lam_t = mode == kBwdStore ? c->lam + (size_t)t * c->n_rows : nullptr;
+        a.r_next = c->r + (size_t)((t + 1) & 1) * c->n_rows;
+        a.r_cur = c->r + (size_t)(t & 1) * c->n_rows;
+        a.P_t = c->P + (size_t)t * c->ntiles * kAges;
+        for (int k = 0; k < kMaxL; ++k) a.ring_slot[k] = (k >= 1 && k < c->L) ? (t + k) % Lm1 : 0;
+        prof_begin(c, 1);
+        LAUNCH(launch_bwd_day(a, c->lanes_bwd, c->grid_bwd, s));
+        prof_end(c, 1);
+    }
+    LAUNCH(launch_bwd_reduce(c->P, c->ntiles, ld, c->d_tile0, c->d_ntiles, T, c->I, c->Q, s));
+    const bool dev = mem_space == GABM_DEVICE;
+    LAUNCH(launch_bwd_finalize(c->Q, c->R, c->S, c->gD, c->newRM_b, ld, T, c->I, dev ? dR : c->dR_s,
+                               dev ? dm : c->dm_s, dev ? dS_age : c->dS_s, s));
+    if (!dev) {
+        CK(cudaMemcpyAsync(dR, c->dR_s, sizeof(double) * (size_t)c->I * T, cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(dm, c->dm_s, sizeof(double) * (size_t)c->I * T, cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(dS_age, c->dS_s, sizeof(double) * (size_t)c->I * kAges, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+    }
+    return GABM_OK;
+}
+
+gabm_status gabm_get_state(gabm_ctx *ctx, int16_t *e_out, int mem_space) {
+    gabm_ctx *c = ctx;
+    if (!c) return fail(nullptr, GABM_EINVAL, "ctx is NULL");
+    TRY(check_ms(c, mem_space));
+    if (!e_out) return fail(c, GABM_EINVAL, "e_out is NULL");
+    int64_t off = 0;
+    for (int g = 0; g < c->G; ++g) {
+        if (c->h_rows[g] > 0)
+            CK(cudaMemcpyAsync(e_out + off, c->e + c->h_row0[g], sizeof(int16_t) * c->h_rows[g], d2h_kind(mem_space), c->stream));
+        off += c->h_rows[g];
+    }
+    if (mem_space == GABM_HOST) CK(cudaStreamSynchronize(c->stream));
+    return GABM_OK;
+}
+
+gabm_status gabm_set_state(gabm_ctx *ctx, int day, const int16_t *e_in, int mem_space) {
+    gabm_ctx *c = ctx;
+    if (!c) return fail(nullptr, GABM_EINVAL, "ctx is NULL");
+    TRY(check_ms(c, mem_space));
+    if (!e_in) return fail(c, GABM_EINVAL, "e_in is NULL");
+    if (day < 0 || day > GABM_MAX_DAYS) return fail(c, GABM_EINVAL, "day %d outside 0..%d", day, GABM_MAX_DAYS);
+    std::vector<int16_t> h((size_t)c->n_total);
+    if (mem_space == GABM_HOST) {
+        memcpy(h.data(), e_in, sizeof(int16_t) * h.size());
+    } else {
+        CK(cudaMemcpyAsync(h.data(), e_in, sizeof(int16_t) * h.size(), cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+    }
+    for (size_t i = 0; i < h.size(); ++i) {
+        const int v = h[i];
+        if (v != kNever && (v < -c->L || v >= day))
+            return fail(c, GABM_EINVAL, "e[%zu] = %d: must be NEVER or in [-%d, %d)", i, v, c->L, day);
+    }
+    CK(cudaStreamSynchronize(c->stream));
+    int64_t off = 0;
+    for (int g = 0; g < c->G; ++g) {
+        if (c->h_rows[g] > 0)
+            CK(cudaMemcpy(c->e + c->h_row0[g], h.data() + off, sizeof(int16_t) * c->h_rows[g], cudaMemcpyHostToDevice));
+        off += c->h_rows[g];
+    }
+    c->t0_next = day;
+    c->resumed = true;
+    c->T_last = -1;
+    c->lam_from = -1;
+    return GABM_OK;
+}
+
+gabm_status gabm_get_lambda(gabm_ctx *ctx, int t, float *lam_out, int mem_space) {
+    gabm_ctx *c = ctx;
+    if (!c) return fail(nullptr, GABM_EINVAL, "ctx is NULL");
+    TRY(check_ms(c, mem_space));
+    if (!lam_out) return fail(c, GABM_EINVAL, "lam_out is NULL");
+    if (c->policy != GABM_STORE_LAMBDA) return fail(c, GABM_ESTATE, "lambda is only stored with GABM_STORE_LAMBDA");
+    if (c->T_last < 1 || t < c->lam_from || t >= c->T_last || c->lam_from < 0)
+        return fail(c, GABM_ESTATE, "day %d was not run by the last forward", t);
+    LAUNCH(launch_get_lambda(c->lam + (size_t)t * c->n_rows, c->e, c->age, graph_ref(c), c->R, c->S, c->Tcap, t,
+                             c->n_rows, c->rows_f, c->stream));
+    int64_t off = 0;
+    for (int g = 0; g < c->G; ++g) {
+        if (c->h_rows[g] > 0)
+            CK(cudaMemcpyAsync(lam_out + off, c->rows_f + c->h_row0[g], sizeof(float) * c->h_rows[g], d2h_kind(mem_space), c->stream));
+        off += c->h_rows[g];
+    }
+    if (mem_space == GABM_HOST) CK(cudaStreamSynchronize(c->stream));
+    return GABM_OK;
+}
+
+gabm_status gabm_mem_stats(const gabm_ctx *ctx, size_t *current, size_t *peak) {
+    if (!ctx) return fail(nullptr, GABM_EINVAL, "ctx is NULL");
+    if (current) *current = ctx->mem_cur;
+    if (peak) *peak = ctx->mem_peak;
+    return GABM_OK;
+}
+
+uint64_t gabm_launch_count(const gabm_ctx *ctx) { return ctx ? ctx->launches : 0; }
+
+gabm_status gabm_set_profiling(gabm_ctx *ctx, int enable) {
+    gabm_ctx *c = ctx;
+    if (!c) return fail(nullptr, GABM_EINVAL, "ctx is NULL");
+    TRY(prof_collect(c));
+    c->profiling = enable != 0;
+    for (int k = 0; k < 2; ++k) { c->prof_ms[k] = 0; c->prof_n[k] = 0; }
+    return GABM_OK;
+}
+
+gabm_status gabm_get_profile(gabm_ctx *ctx, int kind, double *total_ms, int64_t *launches) {
+    gabm_ctx *c = ctx;
+    if (!c) return fail(nullptr, GABM_EINVAL, "ctx is NULL");
+    if (kind < 0 || kind > 1) return fail(c, GABM_EINVAL, "kind must be 0 or 1");
+    TRY(prof_collect(c));
+    if (total_ms) *total_ms = c->prof_ms[kind];
+    if (launches) *launches = c->prof_n[kind];
+    return GABM_OK;
+}
+
+gabm_status gabm_philox(uint64_t seed, const uint32_t *ctr, uint32_t *out, int64_t count, void *cuda_stream) {
+    gabm_ctx *c = nullptr;
+    if (count < 0 || (count > 0 && (!ctr || !out))) return fail(nullptr, GABM_EINVAL, "bad arguments");
+    if (count == 0) return GABM_OK;
+    CK(launch_philox(seed, ctr, out, count, (cudaStream_t)cuda_stream));
+    return GABM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,435 @@
+// forward.cu -- forward day step of the hard GradABM model on sm_103a.
+//
+// One launch per day (Sec. 3.1, Eq. 1-3; A1: one-day steps).  Each warp takes
+// 32 consecutive rows (agents).  Rows whose agent is susceptible are compacted
+// within the warp and processed GL lanes per row: every lane streams 16-byte
+// vectors of 4 (col, w) pairs of its row (destination-sorted CSR, so this is a
+// pull gather with no atomics), gathers the neighbours' exposure days from the
+// L2-resident state, and accumulates w_ji * c[t - e_j].  A butterfly over the
+// GL lanes gives the row sum, which is handed to the lane that owns the row
+// for the fused epilogue: lambda, p = 1 - exp(-lambda) (Eq. 3), the Philox
+// uniform, the hard draw and the in-place state update e_i = t.
+//
+// The in-place update is race-free in effect: a neighbour that reads e_i
+// during the same day sees either NEVER or t, and both give c = 0 (c[0] = 0 by
+// assumption A2 of App. A), so every lambda uses the start-of-day state.
+#include "gabm_internal.cuh"
+#include "rowsum.cuh"
+
+namespace gabm {
+
+namespace {
+
+__device__ __forceinline__ void flush_counts_warp(int32_t *counts, int32_t *newRM, int ldP, int g,
+                                                  int t, int cS, int cE, int cI, int cR, int cN,
+                                                  int lane) {
+    cS = __reduce_add_sync(0xffffffffu, cS);
+    cE = __reduce_add_sync(0xffffffffu, cE);
+    cI = __reduce_add_sync(0xffffffffu, cI);
+    cR = __reduce_add_sync(0xffffffffu, cR);
+    cN = __reduce_add_sync(0xffffffffu, cN);
+    if (lane == 0) {
+        int32_t *cp = counts + ((size_t)g * ldP + t) * 4;
+        if (cS) atomicAdd(cp + 0, cS);
+        if (cE) atomicAdd(cp + 1, cE);
+        if (cI) atomicAdd(cp + 2, cI);
+        if (cR) atomicAdd(cp + 3, cR);
+        if (cN) atomicAdd(newRM + (size_t)g * ldP + t, cN);
+    }
+}
+
+template <int GL>
+__global__ void __launch_bounds__(kBlock) k_fwd_day(const FwdDayArgs a) {
+    __shared__ float c_s[kMaxL];
+    __shared__ uint8_t slot_s[kBlock / 32][32];
+    __shared__ int32_t red_s[kBlock / 32][6];
+    if (threadIdx.x < kMaxL) c_s[threadIdx.x] = a.c[threadIdx.x];
+    __syncthreads();
+
+    constexpr int RPP = 32 / GL;  // rows per pass of the warp
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    const int sub = lane / GL, gl = lane % GL;
+    const int t = a.t, L = a.L, tau_EI = a.tau_EI;
+    const int nwarps = gridDim.x * (kBlock / 32);
+
+    int cur_g = -1;
+    int cS = 0, cE = 0, cI = 0, cR = 0, cN = 0;
+    for (int tile = blockIdx.x * (kBlock / 32) + wib; tile < a.ntiles; tile += nwarps) {
+        const int g = a.gr.tile_graph ? (int)a.gr.tile_graph[tile] : 0;
+        if (g != cur_g) {
+            if (cur_g >= 0) flush_counts_warp(a.counts, a.newRM, a.ldP, cur_g, t, cS, cE, cI, cR, cN, lane);
+            cur_g = g;
+            cS = cE = cI = cR = cN = 0;
+        }
+        const int row = tile * kTile + lane;
+        const int ei = a.e[row];
+        const bool isS = (ei == kNever);
+        if (ei != kPad && !isS) {
+            const int k = t - ei;
+            if (k < tau_EI) ++cE; else if (k < L) ++cI; else ++cR;
+            cN += (k == L);
+        }
+        cS += isS;
+        const unsigned smask = __ballot_sync(0xffffffffu, isS);
+        if (smask == 0u) continue;
+
+        uint32_t rs = 0, re = 0;
+        if (isS) { rs = a.rowptr[row]; re = a.rowptr[row + 1]; }
+        const int rank = __popc(smask & lt_mask);
+        if (isS) slot_s[wib][rank] = (uint8_t)lane;
+        __syncwarp();
+        const int nS = __popc(smask);
+        float acc = 0.f;
+        for (int base = 0; base < nS; base += RPP) {
+            const int j = base + sub;
+            const int src = (j < nS) ? slot_s[wib][j] : 0;
+            const uint32_t rsj = __shfl_sync(0xffffffffu, rs, src);
+            const uint32_t rej = __shfl_sync(0xffffffffu, re, src);
+            float part = 0.f;
+            if (j < nS) part = lane_infectious_sum<GL>(a.col4, a.w4, a.e, c_s, rsj, rej, gl, t, L);
+#pragma unroll
+            for (int o = GL / 2; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+            const int myj = rank - base;
+            const float got = __shfl_sync(0xffffffffu, part, (myj & (RPP - 1)) * GL);
+            if (isS && myj >= 0 && myj < RPP) acc = got;
+        }
+        __syncwarp();
+
+        if (isS) {
+            const float Lam = acc * a.gr.inv_Dbar[g];
+            const int inst = g;
+            const float lam = (a.R[(size_t)inst * a.ldP + t] * a.S[inst * kAges + a.age[row]]) * Lam;
+            const float p = -expm1f(-lam);
+            const uint32_t id = (uint32_t)(row - a.gr.row0[g]);
+            const float u = uniform_from_word(philox_word(a.seed, id, (uint32_t)t, (uint32_t)inst, 0u));
+            if (u < p) a.e[row] = (int16_t)t;
+            if (a.lam_out) a.lam_out[row] = Lam;
+        }
+    }
+
+    // block-level reduction of the last graph's counts, then one atomic per count
+    cS = __reduce_add_sync(0xffffffffu, cS);
+    cE = __reduce_add_sync(0xffffffffu, cE);
+    cI = __reduce_add_sync(0xffffffffu, cI);
+    cR = __reduce_add_sync(0xffffffffu, cR);
+    cN = __reduce_add_sync(0xffffffffu, cN);
+    if (lane == 0) {
+        red_s[wib][0] = cur_g;
+        red_s[wib][1] = cS; red_s[wib][2] = cE; red_s[wib][3] = cI; red_s[wib][4] = cR; red_s[wib][5] = cN;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int g = -1;
+        int32_t acc[5] = {0, 0, 0, 0, 0};
+        for (int w = 0; w <= kBlock / 32; ++w) {
+            const int gw = (w < kBlock / 32) ? red_s[w][0] : -2;
+            if (gw != g) {
+                if (g >= 0) {
+                    int32_t *cp = a.counts + ((size_t)g * a.ldP + t) * 4;
+                    for (int s = 0; s < 4; ++s) if (acc[s]) atomicAdd(cp + s, acc[s]);
+                    if (acc[4]) atomicAdd(a.newRM + (size_t)g * a.ldP + t, acc[4]);
+                }
+                g = gw;
+                for (int s = 0; s < 5; ++s) acc[s] = 0;
+            }
+            if (w < kBlock / 32 && gw >= 0)
+                for (int s = 0; s < 5; ++s) acc[s] += red_s[w][1 + s];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// State initialisation and seeding (initial infections i^0, Sec. 3.1):
+// the n_seed agents of each instance with the smallest 64-bit key
+// (Philox word at (id, 0, inst, 1) << 32 | id).  Exact radix select on the
+// 32-bit word in three digits (11, 11, 10 bits), then ties on the final word
+// are broken by id.
+// ---------------------------------------------------------------------------
+__global__ void k_init_state(int16_t *e, const int32_t *row0, const int32_t *rows, int G, int64_t n_rows) {
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n_rows;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        // binary search the graph of row r
+        int lo = 0, hi = G - 1;
+        while (lo < hi) {
+            int mid = (lo + hi + 1) >> 1;
+            if (row0[mid] <= r) lo = mid; else hi = mid - 1;
+        }
+        e[r] = (r - row0[lo] < rows[lo]) ? (int16_t)kNever : (int16_t)kPad;
+    }
+}
+
+__global__ void k_seed_reset(SeedState *st, const int32_t *n_seed, int I) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= I) return;
+    SeedState s;
+    s.prefix = 0u;
+    s.k_rem = (uint32_t)n_seed[i];
+    s.eq_count = 0u;
+    s.tie_n = 0u;
+    s.none = (n_seed[i] == 0);
+    s.overflow = 0;
+    st[i] = s;
+}
+
+__device__ __forceinline__ void digit_of_pass(int pass, int &shift, int &nbins, uint32_t &himask) {
+    if (pass == 0) { shift = 21; nbins = 2048; himask = 0u; }
+    else if (pass == 1) { shift = 10; nbins = 2048; himask = 0xFFE00000u; }
+    else { shift = 0; nbins = 1024; himask = 0xFFFFFC00u; }
+}
+
+__global__ void __launch_bounds__(256) k_seed_hist(const SeedArgs a) {
+    __shared__ uint32_t h_s[kHistBins];
+    const int inst = blockIdx.y;
+    const SeedState st = a.st[inst];
+    if (st.none) return;
+    int shift, nbins; uint32_t himask;
+    digit_of_pass(a.pass, shift, nbins, himask);
+    for (int b = threadIdx.x; b < nbins; b += blockDim.x) h_s[b] = 0u;
+    __syncthreads();
+    const int g = inst;
+    const int32_t r0 = a.row0[g], nr = a.rows[g];
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nr; i += gridDim.x * blockDim.x) {
+        const uint32_t h = philox_word(a.seed, (uint32_t)i, 0u, (uint32_t)inst, 1u);
+        if ((h & himask) == st.prefix) atomicAdd(&h_s[(h >> shift) & (nbins - 1)], 1u);
+    }
+    (void)r0;
+    __syncthreads();
+    uint32_t *gh = a.hist + (size_t)inst * kHistBins;
+    for (int b = threadIdx.x; b < nbins; b += blockDim.x)
+        if (h_s[b]) atomicAdd(gh + b, h_s[b]);
+}
+
+// One warp per instance: find the digit bin holding the k_rem-th smallest key.
+__global__ void k_seed_scan(const SeedArgs a) {
+    const int inst = blockIdx.x;
+    const int lane = threadIdx.x;
+    SeedState st = a.st[inst];
+    int shift, nbins; uint32_t himask;
+    digit_of_pass(a.pass, shift, nbins, himask);
+    uint32_t *gh = a.hist + (size_t)inst * kHistBins;
+    if (!st.none) {
+        const int per = nbins / 32;
+        uint32_t mine = 0;
+        for (int b = 0; b < per; ++b) mine += gh[lane * per + b];
+        uint32_t incl = mine;
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        const uint32_t excl = incl - mine;
+        const bool here = (excl < st.k_rem) && (st.k_rem <= incl);
+        const unsigned who = __ballot_sync(0xffffffffu, here);
+        const int src = __ffs(who) - 1;
+        uint32_t digit = 0, below = 0, eq = 0;
+        if (lane == src) {
+            uint32_t cum = excl;
+            for (int b = 0; b < per; ++b) {
+                const uint32_t hb = gh[lane * per + b];
+                if (st.k_rem <= cum + hb) { digit = (uint32_t)(lane * per + b); below = cum; eq = hb; break; }
+                cum += hb;
+            }
+        }
+        digit = __shfl_sync(0xffffffffu, digit, src);
+        below = __shfl_sync(0xffffffffu, below, src);
+        eq = __shfl_sync(0xffffffffu, eq, src);
+        __syncwarp();
+        if (lane == 0) {
+            st.prefix |= digit << shift;
+            st.k_rem -= below;
+            if (a.pass == 2) st.eq_count = eq;
+            a.st[inst] = st;
+        }
+    }
+    for (int b = lane; b < nbins; b += 32) gh[b] = 0u;
+}
+
+__global__ void k_seed_mark(const SeedArgs a) {
+    const int inst = blockIdx.y;
+    const SeedState st = a.st[inst];
+    if (st.none) return;
+    const int g = inst;
+    const int32_t r0 = a.row0[g], nr = a.rows[g];
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nr; i += gridDim.x * blockDim.x) {
+        const uint32_t h = philox_word(a.seed, (uint32_t)i, 0u, (uint32_t)inst, 1u);
+        bool mark = h < st.prefix;
+        if (h == st.prefix) {
+            if (st.eq_count == st.k_rem) {
+                mark = true;
+            } else {
+                const uint32_t slot = atomicAdd(&a.st[inst].tie_n, 1u);
+                if (slot < (uint32_t)kTieCap) a.ties[(size_t)inst * kTieCap + slot] = (uint32_t)i;
+                else a.st[inst].overflow = 1;
+            }
+        }
+        if (mark) a.e[r0 + i] = (int16_t)(-a.tau_EI);
+    }
+}
+
+// Ties on the threshold word: the k_rem candidates with the smallest ids win.
+__global__ void k_seed_ties(const SeedArgs a) {
+    const int inst = blockIdx.x;
+    const SeedState st = a.st[inst];
+    if (st.none || st.eq_count == st.k_rem) return;
+    const uint32_t n = min(st.tie_n, (uint32_t)kTieCap);
+    const uint32_t *tl = a.ties + (size_t)inst * kTieCap;
+    const int32_t r0 = a.row0[inst];
+    for (uint32_t c = threadIdx.x; c < n; c += blockDim.x) {
+        const uint32_t id = tl[c];
+        uint32_t rank = 0;
+        for (uint32_t d = 0; d < n; ++d) rank += (tl[d] < id);
+        if (rank < st.k_rem) a.e[r0 + id] = (int16_t)(-a.tau_EI);
+    }
+}
+
+// D_t = m_t * newRM(t) in FP64 (Aggregate, Sec. 3.1); copies counts out.
+__global__ void k_fwd_finalize(const int32_t *newRM, const int32_t *counts, const float *m, int ldP,
+                               int t0, int T, int I, double *D_ctx, double *D_out, int32_t *counts_out) {
+    const int total = I * T;
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
+        const int inst = idx / T, t = idx - inst * T;
+        if (t < t0) continue;
+        const size_t src = (size_t)inst * ldP + t;
+        const double d = (double)m[src] * (double)newRM[src];
+        D_ctx[src] = d;
+        if (D_out) D_out[idx] = d;
+        if (counts_out)
+            for (int s = 0; s < 4; ++s) counts_out[(size_t)idx * 4 + s] = counts[src * 4 + s];
+    }
+}
+
+// MSE on daily deaths (Sec. 3.2, Stage 3); one block per instance, fixed-order FP64 sums.
+__global__ void __launch_bounds__(256) k_mse(const double *D, int ldP, const double *y, int T,
+                                             double *loss, double *gD_ctx, double *gD_out) {
+    __shared__ double s_acc[256];
+    const int inst = blockIdx.x;
+    double acc = 0.0;
+    for (int t = threadIdx.x; t < T; t += blockDim.x) {
+        const double d = D[(size_t)inst * ldP + t] - y[(size_t)inst * T + t];
+        const double g = 2.0 * d / (double)T;
+        gD_ctx[(size_t)inst * ldP + t] = g;
+        if (gD_out) gD_out[(size_t)inst * T + t] = g;
+        acc += d * d;
+    }
+    s_acc[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) s_acc[threadIdx.x] += s_acc[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && loss) loss[inst] = s_acc[0] / (double)T;
+}
+
+// lambda_i(t) = R_t S[a_i] Lam_i(t) for agents susceptible on day t, else 0.
+__global__ void k_get_lambda(const float *lam_t, const int16_t *e, const uint8_t *age, GraphRef gr,
+                             const float *R, const float *S, int ldP, int t, int64_t n_rows, float *out) {
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n_rows;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        const int ei = e[r];
+        const bool wasS = (ei == kNever) || (ei >= t);
+        float v = 0.f;
+        if (ei != kPad && wasS) {
+            const int g = gr.tile_graph ? (int)gr.tile_graph[r / kTile] : 0;
+            v = (R[(size_t)g * ldP + t] * S[g * kAges + age[r]]) * lam_t[r];
+        }
+        out[r] = v;
+    }
+}
+
+__global__ void k_philox(uint64_t seed, const uint32_t *ctr, uint32_t *out, int64_t count) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t x[4] = {ctr[4 * i], ctr[4 * i + 1], ctr[4 * i + 2], ctr[4 * i + 3]};
+        philox4x32_10(x, (uint32_t)seed, (uint32_t)(seed >> 32));
+        for (int k = 0; k < 4; ++k) out[4 * i + k] = x[k];
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_init_state(int16_t *e, const int32_t *row0, const int32_t *rows, int G,
+                              int64_t n_rows, int grid, cudaStream_t s) {
+    k_init_state<<<grid, 256, 0, s>>>(e, row0, rows, G, n_rows);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_seed_reset(SeedState *st, const int32_t *n_seed, int I, cudaStream_t s) {
+    k_seed_reset<<<(I + 127) / 128, 128, 0, s>>>(st, n_seed, I);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_seed_hist(const SeedArgs &a, int G, int grid_x, cudaStream_t s) {
+    k_seed_hist<<<dim3(grid_x, G), 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_seed_scan(const SeedArgs &a, int I, cudaStream_t s) {
+    k_seed_scan<<<I, 32, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_seed_mark(const SeedArgs &a, int G, int grid_x, cudaStream_t s) {
+    k_seed_mark<<<dim3(grid_x, G), 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_seed_ties(const SeedArgs &a, int I, cudaStream_t s) {
+    k_seed_ties<<<I, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fwd_day(const FwdDayArgs &a, int lanes_per_row, int grid, cudaStream_t s) {
+    switch (lanes_per_row) {
+        case 4: k_fwd_day<4><<<grid, kBlock, 0, s>>>(a); break;
+        case 8: k_fwd_day<8><<<grid, kBlock, 0, s>>>(a); break;
+        case 16: k_fwd_day<16><<<grid, kBlock, 0, s>>>(a); break;
+        case 32: k_fwd_day<32><<<grid, kBlock, 0, s>>>(a); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+int occupancy_fwd(int lanes_per_row) {
+    int blocks = 0;
+    switch (lanes_per_row) {
+        case 4: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_fwd_day<4>, kBlock, 0); break;
+        case 8: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_fwd_day<8>, kBlock, 0); break;
+        case 16: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_fwd_day<16>, kBlock, 0); break;
+        case 32: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_fwd_day<32>, kBlock, 0); break;
+        default: break;
+    }
+    return blocks > 0 ? blocks : 1;
+}
+
+cudaError_t launch_fwd_finalize(const int32_t *newRM, const int32_t *counts, const float *m, int ldP,
+                                int t0, int T, int I, double *D_ctx, double *D_out,
+                                int32_t *counts_out, cudaStream_t s) {
+    const int total = I * T;
+    const int grid = (total + 255) / 256;
+    k_fwd_finalize<<<grid > 0 ? grid : 1, 256, 0, s>>>(newRM, counts, m, ldP, t0, T, I, D_ctx, D_out, counts_out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mse(const double *D, int ldP, const double *y, int T, int I, double *loss,
+                       double *gD_ctx, double *gD_out, cudaStream_t s) {
+    k_mse<<<I, 256, 0, s>>>(D, ldP, y, T, loss, gD_ctx, gD_out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_get_lambda(const float *lam_t, const int16_t *e, const uint8_t *age, GraphRef gr,
+                              const float *R, const float *S, int ldP, int t, int64_t n_rows,
+                              float *out_rows, cudaStream_t s) {
+    int grid = (int)((n_rows + 255) / 256);
+    if (grid > 65535) grid = 65535;
+    k_get_lambda<<<grid > 0 ? grid : 1, 256, 0, s>>>(lam_t, e, age, gr, R, S, ldP, t, n_rows, out_rows);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_philox(uint64_t seed, const uint32_t *ctr, uint32_t *out, int64_t count, cudaStream_t s) {
+    int64_t grid = (count + 255) / 256;
+    if (grid > 65535) grid = 65535;
+    k_philox<<<(int)(grid > 0 ? grid : 1), 256, 0, s>>>(seed, ctr, out, count);
+    return cudaGetLastError();
+}
+
+}  // namespace gabm

@@ -1,0 +1,188 @@
+// gabm_internal.cuh -- internal declarations of the GB300 GradABM library.
+//
+// Layout in device memory (one ctx):
+//   graphs are concatenated block-diagonally, each padded to a multiple of 32
+//   rows so that a 32-row tile never straddles two graphs; padding rows have
+//   no edges and exposure day kPad.
+//   rowptr  u32 [n_rows+1]        destination-sorted CSR (row i: in-neighbours)
+//   col     u32 [nnz_pad]         nnz_pad = nnz rounded up to 4, plus one spare
+//   w       f32 [nnz_pad]         vector of 4 edges = one 16-byte load each
+//   age     u8  [n_rows]
+//   e       i16 [n_rows]          exposure day (kNever = susceptible)
+//   lam     f32 [Tcap][n_rows]    normalised neighbour sums (store policy)
+//   ring    f32 [L-1][n_rows]     adjoint of infectiousness, last L-1 days
+//   r       f32 [2][n_rows]       per-day transpose-gather coefficients
+//   P       f64 [Tcap][ntiles][9] per-tile, per-age partial gradient sums
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/gabm.h"
+
+namespace gabm {
+
+constexpr int kNever = GABM_NEVER;
+constexpr int kPad = -32768;       // exposure day of a padding row (not an agent)
+constexpr int kAges = GABM_NUM_AGES;
+constexpr int kMaxL = GABM_MAX_L;
+constexpr int kTile = 32;          // rows per warp tile
+constexpr int kBlock = 256;        // threads per block of the day kernels
+constexpr int kHistBins = 2048;    // radix-select digit bins (11 bits)
+constexpr int kTieCap = 4096;      // agents sharing the threshold hash (seeding)
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), written from its
+// published definition: ten rounds, each multiplying counter words 0 and 2 by
+// the two round multipliers (32x32 -> 64 bits), swapping/xoring the halves
+// with counter words 1 and 3 and the key; the key is advanced by the two Weyl
+// constants between rounds.  Only the first output word is used.
+// ---------------------------------------------------------------------------
+__host__ __device__ __forceinline__ uint32_t mulhi32(uint32_t a, uint32_t b) {
+#ifdef __CUDA_ARCH__
+    return __umulhi(a, b);
+#else
+    return (uint32_t)(((uint64_t)a * (uint64_t)b) >> 32);
+#endif
+}
+
+__host__ __device__ __forceinline__ void philox4x32_10(uint32_t x[4], uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        const uint32_t m0 = 0xD2511F53u, m1 = 0xCD9E8D57u;
+        uint32_t hi0 = mulhi32(m0, x[0]), lo0 = m0 * x[0];
+        uint32_t hi1 = mulhi32(m1, x[2]), lo1 = m1 * x[2];
+        uint32_t y0 = hi1 ^ x[1] ^ k0;
+        uint32_t y2 = hi0 ^ x[3] ^ k1;
+        x[0] = y0; x[1] = lo1; x[2] = y2; x[3] = lo0;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+}
+
+__device__ __forceinline__ uint32_t philox_word(uint64_t seed, uint32_t id, uint32_t day,
+                                                uint32_t inst, uint32_t stream) {
+    uint32_t x[4] = {id, day, inst, stream};
+    philox4x32_10(x, (uint32_t)seed, (uint32_t)(seed >> 32));
+    return x[0];
+}
+
+// u = ((x0 >> 9) + 0.5) * 2^-23 = (2 (x0 >> 9) + 1) * 2^-24: an odd integer below
+// 2^24 times a power of two, so exact in fp32.
+__device__ __forceinline__ float uniform_from_word(uint32_t x0) {
+    return __uint2float_rn(((x0 >> 9) << 1) | 1u) * 5.9604644775390625e-8f;
+}
+
+// ---------------------------------------------------------------------------
+// Kernel arguments
+// ---------------------------------------------------------------------------
+struct GraphRef {                 // where each graph sits in the concatenated arrays
+    const int32_t *row0;          // [G] first row of each graph
+    const uint16_t *tile_graph;   // [ntiles] graph of each tile (nullptr when G == 1)
+    const float *inv_Dbar;        // [G] 1 / mean weighted degree (0 for an edgeless graph)
+};
+
+struct FwdDayArgs {
+    const uint32_t *rowptr;
+    const uint4 *col4;
+    const float4 *w4;
+    const uint8_t *age;
+    GraphRef gr;
+    int16_t *e;
+    float *lam_out;       // day-t slice of the lambda store, or nullptr
+    const float *R;       // [I][ldP]
+    const float *S;       // [I][9]
+    int ldP;              // per-instance stride of R (and m)
+    int32_t *counts;      // [I][ldP][4]
+    int32_t *newRM;       // [I][ldP]
+    int ntiles, t, tau_EI, L;
+    uint64_t seed;
+    float c[kMaxL];
+};
+
+struct BwdDayArgs {
+    // transpose gather (out-edges of each row) -- the forward CSR when symmetric
+    const uint32_t *rowptr;
+    const uint4 *col4;
+    const float4 *w4;
+    // in-edges for lambda recomputation when they differ from the above (else nullptr)
+    const uint32_t *in_rowptr;
+    const uint4 *in_col4;
+    const float4 *in_w4;
+    const uint8_t *age;
+    GraphRef gr;
+    const int16_t *E;          // final exposure days
+    const float *lam_t;        // stored normalised sums for day t (store policy) or nullptr
+    const float *r_next;       // coefficients of day t+1 [n_rows]
+    float *r_cur;              // coefficients of day t   [n_rows]
+    float *ring;               // [L-1][n_rows]
+    size_t ring_stride;
+    float *A;                  // [n_rows] adjoint of s carried back from the infection day
+    const float *R, *m, *S;    // [I][ldP], [I][ldP], [I][9]
+    const double *gD;          // [I][ldP]
+    int ldP;
+    double *P_t;               // [ntiles][9] partial sums of gl * Lam for day t
+    int32_t *newRM;            // [I][ldP]
+    int ntiles, t, T, tau_EI, L;
+    int mode;                  // kBwdStore, kBwdFused or kBwdSplit
+    uint64_t seed;
+    float c[kMaxL];
+    int ring_slot[kMaxL];      // ring slot holding day t + k, k = 1..L-1
+};
+
+enum { kBwdStore = 0, kBwdFused = 1, kBwdSplit = 2 };
+
+struct SeedState {
+    uint32_t prefix;    // high bits of the threshold hash found so far
+    uint32_t k_rem;     // seeds still to choose among keys matching the prefix
+    uint32_t eq_count;  // keys equal to the final threshold hash
+    uint32_t tie_n;     // candidates appended to the tie list
+    int32_t none;       // 1 when no seed is to be chosen
+    int32_t overflow;   // tie list overflowed
+};
+
+struct SeedArgs {
+    const int32_t *row0;  // [G]
+    const int32_t *rows;  // [G] real rows per graph
+    int16_t *e;
+    SeedState *st;        // [I]
+    uint32_t *hist;       // [I][kHistBins]
+    uint32_t *ties;       // [I][kTieCap]
+    uint64_t seed;
+    int tau_EI;
+    int pass;             // 0, 1, 2
+};
+
+// Launchers (forward.cu / backward.cu)
+cudaError_t launch_init_state(int16_t *e, const int32_t *row0, const int32_t *rows, int G,
+                              int64_t n_rows, int grid, cudaStream_t s);
+cudaError_t launch_seed_reset(SeedState *st, const int32_t *n_seed, int I, cudaStream_t s);
+cudaError_t launch_seed_hist(const SeedArgs &a, int G, int grid_x, cudaStream_t s);
+cudaError_t launch_seed_scan(const SeedArgs &a, int I, cudaStream_t s);
+cudaError_t launch_seed_mark(const SeedArgs &a, int G, int grid_x, cudaStream_t s);
+cudaError_t launch_seed_ties(const SeedArgs &a, int I, cudaStream_t s);
+cudaError_t launch_fwd_day(const FwdDayArgs &a, int lanes_per_row, int grid, cudaStream_t s);
+cudaError_t launch_fwd_finalize(const int32_t *newRM, const int32_t *counts, const float *m, int ldP,
+                                int t0, int T, int I, double *D_ctx, double *D_out,
+                                int32_t *counts_out, cudaStream_t s);
+cudaError_t launch_mse(const double *D, int ldP, const double *y, int T, int I, double *loss,
+                       double *gD_ctx, double *gD_out, cudaStream_t s);
+cudaError_t launch_bwd_day(const BwdDayArgs &a, int lanes_per_row, int grid, cudaStream_t s);
+cudaError_t launch_bwd_reduce(const double *P, int ntiles, int ldP, const int32_t *graph_tile0,
+                              const int32_t *graph_ntiles, int T, int I, double *Q,
+                              cudaStream_t s);
+cudaError_t launch_bwd_finalize(const double *Q, const float *R, const float *S, const double *gD,
+                                const int32_t *newRM, int ldP, int T, int I, double *dR,
+                                double *dm, double *dS, cudaStream_t s);
+cudaError_t launch_get_lambda(const float *lam_t, const int16_t *e, const uint8_t *age,
+                              GraphRef gr, const float *R, const float *S, int ldP, int t,
+                              int64_t n_rows, float *out_rows, cudaStream_t s);
+cudaError_t launch_philox(uint64_t seed, const uint32_t *ctr, uint32_t *out, int64_t count,
+                          cudaStream_t s);
+int occupancy_fwd(int lanes_per_row);
+int occupancy_bwd(int lanes_per_row, int mode);
+
+}  // namespace gabm
