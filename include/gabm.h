@@ -65,6 +65,13 @@ enum { GABM_HARD_ST = 0, GABM_SOFT = 1 };
  * model the final exposure-day vector determines every day's state (A3/A4: no
  * reinfection), so recomputation needs no intermediate checkpoints. */
 enum { GABM_STORE_LAMBDA = 0, GABM_RECOMPUTE = 1 };
+/* Device layout of the agents.  GABM_ORDER_BFS relabels the agents of each
+ * graph in breadth-first order of the contact graph so that an agent's
+ * neighbours sit close together in memory (gathers hit fewer cache lines).
+ * Results do not depend on it beyond fp32 summation order: the Philox draws
+ * and every input and output stay keyed by the caller's agent ids, and the
+ * aggregation is permutation invariant (Sec. 2.3, App. A). */
+enum { GABM_ORDER_INPUT = 0, GABM_ORDER_BFS = 1 };
 
 #define GABM_NEVER 32767     /* exposure day of a susceptible agent */
 #define GABM_NUM_AGES 9      /* age bins 0-10, 11-20, ..., 71-80, 80+ (Sec. 3.1) */
@@ -99,6 +106,7 @@ typedef struct {
     int relax_mode;       /* GABM_HARD_ST (GABM_SOFT: GABM_EUNSUPPORTED in this build) */
     int lambda_policy;    /* GABM_STORE_LAMBDA or GABM_RECOMPUTE */
     uint64_t seed;        /* Philox key */
+    int agent_order;      /* GABM_ORDER_INPUT or GABM_ORDER_BFS (device layout only) */
 } gabm_model_desc;
 
 /* Build a ctx: validates and copies the graphs (GABM_EINVAL on bad data, before

@@ -26,6 +26,7 @@ GABM_ETIMEOUT, GABM_ECANCELLED, GABM_EUNSUPPORTED = 5, 6, 7
 GABM_DEVICE, GABM_HOST = 0, 1
 GABM_HARD_ST, GABM_SOFT = 0, 1
 GABM_STORE_LAMBDA, GABM_RECOMPUTE = 0, 1
+GABM_ORDER_INPUT, GABM_ORDER_BFS = 0, 1
 GABM_NEVER = 32767
 GABM_NUM_AGES = 9
 STATUS_NAMES = {0: "GABM_OK", 1: "GABM_EINVAL", 2: "GABM_ENOMEM", 3: "GABM_ECUDA", 4: "GABM_ESTATE",
@@ -47,7 +48,7 @@ class _GraphDesc(ctypes.Structure):
 class _ModelDesc(ctypes.Structure):
     _fields_ = [("tau_EI", ctypes.c_int), ("tau_IR", ctypes.c_int), ("c", ctypes.c_void_p),
                 ("gumbel_tau", ctypes.c_float), ("relax_mode", ctypes.c_int),
-                ("lambda_policy", ctypes.c_int), ("seed", ctypes.c_uint64)]
+                ("lambda_policy", ctypes.c_int), ("seed", ctypes.c_uint64), ("agent_order", ctypes.c_int)]
 
 
 _lib = None
@@ -135,6 +136,11 @@ def _ptr(x, dtype=None):
     return ctypes.c_void_p(x.ctypes.data)
 
 
+def _shape(x, want, name):
+    if x is not None and tuple(x.shape) != tuple(want):
+        raise ValueError(f"{name} must have shape {tuple(want)}, got {tuple(x.shape)}")
+
+
 def _check(status: int, handle=None):
     if status != GABM_OK:
         msg = load_library().gabm_last_error(handle).decode(errors="replace")
@@ -160,6 +166,7 @@ class ModelDesc:
     lambda_policy: int = GABM_STORE_LAMBDA
     gumbel_tau: float = 1.0
     relax_mode: int = GABM_HARD_ST
+    agent_order: int = GABM_ORDER_BFS
 
 
 class GabmCtx:
@@ -210,7 +217,7 @@ def gabm_create(graphs, model: ModelDesc, sets_per_graph: int = 1, stream=None) 
         keep.append(g)
     c = np.ascontiguousarray(model.c, dtype=np.float32)
     md = _ModelDesc(int(model.tau_EI), int(model.tau_IR), _ptr(c, np.float32), float(model.gumbel_tau),
-                    int(model.relax_mode), int(model.lambda_policy), int(model.seed))
+                    int(model.relax_mode), int(model.lambda_policy), int(model.seed), int(model.agent_order))
     s = None
     if stream is not None:
         s = ctypes.c_void_p(int(getattr(stream, "cuda_stream", stream)))
@@ -234,6 +241,11 @@ def gabm_forward(ctx: GabmCtx, T: int, R, m, S_age, n_seed=None, D=None, counts=
     ms = _space(R, m, S_age, D, counts)
     cuda = ms == GABM_DEVICE
     I = ctx.instances
+    _shape(R, (I, T), "R")
+    _shape(m, (I, T), "m")
+    _shape(S_age, (I, GABM_NUM_AGES), "S_age")
+    _shape(D, (I, T), "D")
+    _shape(counts, (I, T, 4), "counts")
     if D is None:
         D = _empty((I, T), np.float64, cuda, ctx.device)
     if counts is None and want_counts:
@@ -254,6 +266,9 @@ def gabm_mse_loss(ctx: GabmCtx, y, loss=None, gD=None):
     ms = _space(y, loss, gD)
     cuda = ms == GABM_DEVICE
     I, T = ctx.instances, (ctx.T if ctx.T is not None else int(y.shape[-1]))
+    _shape(y, (I, T), "y")
+    _shape(loss, (I,), "loss")
+    _shape(gD, (I, T), "gD")
     if loss is None:
         loss = _empty((I,), np.float64, cuda, ctx.device)
     if gD is None:
@@ -269,6 +284,10 @@ def gabm_backward(ctx: GabmCtx, gD, dR=None, dm=None, dS_age=None):
     ms = _space(gD, dR, dm, dS_age)
     cuda = ms == GABM_DEVICE
     I, T = ctx.instances, (ctx.T if ctx.T is not None else int(gD.shape[-1]))
+    _shape(gD, (I, T), "gD")
+    _shape(dR, (I, T), "dR")
+    _shape(dm, (I, T), "dm")
+    _shape(dS_age, (I, GABM_NUM_AGES), "dS_age")
     if dR is None:
         dR = _empty((I, T), np.float64, cuda, ctx.device)
     if dm is None:
@@ -292,6 +311,8 @@ def gabm_get_state(ctx: GabmCtx, out=None, device: bool = False):
 
 
 def gabm_set_state(ctx: GabmCtx, day: int, e):
+    if tuple(e.shape) not in ((ctx.sets, ctx.n_total),) + (((ctx.n_total,),) if ctx.sets == 1 else ()):
+        raise ValueError(f"e must have shape ({ctx.sets}, {ctx.n_total}), got {tuple(e.shape)}")
     st = load_library().gabm_set_state(ctx.handle, int(day), _ptr(e, np.int16), _space(e))
     _check(st, ctx.handle)
 

@@ -21,11 +21,12 @@ namespace gabm {
 
 namespace {
 
-template <int GL, int MODE>
-__global__ void __launch_bounds__(kBlock) k_bwd_day(const BwdDayArgs a) {
+template <int MODE>
+__global__ void __launch_bounds__(kBlock, (MODE == kBwdFused) ? 2 : 3) k_bwd_day(const BwdDayArgs a) {
+    constexpr int NARR = (MODE == kBwdFused) ? 2 : 1;
     __shared__ float c_s[kMaxL];
     __shared__ int slot_k[kMaxL];
-    __shared__ uint8_t slot_s[kBlock / 32][32];
+    __shared__ WarpStage<NARR> stage_s[kBlock / 32];
     __shared__ int32_t red_s[kBlock / 32][2];
     if (threadIdx.x < kMaxL) {
         c_s[threadIdx.x] = a.c[threadIdx.x];
@@ -33,16 +34,25 @@ __global__ void __launch_bounds__(kBlock) k_bwd_day(const BwdDayArgs a) {
     }
     __syncthreads();
 
-    constexpr int RPP = 32 / GL;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const unsigned lt_mask = (1u << lane) - 1u;
-    const int sub = lane / GL, gl = lane % GL;
     const int t = a.t, T = a.T, L = a.L;
     const bool has_next = (t + 1 < T);
-    const int nwarps = gridDim.x * (kBlock / 32);
+    WarpStage<NARR> &ws = stage_s[wib];
+    const int16_t *E = a.E;
+    const float *r_next = a.r_next;
+    // flags: bit 0 = this row needs gx(t+1), bit 1 = this row needs its lambda recomputed
+    auto contrib_adj = [&](uint32_t fl, uint32_t j, float w, float (&out)[NARR]) {
+        if (fl & 1u) out[0] = w * r_next[j];
+        if constexpr (NARR == 2) {
+            if (fl & 2u) out[1] = w * infectiousness(E[j], c_s, t, L);
+        }
+    };
+    auto contrib_lam = [&](uint32_t, uint32_t j, float w, float (&out)[1]) {
+        out[0] = w * infectiousness(E[j], c_s, t, L);
+    };
 
     int cur_g = -1, cN = 0;
-    for (int tile = blockIdx.x * (kBlock / 32) + wib; tile < a.ntiles; tile += nwarps) {
+    for (int tile = next_tile(a.tile_ctr, lane); tile < a.ntiles; tile = next_tile(a.tile_ctr, lane)) {
         const int g = a.gr.tile_graph ? (int)a.gr.tile_graph[tile] : 0;
         if (g != cur_g) {
             if (cur_g >= 0) {
@@ -60,54 +70,22 @@ __global__ void __launch_bounds__(kBlock) k_bwd_day(const BwdDayArgs a) {
         const bool isS = live && (never || Ei >= t);
         const bool needA = has_next && live && (never || Ei >= t + 2 - L);
         cN += (agent && !never && t - Ei == L);
-        const bool act = needA || isS;
-        const unsigned amask = __ballot_sync(0xffffffffu, act);
 
         float gx_mine = 0.f, lam_mine = 0.f;
-        if (amask) {
-            uint32_t rs = 0, re = 0, irs = 0, ire = 0;
-            if (act) { rs = a.rowptr[row]; re = a.rowptr[row + 1]; }
-            if (MODE == kBwdSplit && isS) { irs = a.in_rowptr[row]; ire = a.in_rowptr[row + 1]; }
-            const int rank = __popc(amask & lt_mask);
-            if (act) slot_s[wib][rank] = (uint8_t)lane;
-            __syncwarp();
-            const int nA = __popc(amask);
-            for (int base = 0; base < nA; base += RPP) {
-                const int j = base + sub;
-                const int src = (j < nA) ? slot_s[wib][j] : 0;
-                const uint32_t rsj = __shfl_sync(0xffffffffu, rs, src);
-                const uint32_t rej = __shfl_sync(0xffffffffu, re, src);
-                const bool nAj = __shfl_sync(0xffffffffu, needA, src);
-                const bool Sj = __shfl_sync(0xffffffffu, isS, src);
-                float gxp = 0.f, lmp = 0.f;
-                if (j < nA) {
-                    if (MODE == kBwdFused) {
-                        lane_adjoint_sums<GL, true>(a.col4, a.w4, a.E, a.r_next, c_s, rsj, rej, gl, t, L,
-                                                    nAj, Sj, gxp, lmp);
-                    } else {
-                        if (nAj)
-                            lane_adjoint_sums<GL, false>(a.col4, a.w4, a.E, a.r_next, c_s, rsj, rej, gl, t,
-                                                         L, true, false, gxp, lmp);
-                    }
-                }
-                if (MODE == kBwdSplit) {
-                    const uint32_t irsj = __shfl_sync(0xffffffffu, irs, src);
-                    const uint32_t irej = __shfl_sync(0xffffffffu, ire, src);
-                    if (j < nA && Sj)
-                        lmp = lane_infectious_sum<GL>(a.in_col4, a.in_w4, a.E, c_s, irsj, irej, gl, t, L);
-                }
-#pragma unroll
-                for (int o = GL / 2; o > 0; o >>= 1) {
-                    gxp += __shfl_xor_sync(0xffffffffu, gxp, o);
-                    if (MODE != kBwdStore) lmp += __shfl_xor_sync(0xffffffffu, lmp, o);
-                }
-                const int myj = rank - base;
-                const int from = (myj & (RPP - 1)) * GL;
-                const float g1 = __shfl_sync(0xffffffffu, gxp, from);
-                const float g2 = __shfl_sync(0xffffffffu, lmp, from);
-                if (act && myj >= 0 && myj < RPP) { gx_mine = g1; lam_mine = g2; }
-            }
-            __syncwarp();
+        {
+            const bool act = (MODE == kBwdFused) ? (needA || isS) : needA;
+            const uint32_t rs = a.rowptr[row], re = a.rowptr[row + 1];
+            const uint32_t fl = (needA ? 1u : 0u) | ((MODE == kBwdFused && isS) ? 2u : 0u);
+            float sum[NARR];
+            warp_row_sums<NARR>(ws, a.col4, a.w4, act, rs, re, fl, lane, contrib_adj, sum);
+            gx_mine = sum[0];
+            if constexpr (MODE == kBwdFused) lam_mine = sum[NARR - 1];
+        }
+        if constexpr (MODE == kBwdSplit) {
+            const uint32_t rs = a.in_rowptr[row], re = a.in_rowptr[row + 1];
+            float sum[1];
+            warp_row_sums<1>(ws, a.in_col4, a.in_w4, isS, rs, re, 0u, lane, contrib_lam, sum);
+            lam_mine = sum[0];
         }
 
         if (needA) a.ring[(size_t)slot_k[1] * a.ring_stride + row] = gx_mine;
@@ -132,7 +110,7 @@ __global__ void __launch_bounds__(kBlock) k_bwd_day(const BwdDayArgs a) {
             const float lam = RS * Lam;
             const float q = expf(-lam);
             const float p = -expm1f(-lam);
-            const uint32_t id = (uint32_t)(row - a.gr.row0[g]);
+            const uint32_t id = caller_id(a.gr, row, g);
             const float u = uniform_from_word(philox_word(a.seed, id, (uint32_t)t, (uint32_t)inst, 0u));
             const float den = __fmaf_rn(p, 1.f - u, q * u);
             const float dydl = (u * (1.f - u)) * q / (den * den);
@@ -225,48 +203,26 @@ __global__ void __launch_bounds__(256) k_bwd_finalize(const double *Q, const flo
     }
 }
 
-template <int MODE>
-cudaError_t launch_bwd_mode(const BwdDayArgs &a, int lanes_per_row, int grid, cudaStream_t s) {
-    switch (lanes_per_row) {
-        case 4: k_bwd_day<4, MODE><<<grid, kBlock, 0, s>>>(a); break;
-        case 8: k_bwd_day<8, MODE><<<grid, kBlock, 0, s>>>(a); break;
-        case 16: k_bwd_day<16, MODE><<<grid, kBlock, 0, s>>>(a); break;
-        case 32: k_bwd_day<32, MODE><<<grid, kBlock, 0, s>>>(a); break;
+}  // namespace
+
+cudaError_t launch_bwd_day(const BwdDayArgs &a, int grid, cudaStream_t s) {
+    switch (a.mode) {
+        case kBwdStore: k_bwd_day<kBwdStore><<<grid, kBlock, 0, s>>>(a); break;
+        case kBwdFused: k_bwd_day<kBwdFused><<<grid, kBlock, 0, s>>>(a); break;
+        case kBwdSplit: k_bwd_day<kBwdSplit><<<grid, kBlock, 0, s>>>(a); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
 }
 
-template <int MODE>
-int occupancy_mode(int lanes_per_row) {
+int occupancy_bwd(int mode) {
     int blocks = 0;
-    switch (lanes_per_row) {
-        case 4: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_bwd_day<4, MODE>, kBlock, 0); break;
-        case 8: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_bwd_day<8, MODE>, kBlock, 0); break;
-        case 16: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_bwd_day<16, MODE>, kBlock, 0); break;
-        case 32: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_bwd_day<32, MODE>, kBlock, 0); break;
-        default: break;
+    switch (mode) {
+        case kBwdStore: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_bwd_day<kBwdStore>, kBlock, 0); break;
+        case kBwdFused: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_bwd_day<kBwdFused>, kBlock, 0); break;
+        default: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_bwd_day<kBwdSplit>, kBlock, 0); break;
     }
     return blocks > 0 ? blocks : 1;
-}
-
-}  // namespace
-
-cudaError_t launch_bwd_day(const BwdDayArgs &a, int lanes_per_row, int grid, cudaStream_t s) {
-    switch (a.mode) {
-        case kBwdStore: return launch_bwd_mode<kBwdStore>(a, lanes_per_row, grid, s);
-        case kBwdFused: return launch_bwd_mode<kBwdFused>(a, lanes_per_row, grid, s);
-        case kBwdSplit: return launch_bwd_mode<kBwdSplit>(a, lanes_per_row, grid, s);
-        default: return cudaErrorInvalidValue;
-    }
-}
-
-int occupancy_bwd(int lanes_per_row, int mode) {
-    switch (mode) {
-        case kBwdStore: return occupancy_mode<kBwdStore>(lanes_per_row);
-        case kBwdFused: return occupancy_mode<kBwdFused>(lanes_per_row);
-        default: return occupancy_mode<kBwdSplit>(lanes_per_row);
-    }
 }
 
 cudaError_t launch_bwd_reduce(const double *P, int ntiles, int ldP, const int32_t *graph_tile0,

@@ -45,6 +45,8 @@ struct gabm_ctx {
     uint32_t *t_rowptr = nullptr, *t_col = nullptr;
     float *t_w = nullptr;
     int32_t *d_row0 = nullptr, *d_rows = nullptr, *d_tile0 = nullptr, *d_ntiles = nullptr;
+    int64_t *d_goff = nullptr;      // [G] caller offset of each graph
+    uint32_t *d_orig_id = nullptr;  // [n_rows] caller id of each row (nullptr: input order)
     uint16_t *d_tile_graph = nullptr;
     float *d_inv_Dbar = nullptr;
     int16_t *e = nullptr;
@@ -60,7 +62,7 @@ struct gabm_ctx {
     uint32_t *hist = nullptr, *ties = nullptr;
     int32_t *d_nseed = nullptr;
 
-    float *ring = nullptr, *A = nullptr, *r = nullptr, *rows_f = nullptr;
+    float *ring = nullptr, *A = nullptr, *r = nullptr, *rows_f = nullptr, *stage_f = nullptr;
     int16_t *rows_e = nullptr;
 
     int t0_next = 0;
@@ -68,7 +70,8 @@ struct gabm_ctx {
     int T_last = -1;
     int lam_from = -1;
 
-    int lanes_fwd = 8, lanes_bwd = 8, grid_fwd = 0, grid_bwd = 0;
+    int grid_fwd = 0, grid_bwd = 0;
+    int *tile_ctr = nullptr;        // [2][Tcap] per-launch tile counters (forward, backward)
 
     size_t mem_cur = 0, mem_peak = 0;
     std::unordered_map<void *, size_t> sizes;
@@ -177,6 +180,8 @@ gabm_status validate_model(const gabm_model_desc *md) {
     if (!(md->gumbel_tau == 1.0f)) return fail(nullptr, GABM_EUNSUPPORTED, "only gumbel_tau = 1 is implemented");
     if (md->lambda_policy != GABM_STORE_LAMBDA && md->lambda_policy != GABM_RECOMPUTE)
         return fail(nullptr, GABM_EINVAL, "unknown lambda_policy %d", md->lambda_policy);
+    if (md->agent_order != GABM_ORDER_INPUT && md->agent_order != GABM_ORDER_BFS)
+        return fail(nullptr, GABM_EINVAL, "unknown agent_order %d", md->agent_order);
     return GABM_OK;
 }
 
@@ -236,6 +241,65 @@ void transpose_graph(const HostGraph &h, std::vector<uint64_t> &trp, std::vector
         }
 }
 
+// Breadth-first order over the in-edges: every dequeued agent appends its
+// not-yet-seen neighbours, so groups of mutual contacts (households, schools,
+// workplaces) become adjacent rows and one warp's gathers share cache lines.
+std::vector<uint32_t> bfs_order(const HostGraph &h) {
+    std::vector<uint32_t> order;
+    order.reserve((size_t)h.n);
+    std::vector<uint8_t> seen((size_t)h.n, 0);
+    for (int64_t s = 0; s < h.n; ++s) {
+        if (seen[s]) continue;
+        seen[s] = 1;
+        size_t head = order.size();
+        order.push_back((uint32_t)s);
+        while (head < order.size()) {
+            const uint32_t v = order[head++];
+            for (uint64_t p = h.rowptr[v]; p < h.rowptr[v + 1]; ++p) {
+                const uint32_t u = h.col[p];
+                if (!seen[u]) {
+                    seen[u] = 1;
+                    order.push_back(u);
+                }
+            }
+        }
+    }
+    return order;
+}
+
+// Relabel a graph: new row k is old agent order[k]; each row's entries sorted by new column.
+HostGraph permute_graph(const HostGraph &h, const std::vector<uint32_t> &order) {
+    HostGraph o;
+    o.n = h.n;
+    o.nnz = h.nnz;
+    std::vector<uint32_t> inv((size_t)h.n);
+    for (int64_t k = 0; k < h.n; ++k) inv[order[k]] = (uint32_t)k;
+    o.rowptr.assign((size_t)h.n + 1, 0);
+    o.col.resize((size_t)h.nnz);
+    o.w.resize((size_t)h.nnz);
+    o.age.resize((size_t)h.n);
+    for (int64_t k = 0; k < h.n; ++k) {
+        const uint32_t v = order[k];
+        o.rowptr[k + 1] = o.rowptr[k] + (h.rowptr[v + 1] - h.rowptr[v]);
+        o.age[k] = h.age[v];
+    }
+    std::vector<std::pair<uint32_t, float>> tmp;
+    for (int64_t k = 0; k < h.n; ++k) {
+        const uint32_t v = order[k];
+        tmp.clear();
+        for (uint64_t p = h.rowptr[v]; p < h.rowptr[v + 1]; ++p) tmp.emplace_back(inv[h.col[p]], h.w[p]);
+        std::sort(tmp.begin(), tmp.end(),
+                  [](const std::pair<uint32_t, float> &a, const std::pair<uint32_t, float> &b) { return a.first < b.first; });
+        uint64_t q = o.rowptr[k];
+        for (const auto &e : tmp) {
+            o.col[q] = e.first;
+            o.w[q] = e.second;
+            ++q;
+        }
+    }
+    return o;
+}
+
 gabm_status ensure_days(gabm_ctx *c, int T) {
     if (T <= c->Tcap) return GABM_OK;
     int cap = c->Tcap > 0 ? c->Tcap : 8;
@@ -245,7 +309,7 @@ gabm_status ensure_days(gabm_ctx *c, int T) {
     dfree(c, c->lam); dfree(c, c->counts); dfree(c, c->newRM); dfree(c, c->newRM_b);
     dfree(c, c->D); dfree(c, c->gD); dfree(c, c->y); dfree(c, c->P); dfree(c, c->Q);
     dfree(c, c->R); dfree(c, c->m);
-    dfree(c, c->dR_s); dfree(c, c->dm_s);
+    dfree(c, c->dR_s); dfree(c, c->dm_s); dfree(c, c->tile_ctr);
     c->Tcap = 0;
     const size_t IT = (size_t)c->I * cap;
     if (c->policy == GABM_STORE_LAMBDA) TRY(dalloc(c, &c->lam, (size_t)cap * c->n_rows));
@@ -261,6 +325,7 @@ gabm_status ensure_days(gabm_ctx *c, int T) {
     TRY(dalloc(c, &c->m, IT));
     TRY(dalloc(c, &c->dR_s, IT));
     TRY(dalloc(c, &c->dm_s, IT));
+    TRY(dalloc(c, &c->tile_ctr, (size_t)2 * cap));
     CK(cudaMemsetAsync(c->D, 0, IT * sizeof(double), c->stream));
     c->Tcap = cap;
     c->T_last = -1;
@@ -306,6 +371,7 @@ GraphRef graph_ref(const gabm_ctx *c) {
     gr.row0 = c->d_row0;
     gr.tile_graph = c->G > 1 ? c->d_tile_graph : nullptr;
     gr.inv_Dbar = c->d_inv_Dbar;
+    gr.orig_id = c->d_orig_id;
     return gr;
 }
 
@@ -363,6 +429,15 @@ gabm_status gabm_create(const gabm_graph_desc *graphs, int num_graphs, int sets_
         for (int64_t p = 0; p < hg[g].nnz; ++p) s += (double)hg[g].w[p];
         Dbar[g] = hg[g].n > 0 ? s / (double)hg[g].n : 0.0;
     }
+    // device layout: optionally relabel each graph's agents (D-bar above uses the caller's order)
+    std::vector<std::vector<uint32_t>> orders((size_t)num_graphs);
+    const bool reorder = model->agent_order == GABM_ORDER_BFS;
+    if (reorder) {
+        for (int g = 0; g < num_graphs; ++g) {
+            orders[g] = bfs_order(hg[g]);
+            hg[g] = permute_graph(hg[g], orders[g]);
+        }
+    }
     if (n_rows >= ((int64_t)1 << 31) - 64) return fail(nullptr, GABM_EUNSUPPORTED, "total rows >= 2^31");
     if (nnz >= ((int64_t)1 << 32) - 64) return fail(nullptr, GABM_EUNSUPPORTED, "total nnz >= 2^32");
     if (n_rows == 0) n_rows = kTile;  // keep one (padding) tile so every buffer is non-empty
@@ -375,6 +450,9 @@ gabm_status gabm_create(const gabm_graph_desc *graphs, int num_graphs, int sets_
     std::vector<uint32_t> t_rowptr((size_t)n_rows + 1), t_col((size_t)nnz_pad, 0u);
     std::vector<float> t_w((size_t)nnz_pad, 0.f);
     std::vector<uint16_t> tile_graph((size_t)ntiles, 0);
+    std::vector<uint32_t> h_orig(reorder ? (size_t)n_rows : 0, 0u);
+    std::vector<int64_t> goff((size_t)num_graphs, 0);
+    for (int g = 1; g < num_graphs; ++g) goff[g] = goff[g - 1] + hg[g - 1].n;
     bool symmetric = true;
     {
         int64_t e0 = 0;
@@ -390,6 +468,7 @@ gabm_status gabm_create(const gabm_graph_desc *graphs, int num_graphs, int sets_
                 h_rowptr[r] = (uint32_t)(e0 + (int64_t)h.rowptr[i < h.n ? i : h.n]);
                 t_rowptr[r] = (uint32_t)(e0 + (int64_t)trp[i < h.n ? i : h.n]);
                 if (i < h.n) h_age[r] = h.age[i];
+                if (reorder && i < h.n) h_orig[r] = orders[g][i];
             }
             for (int64_t p = 0; p < h.nnz; ++p) {
                 h_col[e0 + p] = h.col[p] + (uint32_t)row0[g];
@@ -430,8 +509,6 @@ gabm_status gabm_create(const gabm_graph_desc *graphs, int num_graphs, int sets_
     c->h_Dbar = Dbar;
     c->symmetric = symmetric;
     if (const char *f = getenv("GABM_FAIL_ALLOC_AFTER")) c->fail_alloc_after = atol(f);
-    if (const char *f = getenv("GABM_LANES_FWD")) c->lanes_fwd = atoi(f);
-    if (const char *f = getenv("GABM_LANES_BWD")) c->lanes_bwd = atoi(f);
 
     auto bail = [&](gabm_status st) {
         g_create_error = c->err;
@@ -452,8 +529,6 @@ gabm_status gabm_create(const gabm_graph_desc *graphs, int num_graphs, int sets_
 
     CCK(cudaGetDevice(&c->device));
     CCK(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device));
-    if (c->lanes_fwd != 4 && c->lanes_fwd != 8 && c->lanes_fwd != 16 && c->lanes_fwd != 32) c->lanes_fwd = 8;
-    if (c->lanes_bwd != 4 && c->lanes_bwd != 8 && c->lanes_bwd != 16 && c->lanes_bwd != 32) c->lanes_bwd = 8;
 
     CTRY(dalloc(c, &c->rowptr, (size_t)n_rows + 1));
     CTRY(dalloc(c, &c->col, (size_t)nnz_pad));
@@ -483,6 +558,12 @@ gabm_status gabm_create(const gabm_graph_desc *graphs, int num_graphs, int sets_
     CTRY(dalloc(c, &c->d_ntiles, (size_t)num_graphs));
     CTRY(dalloc(c, &c->d_inv_Dbar, (size_t)num_graphs));
     CTRY(dalloc(c, &c->d_tile_graph, (size_t)ntiles));
+    CTRY(dalloc(c, &c->d_goff, (size_t)num_graphs));
+    CCK(cudaMemcpyAsync(c->d_goff, goff.data(), sizeof(int64_t) * num_graphs, cudaMemcpyHostToDevice, c->stream));
+    if (reorder) {
+        CTRY(dalloc(c, &c->d_orig_id, (size_t)n_rows));
+        CCK(cudaMemcpyAsync(c->d_orig_id, h_orig.data(), sizeof(uint32_t) * n_rows, cudaMemcpyHostToDevice, c->stream));
+    }
     CCK(cudaMemcpyAsync(c->d_row0, row0.data(), sizeof(int32_t) * num_graphs, cudaMemcpyHostToDevice, c->stream));
     CCK(cudaMemcpyAsync(c->d_rows, rows.data(), sizeof(int32_t) * num_graphs, cudaMemcpyHostToDevice, c->stream));
     CCK(cudaMemcpyAsync(c->d_tile0, tile0.data(), sizeof(int32_t) * num_graphs, cudaMemcpyHostToDevice, c->stream));
@@ -496,6 +577,7 @@ gabm_status gabm_create(const gabm_graph_desc *graphs, int num_graphs, int sets_
     CTRY(dalloc(c, &c->r, (size_t)2 * n_rows));
     CTRY(dalloc(c, &c->rows_f, (size_t)n_rows));
     CTRY(dalloc(c, &c->rows_e, (size_t)n_rows));
+    CTRY(dalloc(c, &c->stage_f, (size_t)n_rows));
     CTRY(dalloc(c, &c->S, (size_t)c->I * kAges));
     CTRY(dalloc(c, &c->dS_s, (size_t)c->I * kAges));
     CTRY(dalloc(c, &c->loss_s, (size_t)c->I));
@@ -510,9 +592,9 @@ gabm_status gabm_create(const gabm_graph_desc *graphs, int num_graphs, int sets_
         c->launches++;
         if (e != cudaSuccess) return bail(fail(c, GABM_ECUDA, "init state: %s", cudaGetErrorString(e)));
     }
-    c->grid_fwd = c->num_sms * occupancy_fwd(c->lanes_fwd);
+    c->grid_fwd = c->num_sms * occupancy_fwd();
     const int mode = c->policy == GABM_STORE_LAMBDA ? kBwdStore : (symmetric ? kBwdFused : kBwdSplit);
-    c->grid_bwd = c->num_sms * occupancy_bwd(c->lanes_bwd, mode);
+    c->grid_bwd = c->num_sms * occupancy_bwd(mode);
     const int max_grid = (ntiles + kBlock / 32 - 1) / (kBlock / 32);
     if (c->grid_fwd > max_grid) c->grid_fwd = max_grid;
     if (c->grid_bwd > max_grid) c->grid_bwd = max_grid;
@@ -556,6 +638,7 @@ gabm_status gabm_forward(gabm_ctx *ctx, int T, const float *R, const float *m, c
     CK(cudaMemsetAsync(c->counts, 0, sizeof(int32_t) * 4 * (size_t)c->I * ld, s));
     CK(cudaMemsetAsync(c->newRM, 0, sizeof(int32_t) * (size_t)c->I * ld, s));
     CK(cudaMemsetAsync(c->D, 0, sizeof(double) * (size_t)c->I * ld, s));
+    CK(cudaMemsetAsync(c->tile_ctr, 0, sizeof(int) * (size_t)ld, s));
 
     if (!c->resumed) {
         CK(cudaMemcpyAsync(c->d_nseed, n_seed, sizeof(int32_t) * c->I, cudaMemcpyHostToDevice, s));
@@ -564,6 +647,7 @@ gabm_status gabm_forward(gabm_ctx *ctx, int T, const float *R, const float *m, c
         SeedArgs sa;
         sa.row0 = c->d_row0;
         sa.rows = c->d_rows;
+        sa.orig_id = c->d_orig_id;
         sa.e = c->e;
         sa.st = c->seedst;
         sa.hist = c->hist;
@@ -603,8 +687,9 @@ gabm_status gabm_forward(gabm_ctx *ctx, int T, const float *R, const float *m, c
     for (int t = t0; t < T; ++t) {
         a.t = t;
         a.lam_out = c->policy == GABM_STORE_LAMBDA ? c->lam + (size_t)t * c->n_rows : nullptr;
+        a.tile_ctr = c->tile_ctr + t;
         prof_begin(c, 0);
-        LAUNCH(launch_fwd_day(a, c->lanes_fwd, c->grid_fwd, s));
+        LAUNCH(launch_fwd_day(a, c->grid_fwd, s));
         prof_end(c, 0);
     }
     const bool dev = mem_space == GABM_DEVICE;
@@ -659,6 +744,7 @@ gabm_status gabm_backward(gabm_ctx *ctx, const double *gD, double *dR, double *d
     CK(cudaMemcpy2DAsync(c->gD, ld * sizeof(double), gD, T * sizeof(double), T * sizeof(double), c->I, h2d_kind(mem_space), s));
     CK(cudaMemsetAsync(c->r, 0, sizeof(float) * 2 * (size_t)c->n_rows, s));
     CK(cudaMemsetAsync(c->newRM_b, 0, sizeof(int32_t) * (size_t)c->I * ld, s));
+    CK(cudaMemsetAsync(c->tile_ctr + ld, 0, sizeof(int) * (size_t)ld, s));
 
     BwdDayArgs a;
     const int mode = c->policy == GABM_STORE_LAMBDA ? kBwdStore : (c->symmetric ? kBwdFused : kBwdSplit);
@@ -695,8 +781,9 @@ gabm_status gabm_backward(gabm_ctx *ctx, const double *gD, double *dR, double *d
         a.r_cur = c->r + (size_t)(t & 1) * c->n_rows;
         a.P_t = c->P + (size_t)t * c->ntiles * kAges;
         for (int k = 0; k < kMaxL; ++k) a.ring_slot[k] = (k >= 1 && k < c->L) ? (t + k) % Lm1 : 0;
+        a.tile_ctr = c->tile_ctr + ld + t;
         prof_begin(c, 1);
-        LAUNCH(launch_bwd_day(a, c->lanes_bwd, c->grid_bwd, s));
+        LAUNCH(launch_bwd_day(a, c->grid_bwd, s));
         prof_end(c, 1);
     }
     LAUNCH(launch_bwd_reduce(c->P, c->ntiles, ld, c->d_tile0, c->d_ntiles, T, c->I, c->Q, s));
@@ -717,13 +804,13 @@ gabm_status gabm_get_state(gabm_ctx *ctx, int16_t *e_out, int mem_space) {
     if (!c) return fail(nullptr, GABM_EINVAL, "ctx is NULL");
     TRY(check_ms(c, mem_space));
     if (!e_out) return fail(c, GABM_EINVAL, "e_out is NULL");
-    int64_t off = 0;
-    for (int g = 0; g < c->G; ++g) {
-        if (c->h_rows[g] > 0)
-            CK(cudaMemcpyAsync(e_out + off, c->e + c->h_row0[g], sizeof(int16_t) * c->h_rows[g], d2h_kind(mem_space), c->stream));
-        off += c->h_rows[g];
+    const bool dev = mem_space == GABM_DEVICE;
+    LAUNCH(launch_rows_to_caller_i16(c->e, dev ? e_out : c->rows_e, graph_ref(c), c->d_rows, c->d_goff, c->n_rows,
+                                     c->stream));
+    if (!dev) {
+        CK(cudaMemcpyAsync(e_out, c->rows_e, sizeof(int16_t) * (size_t)c->n_total, cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
     }
-    if (mem_space == GABM_HOST) CK(cudaStreamSynchronize(c->stream));
     return GABM_OK;
 }
 
@@ -746,11 +833,10 @@ gabm_status gabm_set_state(gabm_ctx *ctx, int day, const int16_t *e_in, int mem_
             return fail(c, GABM_EINVAL, "e[%zu] = %d: must be NEVER or in [-%d, %d)", i, v, c->L, day);
     }
     CK(cudaStreamSynchronize(c->stream));
-    int64_t off = 0;
-    for (int g = 0; g < c->G; ++g) {
-        if (c->h_rows[g] > 0)
-            CK(cudaMemcpy(c->e + c->h_row0[g], h.data() + off, sizeof(int16_t) * c->h_rows[g], cudaMemcpyHostToDevice));
-        off += c->h_rows[g];
+    if (c->n_total > 0) {
+        CK(cudaMemcpyAsync(c->rows_e, h.data(), sizeof(int16_t) * h.size(), cudaMemcpyHostToDevice, c->stream));
+        LAUNCH(launch_caller_to_rows_i16(c->rows_e, c->e, graph_ref(c), c->d_rows, c->d_goff, c->n_rows, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
     }
     c->t0_next = day;
     c->resumed = true;
@@ -769,13 +855,13 @@ gabm_status gabm_get_lambda(gabm_ctx *ctx, int t, float *lam_out, int mem_space)
         return fail(c, GABM_ESTATE, "day %d was not run by the last forward", t);
     LAUNCH(launch_get_lambda(c->lam + (size_t)t * c->n_rows, c->e, c->age, graph_ref(c), c->R, c->S, c->Tcap, t,
                              c->n_rows, c->rows_f, c->stream));
-    int64_t off = 0;
-    for (int g = 0; g < c->G; ++g) {
-        if (c->h_rows[g] > 0)
-            CK(cudaMemcpyAsync(lam_out + off, c->rows_f + c->h_row0[g], sizeof(float) * c->h_rows[g], d2h_kind(mem_space), c->stream));
-        off += c->h_rows[g];
+    const bool dev = mem_space == GABM_DEVICE;
+    LAUNCH(launch_rows_to_caller_f32(c->rows_f, dev ? lam_out : c->stage_f, graph_ref(c), c->d_rows, c->d_goff,
+                                     c->n_rows, c->stream));
+    if (!dev) {
+        CK(cudaMemcpyAsync(lam_out, c->stage_f, sizeof(float) * (size_t)c->n_total, cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
     }
-    if (mem_space == GABM_HOST) CK(cudaStreamSynchronize(c->stream));
     return GABM_OK;
 }
 

@@ -1,14 +1,12 @@
 // forward.cu -- forward day step of the hard GradABM model on sm_103a.
 //
-// One launch per day (Sec. 3.1, Eq. 1-3; A1: one-day steps).  Each warp takes
-// 32 consecutive rows (agents).  Rows whose agent is susceptible are compacted
-// within the warp and processed GL lanes per row: every lane streams 16-byte
-// vectors of 4 (col, w) pairs of its row (destination-sorted CSR, so this is a
-// pull gather with no atomics), gathers the neighbours' exposure days from the
-// L2-resident state, and accumulates w_ji * c[t - e_j].  A butterfly over the
-// GL lanes gives the row sum, which is handed to the lane that owns the row
-// for the fused epilogue: lambda, p = 1 - exp(-lambda) (Eq. 3), the Philox
-// uniform, the hard draw and the in-place state update e_i = t.
+// One launch per day (Sec. 3.1, Eq. 1-3; A1: one-day steps).  Warps take
+// 32-row tiles from a per-launch counter.  The susceptible rows of a tile are
+// summed by warp_row_sums over the destination-sorted CSR (a pull gather, no
+// atomics): w_ji * c[t - e_j] with the neighbours' exposure days gathered from
+// the L2-resident state.  Each lane then runs the fused epilogue for its own
+// row: lambda, p = 1 - exp(-lambda) (Eq. 3), the Philox uniform, the hard draw
+// and the in-place state update e_i = t.
 //
 // The in-place update is race-free in effect: a neighbour that reads e_i
 // during the same day sees either NEVER or t, and both give c = 0 (c[0] = 0 by
@@ -38,24 +36,24 @@ __device__ __forceinline__ void flush_counts_warp(int32_t *counts, int32_t *newR
     }
 }
 
-template <int GL>
-__global__ void __launch_bounds__(kBlock) k_fwd_day(const FwdDayArgs a) {
+__global__ void __launch_bounds__(kBlock, 3) k_fwd_day(const FwdDayArgs a) {
     __shared__ float c_s[kMaxL];
-    __shared__ uint8_t slot_s[kBlock / 32][32];
+    __shared__ WarpStage<1> stage_s[kBlock / 32];
     __shared__ int32_t red_s[kBlock / 32][6];
     if (threadIdx.x < kMaxL) c_s[threadIdx.x] = a.c[threadIdx.x];
     __syncthreads();
 
-    constexpr int RPP = 32 / GL;  // rows per pass of the warp
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const unsigned lt_mask = (1u << lane) - 1u;
-    const int sub = lane / GL, gl = lane % GL;
     const int t = a.t, L = a.L, tau_EI = a.tau_EI;
-    const int nwarps = gridDim.x * (kBlock / 32);
+    WarpStage<1> &ws = stage_s[wib];
+    const int16_t *e = a.e;
+    auto contrib = [&](uint32_t, uint32_t j, float w, float (&out)[1]) {
+        out[0] = w * infectiousness(e[j], c_s, t, L);
+    };
 
     int cur_g = -1;
     int cS = 0, cE = 0, cI = 0, cR = 0, cN = 0;
-    for (int tile = blockIdx.x * (kBlock / 32) + wib; tile < a.ntiles; tile += nwarps) {
+    for (int tile = next_tile(a.tile_ctr, lane); tile < a.ntiles; tile = next_tile(a.tile_ctr, lane)) {
         const int g = a.gr.tile_graph ? (int)a.gr.tile_graph[tile] : 0;
         if (g != cur_g) {
             if (cur_g >= 0) flush_counts_warp(a.counts, a.newRM, a.ldP, cur_g, t, cS, cE, cI, cR, cN, lane);
@@ -71,37 +69,17 @@ __global__ void __launch_bounds__(kBlock) k_fwd_day(const FwdDayArgs a) {
             cN += (k == L);
         }
         cS += isS;
-        const unsigned smask = __ballot_sync(0xffffffffu, isS);
-        if (smask == 0u) continue;
-
-        uint32_t rs = 0, re = 0;
-        if (isS) { rs = a.rowptr[row]; re = a.rowptr[row + 1]; }
-        const int rank = __popc(smask & lt_mask);
-        if (isS) slot_s[wib][rank] = (uint8_t)lane;
-        __syncwarp();
-        const int nS = __popc(smask);
-        float acc = 0.f;
-        for (int base = 0; base < nS; base += RPP) {
-            const int j = base + sub;
-            const int src = (j < nS) ? slot_s[wib][j] : 0;
-            const uint32_t rsj = __shfl_sync(0xffffffffu, rs, src);
-            const uint32_t rej = __shfl_sync(0xffffffffu, re, src);
-            float part = 0.f;
-            if (j < nS) part = lane_infectious_sum<GL>(a.col4, a.w4, a.e, c_s, rsj, rej, gl, t, L);
-#pragma unroll
-            for (int o = GL / 2; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-            const int myj = rank - base;
-            const float got = __shfl_sync(0xffffffffu, part, (myj & (RPP - 1)) * GL);
-            if (isS && myj >= 0 && myj < RPP) acc = got;
-        }
-        __syncwarp();
+        if (__ballot_sync(0xffffffffu, isS) == 0u) continue;
+        const uint32_t rs = a.rowptr[row], re = a.rowptr[row + 1];
+        float sum[1];
+        warp_row_sums<1>(ws, a.col4, a.w4, isS, rs, re, 0u, lane, contrib, sum);
 
         if (isS) {
-            const float Lam = acc * a.gr.inv_Dbar[g];
+            const float Lam = sum[0] * a.gr.inv_Dbar[g];
             const int inst = g;
             const float lam = (a.R[(size_t)inst * a.ldP + t] * a.S[inst * kAges + a.age[row]]) * Lam;
             const float p = -expm1f(-lam);
-            const uint32_t id = (uint32_t)(row - a.gr.row0[g]);
+            const uint32_t id = caller_id(a.gr, row, g);
             const float u = uniform_from_word(philox_word(a.seed, id, (uint32_t)t, (uint32_t)inst, 0u));
             if (u < p) a.e[row] = (int16_t)t;
             if (a.lam_out) a.lam_out[row] = Lam;
@@ -190,10 +168,10 @@ __global__ void __launch_bounds__(256) k_seed_hist(const SeedArgs a) {
     const int g = inst;
     const int32_t r0 = a.row0[g], nr = a.rows[g];
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nr; i += gridDim.x * blockDim.x) {
-        const uint32_t h = philox_word(a.seed, (uint32_t)i, 0u, (uint32_t)inst, 1u);
+        const uint32_t id = a.orig_id ? a.orig_id[r0 + i] : (uint32_t)i;
+        const uint32_t h = philox_word(a.seed, id, 0u, (uint32_t)inst, 1u);
         if ((h & himask) == st.prefix) atomicAdd(&h_s[(h >> shift) & (nbins - 1)], 1u);
     }
-    (void)r0;
     __syncthreads();
     uint32_t *gh = a.hist + (size_t)inst * kHistBins;
     for (int b = threadIdx.x; b < nbins; b += blockDim.x)
@@ -251,7 +229,8 @@ __global__ void k_seed_mark(const SeedArgs a) {
     const int g = inst;
     const int32_t r0 = a.row0[g], nr = a.rows[g];
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nr; i += gridDim.x * blockDim.x) {
-        const uint32_t h = philox_word(a.seed, (uint32_t)i, 0u, (uint32_t)inst, 1u);
+        const uint32_t id = a.orig_id ? a.orig_id[r0 + i] : (uint32_t)i;
+        const uint32_t h = philox_word(a.seed, id, 0u, (uint32_t)inst, 1u);
         bool mark = h < st.prefix;
         if (h == st.prefix) {
             if (st.eq_count == st.k_rem) {
@@ -266,7 +245,8 @@ __global__ void k_seed_mark(const SeedArgs a) {
     }
 }
 
-// Ties on the threshold word: the k_rem candidates with the smallest ids win.
+// Ties on the threshold word: the k_rem candidates with the smallest caller ids win.
+// The tie list holds local row indices.
 __global__ void k_seed_ties(const SeedArgs a) {
     const int inst = blockIdx.x;
     const SeedState st = a.st[inst];
@@ -275,10 +255,44 @@ __global__ void k_seed_ties(const SeedArgs a) {
     const uint32_t *tl = a.ties + (size_t)inst * kTieCap;
     const int32_t r0 = a.row0[inst];
     for (uint32_t c = threadIdx.x; c < n; c += blockDim.x) {
-        const uint32_t id = tl[c];
+        const uint32_t i = tl[c];
+        const uint32_t id = a.orig_id ? a.orig_id[r0 + i] : i;
         uint32_t rank = 0;
-        for (uint32_t d = 0; d < n; ++d) rank += (tl[d] < id);
-        if (rank < st.k_rem) a.e[r0 + id] = (int16_t)(-a.tau_EI);
+        for (uint32_t d = 0; d < n; ++d) {
+            const uint32_t idd = a.orig_id ? a.orig_id[r0 + tl[d]] : tl[d];
+            rank += (idd < id);
+        }
+        if (rank < st.k_rem) a.e[r0 + i] = (int16_t)(-a.tau_EI);
+    }
+}
+
+// Row order <-> caller order.
+__device__ __forceinline__ bool caller_slot(const GraphRef &gr, const int32_t *rows, const int64_t *goff,
+                                            int64_t r, int64_t &slot) {
+    const int g = gr.tile_graph ? (int)gr.tile_graph[r / kTile] : 0;
+    const int64_t i = r - gr.row0[g];
+    if (i >= rows[g]) return false;
+    slot = goff[g] + (int64_t)(gr.orig_id ? gr.orig_id[r] : (uint32_t)i);
+    return true;
+}
+
+template <typename T>
+__global__ void k_rows_to_caller(const T *src, T *dst, GraphRef gr, const int32_t *rows, const int64_t *goff,
+                                 int64_t n_rows) {
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n_rows;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        int64_t slot;
+        if (caller_slot(gr, rows, goff, r, slot)) dst[slot] = src[r];
+    }
+}
+
+template <typename T>
+__global__ void k_caller_to_rows(const T *src, T *dst, GraphRef gr, const int32_t *rows, const int64_t *goff,
+                                 int64_t n_rows) {
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n_rows;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        int64_t slot;
+        if (caller_slot(gr, rows, goff, r, slot)) dst[r] = src[slot];
     }
 }
 
@@ -378,26 +392,14 @@ cudaError_t launch_seed_ties(const SeedArgs &a, int I, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_fwd_day(const FwdDayArgs &a, int lanes_per_row, int grid, cudaStream_t s) {
-    switch (lanes_per_row) {
-        case 4: k_fwd_day<4><<<grid, kBlock, 0, s>>>(a); break;
-        case 8: k_fwd_day<8><<<grid, kBlock, 0, s>>>(a); break;
-        case 16: k_fwd_day<16><<<grid, kBlock, 0, s>>>(a); break;
-        case 32: k_fwd_day<32><<<grid, kBlock, 0, s>>>(a); break;
-        default: return cudaErrorInvalidValue;
-    }
+cudaError_t launch_fwd_day(const FwdDayArgs &a, int grid, cudaStream_t s) {
+    k_fwd_day<<<grid, kBlock, 0, s>>>(a);
     return cudaGetLastError();
 }
 
-int occupancy_fwd(int lanes_per_row) {
+int occupancy_fwd() {
     int blocks = 0;
-    switch (lanes_per_row) {
-        case 4: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_fwd_day<4>, kBlock, 0); break;
-        case 8: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_fwd_day<8>, kBlock, 0); break;
-        case 16: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_fwd_day<16>, kBlock, 0); break;
-        case 32: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_fwd_day<32>, kBlock, 0); break;
-        default: break;
-    }
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_fwd_day, kBlock, 0);
     return blocks > 0 ? blocks : 1;
 }
 
@@ -422,6 +424,30 @@ cudaError_t launch_get_lambda(const float *lam_t, const int16_t *e, const uint8_
     int grid = (int)((n_rows + 255) / 256);
     if (grid > 65535) grid = 65535;
     k_get_lambda<<<grid > 0 ? grid : 1, 256, 0, s>>>(lam_t, e, age, gr, R, S, ldP, t, n_rows, out_rows);
+    return cudaGetLastError();
+}
+
+static int grid_for(int64_t n) {
+    int64_t g = (n + 255) / 256;
+    if (g > 65535) g = 65535;
+    return (int)(g > 0 ? g : 1);
+}
+
+cudaError_t launch_rows_to_caller_i16(const int16_t *src, int16_t *dst, GraphRef gr, const int32_t *rows,
+                                      const int64_t *goff, int64_t n_rows, cudaStream_t s) {
+    k_rows_to_caller<int16_t><<<grid_for(n_rows), 256, 0, s>>>(src, dst, gr, rows, goff, n_rows);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rows_to_caller_f32(const float *src, float *dst, GraphRef gr, const int32_t *rows,
+                                      const int64_t *goff, int64_t n_rows, cudaStream_t s) {
+    k_rows_to_caller<float><<<grid_for(n_rows), 256, 0, s>>>(src, dst, gr, rows, goff, n_rows);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_caller_to_rows_i16(const int16_t *src, int16_t *dst, GraphRef gr, const int32_t *rows,
+                                      const int64_t *goff, int64_t n_rows, cudaStream_t s) {
+    k_caller_to_rows<int16_t><<<grid_for(n_rows), 256, 0, s>>>(src, dst, gr, rows, goff, n_rows);
     return cudaGetLastError();
 }
 

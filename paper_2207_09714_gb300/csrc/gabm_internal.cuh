@@ -83,7 +83,12 @@ struct GraphRef {                 // where each graph sits in the concatenated a
     const int32_t *row0;          // [G] first row of each graph
     const uint16_t *tile_graph;   // [ntiles] graph of each tile (nullptr when G == 1)
     const float *inv_Dbar;        // [G] 1 / mean weighted degree (0 for an edgeless graph)
+    const uint32_t *orig_id;      // [n_rows] caller's id of each row (nullptr: row - row0)
 };
+
+__device__ __forceinline__ uint32_t caller_id(const GraphRef &gr, int row, int g) {
+    return gr.orig_id ? gr.orig_id[row] : (uint32_t)(row - gr.row0[g]);
+}
 
 struct FwdDayArgs {
     const uint32_t *rowptr;
@@ -98,6 +103,7 @@ struct FwdDayArgs {
     int ldP;              // per-instance stride of R (and m)
     int32_t *counts;      // [I][ldP][4]
     int32_t *newRM;       // [I][ldP]
+    int *tile_ctr;        // tile counter of this launch (zero before the launch)
     int ntiles, t, tau_EI, L;
     uint64_t seed;
     float c[kMaxL];
@@ -126,6 +132,7 @@ struct BwdDayArgs {
     int ldP;
     double *P_t;               // [ntiles][9] partial sums of gl * Lam for day t
     int32_t *newRM;            // [I][ldP]
+    int *tile_ctr;             // tile counter of this launch (zero before the launch)
     int ntiles, t, T, tau_EI, L;
     int mode;                  // kBwdStore, kBwdFused or kBwdSplit
     uint64_t seed;
@@ -147,6 +154,7 @@ struct SeedState {
 struct SeedArgs {
     const int32_t *row0;  // [G]
     const int32_t *rows;  // [G] real rows per graph
+    const uint32_t *orig_id;  // [n_rows] or nullptr
     int16_t *e;
     SeedState *st;        // [I]
     uint32_t *hist;       // [I][kHistBins]
@@ -164,13 +172,13 @@ cudaError_t launch_seed_hist(const SeedArgs &a, int G, int grid_x, cudaStream_t 
 cudaError_t launch_seed_scan(const SeedArgs &a, int I, cudaStream_t s);
 cudaError_t launch_seed_mark(const SeedArgs &a, int G, int grid_x, cudaStream_t s);
 cudaError_t launch_seed_ties(const SeedArgs &a, int I, cudaStream_t s);
-cudaError_t launch_fwd_day(const FwdDayArgs &a, int lanes_per_row, int grid, cudaStream_t s);
+cudaError_t launch_fwd_day(const FwdDayArgs &a, int grid, cudaStream_t s);
 cudaError_t launch_fwd_finalize(const int32_t *newRM, const int32_t *counts, const float *m, int ldP,
                                 int t0, int T, int I, double *D_ctx, double *D_out,
                                 int32_t *counts_out, cudaStream_t s);
 cudaError_t launch_mse(const double *D, int ldP, const double *y, int T, int I, double *loss,
                        double *gD_ctx, double *gD_out, cudaStream_t s);
-cudaError_t launch_bwd_day(const BwdDayArgs &a, int lanes_per_row, int grid, cudaStream_t s);
+cudaError_t launch_bwd_day(const BwdDayArgs &a, int grid, cudaStream_t s);
 cudaError_t launch_bwd_reduce(const double *P, int ntiles, int ldP, const int32_t *graph_tile0,
                               const int32_t *graph_ntiles, int T, int I, double *Q,
                               cudaStream_t s);
@@ -182,7 +190,14 @@ cudaError_t launch_get_lambda(const float *lam_t, const int16_t *e, const uint8_
                               int64_t n_rows, float *out_rows, cudaStream_t s);
 cudaError_t launch_philox(uint64_t seed, const uint32_t *ctr, uint32_t *out, int64_t count,
                           cudaStream_t s);
-int occupancy_fwd(int lanes_per_row);
-int occupancy_bwd(int lanes_per_row, int mode);
+// Row order <-> caller order (graphs concatenated, caller ids within each graph).
+cudaError_t launch_rows_to_caller_i16(const int16_t *src, int16_t *dst, GraphRef gr, const int32_t *rows,
+                                      const int64_t *goff, int64_t n_rows, cudaStream_t s);
+cudaError_t launch_rows_to_caller_f32(const float *src, float *dst, GraphRef gr, const int32_t *rows,
+                                      const int64_t *goff, int64_t n_rows, cudaStream_t s);
+cudaError_t launch_caller_to_rows_i16(const int16_t *src, int16_t *dst, GraphRef gr, const int32_t *rows,
+                                      const int64_t *goff, int64_t n_rows, cudaStream_t s);
+int occupancy_fwd();
+int occupancy_bwd(int mode);
 
 }  // namespace gabm

@@ -13,6 +13,9 @@ NEVER = capi.GABM_NEVER
 LAM_RTOL = 1e-5
 FLIP_MARGIN = 1e-6
 FLIP_FRACTION = 1e-5
+# an oracle run whose every draw has |u - p| above this is reproduced exactly by the GPU
+# (fp32 lambda error ~1e-6 relative moves p by far less)
+EXACT_MARGIN = 1e-6
 # adjoint bar: |gpu - oracle| <= ADJ_RTOL * max(|oracle|, ADJ_FLOOR * max|oracle|) elementwise
 ADJ_RTOL = 1e-3
 ADJ_FLOOR = 1e-3
@@ -35,11 +38,11 @@ def torch_cuda():
     return torch
 
 
-def model(c=None, tau_EI=4, tau_IR=7, seed=0, policy=capi.GABM_STORE_LAMBDA):
+def model(c=None, tau_EI=4, tau_IR=7, seed=0, policy=capi.GABM_STORE_LAMBDA, order=capi.GABM_ORDER_BFS):
     if c is None:
         c = synth.infectiousness_table(tau_EI, tau_IR)
     return capi.ModelDesc(tau_EI=tau_EI, tau_IR=tau_IR, c=np.asarray(c, np.float32), seed=seed,
-                          lambda_policy=policy)
+                          lambda_policy=policy, agent_order=order)
 
 
 def to_dev(*arrays):
