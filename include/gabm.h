@@ -189,6 +189,40 @@ void gabm_destroy(gabm_ctx *ctx);
 /* Library version string. */
 const char *gabm_version(void);
 
+/* ---------------------------------------------------------------------------
+ * Allocation-free entry point.  The paper has no counterpart: this exists for
+ * callers that cannot let a library allocate device memory -- code running
+ * under a fixed device-memory budget, inside another framework's memory pool,
+ * or in a host that hands over only the buffers to be filled.
+ *
+ * gabm_seed_state_noalloc writes the day-0 state that gabm_forward starts
+ * from, for num_instances instances of one n-agent population:
+ * e_out [num_instances][n] (int16, device memory owned by the caller) gets
+ * GABM_NEVER everywhere except, in each instance i, the n_seed[i] agents with
+ * the smallest Philox key at (agent id, 0, i, 1), which get -tau_EI.
+ * n_seed is host memory.  All work is enqueued on cuda_stream (a
+ * cudaStream_t, NULL = legacy default stream); the call does not wait for it.
+ *
+ * Its scratch (selection state, digit histograms, tie lists; about 25 KB per
+ * instance) is one fixed array of device memory inside the library, sized for
+ * GABM_NOALLOC_MAX_INSTANCES instances, which every device that loads the
+ * library keeps until the process exits.  The call performs no device
+ * allocation or release.  Limits: 1 <= num_instances <=
+ * GABM_NOALLOC_MAX_INSTANCES, n >= 1 and n * num_instances < 2^31; anything
+ * else returns GABM_EINVAL with a message in gabm_noalloc_last_error().
+ * The first call on a device looks up the array's device address (once per
+ * device), so make that first call before any stream capture.  All calls
+ * share the array: calls whose GPU work overlaps (different streams without
+ * ordering) race on it and must not be issued.
+ */
+#define GABM_NOALLOC_MAX_INSTANCES 16
+
+gabm_status gabm_seed_state_noalloc(uint64_t seed, int64_t n, int num_instances, const int32_t *n_seed,
+                                    int tau_EI, int16_t *e_out, void *cuda_stream);
+
+/* Message for the last failing gabm_seed_state_noalloc call of this thread. */
+const char *gabm_noalloc_last_error(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -85,6 +85,9 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         L.gabm_destroy.argtypes = [P]
         L.gabm_destroy.restype = None
         L.gabm_version.restype = ctypes.c_char_p
+        L.gabm_seed_state_noalloc.argtypes = [u64, i64, i32, P, i32, P, P]
+        L.gabm_seed_state_noalloc.restype = ctypes.c_int
+        L.gabm_noalloc_last_error.restype = ctypes.c_char_p
         for name in ("gabm_create", "gabm_forward", "gabm_mse_loss", "gabm_backward", "gabm_get_state",
                      "gabm_set_state", "gabm_get_lambda", "gabm_mem_stats", "gabm_set_profiling",
                      "gabm_get_profile", "gabm_philox"):
@@ -359,3 +362,19 @@ def gabm_philox(seed: int, ctr, out=None, stream=None):
 
 def gabm_destroy(ctx: GabmCtx):
     ctx.close()
+
+
+def gabm_seed_state_noalloc(seed: int, n: int, n_seed, tau_EI: int, e_out, stream=None):
+    """Day-0 state of len(n_seed) instances into e_out [instances, n] (int16 CUDA tensor the
+    caller allocated).  The library allocates nothing for this call."""
+    import torch
+    seeds = np.ascontiguousarray(np.asarray(n_seed, dtype=np.int32).reshape(-1))
+    if not _is_cuda(e_out):
+        raise ValueError("e_out must be a CUDA tensor")
+    _shape(e_out, (seeds.size, int(n)), "e_out")
+    s = ctypes.c_void_p((stream or torch.cuda.current_stream()).cuda_stream)
+    st = load_library().gabm_seed_state_noalloc(int(seed), int(n), int(seeds.size), _ptr(seeds, np.int32),
+                                                int(tau_EI), _ptr(e_out, np.int16), s)
+    if st != GABM_OK:
+        raise GabmError(st, load_library().gabm_noalloc_last_error().decode(errors="replace"))
+    return e_out
