@@ -11,9 +11,12 @@
 //       dL/dy = G (t = E_i or never infected) or G - A_i (t < E_i), A_i = G_i(E_i),
 //       gl = dL/dy * dy_soft/dlambda (Gumbel-softmax, tau = 1, straight-through),
 //       r_i(t) = R_t S[a_i] gl / Dbar and per-tile, per-age sums of gl * Lam.
-// lambda_i(t) comes from the forward's store or is recomputed in the same pass
-// from the final exposure days E (no reinfection, A3/A4 of App. A, so E
-// determines every day's state and no checkpoints are needed).
+// lambda_i(t) comes from the forward's store or is recomputed from the final
+// exposure days E (no reinfection, A3/A4 of App. A, so E determines every
+// day's state and no checkpoints are needed): in the same pass when in- and
+// out-edges coincide, else by k_lam_day over the in-edges first.  Each warp
+// prefetches the next tile's id, row data and (into L2) its edge range while
+// it works on the current tile.
 #include "gabm_internal.cuh"
 #include "rowsum.cuh"
 
@@ -22,11 +25,10 @@ namespace gabm {
 namespace {
 
 template <int MODE>
-__global__ void __launch_bounds__(kBlock, (MODE == kBwdFused) ? 2 : 3) k_bwd_day(const BwdDayArgs a) {
+__global__ void __launch_bounds__(kBlock, 3) k_bwd_day(const BwdDayArgs a) {
     constexpr int NARR = (MODE == kBwdFused) ? 2 : 1;
     __shared__ float c_s[kMaxL];
     __shared__ int slot_k[kMaxL];
-    __shared__ WarpStage<NARR> stage_s[kBlock / 32];
     __shared__ int32_t red_s[kBlock / 32][2];
     if (threadIdx.x < kMaxL) {
         c_s[threadIdx.x] = a.c[threadIdx.x];
@@ -35,35 +37,42 @@ __global__ void __launch_bounds__(kBlock, (MODE == kBwdFused) ? 2 : 3) k_bwd_day
     __syncthreads();
 
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int t = a.t, T = a.T, L = a.L;
+    const int t = a.t, T = a.T, L = a.L, ntiles = a.ntiles;
     const bool has_next = (t + 1 < T);
-    WarpStage<NARR> &ws = stage_s[wib];
     const int16_t *E = a.E;
-    const float *r_next = a.r_next;
-    // flags: bit 0 = this row needs gx(t+1), bit 1 = this row needs its lambda recomputed
-    auto contrib_adj = [&](uint32_t fl, uint32_t j, float w, float (&out)[NARR]) {
-        if (fl & 1u) out[0] = w * r_next[j];
-        if constexpr (NARR == 2) {
-            if (fl & 2u) out[1] = w * infectiousness(E[j], c_s, t, L);
-        }
-    };
-    auto contrib_lam = [&](uint32_t, uint32_t j, float w, float (&out)[1]) {
-        out[0] = w * infectiousness(E[j], c_s, t, L);
+    const float *__restrict__ r_next = a.r_next;
+    const uint32_t *bits = a.bits_t;
+    // contribution 0: w * r_j(t+1) (transpose gather); contribution 1 (recompute):
+    // w * c[t - E_j] for neighbours marked infectious on day t
+    auto contrib = [&](uint32_t j, float w, float (&out)[NARR]) {
+        out[0] = w * r_next[j];
+        if constexpr (NARR == 2) out[1] = marked(bits, j) ? w * infectiousness(E[j], c_s, t, L) : 0.f;
     };
 
     int cur_g = -1, cN = 0;
-    for (int tile = next_tile(a.tile_ctr, lane); tile < a.ntiles; tile = next_tile(a.tile_ctr, lane)) {
-        const int g = a.gr.tile_graph ? (int)a.gr.tile_graph[tile] : 0;
+    TileRows cur, nxt;
+    load_tile_rows(a.m, E, a.gr.tile_graph, ntiles, next_tile(a.tile_ctr, lane), lane, cur);
+    int tile_n = next_tile(a.tile_ctr, lane);
+    int raw_nn = (lane == 0) ? atomicAdd(a.tile_ctr, 1) : 0;
+    load_tile_rows(a.m, E, a.gr.tile_graph, ntiles, tile_n, lane, nxt);
+    prefetch_slice(a.m, cur.p0, cur.p1, lane);
+    while (cur.tile < ntiles) {
+        prefetch_slice(a.m, nxt.p0, nxt.p1, lane);
+        const int tile_nn = __shfl_sync(0xffffffffu, raw_nn, 0);
+        TileRows nn;
+        load_tile_rows(a.m, E, a.gr.tile_graph, ntiles, tile_nn, lane, nn);
+        if (lane == 0 && tile_nn < ntiles) raw_nn = atomicAdd(a.tile_ctr, 1);
+
+        const int g = cur.g, tile = cur.tile, Ei = cur.e;
         if (g != cur_g) {
             if (cur_g >= 0) {
-                const int s = __reduce_add_sync(0xffffffffu, cN);
-                if (lane == 0 && s) atomicAdd(a.newRM + (size_t)cur_g * a.ldP + t, s);
+                const int sN = __reduce_add_sync(0xffffffffu, cN);
+                if (lane == 0 && sN) atomicAdd(a.newRM + (size_t)cur_g * a.ldP + t, sN);
             }
             cur_g = g;
             cN = 0;
         }
         const int row = tile * kTile + lane;
-        const int Ei = a.E[row];
         const bool agent = (Ei != kPad);
         const bool never = (Ei == kNever);
         const bool live = agent && (never || Ei >= 0);           // seeds are constants
@@ -71,22 +80,15 @@ __global__ void __launch_bounds__(kBlock, (MODE == kBwdFused) ? 2 : 3) k_bwd_day
         const bool needA = has_next && live && (never || Ei >= t + 2 - L);
         cN += (agent && !never && t - Ei == L);
 
-        float gx_mine = 0.f, lam_mine = 0.f;
+        float sum[NARR];
         {
             const bool act = (MODE == kBwdFused) ? (needA || isS) : needA;
-            const uint32_t rs = a.rowptr[row], re = a.rowptr[row + 1];
-            const uint32_t fl = (needA ? 1u : 0u) | ((MODE == kBwdFused && isS) ? 2u : 0u);
-            float sum[NARR];
-            warp_row_sums<NARR>(ws, a.col4, a.w4, act, rs, re, fl, lane, contrib_adj, sum);
-            gx_mine = sum[0];
-            if constexpr (MODE == kBwdFused) lam_mine = sum[NARR - 1];
+            bool want[NARR];
+            want[0] = needA;
+            if constexpr (NARR == 2) want[1] = isS;
+            row_sums<NARR>(a.m, cur.p0, cur.len, act, lane, contrib, want, sum);
         }
-        if constexpr (MODE == kBwdSplit) {
-            const uint32_t rs = a.in_rowptr[row], re = a.in_rowptr[row + 1];
-            float sum[1];
-            warp_row_sums<1>(ws, a.in_col4, a.in_w4, isS, rs, re, 0u, lane, contrib_lam, sum);
-            lam_mine = sum[0];
-        }
+        const float gx_mine = sum[0];
 
         if (needA) a.ring[(size_t)slot_k[1] * a.ring_stride + row] = gx_mine;
 
@@ -97,7 +99,7 @@ __global__ void __launch_bounds__(kBlock, (MODE == kBwdFused) ? 2 : 3) k_bwd_day
             const int inst = g;
             const size_t pi = (size_t)inst * a.ldP;
             float G = 0.f;
-            if (t + L < T) G = a.m[pi + t + L] * (float)a.gD[pi + t + L];
+            if (t + L < T) G = a.m_t[pi + t + L] * (float)a.gD[pi + t + L];
             if (has_next) G = __fmaf_rn(c_s[1], gx_mine, G);
             for (int k = 2; k < L; ++k)
                 if (t + k < T) G = __fmaf_rn(c_s[k], a.ring[(size_t)slot_k[k] * a.ring_stride + row], G);
@@ -105,7 +107,9 @@ __global__ void __launch_bounds__(kBlock, (MODE == kBwdFused) ? 2 : 3) k_bwd_day
             if (Ei == t) { a.A[row] = G; dy = G; }
             else if (never) dy = G;
             else dy = G - a.A[row];
-            const float Lam = (MODE == kBwdStore) ? a.lam_t[row] : lam_mine * a.gr.inv_Dbar[g];
+            float Lam;
+            if constexpr (MODE == kBwdFused) Lam = sum[NARR - 1] * a.gr.inv_Dbar[g];
+            else Lam = a.lam_t[row];
             const float RS = a.R[pi + t] * a.S[inst * kAges + ai];
             const float lam = RS * Lam;
             const float q = expf(-lam);
@@ -136,10 +140,13 @@ __global__ void __launch_bounds__(kBlock, (MODE == kBwdFused) ? 2 : 3) k_bwd_day
             outv = (double)mine;
         }
         if (lane < kAges) a.P_t[(size_t)tile * kAges + lane] = outv;
+
+        cur = nxt;
+        nxt = nn;
     }
 
-    const int s = __reduce_add_sync(0xffffffffu, cN);
-    if (lane == 0) { red_s[wib][0] = cur_g; red_s[wib][1] = s; }
+    const int sN = __reduce_add_sync(0xffffffffu, cN);
+    if (lane == 0) { red_s[wib][0] = cur_g; red_s[wib][1] = sN; }
     __syncthreads();
     if (threadIdx.x == 0) {
         int g = -1;
@@ -152,6 +159,33 @@ __global__ void __launch_bounds__(kBlock, (MODE == kBwdFused) ? 2 : 3) k_bwd_day
                 acc = 0;
             }
             if (w < kBlock / 32 && gw >= 0) acc += red_s[w][1];
+        }
+    }
+}
+
+// Normalised neighbour sums Lam_i(t) over the in-edges, recomputed from the final
+// exposure days (used when the in- and out-edges differ, ahead of the backward day
+// kernel of day t); the same per-row summation as the forward.
+__global__ void __launch_bounds__(kBlock) k_lam_day(Sell m, const int16_t *E, const uint32_t *bits, GraphRef gr,
+                                                    int t, int L, int ntiles, const float *c, float *lam_out) {
+    __shared__ float c_s[kMaxL];
+    if (threadIdx.x < kMaxL) c_s[threadIdx.x] = c[threadIdx.x];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int nwarps = gridDim.x * (kBlock / 32);
+    auto contrib = [&](uint32_t j, float w, float (&out)[1]) {
+        out[0] = marked(bits, j) ? w * infectiousness(E[j], c_s, t, L) : 0.f;
+    };
+    const bool want[1] = {true};
+    for (int tile = blockIdx.x * (kBlock / 32) + wib; tile < ntiles; tile += nwarps) {
+        const int row = tile * kTile + lane;
+        const int Ei = E[row];
+        const bool act = (Ei != kPad) && (Ei == kNever || Ei >= t);
+        float sum[1];
+        row_sums<1>(m, m.slice_ptr[tile], m.row_len[row], act, lane, contrib, want, sum);
+        if (act) {
+            const int g = gr.tile_graph ? (int)gr.tile_graph[tile] : 0;
+            lam_out[row] = sum[0] * gr.inv_Dbar[g];
         }
     }
 }
@@ -209,18 +243,22 @@ cudaError_t launch_bwd_day(const BwdDayArgs &a, int grid, cudaStream_t s) {
     switch (a.mode) {
         case kBwdStore: k_bwd_day<kBwdStore><<<grid, kBlock, 0, s>>>(a); break;
         case kBwdFused: k_bwd_day<kBwdFused><<<grid, kBlock, 0, s>>>(a); break;
-        case kBwdSplit: k_bwd_day<kBwdSplit><<<grid, kBlock, 0, s>>>(a); break;
         default: return cudaErrorInvalidValue;
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lam_day(Sell m, const int16_t *E, const uint32_t *bits, GraphRef gr, int t, int L, int ntiles,
+                           const float *c, float *lam_out, int grid, cudaStream_t s) {
+    k_lam_day<<<grid, kBlock, 0, s>>>(m, E, bits, gr, t, L, ntiles, c, lam_out);
     return cudaGetLastError();
 }
 
 int occupancy_bwd(int mode) {
     int blocks = 0;
     switch (mode) {
-        case kBwdStore: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_bwd_day<kBwdStore>, kBlock, 0); break;
         case kBwdFused: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_bwd_day<kBwdFused>, kBlock, 0); break;
-        default: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_bwd_day<kBwdSplit>, kBlock, 0); break;
+        default: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_bwd_day<kBwdStore>, kBlock, 0); break;
     }
     return blocks > 0 ? blocks : 1;
 }

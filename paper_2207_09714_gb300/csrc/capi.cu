@@ -39,11 +39,14 @@ struct gabm_ctx {
     std::vector<double> h_Dbar;
     bool symmetric = false;
 
-    uint32_t *rowptr = nullptr, *col = nullptr;
-    float *w = nullptr;
+    // SELL-32 edges: in-edges, and out-edges when the weights are not symmetric
+    uint32_t *slice_ptr = nullptr, *row_len = nullptr, *scol = nullptr;
+    float *sw = nullptr;
+    uint32_t *t_slice_ptr = nullptr, *t_row_len = nullptr, *t_scol = nullptr;
+    float *t_sw = nullptr;
+    int64_t sell_entries = 0;
+    int sigma = 128;
     uint8_t *age = nullptr;
-    uint32_t *t_rowptr = nullptr, *t_col = nullptr;
-    float *t_w = nullptr;
     int32_t *d_row0 = nullptr, *d_rows = nullptr, *d_tile0 = nullptr, *d_ntiles = nullptr;
     int64_t *d_goff = nullptr;      // [G] caller offset of each graph
     uint32_t *d_orig_id = nullptr;  // [n_rows] caller id of each row (nullptr: input order)
@@ -63,6 +66,8 @@ struct gabm_ctx {
     int32_t *d_nseed = nullptr;
 
     float *ring = nullptr, *A = nullptr, *r = nullptr, *rows_f = nullptr, *stage_f = nullptr;
+    float *lam_tmp = nullptr;       // [n_rows] recomputed lambda of one day (in- != out-edges)
+    float *c_dev = nullptr;         // [kMaxL] infectiousness table
     int16_t *rows_e = nullptr;
 
     int t0_next = 0;
@@ -72,6 +77,7 @@ struct gabm_ctx {
 
     int grid_fwd = 0, grid_bwd = 0;
     int *tile_ctr = nullptr;        // [2][Tcap] per-launch tile counters (forward, backward)
+    uint32_t *bits = nullptr;       // [Tcap][ntiles] per-day bitmaps of infectious rows
 
     size_t mem_cur = 0, mem_peak = 0;
     std::unordered_map<void *, size_t> sizes;
@@ -267,6 +273,59 @@ std::vector<uint32_t> bfs_order(const HostGraph &h) {
     return order;
 }
 
+// Within consecutive windows of `sigma` positions of an order, sort the agents by
+// decreasing degree (stable), so that each 32-row slice holds rows of similar
+// length: little padding in the SELL-32 layout, while agents stay near their
+// breadth-first neighbourhood.
+void sort_windows_by_degree(const HostGraph &h, std::vector<uint32_t> &order, int sigma) {
+    if (sigma <= 1) return;
+    for (size_t w0 = 0; w0 < order.size(); w0 += (size_t)sigma) {
+        const size_t w1 = std::min(order.size(), w0 + (size_t)sigma);
+        std::stable_sort(order.begin() + w0, order.begin() + w1, [&](uint32_t a, uint32_t b) {
+            return (h.rowptr[a + 1] - h.rowptr[a]) > (h.rowptr[b + 1] - h.rowptr[b]);
+        });
+    }
+}
+
+// SELL-32 of a device-order CSR: slice s = rows [32 s, 32 s + 32), max_len(s) x 32
+// entries, entry k of the row in lane l at slice_ptr[s] + 32 k + l; padding has
+// column 0 and weight 0 and is never read.
+struct HostSell {
+    std::vector<uint32_t> slice_ptr, row_len, col;
+    std::vector<float> w;
+};
+
+bool build_sell(const std::vector<uint32_t> &rowptr, const std::vector<uint32_t> &col, const std::vector<float> &w,
+                int64_t n_rows, HostSell &hs) {
+    const int64_t ns = n_rows / kTile;
+    hs.slice_ptr.assign((size_t)ns + 1, 0u);
+    hs.row_len.assign((size_t)n_rows, 0u);
+    uint64_t total = 0;
+    for (int64_t sl = 0; sl < ns; ++sl) {
+        uint32_t mx = 0;
+        for (int l = 0; l < kTile; ++l) {
+            const int64_t r = sl * kTile + l;
+            const uint32_t len = rowptr[r + 1] - rowptr[r];
+            hs.row_len[r] = len;
+            mx = std::max(mx, len);
+        }
+        hs.slice_ptr[sl] = (uint32_t)total;
+        total += (uint64_t)mx * kTile;
+        if (total >= ((uint64_t)1 << 32) - 64) return false;
+    }
+    hs.slice_ptr[ns] = (uint32_t)total;
+    hs.col.assign((size_t)std::max<uint64_t>(total, 32), 0u);
+    hs.w.assign((size_t)std::max<uint64_t>(total, 32), 0.f);
+    for (int64_t r = 0; r < n_rows; ++r) {
+        const uint32_t base = hs.slice_ptr[r / kTile] + (uint32_t)(r % kTile);
+        for (uint32_t k = 0; k < hs.row_len[r]; ++k) {
+            hs.col[base + (size_t)k * kTile] = col[rowptr[r] + k];
+            hs.w[base + (size_t)k * kTile] = w[rowptr[r] + k];
+        }
+    }
+    return true;
+}
+
 // Relabel a graph: new row k is old agent order[k]; each row's entries sorted by new column.
 HostGraph permute_graph(const HostGraph &h, const std::vector<uint32_t> &order) {
     HostGraph o;
@@ -309,7 +368,7 @@ gabm_status ensure_days(gabm_ctx *c, int T) {
     dfree(c, c->lam); dfree(c, c->counts); dfree(c, c->newRM); dfree(c, c->newRM_b);
     dfree(c, c->D); dfree(c, c->gD); dfree(c, c->y); dfree(c, c->P); dfree(c, c->Q);
     dfree(c, c->R); dfree(c, c->m);
-    dfree(c, c->dR_s); dfree(c, c->dm_s); dfree(c, c->tile_ctr);
+    dfree(c, c->dR_s); dfree(c, c->dm_s); dfree(c, c->tile_ctr); dfree(c, c->bits);
     c->Tcap = 0;
     const size_t IT = (size_t)c->I * cap;
     if (c->policy == GABM_STORE_LAMBDA) TRY(dalloc(c, &c->lam, (size_t)cap * c->n_rows));
@@ -326,6 +385,7 @@ gabm_status ensure_days(gabm_ctx *c, int T) {
     TRY(dalloc(c, &c->dR_s, IT));
     TRY(dalloc(c, &c->dm_s, IT));
     TRY(dalloc(c, &c->tile_ctr, (size_t)2 * cap));
+    TRY(dalloc(c, &c->bits, (size_t)(cap + 1) * c->ntiles));
     CK(cudaMemsetAsync(c->D, 0, IT * sizeof(double), c->stream));
     c->Tcap = cap;
     c->T_last = -1;
@@ -364,6 +424,15 @@ gabm_status prof_collect(gabm_ctx *c) {
         c->ev_used[k] = 0;
     }
     return GABM_OK;
+}
+
+Sell sell_view(const gabm_ctx *c, bool out_edges) {
+    Sell m;
+    m.slice_ptr = out_edges ? c->t_slice_ptr : c->slice_ptr;
+    m.row_len = out_edges ? c->t_row_len : c->row_len;
+    m.col = out_edges ? c->t_scol : c->scol;
+    m.w = out_edges ? c->t_sw : c->sw;
+    return m;
 }
 
 GraphRef graph_ref(const gabm_ctx *c) {
@@ -431,12 +500,18 @@ gabm_status gabm_create(const gabm_graph_desc *graphs, int num_graphs, int sets_
     }
     // device layout: optionally relabel each graph's agents (D-bar above uses the caller's order)
     std::vector<std::vector<uint32_t>> orders((size_t)num_graphs);
-    const bool reorder = model->agent_order == GABM_ORDER_BFS;
-    if (reorder) {
-        for (int g = 0; g < num_graphs; ++g) {
+    const bool reorder = true;
+    int sigma = 128;
+    if (const char *f = getenv("GABM_SELL_SIGMA")) sigma = std::max(1, atoi(f));
+    for (int g = 0; g < num_graphs; ++g) {
+        if (model->agent_order == GABM_ORDER_BFS) {
             orders[g] = bfs_order(hg[g]);
-            hg[g] = permute_graph(hg[g], orders[g]);
+        } else {
+            orders[g].resize((size_t)hg[g].n);
+            for (int64_t i = 0; i < hg[g].n; ++i) orders[g][i] = (uint32_t)i;
         }
+        sort_windows_by_degree(hg[g], orders[g], sigma);
+        hg[g] = permute_graph(hg[g], orders[g]);
     }
     if (n_rows >= ((int64_t)1 << 31) - 64) return fail(nullptr, GABM_EUNSUPPORTED, "total rows >= 2^31");
     if (nnz >= ((int64_t)1 << 32) - 64) return fail(nullptr, GABM_EUNSUPPORTED, "total nnz >= 2^32");
@@ -484,6 +559,10 @@ gabm_status gabm_create(const gabm_graph_desc *graphs, int num_graphs, int sets_
         symmetric = (h_rowptr == t_rowptr) && (h_col == t_col) &&
                     (memcmp(h_w.data(), t_w.data(), sizeof(float) * h_w.size()) == 0);
     }
+    HostSell sell_in, sell_out;
+    if (!build_sell(h_rowptr, h_col, h_w, n_rows, sell_in) ||
+        (!symmetric && !build_sell(t_rowptr, t_col, t_w, n_rows, sell_out)))
+        return fail(nullptr, GABM_EUNSUPPORTED, "SELL-32 layout needs >= 2^32 entries");
 
     // ---- device side ----
     gabm_ctx *c = new gabm_ctx();
@@ -530,26 +609,32 @@ gabm_status gabm_create(const gabm_graph_desc *graphs, int num_graphs, int sets_
     CCK(cudaGetDevice(&c->device));
     CCK(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device));
 
-    CTRY(dalloc(c, &c->rowptr, (size_t)n_rows + 1));
-    CTRY(dalloc(c, &c->col, (size_t)nnz_pad));
-    CTRY(dalloc(c, &c->w, (size_t)nnz_pad));
-    CTRY(dalloc(c, &c->age, (size_t)n_rows));
-    CCK(cudaMemcpyAsync(c->rowptr, h_rowptr.data(), sizeof(uint32_t) * h_rowptr.size(), cudaMemcpyHostToDevice, c->stream));
-    CCK(cudaMemcpyAsync(c->col, h_col.data(), sizeof(uint32_t) * h_col.size(), cudaMemcpyHostToDevice, c->stream));
-    CCK(cudaMemcpyAsync(c->w, h_w.data(), sizeof(float) * h_w.size(), cudaMemcpyHostToDevice, c->stream));
-    CCK(cudaMemcpyAsync(c->age, h_age.data(), h_age.size(), cudaMemcpyHostToDevice, c->stream));
+    c->sigma = sigma;
+    c->sell_entries = (int64_t)sell_in.slice_ptr.back();
+    auto upload_sell = [&](const HostSell &hs, uint32_t *&sp, uint32_t *&rl, uint32_t *&cl, float *&ww) -> gabm_status {
+        TRY(dalloc(c, &sp, hs.slice_ptr.size()));
+        TRY(dalloc(c, &rl, hs.row_len.size()));
+        TRY(dalloc(c, &cl, hs.col.size()));
+        TRY(dalloc(c, &ww, hs.w.size()));
+        CK(cudaMemcpyAsync(sp, hs.slice_ptr.data(), sizeof(uint32_t) * hs.slice_ptr.size(), cudaMemcpyHostToDevice, c->stream));
+        CK(cudaMemcpyAsync(rl, hs.row_len.data(), sizeof(uint32_t) * hs.row_len.size(), cudaMemcpyHostToDevice, c->stream));
+        CK(cudaMemcpyAsync(cl, hs.col.data(), sizeof(uint32_t) * hs.col.size(), cudaMemcpyHostToDevice, c->stream));
+        CK(cudaMemcpyAsync(ww, hs.w.data(), sizeof(float) * hs.w.size(), cudaMemcpyHostToDevice, c->stream));
+        return GABM_OK;
+    };
+    CTRY(upload_sell(sell_in, c->slice_ptr, c->row_len, c->scol, c->sw));
     if (symmetric) {
-        c->t_rowptr = c->rowptr;
-        c->t_col = c->col;
-        c->t_w = c->w;
+        c->t_slice_ptr = c->slice_ptr;
+        c->t_row_len = c->row_len;
+        c->t_scol = c->scol;
+        c->t_sw = c->sw;
     } else {
-        CTRY(dalloc(c, &c->t_rowptr, (size_t)n_rows + 1));
-        CTRY(dalloc(c, &c->t_col, (size_t)nnz_pad));
-        CTRY(dalloc(c, &c->t_w, (size_t)nnz_pad));
-        CCK(cudaMemcpyAsync(c->t_rowptr, t_rowptr.data(), sizeof(uint32_t) * t_rowptr.size(), cudaMemcpyHostToDevice, c->stream));
-        CCK(cudaMemcpyAsync(c->t_col, t_col.data(), sizeof(uint32_t) * t_col.size(), cudaMemcpyHostToDevice, c->stream));
-        CCK(cudaMemcpyAsync(c->t_w, t_w.data(), sizeof(float) * t_w.size(), cudaMemcpyHostToDevice, c->stream));
+        CTRY(upload_sell(sell_out, c->t_slice_ptr, c->t_row_len, c->t_scol, c->t_sw));
     }
+    CTRY(dalloc(c, &c->age, (size_t)n_rows));
+    CCK(cudaMemcpyAsync(c->age, h_age.data(), h_age.size(), cudaMemcpyHostToDevice, c->stream));
+    // the host copies above read vectors that go out of scope at return
+    CCK(cudaStreamSynchronize(c->stream));
     std::vector<float> inv((size_t)num_graphs);
     for (int g = 0; g < num_graphs; ++g) inv[g] = Dbar[g] > 0.0 ? (float)(1.0 / Dbar[g]) : 0.0f;
     CTRY(dalloc(c, &c->d_row0, (size_t)num_graphs));
@@ -585,6 +670,8 @@ gabm_status gabm_create(const gabm_graph_desc *graphs, int num_graphs, int sets_
     CTRY(dalloc(c, &c->hist, (size_t)c->I * kHistBins));
     CTRY(dalloc(c, &c->ties, (size_t)c->I * kTieCap));
     CTRY(dalloc(c, &c->d_nseed, (size_t)c->I));
+    CTRY(dalloc(c, &c->c_dev, (size_t)kMaxL));
+    CCK(cudaMemcpyAsync(c->c_dev, c->c, sizeof(float) * kMaxL, cudaMemcpyHostToDevice, c->stream));
     CCK(cudaMemsetAsync(c->hist, 0, sizeof(uint32_t) * (size_t)c->I * kHistBins, c->stream));
     {
         int grid = (int)std::min<int64_t>((n_rows + 255) / 256, 65535);
@@ -668,9 +755,7 @@ gabm_status gabm_forward(gabm_ctx *ctx, int T, const float *R, const float *m, c
     }
 
     FwdDayArgs a;
-    a.rowptr = c->rowptr;
-    a.col4 = (const uint4 *)c->col;
-    a.w4 = (const float4 *)c->w;
+    a.m = sell_view(c, false);
     a.age = c->age;
     a.gr = graph_ref(c);
     a.e = c->e;
@@ -684,10 +769,14 @@ gabm_status gabm_forward(gabm_ctx *ctx, int T, const float *R, const float *m, c
     a.L = c->L;
     a.seed = c->seed;
     for (int k = 0; k < kMaxL; ++k) a.c[k] = k < c->L ? c->c[k] : 0.f;
+    if (t0 < T) LAUNCH(launch_infectious_bits(c->e, t0, 1, c->L, c->ntiles, c->bits + (size_t)t0 * c->ntiles,
+                                              (size_t)c->ntiles, s));
     for (int t = t0; t < T; ++t) {
         a.t = t;
         a.lam_out = c->policy == GABM_STORE_LAMBDA ? c->lam + (size_t)t * c->n_rows : nullptr;
         a.tile_ctr = c->tile_ctr + t;
+        a.bits_cur = c->bits + (size_t)t * c->ntiles;
+        a.bits_next = c->bits + (size_t)(t + 1) * c->ntiles;
         prof_begin(c, 0);
         LAUNCH(launch_fwd_day(a, c->grid_fwd, s));
         prof_end(c, 0);
@@ -748,13 +837,9 @@ gabm_status gabm_backward(gabm_ctx *ctx, const double *gD, double *dR, double *d
 
     BwdDayArgs a;
     const int mode = c->policy == GABM_STORE_LAMBDA ? kBwdStore : (c->symmetric ? kBwdFused : kBwdSplit);
-    a.mode = mode;
-    a.rowptr = c->t_rowptr;
-    a.col4 = (const uint4 *)c->t_col;
-    a.w4 = (const float4 *)c->t_w;
-    a.in_rowptr = mode == kBwdSplit ? c->rowptr : nullptr;
-    a.in_col4 = mode == kBwdSplit ? (const uint4 *)c->col : nullptr;
-    a.in_w4 = mode == kBwdSplit ? (const float4 *)c->w : nullptr;
+    if (mode == kBwdSplit && !c->lam_tmp) TRY(dalloc(c, &c->lam_tmp, (size_t)c->n_rows));
+    a.mode = mode == kBwdSplit ? kBwdStore : mode;
+    a.m = sell_view(c, true);
     a.age = c->age;
     a.gr = graph_ref(c);
     a.E = c->e;
@@ -762,7 +847,7 @@ gabm_status gabm_backward(gabm_ctx *ctx, const double *gD, double *dR, double *d
     a.ring_stride = (size_t)c->n_rows;
     a.A = c->A;
     a.R = c->R;
-    a.m = c->m;
+    a.m_t = c->m;
     a.S = c->S;
     a.gD = c->gD;
     a.ldP = ld;
@@ -774,9 +859,15 @@ gabm_status gabm_backward(gabm_ctx *ctx, const double *gD, double *dR, double *d
     a.seed = c->seed;
     for (int k = 0; k < kMaxL; ++k) a.c[k] = k < c->L ? c->c[k] : 0.f;
     const int Lm1 = c->L - 1;
+    if (mode != kBwdStore)   // every day's infectious rows, from the final state
+        LAUNCH(launch_infectious_bits(c->e, 0, T, c->L, c->ntiles, c->bits, (size_t)c->ntiles, s));
     for (int t = T - 1; t >= 0; --t) {
+        a.bits_t = mode != kBwdStore ? c->bits + (size_t)t * c->ntiles : nullptr;
         a.t = t;
-        a.lam_t = mode == kBwdStore ? c->lam + (size_t)t * c->n_rows : nullptr;
+        a.lam_t = mode == kBwdStore ? c->lam + (size_t)t * c->n_rows : (mode == kBwdSplit ? c->lam_tmp : nullptr);
+        if (mode == kBwdSplit)
+            LAUNCH(launch_lam_day(sell_view(c, false), c->e, c->bits + (size_t)t * c->ntiles, graph_ref(c), t, c->L,
+                                  c->ntiles, c->c_dev, c->lam_tmp, c->grid_fwd, s));
         a.r_next = c->r + (size_t)((t + 1) & 1) * c->n_rows;
         a.r_cur = c->r + (size_t)(t & 1) * c->n_rows;
         a.P_t = c->P + (size_t)t * c->ntiles * kAges;

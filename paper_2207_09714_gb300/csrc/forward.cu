@@ -1,10 +1,13 @@
 // forward.cu -- forward day step of the hard GradABM model on sm_103a.
 //
 // One launch per day (Sec. 3.1, Eq. 1-3; A1: one-day steps).  Warps take
-// 32-row tiles from a per-launch counter.  The susceptible rows of a tile are
-// summed by warp_row_sums over the destination-sorted CSR (a pull gather, no
-// atomics): w_ji * c[t - e_j] with the neighbours' exposure days gathered from
-// the L2-resident state.  Each lane then runs the fused epilogue for its own
+// 32-row tiles from a per-launch counter; each lane sums its own susceptible
+// row over the in-edges (a pull gather, no atomics) read from the tile's
+// SELL-32 slice with coalesced loads: w_ji * c[t - e_j] for the neighbours
+// marked infectious in today's bitmap (an L1-resident bit array), whose
+// exposure days are gathered from the L2-resident state.  Each warp prefetches
+// the next tile's id, row data and (into L2) its slice while it works on the
+// current tile.  Each lane then runs the fused epilogue for its own
 // row: lambda, p = 1 - exp(-lambda) (Eq. 3), the Philox uniform, the hard draw
 // and the in-place state update e_i = t.
 //
@@ -38,30 +41,46 @@ __device__ __forceinline__ void flush_counts_warp(int32_t *counts, int32_t *newR
 
 __global__ void __launch_bounds__(kBlock, 3) k_fwd_day(const FwdDayArgs a) {
     __shared__ float c_s[kMaxL];
-    __shared__ WarpStage<1> stage_s[kBlock / 32];
     __shared__ int32_t red_s[kBlock / 32][6];
     if (threadIdx.x < kMaxL) c_s[threadIdx.x] = a.c[threadIdx.x];
     __syncthreads();
 
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int t = a.t, L = a.L, tau_EI = a.tau_EI;
-    WarpStage<1> &ws = stage_s[wib];
+    const int t = a.t, L = a.L, tau_EI = a.tau_EI, ntiles = a.ntiles;
     const int16_t *e = a.e;
-    auto contrib = [&](uint32_t, uint32_t j, float w, float (&out)[1]) {
-        out[0] = w * infectiousness(e[j], c_s, t, L);
+    const uint32_t *bits = a.bits_cur;
+    // only neighbours marked infectious today contribute; their exposure day is gathered
+    auto contrib = [&](uint32_t j, float w, float (&out)[1]) {
+        out[0] = marked(bits, j) ? w * infectiousness(e[j], c_s, t, L) : 0.f;
     };
+    const bool want[1] = {true};
 
     int cur_g = -1;
     int cS = 0, cE = 0, cI = 0, cR = 0, cN = 0;
-    for (int tile = next_tile(a.tile_ctr, lane); tile < a.ntiles; tile = next_tile(a.tile_ctr, lane)) {
-        const int g = a.gr.tile_graph ? (int)a.gr.tile_graph[tile] : 0;
+
+    // Tile ids come from the launch counter two ahead of use; each tile's row data
+    // is loaded one tile ahead, and its slice is prefetched into L2 while the tile
+    // before it is processed.
+    TileRows cur, nxt;
+    load_tile_rows(a.m, e, a.gr.tile_graph, ntiles, next_tile(a.tile_ctr, lane), lane, cur);
+    int tile_n = next_tile(a.tile_ctr, lane);
+    int raw_nn = (lane == 0) ? atomicAdd(a.tile_ctr, 1) : 0;
+    load_tile_rows(a.m, e, a.gr.tile_graph, ntiles, tile_n, lane, nxt);
+    prefetch_slice(a.m, cur.p0, cur.p1, lane);
+    while (cur.tile < ntiles) {
+        prefetch_slice(a.m, nxt.p0, nxt.p1, lane);
+        const int tile_nn = __shfl_sync(0xffffffffu, raw_nn, 0);
+        TileRows nn;
+        load_tile_rows(a.m, e, a.gr.tile_graph, ntiles, tile_nn, lane, nn);
+        if (lane == 0 && tile_nn < ntiles) raw_nn = atomicAdd(a.tile_ctr, 1);
+
+        const int g = cur.g, tile = cur.tile, ei = cur.e;
         if (g != cur_g) {
             if (cur_g >= 0) flush_counts_warp(a.counts, a.newRM, a.ldP, cur_g, t, cS, cE, cI, cR, cN, lane);
             cur_g = g;
             cS = cE = cI = cR = cN = 0;
         }
         const int row = tile * kTile + lane;
-        const int ei = a.e[row];
         const bool isS = (ei == kNever);
         if (ei != kPad && !isS) {
             const int k = t - ei;
@@ -69,11 +88,11 @@ __global__ void __launch_bounds__(kBlock, 3) k_fwd_day(const FwdDayArgs a) {
             cN += (k == L);
         }
         cS += isS;
-        if (__ballot_sync(0xffffffffu, isS) == 0u) continue;
-        const uint32_t rs = a.rowptr[row], re = a.rowptr[row + 1];
-        float sum[1];
-        warp_row_sums<1>(ws, a.col4, a.w4, isS, rs, re, 0u, lane, contrib, sum);
 
+        float sum[1];
+        row_sums<1>(a.m, cur.p0, cur.len, isS, lane, contrib, want, sum);
+
+        int e_next = ei;
         if (isS) {
             const float Lam = sum[0] * a.gr.inv_Dbar[g];
             const int inst = g;
@@ -81,9 +100,19 @@ __global__ void __launch_bounds__(kBlock, 3) k_fwd_day(const FwdDayArgs a) {
             const float p = -expm1f(-lam);
             const uint32_t id = caller_id(a.gr, row, g);
             const float u = uniform_from_word(philox_word(a.seed, id, (uint32_t)t, (uint32_t)inst, 0u));
-            if (u < p) a.e[row] = (int16_t)t;
+            if (u < p) {
+                a.e[row] = (int16_t)t;
+                e_next = t;
+            }
             if (a.lam_out) a.lam_out[row] = Lam;
         }
+        // rows infectious tomorrow (susceptible and padding rows fall outside the window)
+        const int kn = t + 1 - e_next;
+        const unsigned inf_next = __ballot_sync(0xffffffffu, (unsigned)(kn - 1) < (unsigned)(L - 1));
+        if (lane == 0) a.bits_next[tile] = inf_next;
+
+        cur = nxt;
+        nxt = nn;
     }
 
     // block-level reduction of the last graph's counts, then one atomic per count
@@ -105,14 +134,30 @@ __global__ void __launch_bounds__(kBlock, 3) k_fwd_day(const FwdDayArgs a) {
             if (gw != g) {
                 if (g >= 0) {
                     int32_t *cp = a.counts + ((size_t)g * a.ldP + t) * 4;
-                    for (int s = 0; s < 4; ++s) if (acc[s]) atomicAdd(cp + s, acc[s]);
+                    for (int s2 = 0; s2 < 4; ++s2) if (acc[s2]) atomicAdd(cp + s2, acc[s2]);
                     if (acc[4]) atomicAdd(a.newRM + (size_t)g * a.ldP + t, acc[4]);
                 }
                 g = gw;
-                for (int s = 0; s < 5; ++s) acc[s] = 0;
+                for (int s2 = 0; s2 < 5; ++s2) acc[s2] = 0;
             }
             if (w < kBlock / 32 && gw >= 0)
-                for (int s = 0; s < 5; ++s) acc[s] += red_s[w][1 + s];
+                for (int s2 = 0; s2 < 5; ++s2) acc[s2] += red_s[w][1 + s2];
+        }
+    }
+}
+
+// One warp per tile: for every day d of the range, the ballot of rows with
+// 1 <= d - e < L.
+__global__ void k_infectious_bits(const int16_t *e, int t0, int ndays, int L, int ntiles, uint32_t *bits,
+                                  size_t day_stride) {
+    const int lane = threadIdx.x & 31;
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    for (int tile = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; tile < ntiles; tile += warps) {
+        const int ei = e[tile * kTile + lane];
+        for (int d = 0; d < ndays; ++d) {
+            const int k = t0 + d - ei;
+            const unsigned b = __ballot_sync(0xffffffffu, (unsigned)(k - 1) < (unsigned)(L - 1));
+            if (lane == 0) bits[(size_t)d * day_stride + tile] = b;
         }
     }
 }
@@ -360,6 +405,14 @@ __global__ void k_philox(uint64_t seed, const uint32_t *ctr, uint32_t *out, int6
 }
 
 }  // namespace
+
+cudaError_t launch_infectious_bits(const int16_t *e, int t0, int ndays, int L, int ntiles, uint32_t *bits,
+                                   size_t day_stride, cudaStream_t s) {
+    int grid = (ntiles + 7) / 8;
+    if (grid > 65535) grid = 65535;
+    k_infectious_bits<<<grid > 0 ? grid : 1, 256, 0, s>>>(e, t0, ndays, L, ntiles, bits, day_stride);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_init_state(int16_t *e, const int32_t *row0, const int32_t *rows, int G,
                               int64_t n_rows, int grid, cudaStream_t s) {

@@ -4,9 +4,10 @@
 //   graphs are concatenated block-diagonally, each padded to a multiple of 32
 //   rows so that a 32-row tile never straddles two graphs; padding rows have
 //   no edges and exposure day kPad.
-//   rowptr  u32 [n_rows+1]        destination-sorted CSR (row i: in-neighbours)
-//   col     u32 [nnz_pad]         nnz_pad = nnz rounded up to 4, plus one spare
-//   w       f32 [nnz_pad]         vector of 4 edges = one 16-byte load each
+//   SELL-32 in-edges (row i lists its in-neighbours j with w_ji), one slice of
+//   max_len x 32 entries per 32-row tile, column-major:
+//   slice_ptr u32 [ntiles+1], row_len u32 [n_rows], col u32 / w f32 [entries]
+//   (the out-edges in the same layout when the weights are not symmetric)
 //   age     u8  [n_rows]
 //   e       i16 [n_rows]          exposure day (kNever = susceptible)
 //   lam     f32 [Tcap][n_rows]    normalised neighbour sums (store policy)
@@ -90,10 +91,16 @@ __device__ __forceinline__ uint32_t caller_id(const GraphRef &gr, int row, int g
     return gr.orig_id ? gr.orig_id[row] : (uint32_t)(row - gr.row0[g]);
 }
 
+// Edges of one orientation in SELL-32 layout (one slice per 32-row tile).
+struct Sell {
+    const uint32_t *slice_ptr;  // [ntiles+1] first entry of each slice
+    const uint32_t *row_len;    // [n_rows] entries of each row
+    const uint32_t *col;        // [entries] column (neighbour row) of each entry
+    const float *w;             // [entries] weight of each entry (0 in padding)
+};
+
 struct FwdDayArgs {
-    const uint32_t *rowptr;
-    const uint4 *col4;
-    const float4 *w4;
+    Sell m;               // in-edges: row i lists j with w_ji
     const uint8_t *age;
     GraphRef gr;
     int16_t *e;
@@ -104,30 +111,26 @@ struct FwdDayArgs {
     int32_t *counts;      // [I][ldP][4]
     int32_t *newRM;       // [I][ldP]
     int *tile_ctr;        // tile counter of this launch (zero before the launch)
+    const uint32_t *bits_cur;   // [ntiles] bit i of word r/32: row r infectious on day t
+    uint32_t *bits_next;        // [ntiles] the same for day t + 1 (written by this launch)
     int ntiles, t, tau_EI, L;
     uint64_t seed;
     float c[kMaxL];
 };
 
 struct BwdDayArgs {
-    // transpose gather (out-edges of each row) -- the forward CSR when symmetric
-    const uint32_t *rowptr;
-    const uint4 *col4;
-    const float4 *w4;
-    // in-edges for lambda recomputation when they differ from the above (else nullptr)
-    const uint32_t *in_rowptr;
-    const uint4 *in_col4;
-    const float4 *in_w4;
+    Sell m;                    // out-edges (the in-edges themselves when the weights are symmetric)
     const uint8_t *age;
     GraphRef gr;
     const int16_t *E;          // final exposure days
+    const uint32_t *bits_t;    // [ntiles] rows infectious on day t (recompute policy) or nullptr
     const float *lam_t;        // stored normalised sums for day t (store policy) or nullptr
     const float *r_next;       // coefficients of day t+1 [n_rows]
     float *r_cur;              // coefficients of day t   [n_rows]
     float *ring;               // [L-1][n_rows]
     size_t ring_stride;
     float *A;                  // [n_rows] adjoint of s carried back from the infection day
-    const float *R, *m, *S;    // [I][ldP], [I][ldP], [I][9]
+    const float *R, *m_t, *S;  // R and mortality [I][ldP], susceptibility [I][9]
     const double *gD;          // [I][ldP]
     int ldP;
     double *P_t;               // [ntiles][9] partial sums of gl * Lam for day t
@@ -173,12 +176,17 @@ cudaError_t launch_seed_scan(const SeedArgs &a, int I, cudaStream_t s);
 cudaError_t launch_seed_mark(const SeedArgs &a, int G, int grid_x, cudaStream_t s);
 cudaError_t launch_seed_ties(const SeedArgs &a, int I, cudaStream_t s);
 cudaError_t launch_fwd_day(const FwdDayArgs &a, int grid, cudaStream_t s);
+// bits[d][tile] for days t0 .. t0 + ndays - 1: rows with 1 <= t - e < L (infectious on day t).
+cudaError_t launch_infectious_bits(const int16_t *e, int t0, int ndays, int L, int ntiles, uint32_t *bits,
+                                   size_t day_stride, cudaStream_t s);
 cudaError_t launch_fwd_finalize(const int32_t *newRM, const int32_t *counts, const float *m, int ldP,
                                 int t0, int T, int I, double *D_ctx, double *D_out,
                                 int32_t *counts_out, cudaStream_t s);
 cudaError_t launch_mse(const double *D, int ldP, const double *y, int T, int I, double *loss,
                        double *gD_ctx, double *gD_out, cudaStream_t s);
 cudaError_t launch_bwd_day(const BwdDayArgs &a, int grid, cudaStream_t s);
+cudaError_t launch_lam_day(Sell m, const int16_t *E, const uint32_t *bits, GraphRef gr, int t, int L, int ntiles,
+                           const float *c, float *lam_out, int grid, cudaStream_t s);
 cudaError_t launch_bwd_reduce(const double *P, int ntiles, int ldP, const int32_t *graph_tile0,
                               const int32_t *graph_ntiles, int T, int I, double *Q,
                               cudaStream_t s);

@@ -1,36 +1,20 @@
-// rowsum.cuh -- warp-cooperative row sums over a 32-row tile of a CSR matrix,
-// shared by the forward and backward day kernels.
+// rowsum.cuh -- device helpers shared by the forward and backward day kernels.
 //
-// The active rows of a warp tile are laid end to end as one stream of 16-byte
-// edge vectors (4 columns / 4 weights each, aligned to the edge index, so a
-// vector shared by two rows appears once per row with the other row's edges
-// masked).  In chunks of kChunkVec vectors, every lane loads up to four vectors
-// of that stream at once (coalesced, streaming loads), computes the per-edge
-// contributions (which gather the neighbours' state), adds the four of a
-// vector in order and stores that partial in shared memory.  Each lane then
-// adds up its own row's vector partials in order with compensated (Kahan)
-// summation.  The result depends only on the row's edges, not on which rows
-// were active together, so a sum recomputed in the backward is bitwise the
-// forward's, and long rows keep fp32 sums accurate to a few ulps.
+// Edge storage is SELL-32 (sliced ELLPACK, one slice per 32-row warp tile):
+// slice s holds max_len(s) x 32 entries, column-major, so entry k of the row in
+// lane l of the slice sits at slice_ptr[s] + 32 k + l.  A warp reads entry k of
+// its 32 rows with one coalesced 128-byte load per array, and every lane sums
+// its own row in entry order.  The sum of a row therefore depends only on the
+// row (the same operation sequence wherever and whenever it is computed), so a
+// sum recomputed in the backward is bitwise the forward's.  Rows are laid out
+// so that a slice holds rows of similar length (little padding).
 #pragma once
 
 #include "gabm_internal.cuh"
 
 namespace gabm {
 
-constexpr int kChunkVec = 128;   // edge vectors staged per warp and chunk
-constexpr int kVecPerLane = kChunkVec / 32;
-
-template <int NARR>
-struct WarpStage {
-    int pv[32];          // first stream vector of each active row (exclusive prefix)
-    uint32_t vs[32];     // first 16-byte vector of each active row
-    uint32_t rs[32];     // edge range of each active row
-    uint32_t re[32];
-    uint32_t fl[32];     // per-row flags handed to the contribution functor
-    uint8_t rowid[kChunkVec];       // active-row index of each stream vector of the chunk
-    float val[NARR][kChunkVec];     // per-vector partial sums of the chunk
-};
+constexpr int kUnroll = 8;   // entries per lane loaded ahead of use
 
 __device__ __forceinline__ void kahan_add(float &s, float &c, float x) {
     const float y = __fsub_rn(x, c);
@@ -46,99 +30,86 @@ __device__ __forceinline__ float infectiousness(int e_j, const float *c_s, int t
     return ((unsigned)(k - 1) < (unsigned)(L - 1)) ? c_s[k] : 0.f;
 }
 
+// Whether row j is marked in a per-day bitmap of infectious rows (read-only during the launch).
+__device__ __forceinline__ bool marked(const uint32_t *__restrict__ bits, uint32_t j) {
+    return (__ldg(bits + (j >> 5)) >> (j & 31u)) & 1u;
+}
+
 __device__ __forceinline__ int next_tile(int *ctr, int lane) {
     int v = 0;
     if (lane == 0) v = atomicAdd(ctr, 1);
     return __shfl_sync(0xffffffffu, v, 0);
 }
 
-// For every lane with `act`, sum[a] = the sum over the row's edges p in [rs, re)
-// of contribution a of edge p: the edges of each 16-byte vector are added in
-// order into a vector partial, and the row's vector partials are added in order
-// with compensated summation.  Both orders depend only on the row itself.
-// contrib(flags, col, w, out) writes NARR values for one edge.  Called by all 32 lanes.
+// Ask L2 to fetch one slice (entries [p0, p1) of both arrays) ahead of use.
+// Slices start on 128-byte boundaries and hold multiples of 32 entries.
+__device__ __forceinline__ void prefetch_slice(const Sell &m, uint32_t p0, uint32_t p1, int lane) {
+    if (lane == 0 && p1 > p0) {
+        const uint32_t bytes = (p1 - p0) * 4u;
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(m.col + p0), "r"(bytes) : "memory");
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(m.w + p0), "r"(bytes) : "memory");
+    }
+}
+
+// Row data of one tile, loaded one tile ahead of use.
+struct TileRows {
+    int tile;
+    int e;            // exposure day of this lane's row
+    uint32_t len;     // entries of this lane's row
+    uint32_t p0, p1;  // the tile's slice bounds
+    int g;            // graph of the tile
+};
+
+__device__ __forceinline__ void load_tile_rows(const Sell &m, const int16_t *e, const uint16_t *tile_graph,
+                                               int ntiles, int tile, int lane, TileRows &tr) {
+    tr.tile = tile;
+    tr.e = kPad;
+    tr.len = 0;
+    tr.p0 = tr.p1 = 0;
+    tr.g = 0;
+    if (tile < ntiles) {
+        const int row = tile * kTile + lane;
+        tr.e = e[row];
+        tr.len = m.row_len[row];
+        tr.p0 = m.slice_ptr[tile];
+        tr.p1 = m.slice_ptr[tile + 1];
+        tr.g = tile_graph ? (int)tile_graph[tile] : 0;
+    }
+}
+
+// For this lane's row (when act), sum[a] = the sum of contribution a over the
+// row's entries in entry order, with compensated summation; f(j, w, out) writes
+// the NARR contributions of the entry with column j and weight w, and want[a]
+// says whether sum a is taken for this row.  Called by all 32 lanes.
 template <int NARR, class F>
-__device__ __forceinline__ void warp_row_sums(WarpStage<NARR> &ws, const uint4 *__restrict__ col4,
-                                              const float4 *__restrict__ w4, bool act, uint32_t rs,
-                                              uint32_t re, uint32_t flags, int lane, F contrib,
-                                              float (&sum)[NARR]) {
+__device__ __forceinline__ void row_sums(const Sell &m, uint32_t p0, uint32_t len, bool act, int lane, F f,
+                                         const bool (&want)[NARR], float (&sum)[NARR]) {
     float comp[NARR];
 #pragma unroll
     for (int a = 0; a < NARR; ++a) { sum[a] = 0.f; comp[a] = 0.f; }
-    const unsigned amask = __ballot_sync(0xffffffffu, act);
-    if (amask == 0u) return;
-    const uint32_t vs = rs >> 2;
-    const int nv = (act && re > rs) ? (int)(((re + 3u) >> 2) - vs) : 0;
-    int incl = nv;
+    const uint32_t kmax = __reduce_max_sync(0xffffffffu, act ? len : 0u);
+    for (uint32_t k0 = 0; k0 < kmax; k0 += kUnroll) {
+        uint32_t jv[kUnroll];
+        float wv[kUnroll];
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += y;
-    }
-    const int pv = incl - nv;
-    const int total = __shfl_sync(0xffffffffu, incl, 31);
-    const int rank = __popc(amask & ((1u << lane) - 1u));
-    if (act) {
-        ws.pv[rank] = pv;
-        ws.vs[rank] = vs;
-        ws.rs[rank] = rs;
-        ws.re[rank] = re;
-        ws.fl[rank] = flags;
-    }
-    for (int c0 = 0; c0 < total; c0 += kChunkVec) {
-        const int cn = min(kChunkVec, total - c0);
-        const int f_lo = max(pv, c0), f_hi = min(pv + nv, c0 + cn);
-        for (int f = f_lo; f < f_hi; ++f) ws.rowid[f - c0] = (uint8_t)rank;
-        __syncwarp();
-        uint4 cc[kVecPerLane];
-        float4 ww[kVecPerLane];
-        int jr[kVecPerLane];
-        uint32_t vv[kVecPerLane];
+        for (int u = 0; u < kUnroll; ++u) {
+            const uint32_t k = k0 + (uint32_t)u;
+            const bool v = act && k < len;
+            const uint32_t idx = p0 + k * 32u + (uint32_t)lane;
+            jv[u] = v ? __ldcs(m.col + idx) : 0u;
+            wv[u] = v ? __ldcs(m.w + idx) : 0.f;
+        }
 #pragma unroll
-        for (int u = 0; u < kVecPerLane; ++u) {
-            const int k = lane + 32 * u;
-            jr[u] = -1;
-            if (k < cn) {
-                const int j = ws.rowid[k];
-                jr[u] = j;
-                vv[u] = ws.vs[j] + (uint32_t)(c0 + k - ws.pv[j]);
-                cc[u] = __ldcs(col4 + vv[u]);
-                ww[u] = __ldcs(w4 + vv[u]);
+        for (int u = 0; u < kUnroll; ++u) {
+            const uint32_t k = k0 + (uint32_t)u;
+            if (act && k < len) {
+                float out[NARR];
+                f(jv[u], wv[u], out);
+#pragma unroll
+                for (int a = 0; a < NARR; ++a)
+                    if (want[a]) kahan_add(sum[a], comp[a], out[a]);
             }
         }
-#pragma unroll
-        for (int u = 0; u < kVecPerLane; ++u) {
-            if (jr[u] >= 0) {
-                const int k = lane + 32 * u;
-                const uint32_t rsj = ws.rs[jr[u]], rej = ws.re[jr[u]], flj = ws.fl[jr[u]];
-                const uint32_t p0 = vv[u] << 2;
-                const uint32_t cq[4] = {cc[u].x, cc[u].y, cc[u].z, cc[u].w};
-                const float wq[4] = {ww[u].x, ww[u].y, ww[u].z, ww[u].w};
-                float part[NARR];
-#pragma unroll
-                for (int a = 0; a < NARR; ++a) part[a] = 0.f;
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const uint32_t p = p0 + (uint32_t)q;
-                    if (p >= rsj && p < rej) {
-                        float out[NARR];
-#pragma unroll
-                        for (int a = 0; a < NARR; ++a) out[a] = 0.f;
-                        contrib(flj, cq[q], wq[q], out);
-#pragma unroll
-                        for (int a = 0; a < NARR; ++a) part[a] = __fadd_rn(part[a], out[a]);
-                    }
-                }
-#pragma unroll
-                for (int a = 0; a < NARR; ++a) ws.val[a][k] = part[a];
-            }
-        }
-        __syncwarp();
-        for (int f = f_lo; f < f_hi; ++f) {
-#pragma unroll
-            for (int a = 0; a < NARR; ++a) kahan_add(sum[a], comp[a], ws.val[a][f - c0]);
-        }
-        __syncwarp();
     }
 }
 
