@@ -25,7 +25,7 @@ namespace gabm {
 namespace {
 
 template <int MODE>
-__global__ void __launch_bounds__(kBlock, 3) k_bwd_day(const BwdDayArgs a) {
+__global__ void __launch_bounds__(kBlock, GABM_MINBLOCKS) k_bwd_day(const BwdDayArgs a) {
     constexpr int NARR = (MODE == kBwdFused) ? 2 : 1;
     __shared__ float c_s[kMaxL];
     __shared__ int slot_k[kMaxL];
@@ -44,24 +44,26 @@ __global__ void __launch_bounds__(kBlock, 3) k_bwd_day(const BwdDayArgs a) {
     const uint32_t *bits = a.bits_t;
     // contribution 0: w * r_j(t+1) (transpose gather); contribution 1 (recompute):
     // w * c[t - E_j] for neighbours marked infectious on day t
-    auto contrib = [&](uint32_t j, float w, float (&out)[NARR]) {
-        out[0] = w * r_next[j];
-        if constexpr (NARR == 2) out[1] = marked(bits, j) ? w * infectiousness(E[j], c_s, t, L) : 0.f;
+    auto contrib = [&](uint32_t j, float w, bool valid, float (&out)[NARR]) {
+        out[0] = w * ld_if(r_next + j, valid);
+        if constexpr (NARR == 2) {
+            const bool mk = valid && marked(bits, j);
+            const int Ej = ld_if(E + j, mk, kNever);
+            out[1] = mk ? w * infectiousness(Ej, c_s, t, L) : 0.f;
+        }
     };
 
     int cur_g = -1, cN = 0;
+    TileDispenser disp;
+    disp.init(a.tile_ctr, ntiles, gridDim.x * (kBlock / 32), lane);
     TileRows cur, nxt;
-    load_tile_rows(a.m, E, a.gr.tile_graph, ntiles, next_tile(a.tile_ctr, lane), lane, cur);
-    int tile_n = next_tile(a.tile_ctr, lane);
-    int raw_nn = (lane == 0) ? atomicAdd(a.tile_ctr, 1) : 0;
-    load_tile_rows(a.m, E, a.gr.tile_graph, ntiles, tile_n, lane, nxt);
+    load_tile_rows(a.m, E, a.gr.tile_graph, ntiles, disp.get(), lane, cur);
+    load_tile_rows(a.m, E, a.gr.tile_graph, ntiles, disp.get(), lane, nxt);
     prefetch_slice(a.m, cur.p0, cur.p1, lane);
     while (cur.tile < ntiles) {
         prefetch_slice(a.m, nxt.p0, nxt.p1, lane);
-        const int tile_nn = __shfl_sync(0xffffffffu, raw_nn, 0);
         TileRows nn;
-        load_tile_rows(a.m, E, a.gr.tile_graph, ntiles, tile_nn, lane, nn);
-        if (lane == 0 && tile_nn < ntiles) raw_nn = atomicAdd(a.tile_ctr, 1);
+        load_tile_rows(a.m, E, a.gr.tile_graph, ntiles, disp.get(), lane, nn);
 
         const int g = cur.g, tile = cur.tile, Ei = cur.e;
         if (g != cur_g) {
@@ -173,8 +175,10 @@ __global__ void __launch_bounds__(kBlock) k_lam_day(Sell m, const int16_t *E, co
     __syncthreads();
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int nwarps = gridDim.x * (kBlock / 32);
-    auto contrib = [&](uint32_t j, float w, float (&out)[1]) {
-        out[0] = marked(bits, j) ? w * infectiousness(E[j], c_s, t, L) : 0.f;
+    auto contrib = [&](uint32_t j, float w, bool valid, float (&out)[1]) {
+        const bool mk = valid && marked(bits, j);
+        const int Ej = ld_if(E + j, mk, kNever);
+        out[0] = mk ? w * infectiousness(Ej, c_s, t, L) : 0.f;
     };
     const bool want[1] = {true};
     for (int tile = blockIdx.x * (kBlock / 32) + wib; tile < ntiles; tile += nwarps) {

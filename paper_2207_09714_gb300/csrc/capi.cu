@@ -45,7 +45,7 @@ struct gabm_ctx {
     uint32_t *t_slice_ptr = nullptr, *t_row_len = nullptr, *t_scol = nullptr;
     float *t_sw = nullptr;
     int64_t sell_entries = 0;
-    int sigma = 128;
+    int sigma = 1024;
     uint8_t *age = nullptr;
     int32_t *d_row0 = nullptr, *d_rows = nullptr, *d_tile0 = nullptr, *d_ntiles = nullptr;
     int64_t *d_goff = nullptr;      // [G] caller offset of each graph
@@ -76,6 +76,7 @@ struct gabm_ctx {
     int lam_from = -1;
 
     int grid_fwd = 0, grid_bwd = 0;
+    bool smem_bits = false;         // forward keeps the infectious bitmap in shared memory
     int *tile_ctr = nullptr;        // [2][Tcap] per-launch tile counters (forward, backward)
     uint32_t *bits = nullptr;       // [Tcap][ntiles] per-day bitmaps of infectious rows
 
@@ -501,7 +502,7 @@ gabm_status gabm_create(const gabm_graph_desc *graphs, int num_graphs, int sets_
     // device layout: optionally relabel each graph's agents (D-bar above uses the caller's order)
     std::vector<std::vector<uint32_t>> orders((size_t)num_graphs);
     const bool reorder = true;
-    int sigma = 128;
+    int sigma = 1024;
     if (const char *f = getenv("GABM_SELL_SIGMA")) sigma = std::max(1, atoi(f));
     for (int g = 0; g < num_graphs; ++g) {
         if (model->agent_order == GABM_ORDER_BFS) {
@@ -679,11 +680,18 @@ gabm_status gabm_create(const gabm_graph_desc *graphs, int num_graphs, int sets_
         c->launches++;
         if (e != cudaSuccess) return bail(fail(c, GABM_ECUDA, "init state: %s", cudaGetErrorString(e)));
     }
-    c->grid_fwd = c->num_sms * occupancy_fwd();
+    {
+        // the bitmap read through L1 is the default: with branch-free gathers it beats the
+        // shared-memory copy, whose one large block per SM limits the warps in flight
+        const char *f = getenv("GABM_FWD_SMEM_BITS");
+        const int bps = (f && atoi(f) == 1) ? occupancy_fwd(ntiles, true) : 0;
+        c->smem_bits = bps > 0;
+        c->grid_fwd = c->num_sms * (c->smem_bits ? bps : occupancy_fwd(ntiles, false));
+    }
     const int mode = c->policy == GABM_STORE_LAMBDA ? kBwdStore : (symmetric ? kBwdFused : kBwdSplit);
     c->grid_bwd = c->num_sms * occupancy_bwd(mode);
     const int max_grid = (ntiles + kBlock / 32 - 1) / (kBlock / 32);
-    if (c->grid_fwd > max_grid) c->grid_fwd = max_grid;
+    if (!c->smem_bits && c->grid_fwd > max_grid) c->grid_fwd = max_grid;
     if (c->grid_bwd > max_grid) c->grid_bwd = max_grid;
     CTRY(ensure_days(c, 8));
     CCK(cudaStreamSynchronize(c->stream));
@@ -778,7 +786,7 @@ gabm_status gabm_forward(gabm_ctx *ctx, int T, const float *R, const float *m, c
         a.bits_cur = c->bits + (size_t)t * c->ntiles;
         a.bits_next = c->bits + (size_t)(t + 1) * c->ntiles;
         prof_begin(c, 0);
-        LAUNCH(launch_fwd_day(a, c->grid_fwd, s));
+        LAUNCH(launch_fwd_day(a, c->grid_fwd, c->smem_bits, s));
         prof_end(c, 0);
     }
     const bool dev = mem_space == GABM_DEVICE;
@@ -867,7 +875,7 @@ gabm_status gabm_backward(gabm_ctx *ctx, const double *gD, double *dR, double *d
         a.lam_t = mode == kBwdStore ? c->lam + (size_t)t * c->n_rows : (mode == kBwdSplit ? c->lam_tmp : nullptr);
         if (mode == kBwdSplit)
             LAUNCH(launch_lam_day(sell_view(c, false), c->e, c->bits + (size_t)t * c->ntiles, graph_ref(c), t, c->L,
-                                  c->ntiles, c->c_dev, c->lam_tmp, c->grid_fwd, s));
+                                  c->ntiles, c->c_dev, c->lam_tmp, c->grid_bwd, s));
         a.r_next = c->r + (size_t)((t + 1) & 1) * c->n_rows;
         a.r_cur = c->r + (size_t)(t & 1) * c->n_rows;
         a.P_t = c->P + (size_t)t * c->ntiles * kAges;

@@ -39,10 +39,18 @@ __device__ __forceinline__ void flush_counts_warp(int32_t *counts, int32_t *newR
     }
 }
 
-__global__ void __launch_bounds__(kBlock, 3) k_fwd_day(const FwdDayArgs a) {
+// SMEM_BITS: today's infectious bitmap is copied into shared memory (one large
+// block per SM), so the per-edge test is a shared-memory lookup instead of a
+// scattered L1 load; otherwise it is read through L1 from global memory.
+template <bool SMEM_BITS, int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB) k_fwd_day(const FwdDayArgs a) {
+    constexpr int NW = NT / 32;
+    extern __shared__ uint32_t bits_s[];
     __shared__ float c_s[kMaxL];
-    __shared__ int32_t red_s[kBlock / 32][6];
+    __shared__ int32_t red_s[NW][6];
     if (threadIdx.x < kMaxL) c_s[threadIdx.x] = a.c[threadIdx.x];
+    if (SMEM_BITS)
+        for (int i = threadIdx.x; i < a.ntiles; i += NT) bits_s[i] = __ldcg(a.bits_cur + i);
     __syncthreads();
 
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -50,29 +58,28 @@ __global__ void __launch_bounds__(kBlock, 3) k_fwd_day(const FwdDayArgs a) {
     const int16_t *e = a.e;
     const uint32_t *bits = a.bits_cur;
     // only neighbours marked infectious today contribute; their exposure day is gathered
-    auto contrib = [&](uint32_t j, float w, float (&out)[1]) {
-        out[0] = marked(bits, j) ? w * infectiousness(e[j], c_s, t, L) : 0.f;
+    auto contrib = [&](uint32_t j, float w, bool valid, float (&out)[1]) {
+        const bool mk = valid && (SMEM_BITS ? ((bits_s[j >> 5] >> (j & 31u)) & 1u) : marked(bits, j));
+        const int ej = ld_if(e + j, mk, kNever);
+        out[0] = mk ? w * infectiousness(ej, c_s, t, L) : 0.f;
     };
     const bool want[1] = {true};
 
     int cur_g = -1;
     int cS = 0, cE = 0, cI = 0, cR = 0, cN = 0;
 
-    // Tile ids come from the launch counter two ahead of use; each tile's row data
-    // is loaded one tile ahead, and its slice is prefetched into L2 while the tile
-    // before it is processed.
+    // Tiles come from a per-warp dispenser; each tile's row data is loaded one tile
+    // ahead of use (and, when enabled, its slice prefetched into L2).
+    TileDispenser disp;
+    disp.init(a.tile_ctr, ntiles, gridDim.x * NW, lane);
     TileRows cur, nxt;
-    load_tile_rows(a.m, e, a.gr.tile_graph, ntiles, next_tile(a.tile_ctr, lane), lane, cur);
-    int tile_n = next_tile(a.tile_ctr, lane);
-    int raw_nn = (lane == 0) ? atomicAdd(a.tile_ctr, 1) : 0;
-    load_tile_rows(a.m, e, a.gr.tile_graph, ntiles, tile_n, lane, nxt);
+    load_tile_rows(a.m, e, a.gr.tile_graph, ntiles, disp.get(), lane, cur);
+    load_tile_rows(a.m, e, a.gr.tile_graph, ntiles, disp.get(), lane, nxt);
     prefetch_slice(a.m, cur.p0, cur.p1, lane);
     while (cur.tile < ntiles) {
         prefetch_slice(a.m, nxt.p0, nxt.p1, lane);
-        const int tile_nn = __shfl_sync(0xffffffffu, raw_nn, 0);
         TileRows nn;
-        load_tile_rows(a.m, e, a.gr.tile_graph, ntiles, tile_nn, lane, nn);
-        if (lane == 0 && tile_nn < ntiles) raw_nn = atomicAdd(a.tile_ctr, 1);
+        load_tile_rows(a.m, e, a.gr.tile_graph, ntiles, disp.get(), lane, nn);
 
         const int g = cur.g, tile = cur.tile, ei = cur.e;
         if (g != cur_g) {
@@ -129,8 +136,8 @@ __global__ void __launch_bounds__(kBlock, 3) k_fwd_day(const FwdDayArgs a) {
     if (threadIdx.x == 0) {
         int g = -1;
         int32_t acc[5] = {0, 0, 0, 0, 0};
-        for (int w = 0; w <= kBlock / 32; ++w) {
-            const int gw = (w < kBlock / 32) ? red_s[w][0] : -2;
+        for (int w = 0; w <= NW; ++w) {
+            const int gw = (w < NW) ? red_s[w][0] : -2;
             if (gw != g) {
                 if (g >= 0) {
                     int32_t *cp = a.counts + ((size_t)g * a.ldP + t) * 4;
@@ -140,7 +147,7 @@ __global__ void __launch_bounds__(kBlock, 3) k_fwd_day(const FwdDayArgs a) {
                 g = gw;
                 for (int s2 = 0; s2 < 5; ++s2) acc[s2] = 0;
             }
-            if (w < kBlock / 32 && gw >= 0)
+            if (w < NW && gw >= 0)
                 for (int s2 = 0; s2 < 5; ++s2) acc[s2] += red_s[w][1 + s2];
         }
     }
@@ -445,14 +452,33 @@ cudaError_t launch_seed_ties(const SeedArgs &a, int I, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_fwd_day(const FwdDayArgs &a, int grid, cudaStream_t s) {
-    k_fwd_day<<<grid, kBlock, 0, s>>>(a);
+constexpr int kBitsBlock = 768;   // one block of 24 warps per SM when the bitmap lives in shared memory
+
+cudaError_t launch_fwd_day(const FwdDayArgs &a, int grid, bool smem_bits, cudaStream_t s) {
+    if (smem_bits) {
+        const size_t bytes = (size_t)a.ntiles * sizeof(uint32_t);
+        k_fwd_day<true, kBitsBlock, 1><<<grid, kBitsBlock, bytes, s>>>(a);
+    } else {
+        k_fwd_day<false, kBlock, GABM_MINBLOCKS><<<grid, kBlock, 0, s>>>(a);
+    }
     return cudaGetLastError();
 }
 
-int occupancy_fwd() {
+// Blocks per SM of the forward day kernel (global bitmap), or, for the
+// shared-memory bitmap of `ntiles` words, 0 if it does not fit.
+int occupancy_fwd(int ntiles, bool smem_bits) {
     int blocks = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_fwd_day, kBlock, 0);
+    if (smem_bits) {
+        const size_t bytes = (size_t)ntiles * sizeof(uint32_t);
+        int dev = 0, optin = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        if (bytes + 4096 > (size_t)optin) return 0;
+        cudaFuncSetAttribute(k_fwd_day<true, kBitsBlock, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_fwd_day<true, kBitsBlock, 1>, kBitsBlock, bytes);
+        return blocks;
+    }
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_fwd_day<false, kBlock, GABM_MINBLOCKS>, kBlock, 0);
     return blocks > 0 ? blocks : 1;
 }
 

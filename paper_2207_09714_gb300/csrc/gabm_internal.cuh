@@ -175,7 +175,7 @@ cudaError_t launch_seed_hist(const SeedArgs &a, int G, int grid_x, cudaStream_t 
 cudaError_t launch_seed_scan(const SeedArgs &a, int I, cudaStream_t s);
 cudaError_t launch_seed_mark(const SeedArgs &a, int G, int grid_x, cudaStream_t s);
 cudaError_t launch_seed_ties(const SeedArgs &a, int I, cudaStream_t s);
-cudaError_t launch_fwd_day(const FwdDayArgs &a, int grid, cudaStream_t s);
+cudaError_t launch_fwd_day(const FwdDayArgs &a, int grid, bool smem_bits, cudaStream_t s);
 // bits[d][tile] for days t0 .. t0 + ndays - 1: rows with 1 <= t - e < L (infectious on day t).
 cudaError_t launch_infectious_bits(const int16_t *e, int t0, int ndays, int L, int ntiles, uint32_t *bits,
                                    size_t day_stride, cudaStream_t s);
@@ -205,7 +205,7 @@ cudaError_t launch_rows_to_caller_f32(const float *src, float *dst, GraphRef gr,
                                       const int64_t *goff, int64_t n_rows, cudaStream_t s);
 cudaError_t launch_caller_to_rows_i16(const int16_t *src, int16_t *dst, GraphRef gr, const int32_t *rows,
                                       const int64_t *goff, int64_t n_rows, cudaStream_t s);
-int occupancy_fwd();
+int occupancy_fwd(int ntiles, bool smem_bits);
 int occupancy_bwd(int mode);
 
 }  // namespace gabm

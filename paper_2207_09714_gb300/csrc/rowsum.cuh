@@ -14,13 +14,34 @@
 
 namespace gabm {
 
-constexpr int kUnroll = 8;   // entries per lane loaded ahead of use
+#ifndef GABM_UNROLL
+#define GABM_UNROLL 8
+#endif
+#ifndef GABM_PIPE
+#define GABM_PIPE 1
+#endif
+#ifndef GABM_PREFETCH
+#define GABM_PREFETCH 0
+#endif
+#ifndef GABM_MINBLOCKS
+#define GABM_MINBLOCKS 3
+#endif
+constexpr int kUnroll = GABM_UNROLL;   // entries per lane loaded ahead of use
 
 __device__ __forceinline__ void kahan_add(float &s, float &c, float x) {
     const float y = __fsub_rn(x, c);
     const float t = __fadd_rn(s, y);
     c = __fsub_rn(__fsub_rn(t, s), y);
     s = t;
+}
+
+// kahan_add when `take`, else no change (selects instead of a branch).
+__device__ __forceinline__ void kahan_add_if(float &s, float &c, float x, bool take) {
+    const float y = __fsub_rn(x, c);
+    const float t = __fadd_rn(s, y);
+    const float cn = __fsub_rn(__fsub_rn(t, s), y);
+    s = take ? t : s;
+    c = take ? cn : c;
 }
 
 // Infectiousness of a neighbour exposed on day e_j, seen on day t: c[t - e_j] for
@@ -35,15 +56,49 @@ __device__ __forceinline__ bool marked(const uint32_t *__restrict__ bits, uint32
     return (__ldg(bits + (j >> 5)) >> (j & 31u)) & 1u;
 }
 
-__device__ __forceinline__ int next_tile(int *ctr, int lane) {
-    int v = 0;
-    if (lane == 0) v = atomicAdd(ctr, 1);
-    return __shfl_sync(0xffffffffu, v, 0);
-}
+// Hands tiles to a warp in runs claimed with one atomic each from the launch's
+// counter.  All warps hammering one counter with a tile per atomic serialises
+// on that address, so runs hold up to 16 tiles and shrink as the counter nears
+// the end (guided scheduling keeps the tail short); the next run is claimed
+// one run ahead so the atomic's latency is hidden.
+struct TileDispenser {
+    int *ctr;
+    int ntiles, nwarps, lane;
+    int next, end;     // current run [next, end)
+    int pend;          // lane 0: first tile of the claimed next run
+    int pend_len;      // its length (warp-uniform)
+
+    __device__ __forceinline__ int run_len(int from) const {
+        const int rem = ntiles - from;
+        return max(1, min(16, rem / (4 * nwarps)));
+    }
+    __device__ __forceinline__ void init(int *c, int nt, int nw, int ln) {
+        ctr = c;
+        ntiles = nt;
+        nwarps = nw;
+        lane = ln;
+        next = end = 0;
+        pend_len = run_len(0);
+        pend = (lane == 0) ? atomicAdd(ctr, pend_len) : 0;
+    }
+    // the next tile of this warp, or a value >= ntiles when the launch's tiles are gone
+    __device__ __forceinline__ int get() {
+        if (next >= end) {
+            const int base = __shfl_sync(0xffffffffu, pend, 0);
+            if (base >= ntiles) return ntiles;
+            next = base;
+            end = base + pend_len;
+            pend_len = run_len(end);
+            if (lane == 0) pend = atomicAdd(ctr, pend_len);
+        }
+        return next < ntiles ? next++ : ntiles;
+    }
+};
 
 // Ask L2 to fetch one slice (entries [p0, p1) of both arrays) ahead of use.
 // Slices start on 128-byte boundaries and hold multiples of 32 entries.
 __device__ __forceinline__ void prefetch_slice(const Sell &m, uint32_t p0, uint32_t p1, int lane) {
+    if (GABM_PREFETCH == 0) return;
     if (lane == 0 && p1 > p0) {
         const uint32_t bytes = (p1 - p0) * 4u;
         asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(m.col + p0), "r"(bytes) : "memory");
@@ -77,38 +132,91 @@ __device__ __forceinline__ void load_tile_rows(const Sell &m, const int16_t *e, 
     }
 }
 
+// Loads that are skipped (value left at `dflt`) when pred is false, written as
+// predicated PTX so that a batch of them issues without branches.
+__device__ __forceinline__ uint32_t ld_cs_if(const uint32_t *p, bool pred) {
+    uint32_t v = 0u;
+    asm("{ .reg .pred q; setp.ne.u32 q, %2, 0; @q ld.global.cs.u32 %0, [%1]; }" : "+r"(v) : "l"(p), "r"((uint32_t)pred));
+    return v;
+}
+__device__ __forceinline__ float ld_cs_if(const float *p, bool pred) {
+    float v = 0.f;
+    asm("{ .reg .pred q; setp.ne.u32 q, %2, 0; @q ld.global.cs.f32 %0, [%1]; }" : "+f"(v) : "l"(p), "r"((uint32_t)pred));
+    return v;
+}
+__device__ __forceinline__ float ld_if(const float *p, bool pred) {
+    float v = 0.f;
+    asm("{ .reg .pred q; setp.ne.u32 q, %2, 0; @q ld.global.f32 %0, [%1]; }" : "+f"(v) : "l"(p), "r"((uint32_t)pred));
+    return v;
+}
+__device__ __forceinline__ int ld_if(const int16_t *p, bool pred, int dflt) {
+    int v = dflt;
+    asm("{ .reg .pred q; setp.ne.u32 q, %2, 0; @q ld.global.s16 %0, [%1]; }" : "+r"(v) : "l"(p), "r"((uint32_t)pred));
+    return v;
+}
+
 // For this lane's row (when act), sum[a] = the sum of contribution a over the
-// row's entries in entry order, with compensated summation; f(j, w, out) writes
-// the NARR contributions of the entry with column j and weight w, and want[a]
-// says whether sum a is taken for this row.  Called by all 32 lanes.
+// row's entries in entry order, with compensated summation; f(j, w, valid, out)
+// writes the NARR contributions of the entry with column j and weight w (it is
+// also called for invalid entries -- padding, other rows' tails -- and must then
+// touch no memory beyond the slice), and want[a] says whether sum a is taken
+// for this row.  Called by all 32 lanes; the batch runs without branches.
 template <int NARR, class F>
 __device__ __forceinline__ void row_sums(const Sell &m, uint32_t p0, uint32_t len, bool act, int lane, F f,
                                          const bool (&want)[NARR], float (&sum)[NARR]) {
     float comp[NARR];
 #pragma unroll
     for (int a = 0; a < NARR; ++a) { sum[a] = 0.f; comp[a] = 0.f; }
+    const unsigned amask = __ballot_sync(0xffffffffu, act);
     const uint32_t kmax = __reduce_max_sync(0xffffffffu, act ? len : 0u);
-    for (uint32_t k0 = 0; k0 < kmax; k0 += kUnroll) {
-        uint32_t jv[kUnroll];
-        float wv[kUnroll];
+    // Mostly-active slices are read whole (padding and inactive rows included: every
+    // entry below kmax lies inside the slice); sparse ones with predicated loads.
+    const bool dense = __popc(amask) >= 24;
+    auto load_batch = [&](uint32_t k0, uint32_t (&jv)[kUnroll], float (&wv)[kUnroll]) {
 #pragma unroll
         for (int u = 0; u < kUnroll; ++u) {
             const uint32_t k = k0 + (uint32_t)u;
-            const bool v = act && k < len;
             const uint32_t idx = p0 + k * 32u + (uint32_t)lane;
-            jv[u] = v ? __ldcs(m.col + idx) : 0u;
-            wv[u] = v ? __ldcs(m.w + idx) : 0.f;
+            if (dense) {
+                const bool in = k < kmax;
+                jv[u] = ld_cs_if(m.col + idx, in);
+                wv[u] = ld_cs_if(m.w + idx, in);
+            } else {
+                const bool v = act && k < len;
+                jv[u] = ld_cs_if(m.col + idx, v);
+                wv[u] = ld_cs_if(m.w + idx, v);
+            }
         }
+    };
+    auto use_batch = [&](uint32_t k0, const uint32_t (&jv)[kUnroll], const float (&wv)[kUnroll]) {
 #pragma unroll
         for (int u = 0; u < kUnroll; ++u) {
             const uint32_t k = k0 + (uint32_t)u;
-            if (act && k < len) {
-                float out[NARR];
-                f(jv[u], wv[u], out);
+            const bool valid = act && k < len;
+            float out[NARR];
+            f(jv[u], wv[u], valid, out);
 #pragma unroll
-                for (int a = 0; a < NARR; ++a)
-                    if (want[a]) kahan_add(sum[a], comp[a], out[a]);
-            }
+            for (int a = 0; a < NARR; ++a) kahan_add_if(sum[a], comp[a], out[a], valid && want[a]);
+        }
+    };
+    if (GABM_PIPE) {
+        // the next batch is in flight while the current one is used
+        uint32_t ja[kUnroll], jb[kUnroll];
+        float wa[kUnroll], wb[kUnroll];
+        if (kmax > 0) load_batch(0, ja, wa);
+        for (uint32_t k0 = 0; k0 < kmax; k0 += 2 * kUnroll) {
+            if (k0 + kUnroll < kmax) load_batch(k0 + kUnroll, jb, wb);
+            use_batch(k0, ja, wa);
+            if (k0 + kUnroll >= kmax) break;
+            if (k0 + 2 * kUnroll < kmax) load_batch(k0 + 2 * kUnroll, ja, wa);
+            use_batch(k0 + kUnroll, jb, wb);
+        }
+    } else {
+        for (uint32_t k0 = 0; k0 < kmax; k0 += kUnroll) {
+            uint32_t jv[kUnroll];
+            float wv[kUnroll];
+            load_batch(k0, jv, wv);
+            use_batch(k0, jv, wv);
         }
     }
 }
