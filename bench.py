@@ -33,6 +33,10 @@ R0 = 2.5
 MORTALITY = 0.01
 N_SEED = 20
 TAU_EI, TAU_IR = 4, 7
+# batched ensemble: parameter sets sharing one contact graph
+BATCH_AGENTS = 500_000
+BATCH_SETS = 64
+BATCH_DAYS = 45
 
 
 def _peaks():
@@ -162,6 +166,149 @@ def trajectory_bytes(E, deg, T, L, n_rows, policy_store):
     return fwd, bwd, S_cnt, S_nnz
 
 
+def batched_trajectory_bytes(E, deg, T, L, n, B, l2_bytes):
+    """Algorithmic HBM bytes of the batched day launches (B sets sharing one graph) from the
+    final exposure days E [B, n] of every set: rows are read once for all sets, per-set
+    state once per set; a gathered per-agent array that fits in half of L2 costs nothing
+    per edge, else its B values per edge."""
+    E = E.astype(np.int64)
+    NEVER = 32767
+    seed = (E != NEVER) & (E < 0)
+    Ec = np.where(E == NEVER, T, E)
+    Ec = np.where(seed, -1, Ec)                      # [B, n] last susceptible day (>= t: S on day t)
+    last_any = Ec.max(axis=0)                        # a row is read while some set is susceptible
+    hist_r = np.bincount(np.clip(last_any[last_any >= 0], 0, T), minlength=T + 1)
+    hist_e = np.bincount(np.clip(last_any[last_any >= 0], 0, T), weights=deg[last_any >= 0], minlength=T + 1)
+    rows_t = np.cumsum(hist_r[::-1])[::-1]
+    nnz_t = np.cumsum(hist_e[::-1])[::-1]
+    flat = Ec[Ec >= 0]
+    hist_s = np.bincount(np.clip(flat, 0, T), minlength=T + 1)
+    S_t = np.cumsum(hist_s[::-1])[::-1]              # sum over sets of susceptible agents on day t
+    new = np.bincount(E[(E != NEVER) & (E >= 0)], minlength=T)[:T]
+    gath_f = 0.0 if n * B * 2 <= l2_bytes / 2 else 2.0 * B
+    gath_b = 0.0 if n * B * 4 <= l2_bytes / 2 else 4.0 * B
+    fwd = np.zeros(T)
+    bwd = np.zeros(T)
+    for t in range(T):
+        fwd[t] = (8.0 * nnz_t[t] + 8.0 * rows_t[t] + 2.0 * n * B + n + 2.0 * new[t] + 4.0 * S_t[t]
+                  + gath_f * nnz_t[t])
+        ring_reads = max(0, min(L - 1, T - 1 - t) - 1)
+        thr = min(T, max(t + 2 - L, 0))
+        b = 4.0 * S_t[t] + 2.0 * n * B + n + S_t[t] * (4.0 * ring_reads + 4.0 + 4.0)
+        if t + 1 < T:
+            b += 8.0 * nnz_t[thr] + 8.0 * rows_t[thr] + 4.0 * n * B + gath_b * nnz_t[thr]
+        bwd[t] = b
+    return fwd, bwd
+
+
+def bench_batched(args, stream, peak, peak_kind):
+    """B parameter sets on one shared graph, forward + MSE + backward per set: the
+    batched kernels (one launch per day phase, day loops replayed as CUDA graphs,
+    schedule from the autotuner) next to the plain path (one set at a time through
+    the autograd Function, eager launches)."""
+    import torch
+    from paper_2207_09714_gb300 import capi, synth
+    from paper_2207_09714_gb300.autograd import GabmFunction
+    B, T = BATCH_SETS, BATCH_DAYS
+    pop = synth.population_typed(BATCH_AGENTS, seed=0)
+    c = synth.infectiousness_table(TAU_EI, TAU_IR)
+    rng = np.random.default_rng(0)
+    R_np = np.repeat(rng.uniform(1.5, 4.0, (B, 1)), T, axis=1).astype(np.float32)
+    m_np = np.repeat(rng.uniform(0.005, 0.05, (B, 1)), T, axis=1).astype(np.float32)
+    R = torch.from_numpy(R_np).cuda()
+    m = torch.from_numpy(m_np).cuda()
+    S = torch.from_numpy(np.tile(synth.SUSCEPTIBILITY, (B, 1)).astype(np.float32)).cuda()
+    y = torch.from_numpy(np.stack([synth.target_curve(T, pop.n, seed=b) for b in range(B)])).cuda()
+    seeds = [N_SEED] * B
+    with torch.cuda.stream(stream):
+        ctx = capi.gabm_create([pop], capi.ModelDesc(TAU_EI, TAU_IR, c, seed=0), sets_per_graph=B, stream=stream)
+    D = torch.empty((B, T), dtype=torch.float64, device="cuda")
+    loss = torch.empty((B,), dtype=torch.float64, device="cuda")
+    gD = torch.empty((B, T), dtype=torch.float64, device="cuda")
+    dR = torch.empty((B, T), dtype=torch.float64, device="cuda")
+    dm = torch.empty((B, T), dtype=torch.float64, device="cuda")
+    dS = torch.empty((B, 9), dtype=torch.float64, device="cuda")
+
+    def step():
+        capi.gabm_forward(ctx, T, R, m, S, seeds, D=D)
+        capi.gabm_mse_loss(ctx, y, loss=loss, gD=gD)
+        capi.gabm_backward(ctx, gD, dR=dR, dm=dm, dS_age=dS)
+
+    step()
+    schedule = capi.gabm_autotune(ctx, 1)
+    steps = max(args.steps // 2, 2)
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    # per-kernel durations (events around each day launch: eager launches)
+    capi.gabm_set_profiling(ctx, True)
+    step()
+    f_ms, f_n = capi.gabm_get_profile(ctx, 0)
+    b_ms, b_n = capi.gabm_get_profile(ctx, 1)
+    capi.gabm_set_profiling(ctx, False)
+    E = capi.gabm_get_state(ctx)
+    l2 = torch.cuda.get_device_properties(0).L2_cache_size
+    fwd_b, bwd_b = batched_trajectory_bytes(E, pop.degrees().astype(np.float64), T, TAU_EI + TAU_IR, pop.n, B, l2)
+    f_gbs = fwd_b.sum() / (f_ms / 1e3) / 1e9
+    b_gbs = bwd_b.sum() / (b_ms / 1e3) / 1e9
+    both_gbs = (fwd_b.sum() + bwd_b.sum()) / ((f_ms + b_ms) / 1e3) / 1e9
+    counts = capi.gabm_forward(ctx, T, R, m, S, seeds, want_counts=True)[1].cpu().numpy()
+    attack = 1.0 - counts[:, -1, 0] / pop.n
+    del ctx
+
+    # plain: one parameter set at a time through the autograd Function, eager launches
+    os.environ["GABM_CUDA_GRAPHS"] = "0"
+    try:
+        with torch.cuda.stream(stream):
+            pctx = capi.gabm_create([pop], capi.ModelDesc(TAU_EI, TAU_IR, c, seed=0), stream=stream)
+    finally:
+        del os.environ["GABM_CUDA_GRAPHS"]
+
+    def plain_step():
+        with torch.cuda.stream(stream):
+            for b in range(B):
+                Rb = R[b:b + 1].clone().requires_grad_(True)
+                mb = m[b:b + 1].clone().requires_grad_(True)
+                Sb = S[b:b + 1].clone().requires_grad_(True)
+                Db = GabmFunction.apply(pctx, Rb, mb, Sb, [N_SEED])
+                ((Db - y[b:b + 1]) ** 2).mean().backward()
+
+    plain_step()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    plain_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    plain_ms = e0.elapsed_time(e1)
+    units = B * pop.n * T
+    return {
+        "workload": f"one shared {pop.n}-agent typed contact graph, {B} parameter sets (R ~ U[1.5, 4.0], "
+                    f"m ~ U[0.005, 0.05]), {T} days, forward + MSE + backward of every set",
+        "n_agents": pop.n, "nnz": pop.nnz, "sets": B, "days": T,
+        "value": units / (ms / 1e3), "unit": "agent-days/s", "ms_per_step": ms, "steps": steps,
+        "schedule": schedule, "attack_rate_range": [float(attack.min()), float(attack.max())],
+        "plain": {"value": units / (plain_ms / 1e3), "ms_per_step": plain_ms,
+                  "path": "one set at a time: GabmFunction (torch.autograd) over the single-set kernels, "
+                          "eager launches, no CUDA graph"},
+        "speedup_vs_plain": plain_ms / ms,
+        "roofline": {"bound": "hbm", "kernel": "k_bwd_day_b" if b_ms >= f_ms else "k_fwd_day_b",
+                     "achieved": b_gbs if b_ms >= f_ms else f_gbs, "peak": peak, "unit": "GB/s",
+                     "frac": (b_gbs if b_ms >= f_ms else f_gbs) / peak, "peak_source": peak_kind,
+                     "fwd_day": {"achieved": f_gbs, "launches": f_n, "ms_total": f_ms,
+                                 "alg_bytes_per_launch": fwd_b.sum() / T},
+                     "bwd_day": {"achieved": b_gbs, "launches": b_n, "ms_total": b_ms,
+                                 "alg_bytes_per_launch": bwd_b.sum() / T},
+                     "fwd_plus_bwd_frac": both_gbs / peak},
+    }
+
+
 def run_reference(args, world, rank):
     """The FP64 CPU oracle as it stands, on a bounded sample of the workload."""
     if rank != 0:
@@ -232,6 +379,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--policy", default="store", choices=["store", "recompute"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -375,6 +523,10 @@ def main():
     d2h = (Dh.numel() * 8 + lh.numel() * 8 + gDh.numel() * 8 + dRh.numel() * 8 + dmh.numel() * 8 + dSh.numel() * 8)
 
     cur, peak_mem = capi.gabm_mem_stats(ctx)
+    del ctx
+    batched = None
+    if not args.no_batched:
+        batched = bench_batched(args, stream, peak, peak_kind)
     if rank != 0:
         return
     cpu = None
@@ -403,6 +555,7 @@ def main():
         "clocks": clk.summary(),
         "peak_hbm_bytes": peak_mem,
         "cpu_baseline": cpu,
+        "batched": batched,
     }
     print(json.dumps(line), flush=True)
     if dist is not None:

@@ -162,6 +162,34 @@ gabm_status gabm_set_state(gabm_ctx *ctx, int day, const int16_t *e_in, int mem_
  * not susceptible on day t.  Needs GABM_STORE_LAMBDA and t run by the forward. */
 gabm_status gabm_get_lambda(gabm_ctx *ctx, int t, float *lam_out, int mem_space);
 
+/* Kernel schedule of a ctx.  Schedules change how rows and parameter sets map
+ * onto lanes, never what is summed or in which order, so every schedule gives
+ * bitwise the same results.
+ *   fwd_sets_per_lane, bwd_sets_per_lane: sets_per_graph > 1 only -- each lane
+ *     carries 2, 4 or 8 parameter sets of a row (Bp / that many lanes share a
+ *     row, Bp = sets_per_graph rounded up to a power of two; at most Bp);
+ *   fwd_smem_bitmap: sets_per_graph == 1 only -- 1 keeps the day's bitmap of
+ *     infectious agents in shared memory (when it fits), 0 reads it through L1.
+ * Fields that do not apply are reported as 0 and ignored on input. */
+typedef struct {
+    int fwd_sets_per_lane;
+    int bwd_sets_per_lane;
+    int fwd_smem_bitmap;
+} gabm_schedule;
+
+gabm_status gabm_get_schedule(const gabm_ctx *ctx, gabm_schedule *out);
+/* GABM_EINVAL (schedule unchanged) for a value this build has no kernel for. */
+gabm_status gabm_set_schedule(gabm_ctx *ctx, const gabm_schedule *sched);
+
+/* Autotuner: times every schedule this build has for the ctx on the ctx's own
+ * workload -- the last forward's T, parameters and seeds, and a backward over
+ * the same days -- `repetitions` times each (>= 1), keeps the fastest forward
+ * and backward schedules, and re-runs that forward so the state, the stored
+ * lambdas and D are as before the call (the trajectory does not depend on the
+ * schedule).  Needs a preceding gabm_forward that started from seeding
+ * (GABM_ESTATE otherwise).  Synchronises the ctx stream. */
+gabm_status gabm_autotune(gabm_ctx *ctx, int repetitions);
+
 /* Device bytes the ctx holds now and at most so far. */
 gabm_status gabm_mem_stats(const gabm_ctx *ctx, size_t *current, size_t *peak);
 

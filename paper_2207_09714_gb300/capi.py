@@ -51,6 +51,11 @@ class _ModelDesc(ctypes.Structure):
                 ("lambda_policy", ctypes.c_int), ("seed", ctypes.c_uint64), ("agent_order", ctypes.c_int)]
 
 
+class _Schedule(ctypes.Structure):
+    _fields_ = [("fwd_sets_per_lane", ctypes.c_int), ("bwd_sets_per_lane", ctypes.c_int),
+                ("fwd_smem_bitmap", ctypes.c_int)]
+
+
 _lib = None
 _lock = threading.Lock()
 
@@ -88,9 +93,13 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         L.gabm_seed_state_noalloc.argtypes = [u64, i64, i32, P, i32, P, P]
         L.gabm_seed_state_noalloc.restype = ctypes.c_int
         L.gabm_noalloc_last_error.restype = ctypes.c_char_p
+        L.gabm_get_schedule.argtypes = [P, ctypes.POINTER(_Schedule)]
+        L.gabm_set_schedule.argtypes = [P, ctypes.POINTER(_Schedule)]
+        L.gabm_autotune.argtypes = [P, i32]
         for name in ("gabm_create", "gabm_forward", "gabm_mse_loss", "gabm_backward", "gabm_get_state",
                      "gabm_set_state", "gabm_get_lambda", "gabm_mem_stats", "gabm_set_profiling",
-                     "gabm_get_profile", "gabm_philox"):
+                     "gabm_get_profile", "gabm_philox", "gabm_get_schedule", "gabm_set_schedule",
+                     "gabm_autotune"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
         return L
@@ -333,6 +342,23 @@ def gabm_mem_stats(ctx: GabmCtx):
     cur, peak = ctypes.c_size_t(), ctypes.c_size_t()
     _check(load_library().gabm_mem_stats(ctx.handle, ctypes.byref(cur), ctypes.byref(peak)), ctx.handle)
     return int(cur.value), int(peak.value)
+
+
+def gabm_get_schedule(ctx: GabmCtx) -> dict:
+    sc = _Schedule()
+    _check(load_library().gabm_get_schedule(ctx.handle, ctypes.byref(sc)), ctx.handle)
+    return {k: int(getattr(sc, k)) for k, _ in _Schedule._fields_}
+
+
+def gabm_set_schedule(ctx: GabmCtx, fwd_sets_per_lane=0, bwd_sets_per_lane=0, fwd_smem_bitmap=0):
+    sc = _Schedule(int(fwd_sets_per_lane), int(bwd_sets_per_lane), int(fwd_smem_bitmap))
+    _check(load_library().gabm_set_schedule(ctx.handle, ctypes.byref(sc)), ctx.handle)
+
+
+def gabm_autotune(ctx: GabmCtx, repetitions: int = 1) -> dict:
+    """Time every schedule on the last forward's workload, keep the fastest; returns it."""
+    _check(load_library().gabm_autotune(ctx.handle, int(repetitions)), ctx.handle)
+    return gabm_get_schedule(ctx)
 
 
 def gabm_launch_count(ctx: GabmCtx) -> int:

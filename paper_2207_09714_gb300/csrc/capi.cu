@@ -28,6 +28,10 @@ struct gabm_ctx {
     cudaStream_t stream = nullptr;
     int device = 0, num_sms = 0;
     int G = 0, B = 1, I = 0;
+    int Bp = 1;                     // row stride of per-agent arrays: B rounded up to a power of two (1 if B == 1)
+    bool batched = false;           // B > 1: the set-batched kernels over row-compressed edges
+    bool kahan_b = false;           // batched sums: compensated (some row longer than kPlainSumMaxDegree)
+    int spl_fwd = 2, spl_bwd = 2;   // batched schedules: sets per lane of the forward / backward day kernels
     int tau_EI = 0, tau_IR = 0, L = 0;
     float c[kMaxL] = {0};
     uint64_t seed = 0;
@@ -45,6 +49,15 @@ struct gabm_ctx {
     uint32_t *t_slice_ptr = nullptr, *t_row_len = nullptr, *t_scol = nullptr;
     float *t_sw = nullptr;
     int64_t sell_entries = 0;
+    // row-compressed edges (batched kernels): in-edges, and out-edges when not symmetric
+    uint32_t *csr_rowptr = nullptr, *csr_col = nullptr, *t_csr_rowptr = nullptr, *t_csr_col = nullptr;
+    float *csr_w = nullptr, *t_csr_w = nullptr;
+    uint32_t *rbits = nullptr;      // [2][ntiles] rows susceptible in some set (batched backward)
+    double *Pc = nullptr;           // [Tcap][G][max_chunks][9][Bp] first-level gradient sums (batched)
+    int max_chunks = 0, max_graph_tiles = 0;
+    uint8_t *tile_new = nullptr;    // [Tcap][ntiles][Bp] exposures per tile, set and day (batched)
+    int32_t *hist0 = nullptr;       // [I][L+2] exposure-day histogram of the forward's starting state
+    int32_t *newinf = nullptr;      // [I][Tcap] exposures per instance and day
     int sigma = 1024;
     uint8_t *age = nullptr;
     int32_t *d_row0 = nullptr, *d_rows = nullptr, *d_tile0 = nullptr, *d_ntiles = nullptr;
@@ -72,6 +85,9 @@ struct gabm_ctx {
 
     int t0_next = 0;
     bool resumed = false;
+    bool last_from_seeding = false;  // the last forward started from seeding (not from gabm_set_state)
+    bool gD_staged = false;
+    std::vector<int32_t> last_seeds;  // n_seed of the last seeded forward
     int T_last = -1;
     int lam_from = -1;
 
@@ -84,6 +100,18 @@ struct gabm_ctx {
     std::unordered_map<void *, size_t> sizes;
     long fail_alloc_after = -1, alloc_calls = 0;
     uint64_t launches = 0;
+
+    // day loops captured as CUDA graphs (GABM_CUDA_GRAPHS=0: launched eagerly)
+    struct LoopGraph {
+        cudaGraphExec_t exec = nullptr;
+        int t0 = -1, T = -1;
+        uint64_t generation = 0;
+        uint64_t kernels = 0;      // kernel launches in the graph
+    };
+    bool use_graphs = true;
+    cudaStream_t cap_stream = nullptr;
+    LoopGraph loop_graph[2];
+    uint64_t buffer_generation = 0;   // bumped whenever per-day buffers are reallocated
 
     bool profiling = false;
     std::vector<cudaEvent_t> ev[2];
@@ -369,17 +397,23 @@ gabm_status ensure_days(gabm_ctx *c, int T) {
     dfree(c, c->lam); dfree(c, c->counts); dfree(c, c->newRM); dfree(c, c->newRM_b);
     dfree(c, c->D); dfree(c, c->gD); dfree(c, c->y); dfree(c, c->P); dfree(c, c->Q);
     dfree(c, c->R); dfree(c, c->m);
-    dfree(c, c->dR_s); dfree(c, c->dm_s); dfree(c, c->tile_ctr); dfree(c, c->bits);
+    dfree(c, c->dR_s); dfree(c, c->dm_s); dfree(c, c->tile_ctr); dfree(c, c->bits); dfree(c, c->Pc);
+    dfree(c, c->tile_new); dfree(c, c->newinf);
     c->Tcap = 0;
     const size_t IT = (size_t)c->I * cap;
-    if (c->policy == GABM_STORE_LAMBDA) TRY(dalloc(c, &c->lam, (size_t)cap * c->n_rows));
+    if (c->policy == GABM_STORE_LAMBDA) TRY(dalloc(c, &c->lam, (size_t)cap * c->n_rows * c->Bp));
     TRY(dalloc(c, &c->counts, IT * 4));
     TRY(dalloc(c, &c->newRM, IT));
     TRY(dalloc(c, &c->newRM_b, IT));
     TRY(dalloc(c, &c->D, IT));
     TRY(dalloc(c, &c->gD, IT));
     TRY(dalloc(c, &c->y, IT));
-    TRY(dalloc(c, &c->P, (size_t)cap * c->ntiles * kAges));
+    TRY(dalloc(c, &c->P, (size_t)cap * c->ntiles * kAges * c->Bp));
+    if (c->batched) {
+        TRY(dalloc(c, &c->Pc, (size_t)cap * c->G * c->max_chunks * kAges * c->Bp));
+        TRY(dalloc(c, &c->tile_new, (size_t)cap * c->ntiles * c->Bp));
+        TRY(dalloc(c, &c->newinf, IT));
+    }
     TRY(dalloc(c, &c->Q, IT * kAges));
     TRY(dalloc(c, &c->R, IT));
     TRY(dalloc(c, &c->m, IT));
@@ -391,6 +425,7 @@ gabm_status ensure_days(gabm_ctx *c, int T) {
     c->Tcap = cap;
     c->T_last = -1;
     c->lam_from = -1;
+    c->buffer_generation++;
     return GABM_OK;
 }
 
@@ -450,8 +485,312 @@ gabm_status check_ms(gabm_ctx *c, int ms) {
     return GABM_OK;
 }
 
+SetLayout set_layout(const gabm_ctx *c) {
+    SetLayout sl;
+    sl.B = c->B;
+    sl.Bp = c->Bp;
+    sl.n_total = c->n_total;
+    return sl;
+}
+
+Csr csr_view(const gabm_ctx *c, bool out_edges) {
+    Csr m;
+    m.rowptr = out_edges ? c->t_csr_rowptr : c->csr_rowptr;
+    m.col = out_edges ? c->t_csr_col : c->csr_col;
+    m.w = out_edges ? c->t_csr_w : c->csr_w;
+    return m;
+}
+
+// Day loop of the forward for B > 1 sets per graph (parameters already staged).
+gabm_status forward_days_batched(gabm_ctx *c, int t0, int T, cudaStream_t s) {
+    const size_t nb = (size_t)c->n_rows * c->Bp;
+    FwdBatchArgs a;
+    a.m = csr_view(c, false);
+    a.age = c->age;
+    a.gr = graph_ref(c);
+    a.e = c->e;
+    a.R = c->R;
+    a.S = c->S;
+    a.ldP = c->Tcap;
+    a.ntiles = c->ntiles;
+    a.tau_EI = c->tau_EI;
+    a.L = c->L;
+    a.B = c->B;
+    CK(cudaMemsetAsync(c->hist0, 0, sizeof(int32_t) * (size_t)c->I * (c->L + 2), s));
+    CK(cudaMemsetAsync(c->newinf, 0, sizeof(int32_t) * (size_t)c->I * c->Tcap, s));
+    LAUNCH(launch_exposure_hist_b(c->e, graph_ref(c), c->n_rows, c->B, c->Bp, t0, c->L, c->hist0, s));
+    a.seed = c->seed;
+    for (int k = 0; k < kMaxL; ++k) a.c[k] = k < c->L ? c->c[k] : 0.f;
+    if (t0 < T)
+        LAUNCH(launch_infectious_bits_b(c->e, c->Bp, t0, c->L, c->ntiles, c->bits + (size_t)t0 * c->ntiles, s));
+    for (int t = t0; t < T; ++t) {
+        a.t = t;
+        a.lam_out = c->policy == GABM_STORE_LAMBDA ? c->lam + (size_t)t * nb : nullptr;
+        a.tile_ctr = c->tile_ctr + t;
+        a.bits_cur = c->bits + (size_t)t * c->ntiles;
+        a.bits_next = c->bits + (size_t)(t + 1) * c->ntiles;
+        a.tile_new = c->tile_new + (size_t)t * c->ntiles * c->Bp;
+        prof_begin(c, 0);
+        LAUNCH(launch_fwd_day_b(a, c->Bp, c->spl_fwd, c->kahan_b, c->grid_fwd, s));
+        prof_end(c, 0);
+    }
+    LAUNCH(launch_counts_b(c->tile_new, c->ntiles, c->d_tile0, c->d_ntiles, c->d_rows, c->G, c->B, c->Bp,
+                           c->max_graph_tiles, t0, T, c->Tcap, c->tau_EI, c->L, c->hist0, c->newinf, c->counts,
+                           c->newRM, s));
+    return GABM_OK;
+}
+
+// Reverse sweep for B > 1 sets per graph (gD already staged; r and counters cleared).
+gabm_status backward_days_batched(gabm_ctx *c, int T, cudaStream_t s) {
+    const int ld = c->Tcap;
+    const size_t nb = (size_t)c->n_rows * c->Bp;
+    CK(cudaMemsetAsync(c->rbits, 0, sizeof(uint32_t) * 2 * (size_t)c->ntiles, s));
+    BwdBatchArgs a;
+    a.m = csr_view(c, true);
+    a.age = c->age;
+    a.gr = graph_ref(c);
+    a.E = c->e;
+    a.ring = c->ring;
+    a.ring_stride = nb;
+    a.A = c->A;
+    a.R = c->R;
+    a.m_t = c->m;
+    a.S = c->S;
+    a.gD = c->gD;
+    a.ldP = ld;
+    a.ntiles = c->ntiles;
+    a.T = T;
+    a.tau_EI = c->tau_EI;
+    a.L = c->L;
+    a.B = c->B;
+    a.seed = c->seed;
+    for (int k = 0; k < kMaxL; ++k) a.c[k] = k < c->L ? c->c[k] : 0.f;
+    const int Lm1 = c->L - 1;
+    for (int t = T - 1; t >= 0; --t) {
+        a.t = t;
+        a.lam_t = c->lam + (size_t)t * nb;
+        a.r_next = c->r + (size_t)((t + 1) & 1) * nb;
+        a.r_cur = c->r + (size_t)(t & 1) * nb;
+        a.rbits_next = c->rbits + (size_t)((t + 1) & 1) * c->ntiles;
+        a.rbits_cur = c->rbits + (size_t)(t & 1) * c->ntiles;
+        a.P_t = c->P + (size_t)t * c->ntiles * kAges * c->Bp;
+        for (int k = 0; k < kMaxL; ++k) a.ring_slot[k] = (k >= 1 && k < c->L) ? (t + k) % Lm1 : 0;
+        a.tile_ctr = c->tile_ctr + ld + t;
+        prof_begin(c, 1);
+        LAUNCH(launch_bwd_day_b(a, c->Bp, c->spl_bwd, c->kahan_b, c->grid_bwd, s));
+        prof_end(c, 1);
+    }
+    LAUNCH(launch_bwd_reduce_b(c->P, c->ntiles, c->d_tile0, c->d_ntiles, c->G, c->B, c->Bp, T, c->Pc, c->max_chunks,
+                               c->Q, s));
+    return GABM_OK;
+}
+
+// Day loop of the forward, one set per graph (parameters staged, seeding done).
+gabm_status forward_days_plain(gabm_ctx *c, int t0, int T, cudaStream_t s) {
+    const int ld = c->Tcap;
+    FwdDayArgs a;
+    a.m = sell_view(c, false);
+    a.age = c->age;
+    a.gr = graph_ref(c);
+    a.e = c->e;
+    a.R = c->R;
+    a.S = c->S;
+    a.ldP = ld;
+    a.counts = c->counts;
+    a.newRM = c->newRM;
+    a.ntiles = c->ntiles;
+    a.tau_EI = c->tau_EI;
+    a.L = c->L;
+    a.seed = c->seed;
+    for (int k = 0; k < kMaxL; ++k) a.c[k] = k < c->L ? c->c[k] : 0.f;
+    if (t0 < T) LAUNCH(launch_infectious_bits(c->e, t0, 1, c->L, c->ntiles, c->bits + (size_t)t0 * c->ntiles,
+                                              (size_t)c->ntiles, s));
+    for (int t = t0; t < T; ++t) {
+        a.t = t;
+        a.lam_out = c->policy == GABM_STORE_LAMBDA ? c->lam + (size_t)t * c->n_rows : nullptr;
+        a.tile_ctr = c->tile_ctr + t;
+        a.bits_cur = c->bits + (size_t)t * c->ntiles;
+        a.bits_next = c->bits + (size_t)(t + 1) * c->ntiles;
+        prof_begin(c, 0);
+        LAUNCH(launch_fwd_day(a, c->grid_fwd, c->smem_bits, s));
+        prof_end(c, 0);
+    }
+    return GABM_OK;
+}
+
+// Reverse sweep, one set per graph (gD staged; r and counters cleared).
+gabm_status backward_days_plain(gabm_ctx *c, int T, cudaStream_t s) {
+    const int ld = c->Tcap;
+    BwdDayArgs a;
+    const int mode = c->policy == GABM_STORE_LAMBDA ? kBwdStore : (c->symmetric ? kBwdFused : kBwdSplit);
+    a.mode = mode == kBwdSplit ? kBwdStore : mode;
+    a.m = sell_view(c, true);
+    a.age = c->age;
+    a.gr = graph_ref(c);
+    a.E = c->e;
+    a.ring = c->ring;
+    a.ring_stride = (size_t)c->n_rows;
+    a.A = c->A;
+    a.R = c->R;
+    a.m_t = c->m;
+    a.S = c->S;
+    a.gD = c->gD;
+    a.ldP = ld;
+    a.newRM = c->newRM_b;
+    a.ntiles = c->ntiles;
+    a.T = T;
+    a.tau_EI = c->tau_EI;
+    a.L = c->L;
+    a.seed = c->seed;
+    for (int k = 0; k < kMaxL; ++k) a.c[k] = k < c->L ? c->c[k] : 0.f;
+    const int Lm1 = c->L - 1;
+    if (mode != kBwdStore)   // every day's infectious rows, from the final state
+        LAUNCH(launch_infectious_bits(c->e, 0, T, c->L, c->ntiles, c->bits, (size_t)c->ntiles, s));
+    for (int t = T - 1; t >= 0; --t) {
+        a.bits_t = mode != kBwdStore ? c->bits + (size_t)t * c->ntiles : nullptr;
+        a.t = t;
+        a.lam_t = mode == kBwdStore ? c->lam + (size_t)t * c->n_rows : (mode == kBwdSplit ? c->lam_tmp : nullptr);
+        if (mode == kBwdSplit)
+            LAUNCH(launch_lam_day(sell_view(c, false), c->e, c->bits + (size_t)t * c->ntiles, graph_ref(c), t, c->L,
+                                  c->ntiles, c->c_dev, c->lam_tmp, c->grid_bwd, s));
+        a.r_next = c->r + (size_t)((t + 1) & 1) * c->n_rows;
+        a.r_cur = c->r + (size_t)(t & 1) * c->n_rows;
+        a.P_t = c->P + (size_t)t * c->ntiles * kAges;
+        for (int k = 0; k < kMaxL; ++k) a.ring_slot[k] = (k >= 1 && k < c->L) ? (t + k) % Lm1 : 0;
+        a.tile_ctr = c->tile_ctr + ld + t;
+        prof_begin(c, 1);
+        LAUNCH(launch_bwd_day(a, c->grid_bwd, s));
+        prof_end(c, 1);
+    }
+    LAUNCH(launch_bwd_reduce(c->P, c->ntiles, ld, c->d_tile0, c->d_ntiles, T, c->I, c->Q, s));
+    return GABM_OK;
+}
+
+enum { kLoopForward = 0, kLoopBackward = 1 };
+
+gabm_status day_loop(gabm_ctx *c, int which, int t0, int T, cudaStream_t s) {
+    if (which == kLoopForward) return c->batched ? forward_days_batched(c, t0, T, s) : forward_days_plain(c, t0, T, s);
+    return c->batched ? backward_days_batched(c, T, s) : backward_days_plain(c, T, s);
+}
+
+void drop_graph(gabm_ctx::LoopGraph &g) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    g = gabm_ctx::LoopGraph();
+}
+
+// Runs a day loop on the ctx stream: eagerly, or as a CUDA graph captured once
+// per (loop, t0, T, buffer generation) and replayed on later calls.
+gabm_status run_day_loop(gabm_ctx *c, int which, int t0, int T) {
+    if (!c->use_graphs || c->profiling) return day_loop(c, which, t0, T, c->stream);
+    gabm_ctx::LoopGraph &g = c->loop_graph[which];
+    if (!g.exec || g.t0 != t0 || g.T != T || g.generation != c->buffer_generation) {
+        drop_graph(g);
+        if (!c->cap_stream) CK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+        CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+        const uint64_t before = c->launches;
+        gabm_status st = day_loop(c, which, t0, T, c->cap_stream);
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamEndCapture(c->cap_stream, &graph);
+        const uint64_t captured = c->launches - before;
+        c->launches = before;
+        if (st != GABM_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return st;
+        }
+        if (e != cudaSuccess) return fail(c, GABM_ECUDA, "stream capture: %s", cudaGetErrorString(e));
+        e = cudaGraphInstantiate(&g.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            g.exec = nullptr;
+            return fail(c, GABM_ECUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e));
+        }
+        g.t0 = t0;
+        g.T = T;
+        g.generation = c->buffer_generation;
+        g.kernels = captured;
+    }
+    CK(cudaGraphLaunch(g.exec, c->stream));
+    c->launches += g.kernels;
+    return GABM_OK;
+}
+
+// Forward over days t0..T-1 from the staged parameters: clears the per-day
+// outputs, seeds the state (from last_seeds) when `seeding`, runs the day loop.
+gabm_status forward_core(gabm_ctx *c, int t0, int T, bool seeding) {
+    const int ld = c->Tcap;
+    cudaStream_t s = c->stream;
+    CK(cudaMemsetAsync(c->counts, 0, sizeof(int32_t) * 4 * (size_t)c->I * ld, s));
+    CK(cudaMemsetAsync(c->newRM, 0, sizeof(int32_t) * (size_t)c->I * ld, s));
+    CK(cudaMemsetAsync(c->D, 0, sizeof(double) * (size_t)c->I * ld, s));
+    CK(cudaMemsetAsync(c->tile_ctr, 0, sizeof(int) * (size_t)ld, s));
+
+    if (seeding) {
+        CK(cudaMemcpyAsync(c->d_nseed, c->last_seeds.data(), sizeof(int32_t) * c->I, cudaMemcpyHostToDevice, s));
+        const int grid = (int)std::min<int64_t>((c->n_rows + 255) / 256, 65535);
+        LAUNCH(launch_init_state(c->e, c->d_row0, c->d_rows, c->G, c->n_rows, c->B, c->Bp, grid, s));
+        SeedArgs sa;
+        sa.row0 = c->d_row0;
+        sa.rows = c->d_rows;
+        sa.orig_id = c->d_orig_id;
+        sa.e = c->e;
+        sa.B = c->B;
+        sa.Bp = c->Bp;
+        sa.st = c->seedst;
+        sa.hist = c->hist;
+        sa.ties = c->ties;
+        sa.seed = c->seed;
+        sa.tau_EI = c->tau_EI;
+        int max_rows = 1;
+        for (int g = 0; g < c->G; ++g) max_rows = std::max(max_rows, c->h_rows[g]);
+        const int gx = std::max(1, std::min((max_rows + 255) / 256, 4 * c->num_sms / std::max(1, c->I) + 1));
+        LAUNCH(launch_seed_reset(c->seedst, c->d_nseed, c->I, s));
+        for (int pass = 0; pass < 3; ++pass) {
+            sa.pass = pass;
+            LAUNCH(launch_seed_hist(sa, c->I, gx, s));
+            LAUNCH(launch_seed_scan(sa, c->I, s));
+        }
+        LAUNCH(launch_seed_mark(sa, c->I, gx, s));
+        LAUNCH(launch_seed_ties(sa, c->I, s));
+    }
+
+    TRY(run_day_loop(c, kLoopForward, t0, T));
+    return GABM_OK;
+}
+
+// Reverse sweep over days T-1..0 from the staged gD (per-tile sums into Q).
+gabm_status backward_core(gabm_ctx *c, int T) {
+    const int ld = c->Tcap;
+    cudaStream_t s = c->stream;
+    CK(cudaMemsetAsync(c->r, 0, sizeof(float) * 2 * (size_t)c->n_rows * c->Bp, s));
+    CK(cudaMemsetAsync(c->newRM_b, 0, sizeof(int32_t) * (size_t)c->I * ld, s));
+    CK(cudaMemsetAsync(c->tile_ctr + ld, 0, sizeof(int) * (size_t)ld, s));
+    if (!c->batched && c->policy != GABM_STORE_LAMBDA && !c->symmetric && !c->lam_tmp)
+        TRY(dalloc(c, &c->lam_tmp, (size_t)c->n_rows));
+    return run_day_loop(c, kLoopBackward, 0, T);
+}
+
+// Grid sizes for the current schedule (resident blocks per SM x SMs, at most one warp per tile).
+void apply_schedule(gabm_ctx *c) {
+    const int mode = c->policy == GABM_STORE_LAMBDA ? kBwdStore : (c->symmetric ? kBwdFused : kBwdSplit);
+    if (c->batched) {
+        c->grid_fwd = c->num_sms * occupancy_fwd_b(c->Bp, c->spl_fwd, c->kahan_b);
+        c->grid_bwd = c->num_sms * occupancy_bwd_b(c->Bp, c->spl_bwd, c->kahan_b);
+    } else {
+        const int bps = c->smem_bits ? occupancy_fwd(c->ntiles, true) : 0;
+        if (c->smem_bits && bps <= 0) c->smem_bits = false;
+        c->grid_fwd = c->num_sms * (c->smem_bits ? bps : occupancy_fwd(c->ntiles, false));
+        c->grid_bwd = c->num_sms * occupancy_bwd(mode);
+    }
+    const int max_grid = (c->ntiles + kBlock / 32 - 1) / (kBlock / 32);
+    if (!c->smem_bits && c->grid_fwd > max_grid) c->grid_fwd = max_grid;
+    if (c->grid_bwd > max_grid) c->grid_bwd = max_grid;
+    for (auto &g : c->loop_graph) drop_graph(g);   // captured launches carry the old schedule
+}
+
 void destroy_all(gabm_ctx *c) {
     if (c->stream) cudaStreamSynchronize(c->stream);
+    for (auto &g : c->loop_graph) drop_graph(g);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     for (auto &kv : c->sizes) cudaFree(kv.first);
     c->sizes.clear();
     for (int k = 0; k < 2; ++k)
@@ -473,8 +812,10 @@ gabm_status gabm_create(const gabm_graph_desc *graphs, int num_graphs, int sets_
     *out = nullptr;
     if (!graphs || num_graphs < 1 || num_graphs > 65535) return fail(nullptr, GABM_EINVAL, "need 1..65535 graphs");
     if (sets_per_graph < 1) return fail(nullptr, GABM_EINVAL, "sets_per_graph must be >= 1");
-    if (sets_per_graph != 1) return fail(nullptr, GABM_EUNSUPPORTED, "sets_per_graph > 1 is not implemented in this build");
+    if (sets_per_graph > kMaxSets) return fail(nullptr, GABM_EUNSUPPORTED, "sets_per_graph > %d", kMaxSets);
     TRY(validate_model(model));
+    if (sets_per_graph > 1 && model->lambda_policy != GABM_STORE_LAMBDA)
+        return fail(nullptr, GABM_EUNSUPPORTED, "sets_per_graph > 1 needs GABM_STORE_LAMBDA in this build");
 
     // ---- host side: validate, concatenate, transpose ----
     std::vector<HostGraph> hg((size_t)num_graphs);
@@ -561,9 +902,15 @@ gabm_status gabm_create(const gabm_graph_desc *graphs, int num_graphs, int sets_
                     (memcmp(h_w.data(), t_w.data(), sizeof(float) * h_w.size()) == 0);
     }
     HostSell sell_in, sell_out;
-    if (!build_sell(h_rowptr, h_col, h_w, n_rows, sell_in) ||
-        (!symmetric && !build_sell(t_rowptr, t_col, t_w, n_rows, sell_out)))
+    const bool batched = sets_per_graph > 1;
+    if (!batched && (!build_sell(h_rowptr, h_col, h_w, n_rows, sell_in) ||
+                     (!symmetric && !build_sell(t_rowptr, t_col, t_w, n_rows, sell_out))))
         return fail(nullptr, GABM_EUNSUPPORTED, "SELL-32 layout needs >= 2^32 entries");
+    uint32_t max_degree = 0;
+    for (int64_t r = 0; r < n_rows; ++r) {
+        max_degree = std::max(max_degree, h_rowptr[r + 1] - h_rowptr[r]);
+        max_degree = std::max(max_degree, t_rowptr[r + 1] - t_rowptr[r]);
+    }
 
     // ---- device side ----
     gabm_ctx *c = new gabm_ctx();
@@ -571,6 +918,27 @@ gabm_status gabm_create(const gabm_graph_desc *graphs, int num_graphs, int sets_
     c->G = num_graphs;
     c->B = sets_per_graph;
     c->I = num_graphs * sets_per_graph;
+    c->batched = batched;
+    c->Bp = 1;
+    if (batched) {
+        c->Bp = 2;
+        while (c->Bp < sets_per_graph) c->Bp *= 2;
+    }
+    c->kahan_b = max_degree > (uint32_t)kPlainSumMaxDegree;
+    {
+        int mx = 1;
+        for (int g = 0; g < num_graphs; ++g) mx = std::max(mx, ntl[g]);
+        c->max_chunks = (mx + kReduceChunkTiles - 1) / kReduceChunkTiles;
+        c->max_graph_tiles = mx;
+    }
+    if (batched) {
+        // widest vectors first: eight sets per lane keeps 32 / (Bp / 8) rows in flight per warp
+        c->spl_fwd = c->spl_bwd = std::min(c->Bp, 8);
+        if (const char *f = getenv("GABM_BATCH_SPL")) {
+            const int v = atoi(f);
+            if (batch_config_ok(c->Bp, v)) c->spl_fwd = c->spl_bwd = v;
+        }
+    }
     c->tau_EI = model->tau_EI;
     c->tau_IR = model->tau_IR;
     c->L = model->tau_EI + model->tau_IR;
@@ -589,6 +957,7 @@ gabm_status gabm_create(const gabm_graph_desc *graphs, int num_graphs, int sets_
     c->h_Dbar = Dbar;
     c->symmetric = symmetric;
     if (const char *f = getenv("GABM_FAIL_ALLOC_AFTER")) c->fail_alloc_after = atol(f);
+    if (const char *f = getenv("GABM_CUDA_GRAPHS")) c->use_graphs = atoi(f) != 0;
 
     auto bail = [&](gabm_status st) {
         g_create_error = c->err;
@@ -611,7 +980,7 @@ gabm_status gabm_create(const gabm_graph_desc *graphs, int num_graphs, int sets_
     CCK(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device));
 
     c->sigma = sigma;
-    c->sell_entries = (int64_t)sell_in.slice_ptr.back();
+    c->sell_entries = batched ? 0 : (int64_t)sell_in.slice_ptr.back();
     auto upload_sell = [&](const HostSell &hs, uint32_t *&sp, uint32_t *&rl, uint32_t *&cl, float *&ww) -> gabm_status {
         TRY(dalloc(c, &sp, hs.slice_ptr.size()));
         TRY(dalloc(c, &rl, hs.row_len.size()));
@@ -623,14 +992,35 @@ gabm_status gabm_create(const gabm_graph_desc *graphs, int num_graphs, int sets_
         CK(cudaMemcpyAsync(ww, hs.w.data(), sizeof(float) * hs.w.size(), cudaMemcpyHostToDevice, c->stream));
         return GABM_OK;
     };
-    CTRY(upload_sell(sell_in, c->slice_ptr, c->row_len, c->scol, c->sw));
-    if (symmetric) {
-        c->t_slice_ptr = c->slice_ptr;
-        c->t_row_len = c->row_len;
-        c->t_scol = c->scol;
-        c->t_sw = c->sw;
+    auto upload_csr = [&](const std::vector<uint32_t> &rp, const std::vector<uint32_t> &cl, const std::vector<float> &ww,
+                          uint32_t *&drp, uint32_t *&dcl, float *&dw) -> gabm_status {
+        TRY(dalloc(c, &drp, rp.size()));
+        TRY(dalloc(c, &dcl, cl.size()));
+        TRY(dalloc(c, &dw, ww.size()));
+        CK(cudaMemcpyAsync(drp, rp.data(), sizeof(uint32_t) * rp.size(), cudaMemcpyHostToDevice, c->stream));
+        CK(cudaMemcpyAsync(dcl, cl.data(), sizeof(uint32_t) * cl.size(), cudaMemcpyHostToDevice, c->stream));
+        CK(cudaMemcpyAsync(dw, ww.data(), sizeof(float) * ww.size(), cudaMemcpyHostToDevice, c->stream));
+        return GABM_OK;
+    };
+    if (batched) {
+        CTRY(upload_csr(h_rowptr, h_col, h_w, c->csr_rowptr, c->csr_col, c->csr_w));
+        if (symmetric) {
+            c->t_csr_rowptr = c->csr_rowptr;
+            c->t_csr_col = c->csr_col;
+            c->t_csr_w = c->csr_w;
+        } else {
+            CTRY(upload_csr(t_rowptr, t_col, t_w, c->t_csr_rowptr, c->t_csr_col, c->t_csr_w));
+        }
     } else {
-        CTRY(upload_sell(sell_out, c->t_slice_ptr, c->t_row_len, c->t_scol, c->t_sw));
+        CTRY(upload_sell(sell_in, c->slice_ptr, c->row_len, c->scol, c->sw));
+        if (symmetric) {
+            c->t_slice_ptr = c->slice_ptr;
+            c->t_row_len = c->row_len;
+            c->t_scol = c->scol;
+            c->t_sw = c->sw;
+        } else {
+            CTRY(upload_sell(sell_out, c->t_slice_ptr, c->t_row_len, c->t_scol, c->t_sw));
+        }
     }
     CTRY(dalloc(c, &c->age, (size_t)n_rows));
     CCK(cudaMemcpyAsync(c->age, h_age.data(), h_age.size(), cudaMemcpyHostToDevice, c->stream));
@@ -657,13 +1047,18 @@ gabm_status gabm_create(const gabm_graph_desc *graphs, int num_graphs, int sets_
     CCK(cudaMemcpyAsync(c->d_inv_Dbar, inv.data(), sizeof(float) * num_graphs, cudaMemcpyHostToDevice, c->stream));
     CCK(cudaMemcpyAsync(c->d_tile_graph, tile_graph.data(), sizeof(uint16_t) * ntiles, cudaMemcpyHostToDevice, c->stream));
 
-    CTRY(dalloc(c, &c->e, (size_t)n_rows));
-    CTRY(dalloc(c, &c->ring, (size_t)(c->L - 1) * n_rows));
-    CTRY(dalloc(c, &c->A, (size_t)n_rows));
-    CTRY(dalloc(c, &c->r, (size_t)2 * n_rows));
-    CTRY(dalloc(c, &c->rows_f, (size_t)n_rows));
-    CTRY(dalloc(c, &c->rows_e, (size_t)n_rows));
-    CTRY(dalloc(c, &c->stage_f, (size_t)n_rows));
+    const size_t nb = (size_t)n_rows * c->Bp;   // agent-set slots
+    CTRY(dalloc(c, &c->e, nb));
+    CTRY(dalloc(c, &c->ring, (size_t)(c->L - 1) * nb));
+    CTRY(dalloc(c, &c->A, nb));
+    CTRY(dalloc(c, &c->r, (size_t)2 * nb));
+    CTRY(dalloc(c, &c->rows_f, nb));
+    CTRY(dalloc(c, &c->rows_e, nb));
+    CTRY(dalloc(c, &c->stage_f, nb));
+    if (batched) {
+        CTRY(dalloc(c, &c->rbits, (size_t)2 * ntiles));
+        CTRY(dalloc(c, &c->hist0, (size_t)c->I * (c->L + 2)));
+    }
     CTRY(dalloc(c, &c->S, (size_t)c->I * kAges));
     CTRY(dalloc(c, &c->dS_s, (size_t)c->I * kAges));
     CTRY(dalloc(c, &c->loss_s, (size_t)c->I));
@@ -676,7 +1071,7 @@ gabm_status gabm_create(const gabm_graph_desc *graphs, int num_graphs, int sets_
     CCK(cudaMemsetAsync(c->hist, 0, sizeof(uint32_t) * (size_t)c->I * kHistBins, c->stream));
     {
         int grid = (int)std::min<int64_t>((n_rows + 255) / 256, 65535);
-        cudaError_t e = launch_init_state(c->e, c->d_row0, c->d_rows, c->G, n_rows, grid, c->stream);
+        cudaError_t e = launch_init_state(c->e, c->d_row0, c->d_rows, c->G, n_rows, c->B, c->Bp, grid, c->stream);
         c->launches++;
         if (e != cudaSuccess) return bail(fail(c, GABM_ECUDA, "init state: %s", cudaGetErrorString(e)));
     }
@@ -684,15 +1079,9 @@ gabm_status gabm_create(const gabm_graph_desc *graphs, int num_graphs, int sets_
         // the bitmap read through L1 is the default: with branch-free gathers it beats the
         // shared-memory copy, whose one large block per SM limits the warps in flight
         const char *f = getenv("GABM_FWD_SMEM_BITS");
-        const int bps = (f && atoi(f) == 1) ? occupancy_fwd(ntiles, true) : 0;
-        c->smem_bits = bps > 0;
-        c->grid_fwd = c->num_sms * (c->smem_bits ? bps : occupancy_fwd(ntiles, false));
+        c->smem_bits = !batched && f && atoi(f) == 1;
     }
-    const int mode = c->policy == GABM_STORE_LAMBDA ? kBwdStore : (symmetric ? kBwdFused : kBwdSplit);
-    c->grid_bwd = c->num_sms * occupancy_bwd(mode);
-    const int max_grid = (ntiles + kBlock / 32 - 1) / (kBlock / 32);
-    if (!c->smem_bits && c->grid_fwd > max_grid) c->grid_fwd = max_grid;
-    if (c->grid_bwd > max_grid) c->grid_bwd = max_grid;
+    apply_schedule(c);
     CTRY(ensure_days(c, 8));
     CCK(cudaStreamSynchronize(c->stream));
 #undef CTRY
@@ -730,70 +1119,14 @@ gabm_status gabm_forward(gabm_ctx *ctx, int T, const float *R, const float *m, c
     CK(cudaMemcpy2DAsync(c->R, ld * sizeof(float), R, T * sizeof(float), T * sizeof(float), c->I, h2d_kind(mem_space), s));
     CK(cudaMemcpy2DAsync(c->m, ld * sizeof(float), m, T * sizeof(float), T * sizeof(float), c->I, h2d_kind(mem_space), s));
     CK(cudaMemcpyAsync(c->S, S_age, sizeof(float) * c->I * kAges, h2d_kind(mem_space), s));
-    CK(cudaMemsetAsync(c->counts, 0, sizeof(int32_t) * 4 * (size_t)c->I * ld, s));
-    CK(cudaMemsetAsync(c->newRM, 0, sizeof(int32_t) * (size_t)c->I * ld, s));
-    CK(cudaMemsetAsync(c->D, 0, sizeof(double) * (size_t)c->I * ld, s));
-    CK(cudaMemsetAsync(c->tile_ctr, 0, sizeof(int) * (size_t)ld, s));
-
-    if (!c->resumed) {
-        CK(cudaMemcpyAsync(c->d_nseed, n_seed, sizeof(int32_t) * c->I, cudaMemcpyHostToDevice, s));
-        const int grid = (int)std::min<int64_t>((c->n_rows + 255) / 256, 65535);
-        LAUNCH(launch_init_state(c->e, c->d_row0, c->d_rows, c->G, c->n_rows, grid, s));
-        SeedArgs sa;
-        sa.row0 = c->d_row0;
-        sa.rows = c->d_rows;
-        sa.orig_id = c->d_orig_id;
-        sa.e = c->e;
-        sa.st = c->seedst;
-        sa.hist = c->hist;
-        sa.ties = c->ties;
-        sa.seed = c->seed;
-        sa.tau_EI = c->tau_EI;
-        int max_rows = 1;
-        for (int g = 0; g < c->G; ++g) max_rows = std::max(max_rows, c->h_rows[g]);
-        const int gx = std::max(1, std::min((max_rows + 255) / 256, 4 * c->num_sms / std::max(1, c->G) + 1));
-        LAUNCH(launch_seed_reset(c->seedst, c->d_nseed, c->I, s));
-        for (int pass = 0; pass < 3; ++pass) {
-            sa.pass = pass;
-            LAUNCH(launch_seed_hist(sa, c->G, gx, s));
-            LAUNCH(launch_seed_scan(sa, c->I, s));
-        }
-        LAUNCH(launch_seed_mark(sa, c->G, gx, s));
-        LAUNCH(launch_seed_ties(sa, c->I, s));
-    }
-
-    FwdDayArgs a;
-    a.m = sell_view(c, false);
-    a.age = c->age;
-    a.gr = graph_ref(c);
-    a.e = c->e;
-    a.R = c->R;
-    a.S = c->S;
-    a.ldP = ld;
-    a.counts = c->counts;
-    a.newRM = c->newRM;
-    a.ntiles = c->ntiles;
-    a.tau_EI = c->tau_EI;
-    a.L = c->L;
-    a.seed = c->seed;
-    for (int k = 0; k < kMaxL; ++k) a.c[k] = k < c->L ? c->c[k] : 0.f;
-    if (t0 < T) LAUNCH(launch_infectious_bits(c->e, t0, 1, c->L, c->ntiles, c->bits + (size_t)t0 * c->ntiles,
-                                              (size_t)c->ntiles, s));
-    for (int t = t0; t < T; ++t) {
-        a.t = t;
-        a.lam_out = c->policy == GABM_STORE_LAMBDA ? c->lam + (size_t)t * c->n_rows : nullptr;
-        a.tile_ctr = c->tile_ctr + t;
-        a.bits_cur = c->bits + (size_t)t * c->ntiles;
-        a.bits_next = c->bits + (size_t)(t + 1) * c->ntiles;
-        prof_begin(c, 0);
-        LAUNCH(launch_fwd_day(a, c->grid_fwd, c->smem_bits, s));
-        prof_end(c, 0);
-    }
+    if (!c->resumed) c->last_seeds.assign(n_seed, n_seed + c->I);
+    TRY(forward_core(c, t0, T, !c->resumed));
     const bool dev = mem_space == GABM_DEVICE;
     LAUNCH(launch_fwd_finalize(c->newRM, c->counts, c->m, ld, t0, T, c->I, c->D, dev ? D : nullptr,
                                dev ? counts : nullptr, s));
     c->T_last = T;
     c->lam_from = c->policy == GABM_STORE_LAMBDA ? t0 : -1;
+    c->last_from_seeding = !c->resumed;
     c->resumed = false;
     c->t0_next = 0;
     if (!dev) {
@@ -839,55 +1172,11 @@ gabm_status gabm_backward(gabm_ctx *ctx, const double *gD, double *dR, double *d
     const int T = c->T_last, ld = c->Tcap;
     cudaStream_t s = c->stream;
     CK(cudaMemcpy2DAsync(c->gD, ld * sizeof(double), gD, T * sizeof(double), T * sizeof(double), c->I, h2d_kind(mem_space), s));
-    CK(cudaMemsetAsync(c->r, 0, sizeof(float) * 2 * (size_t)c->n_rows, s));
-    CK(cudaMemsetAsync(c->newRM_b, 0, sizeof(int32_t) * (size_t)c->I * ld, s));
-    CK(cudaMemsetAsync(c->tile_ctr + ld, 0, sizeof(int) * (size_t)ld, s));
-
-    BwdDayArgs a;
-    const int mode = c->policy == GABM_STORE_LAMBDA ? kBwdStore : (c->symmetric ? kBwdFused : kBwdSplit);
-    if (mode == kBwdSplit && !c->lam_tmp) TRY(dalloc(c, &c->lam_tmp, (size_t)c->n_rows));
-    a.mode = mode == kBwdSplit ? kBwdStore : mode;
-    a.m = sell_view(c, true);
-    a.age = c->age;
-    a.gr = graph_ref(c);
-    a.E = c->e;
-    a.ring = c->ring;
-    a.ring_stride = (size_t)c->n_rows;
-    a.A = c->A;
-    a.R = c->R;
-    a.m_t = c->m;
-    a.S = c->S;
-    a.gD = c->gD;
-    a.ldP = ld;
-    a.newRM = c->newRM_b;
-    a.ntiles = c->ntiles;
-    a.T = T;
-    a.tau_EI = c->tau_EI;
-    a.L = c->L;
-    a.seed = c->seed;
-    for (int k = 0; k < kMaxL; ++k) a.c[k] = k < c->L ? c->c[k] : 0.f;
-    const int Lm1 = c->L - 1;
-    if (mode != kBwdStore)   // every day's infectious rows, from the final state
-        LAUNCH(launch_infectious_bits(c->e, 0, T, c->L, c->ntiles, c->bits, (size_t)c->ntiles, s));
-    for (int t = T - 1; t >= 0; --t) {
-        a.bits_t = mode != kBwdStore ? c->bits + (size_t)t * c->ntiles : nullptr;
-        a.t = t;
-        a.lam_t = mode == kBwdStore ? c->lam + (size_t)t * c->n_rows : (mode == kBwdSplit ? c->lam_tmp : nullptr);
-        if (mode == kBwdSplit)
-            LAUNCH(launch_lam_day(sell_view(c, false), c->e, c->bits + (size_t)t * c->ntiles, graph_ref(c), t, c->L,
-                                  c->ntiles, c->c_dev, c->lam_tmp, c->grid_bwd, s));
-        a.r_next = c->r + (size_t)((t + 1) & 1) * c->n_rows;
-        a.r_cur = c->r + (size_t)(t & 1) * c->n_rows;
-        a.P_t = c->P + (size_t)t * c->ntiles * kAges;
-        for (int k = 0; k < kMaxL; ++k) a.ring_slot[k] = (k >= 1 && k < c->L) ? (t + k) % Lm1 : 0;
-        a.tile_ctr = c->tile_ctr + ld + t;
-        prof_begin(c, 1);
-        LAUNCH(launch_bwd_day(a, c->grid_bwd, s));
-        prof_end(c, 1);
-    }
-    LAUNCH(launch_bwd_reduce(c->P, c->ntiles, ld, c->d_tile0, c->d_ntiles, T, c->I, c->Q, s));
+    c->gD_staged = true;
+    TRY(backward_core(c, T));
     const bool dev = mem_space == GABM_DEVICE;
-    LAUNCH(launch_bwd_finalize(c->Q, c->R, c->S, c->gD, c->newRM_b, ld, T, c->I, dev ? dR : c->dR_s,
+    LAUNCH(launch_bwd_finalize(c->Q, c->R, c->S, c->gD, c->batched ? c->newRM : c->newRM_b, ld, T, c->I,
+                               dev ? dR : c->dR_s,
                                dev ? dm : c->dm_s, dev ? dS_age : c->dS_s, s));
     if (!dev) {
         CK(cudaMemcpyAsync(dR, c->dR_s, sizeof(double) * (size_t)c->I * T, cudaMemcpyDeviceToHost, s));
@@ -905,9 +1194,10 @@ gabm_status gabm_get_state(gabm_ctx *ctx, int16_t *e_out, int mem_space) {
     if (!e_out) return fail(c, GABM_EINVAL, "e_out is NULL");
     const bool dev = mem_space == GABM_DEVICE;
     LAUNCH(launch_rows_to_caller_i16(c->e, dev ? e_out : c->rows_e, graph_ref(c), c->d_rows, c->d_goff, c->n_rows,
-                                     c->stream));
+                                     set_layout(c), c->stream));
     if (!dev) {
-        CK(cudaMemcpyAsync(e_out, c->rows_e, sizeof(int16_t) * (size_t)c->n_total, cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaMemcpyAsync(e_out, c->rows_e, sizeof(int16_t) * (size_t)c->n_total * c->B, cudaMemcpyDeviceToHost,
+                           c->stream));
         CK(cudaStreamSynchronize(c->stream));
     }
     return GABM_OK;
@@ -919,7 +1209,7 @@ gabm_status gabm_set_state(gabm_ctx *ctx, int day, const int16_t *e_in, int mem_
     TRY(check_ms(c, mem_space));
     if (!e_in) return fail(c, GABM_EINVAL, "e_in is NULL");
     if (day < 0 || day > GABM_MAX_DAYS) return fail(c, GABM_EINVAL, "day %d outside 0..%d", day, GABM_MAX_DAYS);
-    std::vector<int16_t> h((size_t)c->n_total);
+    std::vector<int16_t> h((size_t)c->n_total * c->B);
     if (mem_space == GABM_HOST) {
         memcpy(h.data(), e_in, sizeof(int16_t) * h.size());
     } else {
@@ -934,7 +1224,8 @@ gabm_status gabm_set_state(gabm_ctx *ctx, int day, const int16_t *e_in, int mem_
     CK(cudaStreamSynchronize(c->stream));
     if (c->n_total > 0) {
         CK(cudaMemcpyAsync(c->rows_e, h.data(), sizeof(int16_t) * h.size(), cudaMemcpyHostToDevice, c->stream));
-        LAUNCH(launch_caller_to_rows_i16(c->rows_e, c->e, graph_ref(c), c->d_rows, c->d_goff, c->n_rows, c->stream));
+        LAUNCH(launch_caller_to_rows_i16(c->rows_e, c->e, graph_ref(c), c->d_rows, c->d_goff, c->n_rows, set_layout(c),
+                                         c->stream));
         CK(cudaStreamSynchronize(c->stream));
     }
     c->t0_next = day;
@@ -952,15 +1243,97 @@ gabm_status gabm_get_lambda(gabm_ctx *ctx, int t, float *lam_out, int mem_space)
     if (c->policy != GABM_STORE_LAMBDA) return fail(c, GABM_ESTATE, "lambda is only stored with GABM_STORE_LAMBDA");
     if (c->T_last < 1 || t < c->lam_from || t >= c->T_last || c->lam_from < 0)
         return fail(c, GABM_ESTATE, "day %d was not run by the last forward", t);
-    LAUNCH(launch_get_lambda(c->lam + (size_t)t * c->n_rows, c->e, c->age, graph_ref(c), c->R, c->S, c->Tcap, t,
-                             c->n_rows, c->rows_f, c->stream));
+    LAUNCH(launch_get_lambda(c->lam + (size_t)t * c->n_rows * c->Bp, c->e, c->age, graph_ref(c), c->R, c->S, c->Tcap, t,
+                             c->n_rows, c->B, c->Bp, c->rows_f, c->stream));
     const bool dev = mem_space == GABM_DEVICE;
     LAUNCH(launch_rows_to_caller_f32(c->rows_f, dev ? lam_out : c->stage_f, graph_ref(c), c->d_rows, c->d_goff,
-                                     c->n_rows, c->stream));
+                                     c->n_rows, set_layout(c), c->stream));
     if (!dev) {
-        CK(cudaMemcpyAsync(lam_out, c->stage_f, sizeof(float) * (size_t)c->n_total, cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaMemcpyAsync(lam_out, c->stage_f, sizeof(float) * (size_t)c->n_total * c->B, cudaMemcpyDeviceToHost,
+                           c->stream));
         CK(cudaStreamSynchronize(c->stream));
     }
+    return GABM_OK;
+}
+
+gabm_status gabm_get_schedule(const gabm_ctx *ctx, gabm_schedule *out) {
+    if (!ctx) return fail(nullptr, GABM_EINVAL, "ctx is NULL");
+    if (!out) return GABM_EINVAL;
+    out->fwd_sets_per_lane = ctx->batched ? ctx->spl_fwd : 0;
+    out->bwd_sets_per_lane = ctx->batched ? ctx->spl_bwd : 0;
+    out->fwd_smem_bitmap = ctx->batched ? 0 : (ctx->smem_bits ? 1 : 0);
+    return GABM_OK;
+}
+
+gabm_status gabm_set_schedule(gabm_ctx *ctx, const gabm_schedule *sched) {
+    gabm_ctx *c = ctx;
+    if (!c) return fail(nullptr, GABM_EINVAL, "ctx is NULL");
+    if (!sched) return fail(c, GABM_EINVAL, "schedule is NULL");
+    if (c->batched) {
+        if (!batch_config_ok(c->Bp, sched->fwd_sets_per_lane) || !batch_config_ok(c->Bp, sched->bwd_sets_per_lane))
+            return fail(c, GABM_EINVAL, "sets per lane must be 2, 4 or 8 and at most %d", c->Bp);
+        c->spl_fwd = sched->fwd_sets_per_lane;
+        c->spl_bwd = sched->bwd_sets_per_lane;
+    } else {
+        if (sched->fwd_smem_bitmap && occupancy_fwd(c->ntiles, true) <= 0)
+            return fail(c, GABM_EINVAL, "the infectious bitmap (%d words) does not fit in shared memory", c->ntiles);
+        c->smem_bits = sched->fwd_smem_bitmap != 0;
+    }
+    apply_schedule(c);
+    return GABM_OK;
+}
+
+gabm_status gabm_autotune(gabm_ctx *ctx, int repetitions) {
+    gabm_ctx *c = ctx;
+    if (!c) return fail(nullptr, GABM_EINVAL, "ctx is NULL");
+    if (repetitions < 1) return fail(c, GABM_EINVAL, "repetitions must be >= 1");
+    if (c->T_last < 1 || !c->last_from_seeding)
+        return fail(c, GABM_ESTATE, "autotune needs a preceding forward that started from seeding");
+    const int T = c->T_last, ld = c->Tcap;
+    cudaStream_t s = c->stream;
+    if (!c->gD_staged) CK(cudaMemsetAsync(c->gD, 0, sizeof(double) * (size_t)c->I * ld, s));
+    std::vector<gabm_schedule> cands;
+    if (c->batched) {
+        for (int spl : {2, 4, 8})
+            if (batch_config_ok(c->Bp, spl)) cands.push_back(gabm_schedule{spl, spl, 0});
+    } else {
+        cands.push_back(gabm_schedule{0, 0, 0});
+        if (occupancy_fwd(c->ntiles, true) > 0) cands.push_back(gabm_schedule{0, 0, 1});
+    }
+    cudaEvent_t ev[4];
+    for (auto &e : ev) CK(cudaEventCreate(&e));
+    auto release = [&]() { for (auto &e : ev) cudaEventDestroy(e); };
+    float best_f = 1e30f, best_b = 1e30f;
+    gabm_schedule bf = cands[0], bb = cands[0];
+    for (const gabm_schedule &cand : cands) {
+        gabm_status st = gabm_set_schedule(c, &cand);
+        if (st == GABM_OK) st = forward_core(c, 0, T, true);   // warm-up (and graph capture)
+        if (st == GABM_OK) st = backward_core(c, T);
+        float tf = 0.f, tb = 0.f;
+        for (int r = 0; r < repetitions && st == GABM_OK; ++r) {
+            cudaEventRecord(ev[0], s);
+            st = forward_core(c, 0, T, true);
+            cudaEventRecord(ev[1], s);
+            if (st == GABM_OK) st = backward_core(c, T);
+            cudaEventRecord(ev[2], s);
+            if (cudaEventSynchronize(ev[2]) != cudaSuccess) st = fail(c, GABM_ECUDA, "autotune: %s", cudaGetErrorString(cudaGetLastError()));
+            float a = 0.f, b = 0.f;
+            cudaEventElapsedTime(&a, ev[0], ev[1]);
+            cudaEventElapsedTime(&b, ev[1], ev[2]);
+            tf += a;
+            tb += b;
+        }
+        if (st != GABM_OK) { release(); return st; }
+        if (tf < best_f) { best_f = tf; bf = cand; }
+        if (tb < best_b) { best_b = tb; bb = cand; }
+    }
+    release();
+    const gabm_schedule chosen{bf.fwd_sets_per_lane, bb.bwd_sets_per_lane, bf.fwd_smem_bitmap};
+    TRY(gabm_set_schedule(c, &chosen));
+    // the last forward's outputs again (the trajectory does not depend on the schedule)
+    TRY(forward_core(c, 0, T, true));
+    LAUNCH(launch_fwd_finalize(c->newRM, c->counts, c->m, ld, 0, T, c->I, c->D, nullptr, nullptr, s));
+    CK(cudaStreamSynchronize(s));
     return GABM_OK;
 }
 

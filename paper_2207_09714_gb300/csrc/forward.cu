@@ -176,7 +176,8 @@ __global__ void k_infectious_bits(const int16_t *e, int t0, int ndays, int L, in
 // 32-bit word in three digits (11, 11, 10 bits), then ties on the final word
 // are broken by id.
 // ---------------------------------------------------------------------------
-__global__ void k_init_state(int16_t *e, const int32_t *row0, const int32_t *rows, int G, int64_t n_rows) {
+__global__ void k_init_state(int16_t *e, const int32_t *row0, const int32_t *rows, int G, int64_t n_rows,
+                             int B, int Bp) {
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n_rows;
          r += (int64_t)gridDim.x * blockDim.x) {
         // binary search the graph of row r
@@ -185,7 +186,9 @@ __global__ void k_init_state(int16_t *e, const int32_t *row0, const int32_t *row
             int mid = (lo + hi + 1) >> 1;
             if (row0[mid] <= r) lo = mid; else hi = mid - 1;
         }
-        e[r] = (r - row0[lo] < rows[lo]) ? (int16_t)kNever : (int16_t)kPad;
+        const bool agent = r - row0[lo] < rows[lo];
+        for (int b = 0; b < Bp; ++b)
+            e[(size_t)r * Bp + b] = (agent && b < B) ? (int16_t)kNever : (int16_t)kPad;
     }
 }
 
@@ -217,7 +220,7 @@ __global__ void __launch_bounds__(256) k_seed_hist(const SeedArgs a) {
     digit_of_pass(a.pass, shift, nbins, himask);
     for (int b = threadIdx.x; b < nbins; b += blockDim.x) h_s[b] = 0u;
     __syncthreads();
-    const int g = inst;
+    const int g = inst / a.B;
     const int32_t r0 = a.row0[g], nr = a.rows[g];
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nr; i += gridDim.x * blockDim.x) {
         const uint32_t id = a.orig_id ? a.orig_id[r0 + i] : (uint32_t)i;
@@ -278,7 +281,8 @@ __global__ void k_seed_mark(const SeedArgs a) {
     const int inst = blockIdx.y;
     const SeedState st = a.st[inst];
     if (st.none) return;
-    const int g = inst;
+    const int g = inst / a.B;
+    const size_t set = (size_t)(inst - g * a.B);
     const int32_t r0 = a.row0[g], nr = a.rows[g];
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nr; i += gridDim.x * blockDim.x) {
         const uint32_t id = a.orig_id ? a.orig_id[r0 + i] : (uint32_t)i;
@@ -293,7 +297,7 @@ __global__ void k_seed_mark(const SeedArgs a) {
                 else a.st[inst].overflow = 1;
             }
         }
-        if (mark) a.e[r0 + i] = (int16_t)(-a.tau_EI);
+        if (mark) a.e[(size_t)(r0 + i) * a.Bp + set] = (int16_t)(-a.tau_EI);
     }
 }
 
@@ -305,7 +309,9 @@ __global__ void k_seed_ties(const SeedArgs a) {
     if (st.none || st.eq_count == st.k_rem) return;
     const uint32_t n = min(st.tie_n, (uint32_t)kTieCap);
     const uint32_t *tl = a.ties + (size_t)inst * kTieCap;
-    const int32_t r0 = a.row0[inst];
+    const int g = inst / a.B;
+    const size_t set = (size_t)(inst - g * a.B);
+    const int32_t r0 = a.row0[g];
     for (uint32_t c = threadIdx.x; c < n; c += blockDim.x) {
         const uint32_t i = tl[c];
         const uint32_t id = a.orig_id ? a.orig_id[r0 + i] : i;
@@ -314,7 +320,7 @@ __global__ void k_seed_ties(const SeedArgs a) {
             const uint32_t idd = a.orig_id ? a.orig_id[r0 + tl[d]] : tl[d];
             rank += (idd < id);
         }
-        if (rank < st.k_rem) a.e[r0 + i] = (int16_t)(-a.tau_EI);
+        if (rank < st.k_rem) a.e[(size_t)(r0 + i) * a.Bp + set] = (int16_t)(-a.tau_EI);
     }
 }
 
@@ -330,21 +336,23 @@ __device__ __forceinline__ bool caller_slot(const GraphRef &gr, const int32_t *r
 
 template <typename T>
 __global__ void k_rows_to_caller(const T *src, T *dst, GraphRef gr, const int32_t *rows, const int64_t *goff,
-                                 int64_t n_rows) {
+                                 int64_t n_rows, SetLayout sl) {
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n_rows;
          r += (int64_t)gridDim.x * blockDim.x) {
         int64_t slot;
-        if (caller_slot(gr, rows, goff, r, slot)) dst[slot] = src[r];
+        if (caller_slot(gr, rows, goff, r, slot))
+            for (int b = 0; b < sl.B; ++b) dst[(size_t)b * sl.n_total + slot] = src[(size_t)r * sl.Bp + b];
     }
 }
 
 template <typename T>
 __global__ void k_caller_to_rows(const T *src, T *dst, GraphRef gr, const int32_t *rows, const int64_t *goff,
-                                 int64_t n_rows) {
+                                 int64_t n_rows, SetLayout sl) {
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n_rows;
          r += (int64_t)gridDim.x * blockDim.x) {
         int64_t slot;
-        if (caller_slot(gr, rows, goff, r, slot)) dst[r] = src[slot];
+        if (caller_slot(gr, rows, goff, r, slot))
+            for (int b = 0; b < sl.B; ++b) dst[(size_t)r * sl.Bp + b] = src[(size_t)b * sl.n_total + slot];
     }
 }
 
@@ -388,17 +396,22 @@ __global__ void __launch_bounds__(256) k_mse(const double *D, int ldP, const dou
 
 // lambda_i(t) = R_t S[a_i] Lam_i(t) for agents susceptible on day t, else 0.
 __global__ void k_get_lambda(const float *lam_t, const int16_t *e, const uint8_t *age, GraphRef gr,
-                             const float *R, const float *S, int ldP, int t, int64_t n_rows, float *out) {
+                             const float *R, const float *S, int ldP, int t, int64_t n_rows, int B, int Bp,
+                             float *out) {
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n_rows;
          r += (int64_t)gridDim.x * blockDim.x) {
-        const int ei = e[r];
-        const bool wasS = (ei == kNever) || (ei >= t);
-        float v = 0.f;
-        if (ei != kPad && wasS) {
-            const int g = gr.tile_graph ? (int)gr.tile_graph[r / kTile] : 0;
-            v = (R[(size_t)g * ldP + t] * S[g * kAges + age[r]]) * lam_t[r];
+        const int g = gr.tile_graph ? (int)gr.tile_graph[r / kTile] : 0;
+        for (int b = 0; b < Bp; ++b) {
+            const size_t x = (size_t)r * Bp + b;
+            const int ei = e[x];
+            const bool wasS = (ei == kNever) || (ei >= t);
+            float v = 0.f;
+            if (ei != kPad && wasS) {
+                const int inst = g * B + b;
+                v = (R[(size_t)inst * ldP + t] * S[inst * kAges + age[r]]) * lam_t[x];
+            }
+            out[x] = v;
         }
-        out[r] = v;
     }
 }
 
@@ -422,8 +435,8 @@ cudaError_t launch_infectious_bits(const int16_t *e, int t0, int ndays, int L, i
 }
 
 cudaError_t launch_init_state(int16_t *e, const int32_t *row0, const int32_t *rows, int G,
-                              int64_t n_rows, int grid, cudaStream_t s) {
-    k_init_state<<<grid, 256, 0, s>>>(e, row0, rows, G, n_rows);
+                              int64_t n_rows, int B, int Bp, int grid, cudaStream_t s) {
+    k_init_state<<<grid, 256, 0, s>>>(e, row0, rows, G, n_rows, B, Bp);
     return cudaGetLastError();
 }
 
@@ -432,8 +445,8 @@ cudaError_t launch_seed_reset(SeedState *st, const int32_t *n_seed, int I, cudaS
     return cudaGetLastError();
 }
 
-cudaError_t launch_seed_hist(const SeedArgs &a, int G, int grid_x, cudaStream_t s) {
-    k_seed_hist<<<dim3(grid_x, G), 256, 0, s>>>(a);
+cudaError_t launch_seed_hist(const SeedArgs &a, int I, int grid_x, cudaStream_t s) {
+    k_seed_hist<<<dim3(grid_x, I), 256, 0, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -442,8 +455,8 @@ cudaError_t launch_seed_scan(const SeedArgs &a, int I, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_seed_mark(const SeedArgs &a, int G, int grid_x, cudaStream_t s) {
-    k_seed_mark<<<dim3(grid_x, G), 256, 0, s>>>(a);
+cudaError_t launch_seed_mark(const SeedArgs &a, int I, int grid_x, cudaStream_t s) {
+    k_seed_mark<<<dim3(grid_x, I), 256, 0, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -498,11 +511,11 @@ cudaError_t launch_mse(const double *D, int ldP, const double *y, int T, int I, 
 }
 
 cudaError_t launch_get_lambda(const float *lam_t, const int16_t *e, const uint8_t *age, GraphRef gr,
-                              const float *R, const float *S, int ldP, int t, int64_t n_rows,
+                              const float *R, const float *S, int ldP, int t, int64_t n_rows, int B, int Bp,
                               float *out_rows, cudaStream_t s) {
     int grid = (int)((n_rows + 255) / 256);
     if (grid > 65535) grid = 65535;
-    k_get_lambda<<<grid > 0 ? grid : 1, 256, 0, s>>>(lam_t, e, age, gr, R, S, ldP, t, n_rows, out_rows);
+    k_get_lambda<<<grid > 0 ? grid : 1, 256, 0, s>>>(lam_t, e, age, gr, R, S, ldP, t, n_rows, B, Bp, out_rows);
     return cudaGetLastError();
 }
 
@@ -513,20 +526,20 @@ static int grid_for(int64_t n) {
 }
 
 cudaError_t launch_rows_to_caller_i16(const int16_t *src, int16_t *dst, GraphRef gr, const int32_t *rows,
-                                      const int64_t *goff, int64_t n_rows, cudaStream_t s) {
-    k_rows_to_caller<int16_t><<<grid_for(n_rows), 256, 0, s>>>(src, dst, gr, rows, goff, n_rows);
+                                      const int64_t *goff, int64_t n_rows, SetLayout sl, cudaStream_t s) {
+    k_rows_to_caller<int16_t><<<grid_for(n_rows), 256, 0, s>>>(src, dst, gr, rows, goff, n_rows, sl);
     return cudaGetLastError();
 }
 
 cudaError_t launch_rows_to_caller_f32(const float *src, float *dst, GraphRef gr, const int32_t *rows,
-                                      const int64_t *goff, int64_t n_rows, cudaStream_t s) {
-    k_rows_to_caller<float><<<grid_for(n_rows), 256, 0, s>>>(src, dst, gr, rows, goff, n_rows);
+                                      const int64_t *goff, int64_t n_rows, SetLayout sl, cudaStream_t s) {
+    k_rows_to_caller<float><<<grid_for(n_rows), 256, 0, s>>>(src, dst, gr, rows, goff, n_rows, sl);
     return cudaGetLastError();
 }
 
 cudaError_t launch_caller_to_rows_i16(const int16_t *src, int16_t *dst, GraphRef gr, const int32_t *rows,
-                                      const int64_t *goff, int64_t n_rows, cudaStream_t s) {
-    k_caller_to_rows<int16_t><<<grid_for(n_rows), 256, 0, s>>>(src, dst, gr, rows, goff, n_rows);
+                                      const int64_t *goff, int64_t n_rows, SetLayout sl, cudaStream_t s) {
+    k_caller_to_rows<int16_t><<<grid_for(n_rows), 256, 0, s>>>(src, dst, gr, rows, goff, n_rows, sl);
     return cudaGetLastError();
 }
 

@@ -34,6 +34,10 @@ constexpr int kTile = 32;          // rows per warp tile
 constexpr int kBlock = 256;        // threads per block of the day kernels
 constexpr int kHistBins = 2048;    // radix-select digit bins (11 bits)
 constexpr int kTieCap = 4096;      // agents sharing the threshold hash (seeding)
+constexpr int kMaxSets = 64;       // parameter sets per graph (batched kernels: two per lane)
+// Batched sums use plain fused multiply-adds when no row has more entries than this:
+// a sum of k non-negative terms then carries a relative error below (k + 3) 2^-24 < 1e-5.
+constexpr int kPlainSumMaxDegree = 64;
 
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), written from its
@@ -158,7 +162,8 @@ struct SeedArgs {
     const int32_t *row0;  // [G]
     const int32_t *rows;  // [G] real rows per graph
     const uint32_t *orig_id;  // [n_rows] or nullptr
-    int16_t *e;
+    int16_t *e;           // [n_rows][Bp]: instance i = graph i / B, set i % B
+    int B, Bp;            // parameter sets per graph and the row stride of e
     SeedState *st;        // [I]
     uint32_t *hist;       // [I][kHistBins]
     uint32_t *ties;       // [I][kTieCap]
@@ -167,13 +172,91 @@ struct SeedArgs {
     int pass;             // 0, 1, 2
 };
 
+// ---------------------------------------------------------------------------
+// Batched instances: B parameter sets on each graph (batched.cu).  Per-agent
+// arrays are agent-major, [n_rows][Bp] with Bp = B rounded up to a power of two
+// (2..64); sets B..Bp-1 are padding (exposure day kPad).  One warp handles a
+// row with Bp/2 lanes, two sets per lane, so one neighbour's exposure days for
+// all sets are one contiguous Bp*2-byte gather.
+// ---------------------------------------------------------------------------
+struct Csr {                     // one orientation of the edges, row-compressed
+    const uint32_t *rowptr;      // [n_rows+1]
+    const uint32_t *col;         // [nnz]
+    const float *w;              // [nnz]
+};
+
+struct FwdBatchArgs {
+    Csr m;                       // in-edges
+    const uint8_t *age;
+    GraphRef gr;
+    int16_t *e;                  // [n_rows][Bp]
+    float *lam_out;              // day-t slice [n_rows][Bp] of the lambda store, or nullptr
+    const float *R, *S;          // [I][ldP], [I][9]
+    int ldP;
+    uint8_t *tile_new;           // [ntiles][Bp] agents exposed on day t, by tile and set
+    int *tile_ctr;
+    const uint32_t *bits_cur;    // [ntiles] rows infectious on day t in any set
+    uint32_t *bits_next;         // the same for day t + 1
+    int ntiles, t, tau_EI, L, B;
+    uint64_t seed;
+    float c[kMaxL];
+};
+
+struct BwdBatchArgs {
+    Csr m;                       // out-edges (the in-edges when the weights are symmetric)
+    const uint8_t *age;
+    GraphRef gr;
+    const int16_t *E;            // [n_rows][Bp] final exposure days
+    const float *lam_t;          // [n_rows][Bp] stored normalised sums of day t
+    const float *r_next;         // [n_rows][Bp] coefficients of day t+1
+    float *r_cur;                // [n_rows][Bp] coefficients of day t
+    const uint32_t *rbits_next;  // [ntiles] rows susceptible on day t+1 in some set
+    uint32_t *rbits_cur;         // the same for day t
+    float *ring;                 // [L-1][n_rows][Bp]
+    size_t ring_stride;
+    float *A;                    // [n_rows][Bp]
+    const float *R, *m_t, *S;
+    const double *gD;
+    int ldP;
+    double *P_t;                 // [ntiles][9][Bp] per-tile partial sums of gl * Lam
+    int *tile_ctr;
+    int ntiles, t, T, tau_EI, L, B;
+    uint64_t seed;
+    float c[kMaxL];
+    int ring_slot[kMaxL];
+};
+
+// Schedules: spl sets per lane (2, 4 or 8; Bp / spl lanes share a row).
+bool batch_config_ok(int Bp, int spl);
+cudaError_t launch_fwd_day_b(const FwdBatchArgs &a, int Bp, int spl, bool kahan, int grid, cudaStream_t s);
+cudaError_t launch_bwd_day_b(const BwdBatchArgs &a, int Bp, int spl, bool kahan, int grid, cudaStream_t s);
+int occupancy_fwd_b(int Bp, int spl, bool kahan);
+int occupancy_bwd_b(int Bp, int spl, bool kahan);
+// rows with 1 <= t0 - e < L in any set
+cudaError_t launch_infectious_bits_b(const int16_t *e, int Bp, int t0, int L, int ntiles, uint32_t *bits,
+                                     cudaStream_t s);
+// H [I][L+2] (zeroed by the caller): exposure days of the state at the start of day t0
+cudaError_t launch_exposure_hist_b(const int16_t *e, GraphRef gr, int64_t n_rows, int B, int Bp, int t0, int L,
+                                   int32_t *H, cudaStream_t s);
+// counts [I][ldP][4] and newRM [I][ldP] of days t0..T-1 from H and the per-tile exposures
+// tile_new [T][ntiles][Bp]; newinf [I][ldP] is scratch, zeroed by the caller.
+cudaError_t launch_counts_b(const uint8_t *tile_new, int ntiles, const int32_t *d_tile0, const int32_t *d_ntiles,
+                            const int32_t *d_rows, int G, int B, int Bp, int max_tiles, int t0, int T, int ldP,
+                            int tau_EI, int L, const int32_t *H, int32_t *newinf, int32_t *counts, int32_t *newRM,
+                            cudaStream_t s);
+// Q[g*B+s][t][a] = sum over graph g's tiles of P[t][tile][a][s], in a fixed order (two levels of
+// kReduceChunkTiles tiles); scratch holds T * G * max_chunks * 9 * Bp doubles.
+cudaError_t launch_bwd_reduce_b(const double *P, int ntiles, const int32_t *d_tile0, const int32_t *d_ntiles, int G,
+                                int B, int Bp, int T, double *scratch, int max_chunks, double *Q, cudaStream_t s);
+constexpr int kReduceChunkTiles = 64;
+
 // Launchers (forward.cu / backward.cu)
 cudaError_t launch_init_state(int16_t *e, const int32_t *row0, const int32_t *rows, int G,
-                              int64_t n_rows, int grid, cudaStream_t s);
+                              int64_t n_rows, int B, int Bp, int grid, cudaStream_t s);
 cudaError_t launch_seed_reset(SeedState *st, const int32_t *n_seed, int I, cudaStream_t s);
-cudaError_t launch_seed_hist(const SeedArgs &a, int G, int grid_x, cudaStream_t s);
+cudaError_t launch_seed_hist(const SeedArgs &a, int I, int grid_x, cudaStream_t s);
 cudaError_t launch_seed_scan(const SeedArgs &a, int I, cudaStream_t s);
-cudaError_t launch_seed_mark(const SeedArgs &a, int G, int grid_x, cudaStream_t s);
+cudaError_t launch_seed_mark(const SeedArgs &a, int I, int grid_x, cudaStream_t s);
 cudaError_t launch_seed_ties(const SeedArgs &a, int I, cudaStream_t s);
 cudaError_t launch_fwd_day(const FwdDayArgs &a, int grid, bool smem_bits, cudaStream_t s);
 // bits[d][tile] for days t0 .. t0 + ndays - 1: rows with 1 <= t - e < L (infectious on day t).
@@ -195,16 +278,21 @@ cudaError_t launch_bwd_finalize(const double *Q, const float *R, const float *S,
                                 double *dm, double *dS, cudaStream_t s);
 cudaError_t launch_get_lambda(const float *lam_t, const int16_t *e, const uint8_t *age,
                               GraphRef gr, const float *R, const float *S, int ldP, int t,
-                              int64_t n_rows, float *out_rows, cudaStream_t s);
+                              int64_t n_rows, int B, int Bp, float *out_rows, cudaStream_t s);
 cudaError_t launch_philox(uint64_t seed, const uint32_t *ctr, uint32_t *out, int64_t count,
                           cudaStream_t s);
-// Row order <-> caller order (graphs concatenated, caller ids within each graph).
+// Row order [n_rows][Bp] <-> caller order [B][n_total] (graphs concatenated, caller ids
+// within each graph; B = Bp = 1 for one set per graph).
+struct SetLayout {
+    int B, Bp;
+    int64_t n_total;
+};
 cudaError_t launch_rows_to_caller_i16(const int16_t *src, int16_t *dst, GraphRef gr, const int32_t *rows,
-                                      const int64_t *goff, int64_t n_rows, cudaStream_t s);
+                                      const int64_t *goff, int64_t n_rows, SetLayout sl, cudaStream_t s);
 cudaError_t launch_rows_to_caller_f32(const float *src, float *dst, GraphRef gr, const int32_t *rows,
-                                      const int64_t *goff, int64_t n_rows, cudaStream_t s);
+                                      const int64_t *goff, int64_t n_rows, SetLayout sl, cudaStream_t s);
 cudaError_t launch_caller_to_rows_i16(const int16_t *src, int16_t *dst, GraphRef gr, const int32_t *rows,
-                                      const int64_t *goff, int64_t n_rows, cudaStream_t s);
+                                      const int64_t *goff, int64_t n_rows, SetLayout sl, cudaStream_t s);
 int occupancy_fwd(int ntiles, bool smem_bits);
 int occupancy_bwd(int mode);
 

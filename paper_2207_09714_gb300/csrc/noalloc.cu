@@ -115,12 +115,14 @@ gabm_status gabm_seed_state_noalloc(uint64_t seed, int64_t n, int num_instances,
     NA_CK(cudaGetLastError());
     const int64_t n_rows = n * num_instances;
     const int grid = (int)std::min<int64_t>((n_rows + 255) / 256, 65535);
-    NA_CK(launch_init_state(e_out, sc->row0, sc->rows, num_instances, n_rows, grid, s));
+    NA_CK(launch_init_state(e_out, sc->row0, sc->rows, num_instances, n_rows, 1, 1, grid, s));
     SeedArgs sa;
     sa.row0 = sc->row0;
     sa.rows = sc->rows;
     sa.orig_id = nullptr;
     sa.e = e_out;
+    sa.B = 1;
+    sa.Bp = 1;
     sa.st = sc->st;
     sa.hist = &sc->hist[0][0];
     sa.ties = &sc->ties[0][0];

@@ -149,6 +149,17 @@ __device__ __forceinline__ float ld_if(const float *p, bool pred) {
     asm("{ .reg .pred q; setp.ne.u32 q, %2, 0; @q ld.global.f32 %0, [%1]; }" : "+f"(v) : "l"(p), "r"((uint32_t)pred));
     return v;
 }
+__device__ __forceinline__ uint32_t ld_if(const uint32_t *p, bool pred) {
+    uint32_t v = 0u;
+    asm("{ .reg .pred q; setp.ne.u32 q, %2, 0; @q ld.global.u32 %0, [%1]; }" : "+r"(v) : "l"(p), "r"((uint32_t)pred));
+    return v;
+}
+__device__ __forceinline__ float2 ld_if(const float2 *p, bool pred) {
+    float2 v = make_float2(0.f, 0.f);
+    asm("{ .reg .pred q; setp.ne.u32 q, %3, 0; @q ld.global.v2.f32 {%0, %1}, [%2]; }"
+        : "+f"(v.x), "+f"(v.y) : "l"(p), "r"((uint32_t)pred));
+    return v;
+}
 __device__ __forceinline__ int ld_if(const int16_t *p, bool pred, int dflt) {
     int v = dflt;
     asm("{ .reg .pred q; setp.ne.u32 q, %2, 0; @q ld.global.s16 %0, [%1]; }" : "+r"(v) : "l"(p), "r"((uint32_t)pred));

@@ -145,6 +145,13 @@ def test_layout_and_bitmap_variants_are_bitwise_equal(knobs, monkeypatch):
     assert np.array_equal(c0.cpu().numpy(), c1.cpu().numpy())
     for t in (0, 11, 29):
         assert np.array_equal(capi.gabm_get_lambda(base, t)[0], capi.gabm_get_lambda(var, t)[0])
+    # the same switch through the schedule API
+    capi.gabm_set_schedule(base, fwd_smem_bitmap=1)
+    assert capi.gabm_get_schedule(base)["fwd_smem_bitmap"] == 1
+    D2, _ = capi.gabm_forward(base, T, Rd, md_, Sd, [15])
+    assert np.array_equal(D2.cpu().numpy(), D0.cpu().numpy())
+    assert capi.gabm_autotune(base, 1)["fwd_smem_bitmap"] in (0, 1)
+    assert np.array_equal(capi.gabm_get_state(base)[0], e0)
 
 
 @pytest.mark.parametrize("order", [capi.GABM_ORDER_INPUT, capi.GABM_ORDER_BFS])
