@@ -39,6 +39,22 @@ BATCH_SETS = 64
 BATCH_DAYS = 45
 
 
+def max_over_ranks(ms: float, dist=None, device="cpu") -> float:
+    """Whole-job time of a timed region: the maximum over ranks (each rank's own CUDA-event
+    time); the plain value with one rank."""
+    if dist is None:
+        return float(ms)
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank: float, world: int, ms_per_step_max: float) -> float:
+    """Units all ranks processed per second (weak scaling: every rank runs the full workload)."""
+    return world * units_per_rank / (ms_per_step_max / 1e3)
+
+
 def _peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -259,7 +275,9 @@ def bench_batched(args, stream, peak, peak_kind):
     f_gbs = fwd_b.sum() / (f_ms / 1e3) / 1e9
     b_gbs = bwd_b.sum() / (b_ms / 1e3) / 1e9
     both_gbs = (fwd_b.sum() + bwd_b.sum()) / ((f_ms + b_ms) / 1e3) / 1e9
-    counts = capi.gabm_forward(ctx, T, R, m, S, seeds, want_counts=True)[1].cpu().numpy()
+    counts = capi.gabm_forward(ctx, T, R, m, S, seeds, want_counts=True)[1]
+    torch.cuda.synchronize()   # the ctx works on its own stream
+    counts = counts.cpu().numpy()
     attack = 1.0 - counts[:, -1, 0] / pop.n
     del ctx
 
@@ -457,14 +475,10 @@ def main():
     capi.gabm_set_profiling(ctx, False)
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     fwd_ms = [s.elapsed_time(e) for s, e in zip(starts, mids)]
-    total_ms = sum(step_ms)
-    if dist is not None:
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(step_ms), dist, "cuda")
     ms_per_step = total_ms / args.steps
     units = world * pop.n * DAYS
-    value = units / (ms_per_step / 1e3)
+    value = job_throughput(pop.n * DAYS, world, ms_per_step)
     fwd_value = world * pop.n * DAYS / (statistics.median(fwd_ms) / 1e3)
 
     # ---- algorithmic bytes of the day kernels, from this trajectory ----
@@ -513,12 +527,8 @@ def main():
         e2e_step()
     e1.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1)
-    if dist is not None:
-        t = torch.tensor([e2e_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e_value = units / (e2e_ms / args.steps / 1e3)
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1), dist, "cuda")
+    e2e_value = job_throughput(pop.n * DAYS, world, e2e_ms / args.steps)
     h2d = (Rh.numel() * 4 + mh.numel() * 4 + Sh.numel() * 4 + yh.numel() * 8 + gDh.numel() * 8)
     d2h = (Dh.numel() * 8 + lh.numel() * 8 + gDh.numel() * 8 + dRh.numel() * 8 + dmh.numel() * 8 + dSh.numel() * 8)
 

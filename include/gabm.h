@@ -103,7 +103,12 @@ typedef struct {
     int tau_EI, tau_IR;   /* days E->I and I->RM; 1 <= each, L = sum <= GABM_MAX_L */
     const float *c;       /* host [L]: infectiousness by days since exposure, c[0] = 0, c >= 0 */
     float gumbel_tau;     /* relaxation temperature; this build supports 1.0 */
-    int relax_mode;       /* GABM_HARD_ST (GABM_SOFT: GABM_EUNSUPPORTED in this build) */
+    int relax_mode;       /* GABM_HARD_ST, or GABM_SOFT (sets_per_graph = 1 and GABM_STORE_LAMBDA):
+                           * the fixed-noise soft relaxation -- every agent draws every day
+                           * with y = sigmoid(logit p - logit u) and moves mass s y from S to
+                           * E; smooth in the parameters (finite-difference checks of the
+                           * adjoint).  Its state is masses: gabm_get_state / gabm_set_state
+                           * return GABM_EUNSUPPORTED and gabm_forward's counts must be NULL. */
     int lambda_policy;    /* GABM_STORE_LAMBDA or GABM_RECOMPUTE */
     uint64_t seed;        /* Philox key */
     int agent_order;      /* GABM_ORDER_INPUT or GABM_ORDER_BFS (device layout only) */
@@ -159,7 +164,8 @@ gabm_status gabm_get_state(gabm_ctx *ctx, int16_t *e_out, int mem_space);
 gabm_status gabm_set_state(gabm_ctx *ctx, int day, const int16_t *e_in, int mem_space);
 
 /* lambda_i(t) of the last forward for day t, [sets_per_graph][n_total] float, 0 for agents
- * not susceptible on day t.  Needs GABM_STORE_LAMBDA and t run by the forward. */
+ * not susceptible on day t (GABM_SOFT: 0 for the seeds, which hold no susceptible
+ * mass).  Needs GABM_STORE_LAMBDA and t run by the forward. */
 gabm_status gabm_get_lambda(gabm_ctx *ctx, int t, float *lam_out, int mem_space);
 
 /* Kernel schedule of a ctx.  Schedules change how rows and parameter sets map

@@ -233,15 +233,16 @@ def gabm_create(graphs, model: ModelDesc, sets_per_graph: int = 1, stream=None) 
     s = None
     if stream is not None:
         s = ctypes.c_void_p(int(getattr(stream, "cuda_stream", stream)))
-    else:
-        try:
-            import torch
-            if torch.cuda.is_available():
+        device = device or getattr(stream, "device", None)
+    try:
+        import torch
+        if torch.cuda.is_available():
+            if stream is None:
                 stream = torch.cuda.current_stream()
                 s = ctypes.c_void_p(stream.cuda_stream)
-                device = device or torch.device("cuda", torch.cuda.current_device())
-        except ImportError:
-            pass
+            device = device or torch.device("cuda", torch.cuda.current_device())
+    except ImportError:
+        pass
     out = ctypes.c_void_p()
     st = L.gabm_create(descs, len(graphs), int(sets_per_graph), ctypes.byref(md), s, ctypes.byref(out))
     _check(st, None)

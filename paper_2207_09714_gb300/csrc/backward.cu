@@ -27,6 +27,7 @@ namespace {
 template <int MODE>
 __global__ void __launch_bounds__(kBlock, GABM_MINBLOCKS) k_bwd_day(const BwdDayArgs a) {
     constexpr int NARR = (MODE == kBwdFused) ? 2 : 1;
+    constexpr bool SOFT = MODE == kBwdSoft;
     __shared__ float c_s[kMaxL];
     __shared__ int slot_k[kMaxL];
     __shared__ int32_t red_s[kBlock / 32][2];
@@ -78,9 +79,10 @@ __global__ void __launch_bounds__(kBlock, GABM_MINBLOCKS) k_bwd_day(const BwdDay
         const bool agent = (Ei != kPad);
         const bool never = (Ei == kNever);
         const bool live = agent && (never || Ei >= 0);           // seeds are constants
-        const bool isS = live && (never || Ei >= t);
-        const bool needA = has_next && live && (never || Ei >= t + 2 - L);
-        cN += (agent && !never && t - Ei == L);
+        // soft relaxation: every agent carries susceptible mass and draws every day
+        const bool isS = SOFT ? agent : live && (never || Ei >= t);
+        const bool needA = has_next && (SOFT ? agent : live && (never || Ei >= t + 2 - L));
+        if (!SOFT) cN += (agent && !never && t - Ei == L);
 
         float sum[NARR];
         {
@@ -106,7 +108,13 @@ __global__ void __launch_bounds__(kBlock, GABM_MINBLOCKS) k_bwd_day(const BwdDay
             for (int k = 2; k < L; ++k)
                 if (t + k < T) G = __fmaf_rn(c_s[k], a.ring[(size_t)slot_k[k] * a.ring_stride + row], G);
             float dy;
-            if (Ei == t) { a.A[row] = G; dy = G; }
+            if (SOFT) {
+                // dL/dy = s(t) (G - dL/ds(t+1));  dL/ds(t) = y G + (1 - y) dL/ds(t+1)
+                const float ds = a.A[row];
+                const float yv = a.y_hist_t[row];
+                dy = a.s_hist_t[row] * (G - ds);
+                a.A[row] = __fmaf_rn(yv, G, (1.f - yv) * ds);
+            } else if (Ei == t) { a.A[row] = G; dy = G; }
             else if (never) dy = G;
             else dy = G - a.A[row];
             float Lam;
@@ -223,15 +231,17 @@ __global__ void __launch_bounds__(256) k_bwd_reduce(const double *P, int ntiles,
 
 // dR_t = sum_a S_a Q[t][a];  dS_a = sum_t R_t Q[t][a];  dm_t = gD_t newRM(t).
 __global__ void __launch_bounds__(256) k_bwd_finalize(const double *Q, const float *R, const float *S,
-                                                      const double *gD, const int32_t *newRM, int ldP,
-                                                      int T, double *dR, double *dm, double *dS) {
+                                                      const double *gD, const int32_t *newRM,
+                                                      const double *newRM_real, int ldP, int T, double *dR,
+                                                      double *dm, double *dS) {
     const int inst = blockIdx.x;
     for (int t = threadIdx.x; t < T; t += blockDim.x) {
         const double *q = Q + ((size_t)inst * T + t) * kAges;
         double acc = 0.0;
         for (int b = 0; b < kAges; ++b) acc += (double)S[inst * kAges + b] * q[b];
         dR[(size_t)inst * T + t] = acc;
-        dm[(size_t)inst * T + t] = gD[(size_t)inst * ldP + t] * (double)newRM[(size_t)inst * ldP + t];
+        const size_t pi = (size_t)inst * ldP + t;
+        dm[(size_t)inst * T + t] = gD[pi] * (newRM_real ? newRM_real[pi] : (double)newRM[pi]);
     }
     if (threadIdx.x < kAges) {
         const int b = threadIdx.x;
@@ -247,6 +257,7 @@ cudaError_t launch_bwd_day(const BwdDayArgs &a, int grid, cudaStream_t s) {
     switch (a.mode) {
         case kBwdStore: k_bwd_day<kBwdStore><<<grid, kBlock, 0, s>>>(a); break;
         case kBwdFused: k_bwd_day<kBwdFused><<<grid, kBlock, 0, s>>>(a); break;
+        case kBwdSoft: k_bwd_day<kBwdSoft><<<grid, kBlock, 0, s>>>(a); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -262,6 +273,7 @@ int occupancy_bwd(int mode) {
     int blocks = 0;
     switch (mode) {
         case kBwdFused: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_bwd_day<kBwdFused>, kBlock, 0); break;
+        case kBwdSoft: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_bwd_day<kBwdSoft>, kBlock, 0); break;
         default: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_bwd_day<kBwdStore>, kBlock, 0); break;
     }
     return blocks > 0 ? blocks : 1;
@@ -275,9 +287,9 @@ cudaError_t launch_bwd_reduce(const double *P, int ntiles, int ldP, const int32_
 }
 
 cudaError_t launch_bwd_finalize(const double *Q, const float *R, const float *S, const double *gD,
-                                const int32_t *newRM, int ldP, int T, int I, double *dR, double *dm,
-                                double *dS, cudaStream_t s) {
-    k_bwd_finalize<<<I, 256, 0, s>>>(Q, R, S, gD, newRM, ldP, T, dR, dm, dS);
+                                const int32_t *newRM, const double *newRM_real, int ldP, int T, int I, double *dR,
+                                double *dm, double *dS, cudaStream_t s) {
+    k_bwd_finalize<<<I, 256, 0, s>>>(Q, R, S, gD, newRM, newRM_real, ldP, T, dR, dm, dS);
     return cudaGetLastError();
 }
 

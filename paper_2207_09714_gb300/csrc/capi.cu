@@ -32,6 +32,10 @@ struct gabm_ctx {
     bool batched = false;           // B > 1: the set-batched kernels over row-compressed edges
     bool kahan_b = false;           // batched sums: compensated (some row longer than kPlainSumMaxDegree)
     int spl_fwd = 2, spl_bwd = 2;   // batched schedules: sets per lane of the forward / backward day kernels
+    bool soft = false;              // fixed-noise soft relaxation instead of hard draws
+    float *s_soft = nullptr, *nh = nullptr, *x2 = nullptr;      // [n_rows], [L][n_rows], [2][n_rows]
+    float *s_hist = nullptr, *y_hist = nullptr;                 // [Tcap][n_rows] soft histories
+    double *P_nrm = nullptr, *newRM_real = nullptr;             // [Tcap][ntiles], [I][Tcap]
     int tau_EI = 0, tau_IR = 0, L = 0;
     float c[kMaxL] = {0};
     uint64_t seed = 0;
@@ -211,7 +215,6 @@ gabm_status validate_model(const gabm_model_desc *md) {
             return fail(nullptr, GABM_EINVAL, "c[%d] must be finite and >= 0", k);
     if (md->relax_mode != GABM_HARD_ST && md->relax_mode != GABM_SOFT)
         return fail(nullptr, GABM_EINVAL, "unknown relax_mode %d", md->relax_mode);
-    if (md->relax_mode == GABM_SOFT) return fail(nullptr, GABM_EUNSUPPORTED, "GABM_SOFT is not implemented in this build");
     if (!(md->gumbel_tau == 1.0f)) return fail(nullptr, GABM_EUNSUPPORTED, "only gumbel_tau = 1 is implemented");
     if (md->lambda_policy != GABM_STORE_LAMBDA && md->lambda_policy != GABM_RECOMPUTE)
         return fail(nullptr, GABM_EINVAL, "unknown lambda_policy %d", md->lambda_policy);
@@ -399,6 +402,7 @@ gabm_status ensure_days(gabm_ctx *c, int T) {
     dfree(c, c->R); dfree(c, c->m);
     dfree(c, c->dR_s); dfree(c, c->dm_s); dfree(c, c->tile_ctr); dfree(c, c->bits); dfree(c, c->Pc);
     dfree(c, c->tile_new); dfree(c, c->newinf);
+    dfree(c, c->s_hist); dfree(c, c->y_hist); dfree(c, c->P_nrm); dfree(c, c->newRM_real);
     c->Tcap = 0;
     const size_t IT = (size_t)c->I * cap;
     if (c->policy == GABM_STORE_LAMBDA) TRY(dalloc(c, &c->lam, (size_t)cap * c->n_rows * c->Bp));
@@ -409,6 +413,12 @@ gabm_status ensure_days(gabm_ctx *c, int T) {
     TRY(dalloc(c, &c->gD, IT));
     TRY(dalloc(c, &c->y, IT));
     TRY(dalloc(c, &c->P, (size_t)cap * c->ntiles * kAges * c->Bp));
+    if (c->soft) {
+        TRY(dalloc(c, &c->s_hist, (size_t)cap * c->n_rows));
+        TRY(dalloc(c, &c->y_hist, (size_t)cap * c->n_rows));
+        TRY(dalloc(c, &c->P_nrm, (size_t)cap * c->ntiles));
+        TRY(dalloc(c, &c->newRM_real, IT));
+    }
     if (c->batched) {
         TRY(dalloc(c, &c->Pc, (size_t)cap * c->G * c->max_chunks * kAges * c->Bp));
         TRY(dalloc(c, &c->tile_new, (size_t)cap * c->ntiles * c->Bp));
@@ -622,7 +632,8 @@ gabm_status forward_days_plain(gabm_ctx *c, int t0, int T, cudaStream_t s) {
 gabm_status backward_days_plain(gabm_ctx *c, int T, cudaStream_t s) {
     const int ld = c->Tcap;
     BwdDayArgs a;
-    const int mode = c->policy == GABM_STORE_LAMBDA ? kBwdStore : (c->symmetric ? kBwdFused : kBwdSplit);
+    const int mode = c->soft ? kBwdSoft
+                             : (c->policy == GABM_STORE_LAMBDA ? kBwdStore : (c->symmetric ? kBwdFused : kBwdSplit));
     a.mode = mode == kBwdSplit ? kBwdStore : mode;
     a.m = sell_view(c, true);
     a.age = c->age;
@@ -644,12 +655,18 @@ gabm_status backward_days_plain(gabm_ctx *c, int T, cudaStream_t s) {
     a.seed = c->seed;
     for (int k = 0; k < kMaxL; ++k) a.c[k] = k < c->L ? c->c[k] : 0.f;
     const int Lm1 = c->L - 1;
-    if (mode != kBwdStore)   // every day's infectious rows, from the final state
+    if (mode == kBwdFused || mode == kBwdSplit)   // every day's infectious rows, from the final state
         LAUNCH(launch_infectious_bits(c->e, 0, T, c->L, c->ntiles, c->bits, (size_t)c->ntiles, s));
+    a.s_hist_t = a.y_hist_t = nullptr;
     for (int t = T - 1; t >= 0; --t) {
-        a.bits_t = mode != kBwdStore ? c->bits + (size_t)t * c->ntiles : nullptr;
+        a.bits_t = (mode == kBwdFused || mode == kBwdSplit) ? c->bits + (size_t)t * c->ntiles : nullptr;
         a.t = t;
-        a.lam_t = mode == kBwdStore ? c->lam + (size_t)t * c->n_rows : (mode == kBwdSplit ? c->lam_tmp : nullptr);
+        a.lam_t = (mode == kBwdStore || mode == kBwdSoft) ? c->lam + (size_t)t * c->n_rows
+                                                          : (mode == kBwdSplit ? c->lam_tmp : nullptr);
+        if (mode == kBwdSoft) {
+            a.s_hist_t = c->s_hist + (size_t)t * c->n_rows;
+            a.y_hist_t = c->y_hist + (size_t)t * c->n_rows;
+        }
         if (mode == kBwdSplit)
             LAUNCH(launch_lam_day(sell_view(c, false), c->e, c->bits + (size_t)t * c->ntiles, graph_ref(c), t, c->L,
                                   c->ntiles, c->c_dev, c->lam_tmp, c->grid_bwd, s));
@@ -666,9 +683,44 @@ gabm_status backward_days_plain(gabm_ctx *c, int T, cudaStream_t s) {
     return GABM_OK;
 }
 
+// Day loop of the soft relaxation (from day 0: the state comes from the seeded exposure days).
+gabm_status forward_days_soft(gabm_ctx *c, int T, cudaStream_t s) {
+    const size_t n = (size_t)c->n_rows;
+    LAUNCH(launch_soft_init(c->e, c->n_rows, c->L, c->c_dev, c->s_soft, c->nh, c->x2, s));
+    SoftDayArgs a;
+    a.m = sell_view(c, false);
+    a.age = c->age;
+    a.gr = graph_ref(c);
+    a.e = c->e;
+    a.s = c->s_soft;
+    a.nh = c->nh;
+    a.R = c->R;
+    a.S = c->S;
+    a.ldP = c->Tcap;
+    a.ntiles = c->ntiles;
+    a.L = c->L;
+    a.seed = c->seed;
+    for (int k = 0; k < kMaxL; ++k) a.c[k] = k < c->L ? c->c[k] : 0.f;
+    for (int t = 0; t < T; ++t) {
+        a.t = t;
+        a.x_cur = c->x2 + (size_t)(t & 1) * n;
+        a.x_next = c->x2 + (size_t)((t + 1) & 1) * n;
+        a.s_hist_t = c->s_hist + (size_t)t * n;
+        a.y_hist_t = c->y_hist + (size_t)t * n;
+        a.lam_t = c->lam + (size_t)t * n;
+        a.P_nrm_t = c->P_nrm + (size_t)t * c->ntiles;
+        a.tile_ctr = c->tile_ctr + t;
+        prof_begin(c, 0);
+        LAUNCH(launch_fwd_day_soft(a, c->grid_fwd, s));
+        prof_end(c, 0);
+    }
+    return GABM_OK;
+}
+
 enum { kLoopForward = 0, kLoopBackward = 1 };
 
 gabm_status day_loop(gabm_ctx *c, int which, int t0, int T, cudaStream_t s) {
+    if (which == kLoopForward && c->soft) return forward_days_soft(c, T, s);
     if (which == kLoopForward) return c->batched ? forward_days_batched(c, t0, T, s) : forward_days_plain(c, t0, T, s);
     return c->batched ? backward_days_batched(c, T, s) : backward_days_plain(c, T, s);
 }
@@ -764,6 +816,7 @@ gabm_status backward_core(gabm_ctx *c, int T) {
     CK(cudaMemsetAsync(c->r, 0, sizeof(float) * 2 * (size_t)c->n_rows * c->Bp, s));
     CK(cudaMemsetAsync(c->newRM_b, 0, sizeof(int32_t) * (size_t)c->I * ld, s));
     CK(cudaMemsetAsync(c->tile_ctr + ld, 0, sizeof(int) * (size_t)ld, s));
+    if (c->soft) CK(cudaMemsetAsync(c->A, 0, sizeof(float) * (size_t)c->n_rows, s));   // dL/ds(T) = 0
     if (!c->batched && c->policy != GABM_STORE_LAMBDA && !c->symmetric && !c->lam_tmp)
         TRY(dalloc(c, &c->lam_tmp, (size_t)c->n_rows));
     return run_day_loop(c, kLoopBackward, 0, T);
@@ -771,8 +824,13 @@ gabm_status backward_core(gabm_ctx *c, int T) {
 
 // Grid sizes for the current schedule (resident blocks per SM x SMs, at most one warp per tile).
 void apply_schedule(gabm_ctx *c) {
-    const int mode = c->policy == GABM_STORE_LAMBDA ? kBwdStore : (c->symmetric ? kBwdFused : kBwdSplit);
-    if (c->batched) {
+    const int mode = c->soft ? kBwdSoft
+                             : (c->policy == GABM_STORE_LAMBDA ? kBwdStore : (c->symmetric ? kBwdFused : kBwdSplit));
+    if (c->soft) {
+        c->smem_bits = false;
+        c->grid_fwd = c->num_sms * occupancy_fwd_soft();
+        c->grid_bwd = c->num_sms * occupancy_bwd(mode);
+    } else if (c->batched) {
         c->grid_fwd = c->num_sms * occupancy_fwd_b(c->Bp, c->spl_fwd, c->kahan_b);
         c->grid_bwd = c->num_sms * occupancy_bwd_b(c->Bp, c->spl_bwd, c->kahan_b);
     } else {
@@ -816,6 +874,8 @@ gabm_status gabm_create(const gabm_graph_desc *graphs, int num_graphs, int sets_
     TRY(validate_model(model));
     if (sets_per_graph > 1 && model->lambda_policy != GABM_STORE_LAMBDA)
         return fail(nullptr, GABM_EUNSUPPORTED, "sets_per_graph > 1 needs GABM_STORE_LAMBDA in this build");
+    if (model->relax_mode == GABM_SOFT && (sets_per_graph > 1 || model->lambda_policy != GABM_STORE_LAMBDA))
+        return fail(nullptr, GABM_EUNSUPPORTED, "GABM_SOFT needs sets_per_graph = 1 and GABM_STORE_LAMBDA in this build");
 
     // ---- host side: validate, concatenate, transpose ----
     std::vector<HostGraph> hg((size_t)num_graphs);
@@ -919,6 +979,7 @@ gabm_status gabm_create(const gabm_graph_desc *graphs, int num_graphs, int sets_
     c->B = sets_per_graph;
     c->I = num_graphs * sets_per_graph;
     c->batched = batched;
+    c->soft = model->relax_mode == GABM_SOFT;
     c->Bp = 1;
     if (batched) {
         c->Bp = 2;
@@ -1059,6 +1120,11 @@ gabm_status gabm_create(const gabm_graph_desc *graphs, int num_graphs, int sets_
         CTRY(dalloc(c, &c->rbits, (size_t)2 * ntiles));
         CTRY(dalloc(c, &c->hist0, (size_t)c->I * (c->L + 2)));
     }
+    if (c->soft) {
+        CTRY(dalloc(c, &c->s_soft, (size_t)n_rows));
+        CTRY(dalloc(c, &c->nh, (size_t)c->L * n_rows));
+        CTRY(dalloc(c, &c->x2, (size_t)2 * n_rows));
+    }
     CTRY(dalloc(c, &c->S, (size_t)c->I * kAges));
     CTRY(dalloc(c, &c->dS_s, (size_t)c->I * kAges));
     CTRY(dalloc(c, &c->loss_s, (size_t)c->I));
@@ -1105,6 +1171,7 @@ gabm_status gabm_forward(gabm_ctx *ctx, int T, const float *R, const float *m, c
     if (!R || !m || !S_age) return fail(c, GABM_EINVAL, "R, m and S_age are required");
     const int t0 = c->resumed ? c->t0_next : 0;
     if (t0 > T) return fail(c, GABM_EINVAL, "state was set for day %d > T = %d", t0, T);
+    if (c->soft && counts) return fail(c, GABM_EINVAL, "counts are not defined for GABM_SOFT (masses, not agents)");
     if (!c->resumed) {
         if (!n_seed) return fail(c, GABM_EINVAL, "n_seed is required when not resuming");
         for (int i = 0; i < c->I; ++i) {
@@ -1122,8 +1189,12 @@ gabm_status gabm_forward(gabm_ctx *ctx, int T, const float *R, const float *m, c
     if (!c->resumed) c->last_seeds.assign(n_seed, n_seed + c->I);
     TRY(forward_core(c, t0, T, !c->resumed));
     const bool dev = mem_space == GABM_DEVICE;
-    LAUNCH(launch_fwd_finalize(c->newRM, c->counts, c->m, ld, t0, T, c->I, c->D, dev ? D : nullptr,
-                               dev ? counts : nullptr, s));
+    if (c->soft)
+        LAUNCH(launch_soft_finalize(c->P_nrm, c->ntiles, c->d_tile0, c->d_ntiles, c->m, ld, T, c->G, c->newRM_real,
+                                    c->D, dev ? D : nullptr, s));
+    else
+        LAUNCH(launch_fwd_finalize(c->newRM, c->counts, c->m, ld, t0, T, c->I, c->D, dev ? D : nullptr,
+                                   dev ? counts : nullptr, s));
     c->T_last = T;
     c->lam_from = c->policy == GABM_STORE_LAMBDA ? t0 : -1;
     c->last_from_seeding = !c->resumed;
@@ -1175,7 +1246,8 @@ gabm_status gabm_backward(gabm_ctx *ctx, const double *gD, double *dR, double *d
     c->gD_staged = true;
     TRY(backward_core(c, T));
     const bool dev = mem_space == GABM_DEVICE;
-    LAUNCH(launch_bwd_finalize(c->Q, c->R, c->S, c->gD, c->batched ? c->newRM : c->newRM_b, ld, T, c->I,
+    LAUNCH(launch_bwd_finalize(c->Q, c->R, c->S, c->gD, c->batched ? c->newRM : c->newRM_b,
+                               c->soft ? c->newRM_real : nullptr, ld, T, c->I,
                                dev ? dR : c->dR_s,
                                dev ? dm : c->dm_s, dev ? dS_age : c->dS_s, s));
     if (!dev) {
@@ -1192,6 +1264,7 @@ gabm_status gabm_get_state(gabm_ctx *ctx, int16_t *e_out, int mem_space) {
     if (!c) return fail(nullptr, GABM_EINVAL, "ctx is NULL");
     TRY(check_ms(c, mem_space));
     if (!e_out) return fail(c, GABM_EINVAL, "e_out is NULL");
+    if (c->soft) return fail(c, GABM_EUNSUPPORTED, "GABM_SOFT has masses, not exposure days");
     const bool dev = mem_space == GABM_DEVICE;
     LAUNCH(launch_rows_to_caller_i16(c->e, dev ? e_out : c->rows_e, graph_ref(c), c->d_rows, c->d_goff, c->n_rows,
                                      set_layout(c), c->stream));
@@ -1208,6 +1281,7 @@ gabm_status gabm_set_state(gabm_ctx *ctx, int day, const int16_t *e_in, int mem_
     if (!c) return fail(nullptr, GABM_EINVAL, "ctx is NULL");
     TRY(check_ms(c, mem_space));
     if (!e_in) return fail(c, GABM_EINVAL, "e_in is NULL");
+    if (c->soft) return fail(c, GABM_EUNSUPPORTED, "GABM_SOFT has masses, not exposure days");
     if (day < 0 || day > GABM_MAX_DAYS) return fail(c, GABM_EINVAL, "day %d outside 0..%d", day, GABM_MAX_DAYS);
     std::vector<int16_t> h((size_t)c->n_total * c->B);
     if (mem_space == GABM_HOST) {
@@ -1275,7 +1349,7 @@ gabm_status gabm_set_schedule(gabm_ctx *ctx, const gabm_schedule *sched) {
         c->spl_fwd = sched->fwd_sets_per_lane;
         c->spl_bwd = sched->bwd_sets_per_lane;
     } else {
-        if (sched->fwd_smem_bitmap && occupancy_fwd(c->ntiles, true) <= 0)
+        if (sched->fwd_smem_bitmap && (c->soft || occupancy_fwd(c->ntiles, true) <= 0))
             return fail(c, GABM_EINVAL, "the infectious bitmap (%d words) does not fit in shared memory", c->ntiles);
         c->smem_bits = sched->fwd_smem_bitmap != 0;
     }
@@ -1298,7 +1372,7 @@ gabm_status gabm_autotune(gabm_ctx *ctx, int repetitions) {
             if (batch_config_ok(c->Bp, spl)) cands.push_back(gabm_schedule{spl, spl, 0});
     } else {
         cands.push_back(gabm_schedule{0, 0, 0});
-        if (occupancy_fwd(c->ntiles, true) > 0) cands.push_back(gabm_schedule{0, 0, 1});
+        if (!c->soft && occupancy_fwd(c->ntiles, true) > 0) cands.push_back(gabm_schedule{0, 0, 1});
     }
     cudaEvent_t ev[4];
     for (auto &e : ev) CK(cudaEventCreate(&e));
@@ -1332,7 +1406,11 @@ gabm_status gabm_autotune(gabm_ctx *ctx, int repetitions) {
     TRY(gabm_set_schedule(c, &chosen));
     // the last forward's outputs again (the trajectory does not depend on the schedule)
     TRY(forward_core(c, 0, T, true));
-    LAUNCH(launch_fwd_finalize(c->newRM, c->counts, c->m, ld, 0, T, c->I, c->D, nullptr, nullptr, s));
+    if (c->soft)
+        LAUNCH(launch_soft_finalize(c->P_nrm, c->ntiles, c->d_tile0, c->d_ntiles, c->m, ld, T, c->G, c->newRM_real,
+                                    c->D, nullptr, s));
+    else
+        LAUNCH(launch_fwd_finalize(c->newRM, c->counts, c->m, ld, 0, T, c->I, c->D, nullptr, nullptr, s));
     CK(cudaStreamSynchronize(s));
     return GABM_OK;
 }

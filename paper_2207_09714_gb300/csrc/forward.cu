@@ -153,6 +153,110 @@ __global__ void __launch_bounds__(NT, MINB) k_fwd_day(const FwdDayArgs a) {
     }
 }
 
+// ---------------------------------------------------------------------------
+// Fixed-noise soft relaxation (the smooth model whose gradient the
+// straight-through estimator stands in for; used for finite-difference checks):
+// every agent draws every day with y = sigmoid(logit p - logit u) (Gumbel-softmax,
+// tau = 1, the same u as the hard draw), moving mass n = s y from S to E:
+//   s_i(t+1) = s_i(t) - n_i(t),  x_i(t) = sum_{k=1}^{L-1} c[k] n_i(t-k),
+//   newRM(t) = sum_i n_i(t-L),  D_t = m_t newRM(t).
+// ---------------------------------------------------------------------------
+__global__ void k_soft_init(const int16_t *e, int64_t n_rows, int L, const float *c, float *s, float *nh,
+                            float *x_cur) {
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n_rows;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        const int ei = e[r];
+        const bool seedr = (ei != kNever) && (ei != kPad);   // exposed before day 0 (e in [-L, -1])
+        s[r] = (ei == kNever) ? 1.f : 0.f;
+        float x = 0.f;
+        for (int k = 0; k < L; ++k) {
+            // slot k holds day d with d mod L == k, d in [-L, -1]
+            const int d = k - L;
+            const float v = (seedr && ei == d) ? 1.f : 0.f;
+            nh[(size_t)k * n_rows + r] = v;
+        }
+        if (seedr && -ei >= 1 && -ei < L) x = c[-ei];
+        x_cur[r] = x;
+    }
+}
+
+__global__ void __launch_bounds__(kBlock, GABM_MINBLOCKS) k_fwd_day_soft(const SoftDayArgs a) {
+    __shared__ float c_s[kMaxL];
+    if (threadIdx.x < kMaxL) c_s[threadIdx.x] = a.c[threadIdx.x];
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int t = a.t, L = a.L, ntiles = a.ntiles;
+    const float *__restrict__ x_cur = a.x_cur;
+    auto contrib = [&](uint32_t j, float w, bool valid, float (&out)[1]) { out[0] = w * ld_if(x_cur + j, valid); };
+    const bool want[1] = {true};
+    const size_t n_rows = (size_t)ntiles * kTile;
+    const int slot_t = t % L;   // holds n(t - L) before this launch overwrites it with n(t)
+    TileDispenser disp;
+    disp.init(a.tile_ctr, ntiles, gridDim.x * (kBlock / 32), lane);
+    for (int tile = disp.get(); tile < ntiles; tile = disp.get()) {
+        const int row = tile * kTile + lane;
+        const int ei = a.e[row];
+        const bool agent = ei != kPad;
+        const int g = a.gr.tile_graph ? (int)a.gr.tile_graph[tile] : 0;
+        float sum[1];
+        row_sums<1>(a.m, a.m.slice_ptr[tile], a.m.row_len[row], agent, lane, contrib, want, sum);
+        float n_old = 0.f;
+        if (agent) {
+            const float Lam = sum[0] * a.gr.inv_Dbar[g];
+            const float lam = (a.R[(size_t)g * a.ldP + t] * a.S[g * kAges + a.age[row]]) * Lam;
+            const float q = expf(-lam);
+            const float p = -expm1f(-lam);
+            const uint32_t id = caller_id(a.gr, row, g);
+            const float u = uniform_from_word(philox_word(a.seed, id, (uint32_t)t, (uint32_t)g, 0u));
+            const float num = p * (1.f - u);
+            const float y = num / __fmaf_rn(q, u, num);
+            const float s_old = a.s[row];
+            const float n = s_old * y;
+            a.s[row] = s_old - n;
+            n_old = a.nh[(size_t)slot_t * n_rows + row];
+            a.nh[(size_t)slot_t * n_rows + row] = n;
+            // x(t+1) = c[1] n(t) + sum_{k=2}^{L-1} c[k] n(t+1-k)
+            float x = c_s[1] * n;
+            for (int k = 2; k < L; ++k) x = __fmaf_rn(c_s[k], a.nh[(size_t)((t + 1 - k + L) % L) * n_rows + row], x);
+            a.x_next[row] = x;
+            a.s_hist_t[row] = s_old;
+            a.y_hist_t[row] = y;
+            a.lam_t[row] = Lam;
+        } else {
+            a.x_next[row] = 0.f;
+        }
+        float v = n_old;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) a.P_nrm_t[tile] = (double)v;
+    }
+}
+
+// newRM_real[g][t] = sum over graph g's tiles of P_nrm[t][tile] (fixed order, FP64);
+// D = m newRM in FP64, copied out when D_out is given ([G][T]).
+__global__ void __launch_bounds__(256) k_soft_finalize(const double *P_nrm, int ntiles, const int32_t *tile0,
+                                                       const int32_t *ntl, const float *m, int ldP, int T,
+                                                       double *newRM_real, double *D_ctx, double *D_out) {
+    __shared__ double sh[256];
+    const int t = blockIdx.x, g = blockIdx.y;
+    double acc = 0.0;
+    const double *p = P_nrm + (size_t)t * ntiles + tile0[g];
+    for (int i = threadIdx.x; i < ntl[g]; i += blockDim.x) acc += p[i];
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int h = 128; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h) sh[threadIdx.x] += sh[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const size_t pi = (size_t)g * ldP + t;
+        newRM_real[pi] = sh[0];
+        const double d = (double)m[pi] * sh[0];
+        D_ctx[pi] = d;
+        if (D_out) D_out[(size_t)g * T + t] = d;
+    }
+}
+
 // One warp per tile: for every day d of the range, the ballot of rows with
 // 1 <= d - e < L.
 __global__ void k_infectious_bits(const int16_t *e, int t0, int ndays, int L, int ntiles, uint32_t *bits,
@@ -493,6 +597,33 @@ int occupancy_fwd(int ntiles, bool smem_bits) {
     }
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_fwd_day<false, kBlock, GABM_MINBLOCKS>, kBlock, 0);
     return blocks > 0 ? blocks : 1;
+}
+
+cudaError_t launch_soft_init(const int16_t *e, int64_t n_rows, int L, const float *c, float *s, float *nh,
+                             float *x_cur, cudaStream_t st) {
+    int64_t grid = (n_rows + 255) / 256;
+    if (grid > 65535) grid = 65535;
+    k_soft_init<<<(int)(grid > 0 ? grid : 1), 256, 0, st>>>(e, n_rows, L, c, s, nh, x_cur);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fwd_day_soft(const SoftDayArgs &a, int grid, cudaStream_t s) {
+    k_fwd_day_soft<<<grid, kBlock, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+int occupancy_fwd_soft() {
+    int blocks = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_fwd_day_soft, kBlock, 0);
+    return blocks > 0 ? blocks : 1;
+}
+
+cudaError_t launch_soft_finalize(const double *P_nrm, int ntiles, const int32_t *graph_tile0,
+                                 const int32_t *graph_ntiles, const float *m, int ldP, int T, int G,
+                                 double *newRM_real, double *D_ctx, double *D_out, cudaStream_t s) {
+    k_soft_finalize<<<dim3(T, G), 256, 0, s>>>(P_nrm, ntiles, graph_tile0, graph_ntiles, m, ldP, T, newRM_real,
+                                               D_ctx, D_out);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_fwd_finalize(const int32_t *newRM, const int32_t *counts, const float *m, int ldP,

@@ -122,6 +122,28 @@ struct FwdDayArgs {
     float c[kMaxL];
 };
 
+// Fixed-noise soft relaxation (every draw uses y = sigmoid(logit p - logit u)):
+// the state is the susceptible mass s_i and the newly exposed mass n_i(d) of
+// the last L days; x_i(t) = sum_{k=1}^{L-1} c[k] n_i(t-k) is what neighbours pull.
+struct SoftDayArgs {
+    Sell m;                  // in-edges
+    const uint8_t *age;
+    GraphRef gr;
+    const int16_t *e;        // exposure days after seeding (padding rows: kPad)
+    const float *x_cur;      // [n_rows] x_i(t)
+    float *x_next;           // [n_rows] x_i(t+1)
+    float *s;                // [n_rows] susceptible mass
+    float *nh;               // [L][n_rows] n_i(d) in slot d mod L
+    float *s_hist_t, *y_hist_t, *lam_t;   // day-t histories [n_rows]: s_i(t), y_i(t), Lam_i(t)
+    const float *R, *S;
+    int ldP;
+    double *P_nrm_t;         // [ntiles] per-tile sums of n_i(t - L) (newRM of day t)
+    int *tile_ctr;
+    int ntiles, t, L;
+    uint64_t seed;
+    float c[kMaxL];
+};
+
 struct BwdDayArgs {
     Sell m;                    // out-edges (the in-edges themselves when the weights are symmetric)
     const uint8_t *age;
@@ -133,7 +155,8 @@ struct BwdDayArgs {
     float *r_cur;              // coefficients of day t   [n_rows]
     float *ring;               // [L-1][n_rows]
     size_t ring_stride;
-    float *A;                  // [n_rows] adjoint of s carried back from the infection day
+    float *A;                  // [n_rows] adjoint of s carried back from the infection day (soft: dL/ds(t+1))
+    const float *s_hist_t, *y_hist_t;   // soft mode: s_i(t), y_i(t)
     const float *R, *m_t, *S;  // R and mortality [I][ldP], susceptibility [I][9]
     const double *gD;          // [I][ldP]
     int ldP;
@@ -147,7 +170,7 @@ struct BwdDayArgs {
     int ring_slot[kMaxL];      // ring slot holding day t + k, k = 1..L-1
 };
 
-enum { kBwdStore = 0, kBwdFused = 1, kBwdSplit = 2 };
+enum { kBwdStore = 0, kBwdFused = 1, kBwdSplit = 2, kBwdSoft = 3 };
 
 struct SeedState {
     uint32_t prefix;    // high bits of the threshold hash found so far
@@ -273,9 +296,19 @@ cudaError_t launch_lam_day(Sell m, const int16_t *E, const uint32_t *bits, Graph
 cudaError_t launch_bwd_reduce(const double *P, int ntiles, int ldP, const int32_t *graph_tile0,
                               const int32_t *graph_ntiles, int T, int I, double *Q,
                               cudaStream_t s);
+// newRM_real (soft mode, [I][ldP]) replaces the integer newRM when non-null.
 cudaError_t launch_bwd_finalize(const double *Q, const float *R, const float *S, const double *gD,
-                                const int32_t *newRM, int ldP, int T, int I, double *dR,
+                                const int32_t *newRM, const double *newRM_real, int ldP, int T, int I, double *dR,
                                 double *dm, double *dS, cudaStream_t s);
+// Soft relaxation (forward.cu): state from the seeded exposure days, one day, newRM reduction,
+// and D = m newRM with copies out.
+cudaError_t launch_soft_init(const int16_t *e, int64_t n_rows, int L, const float *c, float *s, float *nh,
+                             float *x_cur, cudaStream_t st);
+cudaError_t launch_fwd_day_soft(const SoftDayArgs &a, int grid, cudaStream_t s);
+int occupancy_fwd_soft();
+cudaError_t launch_soft_finalize(const double *P_nrm, int ntiles, const int32_t *graph_tile0,
+                                 const int32_t *graph_ntiles, const float *m, int ldP, int T, int G,
+                                 double *newRM_real, double *D_ctx, double *D_out, cudaStream_t s);
 cudaError_t launch_get_lambda(const float *lam_t, const int16_t *e, const uint8_t *age,
                               GraphRef gr, const float *R, const float *S, int ldP, int t,
                               int64_t n_rows, int B, int Bp, float *out_rows, cudaStream_t s);

@@ -73,7 +73,8 @@ def test_create_rejects_bad_models(lib):
     _expect(capi.GABM_EINVAL, [pop], _md(tau_EI=0, c=c[:7]))
     _expect(capi.GABM_EINVAL, [pop], _md(tau_EI=20, tau_IR=20, c=np.zeros(40, np.float32)))
     _expect(capi.GABM_EUNSUPPORTED, [pop], _md(gumbel_tau=0.5))
-    _expect(capi.GABM_EUNSUPPORTED, [pop], _md(relax_mode=capi.GABM_SOFT))
+    _expect(capi.GABM_EUNSUPPORTED, [pop], _md(relax_mode=capi.GABM_SOFT, lambda_policy=capi.GABM_RECOMPUTE))
+    _expect(capi.GABM_EUNSUPPORTED, [pop], _md(relax_mode=capi.GABM_SOFT), sets=2)
     _expect(capi.GABM_EINVAL, [pop], _md(lambda_policy=7))
     _expect(capi.GABM_EINVAL, [pop], _md(), sets=0)
     _expect(capi.GABM_EINVAL, [], _md())
