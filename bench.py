@@ -257,11 +257,13 @@ def bench_batched(args, stream, peak, peak_kind):
         step()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l0 = capi.gabm_launch_count(ctx)
     e0.record(stream)
     for _ in range(steps):
         step()
     e1.record(stream)
     torch.cuda.synchronize()
+    launches = capi.gabm_launch_count(ctx) - l0
     ms = e0.elapsed_time(e1) / steps
     # per-kernel durations (events around each day launch: eager launches)
     capi.gabm_set_profiling(ctx, True)
@@ -280,6 +282,29 @@ def bench_batched(args, stream, peak, peak_kind):
     counts = counts.cpu().numpy()
     attack = 1.0 - counts[:, -1, 0] / pop.n
     del ctx
+    units = B * pop.n * T
+    dom = "k_bwd_day_b" if b_ms >= f_ms else "k_fwd_day_b"
+    traffic = _ncu_traffic(dom, _kernel_source_sha(["batched.cu", "rowsum.cuh", "gabm_internal.cuh"]),
+                           f"typed500k_B{B}_T{T}_store")
+    result = {
+        "workload": f"one shared {pop.n}-agent typed contact graph, {B} parameter sets (R ~ U[1.5, 4.0], "
+                    f"m ~ U[0.005, 0.05]), {T} days, forward + MSE + backward of every set",
+        "n_agents": pop.n, "nnz": pop.nnz, "sets": B, "days": T,
+        "value": units / (ms / 1e3), "unit": "agent-days/s", "ms_per_step": ms, "steps": steps,
+        "schedule": schedule, "attack_rate_range": [float(attack.min()), float(attack.max())],
+        "gpu_launches": launches,
+        "roofline": {"bound": "hbm", "kernel": dom,
+                     "achieved": b_gbs if dom == "k_bwd_day_b" else f_gbs, "peak": peak, "unit": "GB/s",
+                     "frac": (b_gbs if dom == "k_bwd_day_b" else f_gbs) / peak, "peak_source": peak_kind,
+                     "traffic": traffic,
+                     "fwd_day": {"achieved": f_gbs, "launches": f_n, "ms_total": f_ms,
+                                 "alg_bytes_per_launch": fwd_b.sum() / T},
+                     "bwd_day": {"achieved": b_gbs, "launches": b_n, "ms_total": b_ms,
+                                 "alg_bytes_per_launch": bwd_b.sum() / T},
+                     "fwd_plus_bwd_frac": both_gbs / peak},
+    }
+    if args.no_plain:
+        return result
 
     # plain: one parameter set at a time through the autograd Function, eager launches
     os.environ["GABM_CUDA_GRAPHS"] = "0"
@@ -305,26 +330,11 @@ def bench_batched(args, stream, peak, peak_kind):
     e1.record(stream)
     torch.cuda.synchronize()
     plain_ms = e0.elapsed_time(e1)
-    units = B * pop.n * T
-    return {
-        "workload": f"one shared {pop.n}-agent typed contact graph, {B} parameter sets (R ~ U[1.5, 4.0], "
-                    f"m ~ U[0.005, 0.05]), {T} days, forward + MSE + backward of every set",
-        "n_agents": pop.n, "nnz": pop.nnz, "sets": B, "days": T,
-        "value": units / (ms / 1e3), "unit": "agent-days/s", "ms_per_step": ms, "steps": steps,
-        "schedule": schedule, "attack_rate_range": [float(attack.min()), float(attack.max())],
-        "plain": {"value": units / (plain_ms / 1e3), "ms_per_step": plain_ms,
-                  "path": "one set at a time: GabmFunction (torch.autograd) over the single-set kernels, "
-                          "eager launches, no CUDA graph"},
-        "speedup_vs_plain": plain_ms / ms,
-        "roofline": {"bound": "hbm", "kernel": "k_bwd_day_b" if b_ms >= f_ms else "k_fwd_day_b",
-                     "achieved": b_gbs if b_ms >= f_ms else f_gbs, "peak": peak, "unit": "GB/s",
-                     "frac": (b_gbs if b_ms >= f_ms else f_gbs) / peak, "peak_source": peak_kind,
-                     "fwd_day": {"achieved": f_gbs, "launches": f_n, "ms_total": f_ms,
-                                 "alg_bytes_per_launch": fwd_b.sum() / T},
-                     "bwd_day": {"achieved": b_gbs, "launches": b_n, "ms_total": b_ms,
-                                 "alg_bytes_per_launch": bwd_b.sum() / T},
-                     "fwd_plus_bwd_frac": both_gbs / peak},
-    }
+    result["plain"] = {"value": units / (plain_ms / 1e3), "ms_per_step": plain_ms,
+                       "path": "one set at a time: GabmFunction (torch.autograd) over the single-set kernels, "
+                               "eager launches, no CUDA graph"}
+    result["speedup_vs_plain"] = plain_ms / ms
+    return result
 
 
 def run_reference(args, world, rank):
@@ -398,6 +408,9 @@ def main():
     ap.add_argument("--policy", default="store", choices=["store", "recompute"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--batched-only", action="store_true",
+                    help="run only the batched ensemble; its result is the printed line")
+    ap.add_argument("--no-plain", action="store_true", help="skip the per-set plain comparator")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -420,6 +433,19 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     gbuild.build()
+    if args.batched_only:
+        stream = torch.cuda.Stream()
+        peak, peak_kind = _peaks()
+        with ClockSampler(local) as clk:
+            b = bench_batched(args, stream, peak, peak_kind)
+        if rank == 0:
+            line = {"metric": METRIC, "value": b["value"], "unit": "agent-days/s", "n_gpus": world,
+                    "steps": b["steps"], "warmup": max(args.warmup, 3), "ms_per_step": b["ms_per_step"],
+                    "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                    "data": "synthetic", "config": {"workload": b["workload"]}, "roofline": b["roofline"],
+                    "gpu_launches": b["gpu_launches"], "clocks": clk.summary(), "batched": b}
+            print(json.dumps(line), flush=True)
+        return
 
     pop = synth.population_typed(N_AGENTS, seed=0)
     c = synth.infectiousness_table(TAU_EI, TAU_IR)

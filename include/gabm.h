@@ -163,9 +163,11 @@ gabm_status gabm_get_state(gabm_ctx *ctx, int16_t *e_out, int mem_space);
  * Values must be GABM_NEVER or in [-GABM_MAX_L, day). */
 gabm_status gabm_set_state(gabm_ctx *ctx, int day, const int16_t *e_in, int mem_space);
 
-/* lambda_i(t) of the last forward for day t, [sets_per_graph][n_total] float, 0 for agents
- * not susceptible on day t (GABM_SOFT: 0 for the seeds, which hold no susceptible
- * mass).  Needs GABM_STORE_LAMBDA and t run by the forward. */
+/* lambda_i(t) for day t, [sets_per_graph][n_total] float, 0 for agents not
+ * susceptible on day t (GABM_SOFT: 0 for the seeds, which hold no susceptible mass).
+ * GABM_STORE_LAMBDA: the stored value; t must have been run by the last forward.
+ * GABM_RECOMPUTE: recomputed from the current state, which fixes every earlier day
+ * (no reinfection); 0 <= t < the last forward's T.  GABM_ESTATE otherwise. */
 gabm_status gabm_get_lambda(gabm_ctx *ctx, int t, float *lam_out, int mem_space);
 
 /* Kernel schedule of a ctx.  Schedules change how rows and parameter sets map

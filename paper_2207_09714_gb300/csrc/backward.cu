@@ -31,6 +31,7 @@ __global__ void __launch_bounds__(kBlock, GABM_MINBLOCKS) k_bwd_day(const BwdDay
     __shared__ float c_s[kMaxL];
     __shared__ int slot_k[kMaxL];
     __shared__ int32_t red_s[kBlock / 32][2];
+    __shared__ float fac_s[kBlock / 32][kMaxL];   // 2^(sigma(t+k) - sigma(t)) of the warp's graph
     if (threadIdx.x < kMaxL) {
         c_s[threadIdx.x] = a.c[threadIdx.x];
         slot_k[threadIdx.x] = a.ring_slot[threadIdx.x];
@@ -39,6 +40,10 @@ __global__ void __launch_bounds__(kBlock, GABM_MINBLOCKS) k_bwd_day(const BwdDay
 
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int t = a.t, T = a.T, L = a.L, ntiles = a.ntiles;
+    const int32_t *sg = nullptr;   // scale exponents of the current graph
+    int sig_t = 0;                 // sigma(t) of the current graph
+    unsigned emax_w = 0u;          // largest exponent stored by this warp (+128)
+    float gtail = 0.f;             // m_{t+L} gD_{t+L} at day t's scale
     const bool has_next = (t + 1 < T);
     const int16_t *E = a.E;
     const float *__restrict__ r_next = a.r_next;
@@ -71,7 +76,21 @@ __global__ void __launch_bounds__(kBlock, GABM_MINBLOCKS) k_bwd_day(const BwdDay
             if (cur_g >= 0) {
                 const int sN = __reduce_add_sync(0xffffffffu, cN);
                 if (lane == 0 && sN) atomicAdd(a.newRM + (size_t)cur_g * a.ldP + t, sN);
+                flush_emax(a.emax + (size_t)cur_g * a.ld_sig + t, emax_w);
+                emax_w = 0u;
             }
+            // this day's scale for graph g (every warp computes the same value; the warp
+            // holding the graph's first tile records it)
+            sg = a.sig + (size_t)g * a.ld_sig;
+            sig_t = next_sigma(sg[t + 1], a.emax[(size_t)g * a.ld_sig + t + 1]);
+            if (lane == 0 && tile * kTile == a.gr.row0[g]) a.sig[(size_t)g * a.ld_sig + t] = sig_t;
+            if (lane < kMaxL)
+                fac_s[wib][lane] = (lane >= 1 && lane < L && t + lane <= T) ? exp2i(sg[t + lane] - sig_t) : 0.f;
+            {
+                const size_t pg = (size_t)g * a.ldP;
+                gtail = (t + L < T) ? a.m_t[pg + t + L] * (float)a.gD[pg + t + L] * exp2i(-sig_t) : 0.f;
+            }
+            __syncwarp();
             cur_g = g;
             cN = 0;
         }
@@ -102,24 +121,42 @@ __global__ void __launch_bounds__(kBlock, GABM_MINBLOCKS) k_bwd_day(const BwdDay
             ai = a.age[row];
             const int inst = g;
             const size_t pi = (size_t)inst * a.ldP;
-            float G = 0.f;
-            if (t + L < T) G = a.m_t[pi + t + L] * (float)a.gD[pi + t + L];
-            if (has_next) G = __fmaf_rn(c_s[1], gx_mine, G);
-            for (int k = 2; k < L; ++k)
-                if (t + k < T) G = __fmaf_rn(c_s[k], a.ring[(size_t)slot_k[k] * a.ring_stride + row], G);
-            float dy;
-            if (SOFT) {
-                // dL/dy = s(t) (G - dL/ds(t+1));  dL/ds(t) = y G + (1 - y) dL/ds(t+1)
-                const float ds = a.A[row];
-                const float yv = a.y_hist_t[row];
-                dy = a.s_hist_t[row] * (G - ds);
-                a.A[row] = __fmaf_rn(yv, G, (1.f - yv) * ds);
-            } else if (Ei == t) { a.A[row] = G; dy = G; }
-            else if (never) dy = G;
-            else dy = G - a.A[row];
+            // loads that do not depend on G first, then the ring in batches of 8 slots; A was
+            // stored on day E_i (soft: dL/ds on day t+1) at that day's scale
+            const bool readA = SOFT || (!never && Ei != t);
+            const float Apre = readA ? a.A[row] * (SOFT ? fac_s[wib][1] : exp2i(sg[Ei] - sig_t)) : 0.f;
             float Lam;
             if constexpr (MODE == kBwdFused) Lam = sum[NARR - 1] * a.gr.inv_Dbar[g];
             else Lam = a.lam_t[row];
+            float G = gtail;
+            if (has_next) G = __fmaf_rn(c_s[1], gx_mine * fac_s[wib][1], G);
+            for (int k0 = 2; k0 < L; k0 += 8) {
+                float rv[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int k = k0 + u;
+                    const bool ok = k < L && t + k < T;
+                    rv[u] = ld_if(a.ring + (size_t)slot_k[ok ? k : 0] * a.ring_stride + row, ok);
+                }
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int k = k0 + u;
+                    if (k < L && t + k < T) G = __fmaf_rn(c_s[k], rv[u] * fac_s[wib][k], G);
+                }
+            }
+            float dy;
+            float stored = fabsf(G);
+            if (SOFT) {
+                // dL/dy = s(t) (G - dL/ds(t+1));  dL/ds(t) = y G + (1 - y) dL/ds(t+1)
+                const float ds = Apre;
+                const float yv = a.y_hist_t[row];
+                dy = a.s_hist_t[row] * (G - ds);
+                const float dsn = __fmaf_rn(yv, G, (1.f - yv) * ds);
+                a.A[row] = dsn;
+                stored = fmaxf(stored, fabsf(dsn));
+            } else if (Ei == t) { a.A[row] = G; dy = G; }
+            else if (never) dy = G;
+            else dy = G - Apre;
             const float RS = a.R[pi + t] * a.S[inst * kAges + ai];
             const float lam = RS * Lam;
             const float q = expf(-lam);
@@ -129,8 +166,11 @@ __global__ void __launch_bounds__(kBlock, GABM_MINBLOCKS) k_bwd_day(const BwdDay
             const float den = __fmaf_rn(p, 1.f - u, q * u);
             const float dydl = (u * (1.f - u)) * q / (den * den);
             const float glam = dy * dydl;
-            a.r_cur[row] = RS * glam * a.gr.inv_Dbar[g];
+            const float rc = RS * glam * a.gr.inv_Dbar[g];
+            a.r_cur[row] = rc;
             v = glam * Lam;
+            stored = fmaxf(stored, fabsf(rc));
+            emax_w = max(emax_w, (unsigned)(float_exponent(stored) + 128));
         }
 
         // per-tile sums of gl * Lam by age bin (fp32 over 32 rows, FP64 from here on)
@@ -156,6 +196,7 @@ __global__ void __launch_bounds__(kBlock, GABM_MINBLOCKS) k_bwd_day(const BwdDay
     }
 
     const int sN = __reduce_add_sync(0xffffffffu, cN);
+    if (cur_g >= 0) flush_emax(a.emax + (size_t)cur_g * a.ld_sig + t, emax_w);
     if (lane == 0) { red_s[wib][0] = cur_g; red_s[wib][1] = sN; }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -204,7 +245,8 @@ __global__ void __launch_bounds__(kBlock) k_lam_day(Sell m, const int16_t *E, co
 
 // Q[inst][t][a] = sum over the graph's tiles of P[t][tile][a], fixed order, FP64.
 __global__ void __launch_bounds__(256) k_bwd_reduce(const double *P, int ntiles, const int32_t *graph_tile0,
-                                                    const int32_t *graph_ntiles, int T, double *Q) {
+                                                    const int32_t *graph_ntiles, int T, const int32_t *sig,
+                                                    int ld_sig, double *Q) {
     __shared__ double s[256][kAges];
     const int t = blockIdx.x, inst = blockIdx.y;
     const int g = inst;
@@ -226,7 +268,8 @@ __global__ void __launch_bounds__(256) k_bwd_reduce(const double *P, int ntiles,
             for (int b = 0; b < kAges; ++b) s[threadIdx.x][b] += s[threadIdx.x + h][b];
         __syncthreads();
     }
-    if (threadIdx.x < kAges) Q[((size_t)inst * T + t) * kAges + threadIdx.x] = s[0][threadIdx.x];
+    if (threadIdx.x < kAges)
+        Q[((size_t)inst * T + t) * kAges + threadIdx.x] = ldexp(s[0][threadIdx.x], sig[(size_t)g * ld_sig + t]);
 }
 
 // dR_t = sum_a S_a Q[t][a];  dS_a = sum_t R_t Q[t][a];  dm_t = gD_t newRM(t).
@@ -280,9 +323,10 @@ int occupancy_bwd(int mode) {
 }
 
 cudaError_t launch_bwd_reduce(const double *P, int ntiles, int ldP, const int32_t *graph_tile0,
-                              const int32_t *graph_ntiles, int T, int I, double *Q, cudaStream_t s) {
+                              const int32_t *graph_ntiles, int T, int I, const int32_t *sig, int ld_sig,
+                              double *Q, cudaStream_t s) {
     (void)ldP;
-    k_bwd_reduce<<<dim3(T, I), 256, 0, s>>>(P, ntiles, graph_tile0, graph_ntiles, T, Q);
+    k_bwd_reduce<<<dim3(T, I), 256, 0, s>>>(P, ntiles, graph_tile0, graph_ntiles, T, sig, ld_sig, Q);
     return cudaGetLastError();
 }
 

@@ -39,14 +39,12 @@ namespace {
 constexpr unsigned kFull = 0xffffffffu;
 constexpr float kUmin = 5.9604644775390625e-8f;   // 2^-24: the smallest uniform (u < p is then impossible)
 
+// Adds w * x (x finite).  Invalid entries carry w = 0: s + 0 * x = s exactly for the
+// plain sum (s is never -0); the compensated sum skips them explicitly.
 template <bool KAHAN>
 __device__ __forceinline__ void acc_add(float &s, float &c, float w, float x, bool take) {
-    if (KAHAN) {
-        kahan_add_if(s, c, w * x, take);
-    } else {
-        const float y = __fmaf_rn(w, x, s);
-        s = take ? y : s;
-    }
+    if (KAHAN) kahan_add_if(s, c, w * x, take);
+    else s = __fmaf_rn(w, x, s);
 }
 
 // ---- per-lane vectors of SPL sets ----------------------------------------
@@ -57,14 +55,14 @@ __device__ __forceinline__ void ld_words(const uint32_t *p, bool ok, uint32_t (&
     const uint32_t pr = ok;
     if constexpr (SPL == 2) {
         w[0] = 0u;
-        asm volatile("{ .reg .pred q; setp.ne.u32 q, %2, 0; @q ld.global.u32 %0, [%1]; }" : "+r"(w[0]) : "l"(p), "r"(pr));
+        asm("{ .reg .pred q; setp.ne.u32 q, %2, 0; @q ld.global.u32 %0, [%1]; }" : "+r"(w[0]) : "l"(p), "r"(pr));
     } else if constexpr (SPL == 4) {
         w[0] = w[1] = 0u;
-        asm volatile("{ .reg .pred q; setp.ne.u32 q, %3, 0; @q ld.global.v2.u32 {%0, %1}, [%2]; }"
+        asm("{ .reg .pred q; setp.ne.u32 q, %3, 0; @q ld.global.v2.u32 {%0, %1}, [%2]; }"
                      : "+r"(w[0]), "+r"(w[1]) : "l"(p), "r"(pr));
     } else {
         w[0] = w[1] = w[2] = w[3] = 0u;
-        asm volatile("{ .reg .pred q; setp.ne.u32 q, %5, 0; @q ld.global.v4.u32 {%0, %1, %2, %3}, [%4]; }"
+        asm("{ .reg .pred q; setp.ne.u32 q, %5, 0; @q ld.global.v4.u32 {%0, %1, %2, %3}, [%4]; }"
                      : "+r"(w[0]), "+r"(w[1]), "+r"(w[2]), "+r"(w[3]) : "l"(p), "r"(pr));
     }
 }
@@ -75,12 +73,12 @@ __device__ __forceinline__ void ld_floats(const float *p, bool ok, float (&v)[SP
 #pragma unroll
     for (int h = 0; h < SPL; ++h) v[h] = 0.f;
     if constexpr (SPL == 2) {
-        asm volatile("{ .reg .pred q; setp.ne.u32 q, %3, 0; @q ld.global.v2.f32 {%0, %1}, [%2]; }"
+        asm("{ .reg .pred q; setp.ne.u32 q, %3, 0; @q ld.global.v2.f32 {%0, %1}, [%2]; }"
                      : "+f"(v[0]), "+f"(v[1]) : "l"(p), "r"(pr));
     } else {
 #pragma unroll
         for (int h = 0; h < SPL; h += 4)
-            asm volatile("{ .reg .pred q; setp.ne.u32 q, %5, 0; @q ld.global.v4.f32 {%0, %1, %2, %3}, [%4]; }"
+            asm("{ .reg .pred q; setp.ne.u32 q, %5, 0; @q ld.global.v4.f32 {%0, %1, %2, %3}, [%4]; }"
                          : "+f"(v[h]), "+f"(v[h + 1]), "+f"(v[h + 2]), "+f"(v[h + 3]) : "l"(p + h), "r"(pr));
     }
 }
@@ -104,6 +102,13 @@ __device__ __forceinline__ void st_words(uint32_t *p, const uint32_t (&w)[SPL / 
 }
 
 __device__ __forceinline__ int half_of(uint32_t w, int h) { return (int16_t)(h ? (w >> 16) : (w & 0xffffu)); }
+
+// c[t - e] for 1 <= t - e < L, else 0, from a table c_s[0..kMaxL] with c_s[k] = 0 for k >= L:
+// t - e is negative for susceptible agents (e = NEVER) and huge for padding (e = kPad), both
+// of which clamp (as unsigned) to L, and c[0] = 0.
+__device__ __forceinline__ float infect_lut(int e, const float *c_s, int t, unsigned L) {
+    return c_s[min((unsigned)(t - e), L)];
+}
 
 // For this lane's group row (entries [p0, p0 + len)), sum[h] = sum over the
 // entries whose column is marked in `bits` of w * x_h(j), in entry order, where
@@ -138,7 +143,8 @@ __device__ __forceinline__ void group_row_sums(const Csr &m, uint32_t p0, uint32
                 const int src = ok[u] ? __ffs(mm) - 1 : 0;
                 mm &= mm - 1u;
                 jv[u] = __shfl_sync(kFull, j, src, LPR);
-                wv[u] = __shfl_sync(kFull, w, src, LPR);
+                const float ws = __shfl_sync(kFull, w, src, LPR);
+                wv[u] = ok[u] ? ws : 0.f;   // a zero weight leaves a plain sum unchanged
             }
             Raw rv[U];
 #pragma unroll
@@ -187,8 +193,8 @@ __global__ void __launch_bounds__(kBlock, 2) k_fwd_day_b(const FwdBatchArgs a) {
     constexpr int RPW = 32 / LPR;
     constexpr int Bp = LPR * SPL;
     constexpr int NW = kBlock / 32;
-    __shared__ float c_s[kMaxL];
-    if (threadIdx.x < kMaxL) c_s[threadIdx.x] = a.c[threadIdx.x];
+    __shared__ float c_s[kMaxL + 1];
+    if (threadIdx.x <= kMaxL) c_s[threadIdx.x] = threadIdx.x < kMaxL ? a.c[threadIdx.x] : 0.f;
     __syncthreads();
 
     const int lane = threadIdx.x & 31;
@@ -199,7 +205,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_fwd_day_b(const FwdBatchArgs a) {
     constexpr int WPR = Bp / 2;   // 32-bit words per row of e
 
     auto ld = [&](uint32_t j, bool ok, EWords<SPL> &r) { ld_words<SPL>(e32r + (size_t)j * WPR + q * (SPL / 2), ok, r.w); };
-    auto val = [&](const EWords<SPL> &r, int h) { return infectiousness(half_of(r.w[h >> 1], h & 1), c_s, t, L); };
+    auto val = [&](const EWords<SPL> &r, int h) { return infect_lut(half_of(r.w[h >> 1], h & 1), c_s, t, (unsigned)L); };
 
     int cur_g = -1;
     float Rt[SPL];
@@ -234,11 +240,11 @@ __global__ void __launch_bounds__(kBlock, 2) k_fwd_day_b(const FwdBatchArgs a) {
                 sS[h] = half_of(ew[h >> 1], h & 1) == kNever;
                 mine |= sS[h];
             }
+            const uint32_t p0 = a.m.rowptr[row];
+            const uint32_t p1 = a.m.rowptr[row + 1];
             const bool act = (group_bits<LPR>(__ballot_sync(kFull, mine)) >> grp) & 1u;
-            const uint32_t p0 = ld_if(a.m.rowptr + row, act);
-            const uint32_t p1 = ld_if(a.m.rowptr + row + 1, act);
             float sum[SPL];
-            group_row_sums<LPR, SPL, KAHAN, EWords<SPL>>(a.m, p0, p1 - p0, a.bits_cur, lane, ld, val, sum);
+            group_row_sums<LPR, SPL, KAHAN, EWords<SPL>>(a.m, p0, act ? p1 - p0 : 0u, a.bits_cur, lane, ld, val, sum);
 
             bool inf = false;
             if (mine) {
@@ -252,7 +258,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_fwd_day_b(const FwdBatchArgs a) {
 #pragma unroll
                 for (int h = 0; h < SPL; ++h) {
                     Lam[h] = 0.f;
-                    if (!sS[h]) continue;
+                    if (!sS[h] || sum[h] == 0.f) continue;   // lambda = 0: p = 0, no draw
                     const int inst = g * B + q * SPL + h;
                     Lam[h] = sum[h] * inv_D;
                     const float lam = (Rt[h] * a.S[inst * kAges + ai]) * Lam[h];
@@ -303,6 +309,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_bwd_day_b(const BwdBatchArgs a) {
     __shared__ float c_s[kMaxL];
     __shared__ int slot_k[kMaxL];
     __shared__ float pacc[NW][kAges][Bp];   // per-warp tile sums of gl * Lam by age and set
+    __shared__ float fac_s[NW][kMaxL];       // 2^(sigma(t+k) - sigma(t)) of the warp's graph
     if (threadIdx.x < kMaxL) {
         c_s[threadIdx.x] = a.c[threadIdx.x];
         slot_k[threadIdx.x] = a.ring_slot[threadIdx.x];
@@ -325,18 +332,31 @@ __global__ void __launch_bounds__(kBlock, 2) k_bwd_day_b(const BwdBatchArgs a) {
     float Rt[SPL], Gtail[SPL];
 #pragma unroll
     for (int h = 0; h < SPL; ++h) Rt[h] = Gtail[h] = 0.f;
+    const int32_t *sg = nullptr;   // scale exponents of the current graph (shared by its sets)
+    int sig_t = 0;
+    unsigned emax_w = 0u;          // largest exponent stored by this warp (+128)
     TileDispenser disp;
     disp.init(a.tile_ctr, ntiles, gridDim.x * NW, lane);
     for (int tile = disp.get(); tile < ntiles; tile = disp.get()) {
         const int g = a.gr.tile_graph ? (int)a.gr.tile_graph[tile] : 0;
         if (g != cur_g) {
+            if (cur_g >= 0) {
+                flush_emax(a.emax + (size_t)cur_g * a.ld_sig + t, emax_w);
+                emax_w = 0u;
+            }
             cur_g = g;
+            sg = a.sig + (size_t)g * a.ld_sig;
+            sig_t = next_sigma(sg[t + 1], a.emax[(size_t)g * a.ld_sig + t + 1]);
+            if (lane == 0 && tile * kTile == a.gr.row0[g]) a.sig[(size_t)g * a.ld_sig + t] = sig_t;  // one writer
+            if (lane < kMaxL)
+                fac_s[wib][lane] = (lane >= 1 && lane < L && t + lane <= T) ? exp2i(sg[t + lane] - sig_t) : 0.f;
+            __syncwarp();
 #pragma unroll
             for (int h = 0; h < SPL; ++h) {
                 const int s = q * SPL + h;
                 const size_t pi = (size_t)(g * B + s) * a.ldP;
                 Rt[h] = (s < B) ? a.R[pi + t] : 0.f;
-                Gtail[h] = (s < B && t + L < T) ? a.m_t[pi + t + L] * (float)a.gD[pi + t + L] : 0.f;
+                Gtail[h] = (s < B && t + L < T) ? a.m_t[pi + t + L] * (float)a.gD[pi + t + L] * exp2i(-sig_t) : 0.f;
             }
         }
         const float inv_D = a.gr.inv_Dbar[g];
@@ -357,11 +377,11 @@ __global__ void __launch_bounds__(kBlock, 2) k_bwd_day_b(const BwdBatchArgs a) {
                 needA_any |= has_next && live && (never || Eh >= t + 2 - L);
                 anyS |= isS[h];
             }
+            const uint32_t p0 = a.m.rowptr[row];
+            const uint32_t p1 = a.m.rowptr[row + 1];
             const bool act = (group_bits<LPR>(__ballot_sync(kFull, needA_any)) >> grp) & 1u;
-            const uint32_t p0 = ld_if(a.m.rowptr + row, act);
-            const uint32_t p1 = ld_if(a.m.rowptr + row + 1, act);
             float gx[SPL];
-            group_row_sums<LPR, SPL, KAHAN, FVec<SPL>>(a.m, p0, p1 - p0, a.rbits_next, lane, ld, val, gx);
+            group_row_sums<LPR, SPL, KAHAN, FVec<SPL>>(a.m, p0, act ? p1 - p0 : 0u, a.rbits_next, lane, ld, val, gx);
             if (needA_any) st_floats<SPL>(a.ring + (size_t)slot_k[1] * stride + xo, gx);
 
             float v[SPL];
@@ -371,16 +391,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_bwd_day_b(const BwdBatchArgs a) {
             if (anyS) {
                 ai = a.age[row];
                 const uint32_t id = caller_id(a.gr, row, g);
-                float G[SPL];
-#pragma unroll
-                for (int h = 0; h < SPL; ++h) G[h] = has_next ? __fmaf_rn(c_s[1], gx[h], Gtail[h]) : Gtail[h];
-                for (int k = 2; k < L; ++k)
-                    if (t + k < T) {
-                        float rv[SPL];
-                        ld_floats<SPL>(a.ring + (size_t)slot_k[k] * stride + xo, true, rv);
-#pragma unroll
-                        for (int h = 0; h < SPL; ++h) G[h] = __fmaf_rn(c_s[k], rv[h], G[h]);
-                    }
+                // loads that do not depend on G first, then the ring in batches of 4 slots
                 bool readA = false, writeA = false;
 #pragma unroll
                 for (int h = 0; h < SPL; ++h) {
@@ -392,7 +403,28 @@ __global__ void __launch_bounds__(kBlock, 2) k_bwd_day_b(const BwdBatchArgs a) {
                 ld_floats<SPL>(a.A + xo, readA || writeA, Av);
                 float Lv[SPL];
                 ld_floats<SPL>(a.lam_t + xo, true, Lv);
+                float G[SPL];
+#pragma unroll
+                for (int h = 0; h < SPL; ++h)
+                    G[h] = has_next ? __fmaf_rn(c_s[1], gx[h] * fac_s[wib][1], Gtail[h]) : Gtail[h];
+                for (int k0 = 2; k0 < L; k0 += 4) {
+                    float rv[4][SPL];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int k = k0 + u;
+                        const bool ok = k < L && t + k < T;
+                        ld_floats<SPL>(a.ring + (size_t)slot_k[ok ? k : 0] * stride + xo, ok, rv[u]);
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int k = k0 + u;
+                        if (k < L && t + k < T)
+#pragma unroll
+                            for (int h = 0; h < SPL; ++h) G[h] = __fmaf_rn(c_s[k], rv[u][h] * fac_s[wib][k], G[h]);
+                    }
+                }
                 float rc[SPL];
+                float stored = 0.f;
 #pragma unroll
                 for (int h = 0; h < SPL; ++h) {
                     rc[h] = 0.f;
@@ -401,7 +433,8 @@ __global__ void __launch_bounds__(kBlock, 2) k_bwd_day_b(const BwdBatchArgs a) {
                     float dy;
                     if (Eh == t) { Av[h] = G[h]; dy = G[h]; }
                     else if (Eh == kNever) dy = G[h];
-                    else dy = G[h] - Av[h];
+                    else dy = G[h] - Av[h] * exp2i(sg[Eh] - sig_t);   // A was stored on day Eh
+                    stored = fmaxf(stored, fabsf(G[h]));
                     const int inst = g * B + q * SPL + h;
                     const float RS = Rt[h] * a.S[inst * kAges + ai];
                     const float lam = RS * Lv[h];
@@ -413,7 +446,9 @@ __global__ void __launch_bounds__(kBlock, 2) k_bwd_day_b(const BwdBatchArgs a) {
                     const float glam = dy * dydl;
                     rc[h] = RS * glam * inv_D;
                     v[h] = glam * Lv[h];
+                    stored = fmaxf(stored, fabsf(rc[h]));
                 }
+                emax_w = max(emax_w, (unsigned)(float_exponent(stored) + 128));
                 if (writeA) st_floats<SPL>(a.A + xo, Av);
                 st_floats<SPL>(a.r_cur + xo, rc);
             }
@@ -437,6 +472,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_bwd_day_b(const BwdBatchArgs a) {
         __syncwarp();
         if (lane == 0) a.rbits_cur[tile] = word;
     }
+    if (cur_g >= 0) flush_emax(a.emax + (size_t)cur_g * a.ld_sig + t, emax_w);
 }
 
 // One warp per tile: rows infectious on day t0 (1 <= t0 - e < L) in any set.
@@ -536,7 +572,8 @@ __global__ void k_reduce_b1(const double *P, int ntiles, const int32_t *tile0, c
 }
 
 // Level 2: Q[g*B+s][t][a] = sum over the chunks, in order.
-__global__ void k_reduce_b2(const double *Pc, int G, int B, int Bp, int T, int max_chunks, double *Q) {
+__global__ void k_reduce_b2(const double *Pc, int G, int B, int Bp, int T, int max_chunks, const int32_t *sig,
+                            int ld_sig, double *Q) {
     const int t = blockIdx.x, g = blockIdx.y;
     const int wdt = kAges * Bp;
     for (int k = threadIdx.x; k < wdt; k += blockDim.x) {
@@ -544,7 +581,7 @@ __global__ void k_reduce_b2(const double *Pc, int G, int B, int Bp, int T, int m
         double acc = 0.0;
         const double *p = Pc + ((size_t)t * G + g) * max_chunks * wdt + k;
         for (int c = 0; c < max_chunks; ++c) acc += p[(size_t)c * wdt];
-        if (s < B) Q[((size_t)(g * B + s) * T + t) * kAges + b] = acc;
+        if (s < B) Q[((size_t)(g * B + s) * T + t) * kAges + b] = ldexp(acc, sig[(size_t)g * ld_sig + t]);
     }
 }
 
@@ -655,13 +692,14 @@ cudaError_t launch_counts_b(const uint8_t *tile_new, int ntiles, const int32_t *
 }
 
 cudaError_t launch_bwd_reduce_b(const double *P, int ntiles, const int32_t *d_tile0, const int32_t *d_ntiles, int G,
-                                int B, int Bp, int T, double *scratch, int max_chunks, double *Q, cudaStream_t s) {
+                                int B, int Bp, int T, double *scratch, int max_chunks, const int32_t *sig,
+                                int ld_sig, double *Q, cudaStream_t s) {
     const int wdt = kAges * Bp;
     const int threads = std::min(1024, (wdt + 31) / 32 * 32);
     k_reduce_b1<<<dim3(max_chunks, T, G), threads, 0, s>>>(P, ntiles, d_tile0, d_ntiles, G, Bp, max_chunks, scratch);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_reduce_b2<<<dim3(T, G), threads, 0, s>>>(scratch, G, B, Bp, T, max_chunks, Q);
+    k_reduce_b2<<<dim3(T, G), threads, 0, s>>>(scratch, G, B, Bp, T, max_chunks, sig, ld_sig, Q);
     return cudaGetLastError();
 }
 

@@ -36,6 +36,7 @@ struct gabm_ctx {
     float *s_soft = nullptr, *nh = nullptr, *x2 = nullptr;      // [n_rows], [L][n_rows], [2][n_rows]
     float *s_hist = nullptr, *y_hist = nullptr;                 // [Tcap][n_rows] soft histories
     double *P_nrm = nullptr, *newRM_real = nullptr;             // [Tcap][ntiles], [I][Tcap]
+    int32_t *sig = nullptr, *emax = nullptr;   // [G][Tcap+1] reverse-sweep scale exponents per graph and day
     int tau_EI = 0, tau_IR = 0, L = 0;
     float c[kMaxL] = {0};
     uint64_t seed = 0;
@@ -403,6 +404,7 @@ gabm_status ensure_days(gabm_ctx *c, int T) {
     dfree(c, c->dR_s); dfree(c, c->dm_s); dfree(c, c->tile_ctr); dfree(c, c->bits); dfree(c, c->Pc);
     dfree(c, c->tile_new); dfree(c, c->newinf);
     dfree(c, c->s_hist); dfree(c, c->y_hist); dfree(c, c->P_nrm); dfree(c, c->newRM_real);
+    dfree(c, c->sig); dfree(c, c->emax);
     c->Tcap = 0;
     const size_t IT = (size_t)c->I * cap;
     if (c->policy == GABM_STORE_LAMBDA) TRY(dalloc(c, &c->lam, (size_t)cap * c->n_rows * c->Bp));
@@ -431,6 +433,8 @@ gabm_status ensure_days(gabm_ctx *c, int T) {
     TRY(dalloc(c, &c->dm_s, IT));
     TRY(dalloc(c, &c->tile_ctr, (size_t)2 * cap));
     TRY(dalloc(c, &c->bits, (size_t)(cap + 1) * c->ntiles));
+    TRY(dalloc(c, &c->sig, (size_t)c->G * (cap + 1)));
+    TRY(dalloc(c, &c->emax, (size_t)c->G * (cap + 1)));
     CK(cudaMemsetAsync(c->D, 0, IT * sizeof(double), c->stream));
     c->Tcap = cap;
     c->T_last = -1;
@@ -575,6 +579,9 @@ gabm_status backward_days_batched(gabm_ctx *c, int T, cudaStream_t s) {
     a.B = c->B;
     a.seed = c->seed;
     for (int k = 0; k < kMaxL; ++k) a.c[k] = k < c->L ? c->c[k] : 0.f;
+    a.sig = c->sig;
+    a.emax = c->emax;
+    a.ld_sig = ld + 1;
     const int Lm1 = c->L - 1;
     for (int t = T - 1; t >= 0; --t) {
         a.t = t;
@@ -591,7 +598,7 @@ gabm_status backward_days_batched(gabm_ctx *c, int T, cudaStream_t s) {
         prof_end(c, 1);
     }
     LAUNCH(launch_bwd_reduce_b(c->P, c->ntiles, c->d_tile0, c->d_ntiles, c->G, c->B, c->Bp, T, c->Pc, c->max_chunks,
-                               c->Q, s));
+                               c->sig, ld + 1, c->Q, s));
     return GABM_OK;
 }
 
@@ -658,6 +665,9 @@ gabm_status backward_days_plain(gabm_ctx *c, int T, cudaStream_t s) {
     if (mode == kBwdFused || mode == kBwdSplit)   // every day's infectious rows, from the final state
         LAUNCH(launch_infectious_bits(c->e, 0, T, c->L, c->ntiles, c->bits, (size_t)c->ntiles, s));
     a.s_hist_t = a.y_hist_t = nullptr;
+    a.sig = c->sig;
+    a.emax = c->emax;
+    a.ld_sig = ld + 1;
     for (int t = T - 1; t >= 0; --t) {
         a.bits_t = (mode == kBwdFused || mode == kBwdSplit) ? c->bits + (size_t)t * c->ntiles : nullptr;
         a.t = t;
@@ -679,7 +689,7 @@ gabm_status backward_days_plain(gabm_ctx *c, int T, cudaStream_t s) {
         LAUNCH(launch_bwd_day(a, c->grid_bwd, s));
         prof_end(c, 1);
     }
-    LAUNCH(launch_bwd_reduce(c->P, c->ntiles, ld, c->d_tile0, c->d_ntiles, T, c->I, c->Q, s));
+    LAUNCH(launch_bwd_reduce(c->P, c->ntiles, ld, c->d_tile0, c->d_ntiles, T, c->I, c->sig, ld + 1, c->Q, s));
     return GABM_OK;
 }
 
@@ -816,6 +826,9 @@ gabm_status backward_core(gabm_ctx *c, int T) {
     CK(cudaMemsetAsync(c->r, 0, sizeof(float) * 2 * (size_t)c->n_rows * c->Bp, s));
     CK(cudaMemsetAsync(c->newRM_b, 0, sizeof(int32_t) * (size_t)c->I * ld, s));
     CK(cudaMemsetAsync(c->tile_ctr + ld, 0, sizeof(int) * (size_t)ld, s));
+    // sigma(T) = 0 and no stored exponent yet
+    CK(cudaMemsetAsync(c->sig, 0, sizeof(int32_t) * (size_t)c->G * (ld + 1), s));
+    CK(cudaMemsetAsync(c->emax, 0, sizeof(int32_t) * (size_t)c->G * (ld + 1), s));
     if (c->soft) CK(cudaMemsetAsync(c->A, 0, sizeof(float) * (size_t)c->n_rows, s));   // dL/ds(T) = 0
     if (!c->batched && c->policy != GABM_STORE_LAMBDA && !c->symmetric && !c->lam_tmp)
         TRY(dalloc(c, &c->lam_tmp, (size_t)c->n_rows));
@@ -1314,10 +1327,23 @@ gabm_status gabm_get_lambda(gabm_ctx *ctx, int t, float *lam_out, int mem_space)
     if (!c) return fail(nullptr, GABM_EINVAL, "ctx is NULL");
     TRY(check_ms(c, mem_space));
     if (!lam_out) return fail(c, GABM_EINVAL, "lam_out is NULL");
-    if (c->policy != GABM_STORE_LAMBDA) return fail(c, GABM_ESTATE, "lambda is only stored with GABM_STORE_LAMBDA");
-    if (c->T_last < 1 || t < c->lam_from || t >= c->T_last || c->lam_from < 0)
-        return fail(c, GABM_ESTATE, "day %d was not run by the last forward", t);
-    LAUNCH(launch_get_lambda(c->lam + (size_t)t * c->n_rows * c->Bp, c->e, c->age, graph_ref(c), c->R, c->S, c->Tcap, t,
+    const float *lam_t = nullptr;
+    if (c->policy == GABM_STORE_LAMBDA) {
+        if (c->T_last < 1 || t < c->lam_from || t >= c->T_last || c->lam_from < 0)
+            return fail(c, GABM_ESTATE, "day %d was not run by the last forward", t);
+        lam_t = c->lam + (size_t)t * c->n_rows * c->Bp;
+    } else {
+        // recomputed from the current state, which (no reinfection) fixes every earlier day
+        if (c->T_last < 1 || t < 0 || t >= c->T_last)
+            return fail(c, GABM_ESTATE, "day %d is not before the last forward's horizon", t);
+        if (!c->lam_tmp) TRY(dalloc(c, &c->lam_tmp, (size_t)c->n_rows));
+        uint32_t *bits_t = c->bits + (size_t)c->Tcap * c->ntiles;   // the last day slot, free after a forward
+        LAUNCH(launch_infectious_bits(c->e, t, 1, c->L, c->ntiles, bits_t, (size_t)c->ntiles, c->stream));
+        LAUNCH(launch_lam_day(sell_view(c, false), c->e, bits_t, graph_ref(c), t, c->L, c->ntiles, c->c_dev,
+                              c->lam_tmp, c->grid_bwd, c->stream));
+        lam_t = c->lam_tmp;
+    }
+    LAUNCH(launch_get_lambda(lam_t, c->e, c->age, graph_ref(c), c->R, c->S, c->Tcap, t,
                              c->n_rows, c->B, c->Bp, c->rows_f, c->stream));
     const bool dev = mem_space == GABM_DEVICE;
     LAUNCH(launch_rows_to_caller_f32(c->rows_f, dev ? lam_out : c->stage_f, graph_ref(c), c->d_rows, c->d_goff,

@@ -168,6 +168,8 @@ struct BwdDayArgs {
     uint64_t seed;
     float c[kMaxL];
     int ring_slot[kMaxL];      // ring slot holding day t + k, k = 1..L-1
+    int32_t *sig, *emax;       // [G][ld_sig] scale exponent and largest stored exponent per day
+    int ld_sig;
 };
 
 enum { kBwdStore = 0, kBwdFused = 1, kBwdSplit = 2, kBwdSoft = 3 };
@@ -247,6 +249,8 @@ struct BwdBatchArgs {
     uint64_t seed;
     float c[kMaxL];
     int ring_slot[kMaxL];
+    int32_t *sig, *emax;         // [G][ld_sig] per graph (shared by its sets)
+    int ld_sig;
 };
 
 // Schedules: spl sets per lane (2, 4 or 8; Bp / spl lanes share a row).
@@ -270,8 +274,46 @@ cudaError_t launch_counts_b(const uint8_t *tile_new, int ntiles, const int32_t *
 // Q[g*B+s][t][a] = sum over graph g's tiles of P[t][tile][a][s], in a fixed order (two levels of
 // kReduceChunkTiles tiles); scratch holds T * G * max_chunks * 9 * Bp doubles.
 cudaError_t launch_bwd_reduce_b(const double *P, int ntiles, const int32_t *d_tile0, const int32_t *d_ntiles, int G,
-                                int B, int Bp, int T, double *scratch, int max_chunks, double *Q, cudaStream_t s);
+                                int B, int Bp, int T, double *scratch, int max_chunks, const int32_t *sig,
+                                int ld_sig, double *Q, cudaStream_t s);
 constexpr int kReduceChunkTiles = 64;
+
+// ---------------------------------------------------------------------------
+// Range of the reverse sweep.  The straight-through factor dy/dlambda = (1-u)/u at
+// p -> 0 is heavy-tailed, so the adjoint grows multiplicatively along infection
+// chains and can leave the fp32 range over long horizons.  Every value the sweep
+// stores for day d of graph g (ring entries, A, r, per-tile partial sums) is kept
+// at scale 2^-sigma_g(d): sigma_g(T) = 0 and, going back, sigma_g(t) = sigma_g(t+1)
+// + (emax_g(t+1) > kScaleHigh ? emax_g(t+1) - kScaleTarget : 0), where emax_g(d) is
+// the largest binary exponent of the values stored on day d (a max, so the same in
+// every block and every run).  Terms of different days are combined with exact
+// power-of-two factors; the FP64 reductions multiply 2^sigma back in.
+// ---------------------------------------------------------------------------
+constexpr int kScaleHigh = 64;
+constexpr int kScaleTarget = 32;
+
+__device__ __forceinline__ int float_exponent(float x) {   // floor(log2 |x|), -127 for 0
+    return (int)((__float_as_uint(x) >> 23) & 0xffu) - 127;
+}
+
+__device__ __forceinline__ int next_sigma(int sigma_next, int emax_next) {
+    return sigma_next + (emax_next > kScaleHigh ? emax_next - kScaleTarget : 0);
+}
+
+// 2^k for k <= 127 (0 below the normal range: such terms are negligible at this day's scale)
+__device__ __forceinline__ float exp2i(int k) {
+    return k < -126 ? 0.f : __int_as_float((k + 127) << 23);
+}
+
+// Record this warp's largest stored exponent (+128, 0 = none) for one day of one graph;
+// the atomic is skipped when the stored maximum is already as large.
+__device__ __forceinline__ void flush_emax(int32_t *emax_gt, unsigned em_lane) {
+    const unsigned em = __reduce_max_sync(0xffffffffu, em_lane);
+    if ((threadIdx.x & 31) == 0 && em) {
+        const int v = (int)em - 128;
+        if (*(volatile int32_t *)emax_gt < v) atomicMax(emax_gt, v);
+    }
+}
 
 // Launchers (forward.cu / backward.cu)
 cudaError_t launch_init_state(int16_t *e, const int32_t *row0, const int32_t *rows, int G,
@@ -293,9 +335,10 @@ cudaError_t launch_mse(const double *D, int ldP, const double *y, int T, int I, 
 cudaError_t launch_bwd_day(const BwdDayArgs &a, int grid, cudaStream_t s);
 cudaError_t launch_lam_day(Sell m, const int16_t *E, const uint32_t *bits, GraphRef gr, int t, int L, int ntiles,
                            const float *c, float *lam_out, int grid, cudaStream_t s);
+// Q[g][t][a] = 2^sigma_g(t) x (sum over graph g's tiles of P[t][tile][a]), FP64.
 cudaError_t launch_bwd_reduce(const double *P, int ntiles, int ldP, const int32_t *graph_tile0,
-                              const int32_t *graph_ntiles, int T, int I, double *Q,
-                              cudaStream_t s);
+                              const int32_t *graph_ntiles, int T, int I, const int32_t *sig, int ld_sig,
+                              double *Q, cudaStream_t s);
 // newRM_real (soft mode, [I][ldP]) replaces the integer newRM when non-null.
 cudaError_t launch_bwd_finalize(const double *Q, const float *R, const float *S, const double *gD,
                                 const int32_t *newRM, const double *newRM_real, int ldP, int T, int I, double *dR,

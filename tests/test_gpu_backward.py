@@ -245,3 +245,22 @@ def test_full_size_store_policy_pipeline(full_size_adjoint):
         check_adjoint(dR, g["dR"], "dR")
         check_adjoint(dm, g["dm"], "dm")
         check_adjoint(dS, g["dS"], "dS")
+
+
+def test_long_horizon_adjoint_beyond_fp32_range():
+    """200 days at R = 1.3: the exact adjoint reaches ~1e42, beyond fp32.  The reverse sweep
+    keeps each day's values at a power-of-two scale, so the GPU still matches the FP64 oracle."""
+    pop = synth.population_small(n=3000, seed=3)
+    T = 200
+    Rv = np.full(T, 1.3, np.float32)
+    mv = np.full(T, 0.02, np.float32)
+    S = synth.SUSCEPTIBILITY.astype(np.float32)
+    md_o = O.Model(4, 7, synth.infectiousness_table(), seed=1)
+    ref = O.forward_hard(pop, md_o, Rv, mv, S, n_seed=10)
+    _, gD = O.mse(ref["D"], synth.target_curve(T, pop.n, seed=2, level=5e-5))
+    g = O.backward_hard(pop, md_o, Rv, mv, S, ref["e_final"], gD)
+    assert np.abs(g["dR"]).max() > 3.4e38          # the case the scaling exists for
+    dR, dm, dS = _replay(pop, T, Rv, mv, S, 1, ref["e_final"], gD)
+    check_adjoint(dR, g["dR"], "dR")
+    check_adjoint(dm, g["dm"], "dm")
+    check_adjoint(dS, g["dS"], "dS")

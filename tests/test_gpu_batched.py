@@ -254,3 +254,34 @@ def test_cuda_graph_replay_equals_eager_launches(B, monkeypatch):
     _run_all(graphs, 26, R, m, S, [7] * B, y)
     _run_all(eager, 26, R, m, S, [7] * B, y)
     assert capi.gabm_launch_count(graphs) - n0g == capi.gabm_launch_count(eager) - n0e
+
+
+def test_batched_long_horizon_beyond_fp32_range():
+    """Four sets over 200 days whose exact adjoints reach 1e39..1e51 (beyond fp32): the
+    sets share a power-of-two scale per day, and every set without a near-tie matches
+    the FP64 oracle adjoint."""
+    pop = synth.population_small(n=3000, seed=3)
+    T, B = 200, 4
+    R = np.repeat(np.array([1.2, 1.3, 1.35, 1.45], np.float32)[:, None], T, axis=1)
+    m = np.full((B, T), 0.02, np.float32)
+    S = np.tile(synth.SUSCEPTIBILITY, (B, 1)).astype(np.float32)
+    md_o, refs = _oracle_runs([pop], B, R, m, S, [10] * B, seed=1)
+    y = synth.target_curve(T, pop.n, seed=2, level=5e-5)
+    gDs = np.stack([O.mse(r["D"], y)[1] for r in refs])
+    ctx = capi.gabm_create([pop], model(seed=1), sets_per_graph=B)
+    Rd, md_, Sd, gDd = to_dev(R, m, S, gDs)
+    capi.gabm_forward(ctx, T, Rd, md_, Sd, [10] * B)
+    e = capi.gabm_get_state(ctx)
+    dR, dm, dS = [x.cpu().numpy() for x in capi.gabm_backward(ctx, gDd)]
+    checked = 0
+    for s, ref in enumerate(refs):
+        if ref["margin"] <= EXACT_MARGIN:
+            continue
+        assert np.array_equal(e[s], ref["e_final"])
+        g = O.backward_hard(pop, md_o, R[s], m[s], S[s], ref["e_final"], gDs[s], inst=s)
+        assert np.abs(g["dR"]).max() > 3.4e38
+        check_adjoint(dR[s], g["dR"], f"dR[{s}]")
+        check_adjoint(dm[s], g["dm"], f"dm[{s}]")
+        check_adjoint(dS[s], g["dS"], f"dS[{s}]")
+        checked += 1
+    assert checked >= 2
