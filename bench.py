@@ -88,9 +88,10 @@ def _ncu_traffic(kernel: str, sha: str, workload: str):
 
 
 class ClockSampler:
-    """nvidia-smi clocks / throttle reasons sampled every 200 ms while running."""
+    """nvidia-smi clocks / throttle reasons sampled every 100 ms while running.  Entering
+    waits until the sampler is up, so its samples cover the region it brackets."""
 
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -102,12 +103,15 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            time.sleep(0.5)
         except (OSError, FileNotFoundError):
             self.proc = None
+        self.t0 = time.time()
         return self
 
     def __exit__(self, *exc):
+        self.t1 = time.time()
         self.lines = []
         if self.proc is not None:
             self.proc.terminate()
@@ -118,11 +122,23 @@ class ClockSampler:
                 out, _ = self.proc.communicate()
             self.lines = [l for l in out.splitlines() if l.strip()]
 
+    def _within(self, stamp):
+        try:
+            whole, _, frac = stamp.partition(".")
+            t = time.mktime(time.strptime(whole, "%Y/%m/%d %H:%M:%S")) + float("0." + (frac or "0"))
+        except (ValueError, IndexError):
+            return None
+        return self.t0 - 0.05 <= t <= self.t1 + 0.05
+
     def summary(self):
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for l in getattr(self, "lines", []):
-            p = [x.strip() for x in l.split(",")]
+        lines = [[x.strip() for x in l.split(",")] for l in getattr(self, "lines", [])]
+        stamped = [(self._within(p[0]), p) for p in lines]
+        if any(w is not None for w, _ in stamped):    # keep the samples inside the bracketed region
+            lines = [p for w, p in stamped if w]
+        for p in lines:
+            p = p[1:]
             if len(p) < 9:
                 continue
             try:
@@ -402,7 +418,7 @@ def cpu_baseline(pop, c, y):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--policy", default="store", choices=["store", "recompute"])
@@ -478,8 +494,7 @@ def main():
         step()
     torch.cuda.synchronize()
 
-    # ---- timed region (device-resident inputs) ----
-    capi.gabm_set_profiling(ctx, True)
+    # ---- timed region (device-resident inputs; day loops replayed as CUDA graphs) ----
     launches0 = capi.gabm_launch_count(ctx)
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     mids = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
@@ -496,9 +511,6 @@ def main():
     if dist is not None:
         dist.barrier()
     launches = capi.gabm_launch_count(ctx) - launches0
-    fwd_ms_k, fwd_n = capi.gabm_get_profile(ctx, 0)
-    bwd_ms_k, bwd_n = capi.gabm_get_profile(ctx, 1)
-    capi.gabm_set_profiling(ctx, False)
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     fwd_ms = [s.elapsed_time(e) for s, e in zip(starts, mids)]
     total_ms = max_over_ranks(sum(step_ms), dist, "cuda")
@@ -506,6 +518,21 @@ def main():
     units = world * pop.n * DAYS
     value = job_throughput(pop.n * DAYS, world, ms_per_step)
     fwd_value = world * pop.n * DAYS / (statistics.median(fwd_ms) / 1e3)
+
+    # ---- the same steps again with CUDA events around every day launch (eager launches):
+    # per-kernel durations for the roofline ----
+    capi.gabm_set_profiling(ctx, True)
+    torch.cuda.synchronize()
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    p0.record(stream)
+    for k in range(args.steps):
+        step()
+    p1.record(stream)
+    torch.cuda.synchronize()
+    ms_per_step_profiled = p0.elapsed_time(p1) / args.steps
+    fwd_ms_k, fwd_n = capi.gabm_get_profile(ctx, 0)
+    bwd_ms_k, bwd_n = capi.gabm_get_profile(ctx, 1)
+    capi.gabm_set_profiling(ctx, False)
 
     # ---- algorithmic bytes of the day kernels, from this trajectory ----
     E = capi.gabm_get_state(ctx)[0]
@@ -578,6 +605,7 @@ def main():
                    "lambda_policy": args.policy, "R": R0, "n_seed": N_SEED,
                    "l2": f"inputs larger than L2 (edge arrays {pop.nnz * 8 / 1e6:.0f} MB > 129 MB), no flush"},
         "fwd_agent_days_per_s": fwd_value,
+        "ms_per_step_profiled": ms_per_step_profiled,
         "edge_updates_per_s": world * pop.nnz * DAYS / (ms_per_step / 1e3),
         "sus_edges_per_day_mean": float(S_nnz.mean()),
         "roofline": {"bound": "hbm", "kernel": dominant, "achieved": dom_gbs, "peak": peak, "unit": "GB/s",

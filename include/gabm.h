@@ -177,12 +177,17 @@ gabm_status gabm_get_lambda(gabm_ctx *ctx, int t, float *lam_out, int mem_space)
  *     carries 2, 4 or 8 parameter sets of a row (Bp / that many lanes share a
  *     row, Bp = sets_per_graph rounded up to a power of two; at most Bp);
  *   fwd_smem_bitmap: sets_per_graph == 1 only -- 1 keeps the day's bitmap of
- *     infectious agents in shared memory (when it fits), 0 reads it through L1.
+ *     infectious agents in shared memory (when it fits), 0 reads it through L1;
+ *   bwd_sets_per_launch: sets_per_graph > 1 only -- the backward runs a row's Bp
+ *     sets in launches of this many (a power of two dividing Bp, at least
+ *     bwd_sets_per_lane; 0 on input means Bp), so that the coefficients one
+ *     launch gathers can stay in L2.
  * Fields that do not apply are reported as 0 and ignored on input. */
 typedef struct {
     int fwd_sets_per_lane;
     int bwd_sets_per_lane;
     int fwd_smem_bitmap;
+    int bwd_sets_per_launch;
 } gabm_schedule;
 
 gabm_status gabm_get_schedule(const gabm_ctx *ctx, gabm_schedule *out);

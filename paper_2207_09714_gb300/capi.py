@@ -53,7 +53,7 @@ class _ModelDesc(ctypes.Structure):
 
 class _Schedule(ctypes.Structure):
     _fields_ = [("fwd_sets_per_lane", ctypes.c_int), ("bwd_sets_per_lane", ctypes.c_int),
-                ("fwd_smem_bitmap", ctypes.c_int)]
+                ("fwd_smem_bitmap", ctypes.c_int), ("bwd_sets_per_launch", ctypes.c_int)]
 
 
 _lib = None
@@ -351,8 +351,9 @@ def gabm_get_schedule(ctx: GabmCtx) -> dict:
     return {k: int(getattr(sc, k)) for k, _ in _Schedule._fields_}
 
 
-def gabm_set_schedule(ctx: GabmCtx, fwd_sets_per_lane=0, bwd_sets_per_lane=0, fwd_smem_bitmap=0):
-    sc = _Schedule(int(fwd_sets_per_lane), int(bwd_sets_per_lane), int(fwd_smem_bitmap))
+def gabm_set_schedule(ctx: GabmCtx, fwd_sets_per_lane=0, bwd_sets_per_lane=0, fwd_smem_bitmap=0,
+                      bwd_sets_per_launch=0):
+    sc = _Schedule(int(fwd_sets_per_lane), int(bwd_sets_per_lane), int(fwd_smem_bitmap), int(bwd_sets_per_launch))
     _check(load_library().gabm_set_schedule(ctx.handle, ctypes.byref(sc)), ctx.handle)
 
 

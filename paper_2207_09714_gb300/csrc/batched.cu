@@ -304,28 +304,29 @@ __global__ void __launch_bounds__(kBlock, 2) k_fwd_day_b(const FwdBatchArgs a) {
 template <int LPR, int SPL, bool KAHAN>
 __global__ void __launch_bounds__(kBlock, 2) k_bwd_day_b(const BwdBatchArgs a) {
     constexpr int RPW = 32 / LPR;
-    constexpr int Bp = LPR * SPL;
+    constexpr int Bc = LPR * SPL;        // sets of this launch (a chunk of the row's Bw)
     constexpr int NW = kBlock / 32;
     __shared__ float c_s[kMaxL];
     __shared__ int slot_k[kMaxL];
-    __shared__ float pacc[NW][kAges][Bp];   // per-warp tile sums of gl * Lam by age and set
+    __shared__ float pacc[NW][kAges][Bc];   // per-warp tile sums of gl * Lam by age and set
     __shared__ float fac_s[NW][kMaxL];       // 2^(sigma(t+k) - sigma(t)) of the warp's graph
     if (threadIdx.x < kMaxL) {
         c_s[threadIdx.x] = a.c[threadIdx.x];
         slot_k[threadIdx.x] = a.ring_slot[threadIdx.x];
     }
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    for (int i = lane; i < kAges * Bp; i += 32) (&pacc[wib][0][0])[i] = 0.f;
+    for (int i = lane; i < kAges * Bc; i += 32) (&pacc[wib][0][0])[i] = 0.f;
     __syncthreads();
 
     const int grp = lane / LPR, q = lane % LPR;
     const int t = a.t, T = a.T, L = a.L, B = a.B, ntiles = a.ntiles;
     const bool has_next = t + 1 < T;
     const uint32_t *E32 = reinterpret_cast<const uint32_t *>(a.E);
-    constexpr int WPR = Bp / 2;
+    const int Bw = a.Bw;                 // row width of the per-agent arrays
+    const int s0 = a.s0 + q * SPL;       // this lane's first set
     const size_t stride = a.ring_stride;
 
-    auto ld = [&](uint32_t j, bool ok, FVec<SPL> &r) { ld_floats<SPL>(a.r_next + (size_t)j * Bp + q * SPL, ok, r.v); };
+    auto ld = [&](uint32_t j, bool ok, FVec<SPL> &r) { ld_floats<SPL>(a.r_next + (size_t)j * Bw + s0, ok, r.v); };
     auto val = [](const FVec<SPL> &r, int h) { return r.v[h]; };
 
     int cur_g = -1;
@@ -353,7 +354,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_bwd_day_b(const BwdBatchArgs a) {
             __syncwarp();
 #pragma unroll
             for (int h = 0; h < SPL; ++h) {
-                const int s = q * SPL + h;
+                const int s = s0 + h;
                 const size_t pi = (size_t)(g * B + s) * a.ldP;
                 Rt[h] = (s < B) ? a.R[pi + t] : 0.f;
                 Gtail[h] = (s < B && t + L < T) ? a.m_t[pi + t + L] * (float)a.gD[pi + t + L] * exp2i(-sig_t) : 0.f;
@@ -363,9 +364,9 @@ __global__ void __launch_bounds__(kBlock, 2) k_bwd_day_b(const BwdBatchArgs a) {
         uint32_t word = 0u;
         for (int pass = 0; pass < LPR; ++pass) {
             const int row = tile * kTile + pass * RPW + grp;
-            const size_t xo = (size_t)row * Bp + q * SPL;   // this lane's first slot
+            const size_t xo = (size_t)row * Bw + s0;   // this lane's first slot
             uint32_t ew[SPL / 2];
-            ld_words<SPL>(E32 + (size_t)row * WPR + q * (SPL / 2), true, ew);
+            ld_words<SPL>(E32 + xo / 2, true, ew);
             bool isS[SPL];
             bool needA_any = false, anyS = false;
 #pragma unroll
@@ -435,7 +436,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_bwd_day_b(const BwdBatchArgs a) {
                     else if (Eh == kNever) dy = G[h];
                     else dy = G[h] - Av[h] * exp2i(sg[Eh] - sig_t);   // A was stored on day Eh
                     stored = fmaxf(stored, fabsf(G[h]));
-                    const int inst = g * B + q * SPL + h;
+                    const int inst = g * B + s0 + h;
                     const float RS = Rt[h] * a.S[inst * kAges + ai];
                     const float lam = RS * Lv[h];
                     const float qv = expf(-lam);
@@ -463,10 +464,10 @@ __global__ void __launch_bounds__(kBlock, 2) k_bwd_day_b(const BwdBatchArgs a) {
             word |= group_bits<LPR>(__ballot_sync(kFull, anyS)) << (pass * RPW);
         }
         // per-tile sums by age and set: fp32 over the tile's 32 rows, FP64 from here on
-        double *Pt = a.P_t + (size_t)tile * kAges * Bp;
-        for (int i = lane; i < kAges * Bp; i += 32) {
+        double *Pt = a.P_t + (size_t)tile * kAges * Bw + a.s0;
+        for (int i = lane; i < kAges * Bc; i += 32) {
             float *cell = &pacc[wib][0][0] + i;
-            Pt[i] = (double)*cell;
+            Pt[(i / Bc) * Bw + (i % Bc)] = (double)*cell;
             *cell = 0.f;
         }
         __syncwarp();
@@ -638,8 +639,8 @@ cudaError_t launch_fwd_day_b(const FwdBatchArgs &a, int Bp, int spl, bool kahan,
     return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_bwd_day_b(const BwdBatchArgs &a, int Bp, int spl, bool kahan, int grid, cudaStream_t s) {
-#define X(bp, sp) if (Bp == bp && spl == sp) return launch_bwd_cfg<bp / sp, sp>(a, kahan, grid, s);
+cudaError_t launch_bwd_day_b(const BwdBatchArgs &a, int Bc, int spl, bool kahan, int grid, cudaStream_t s) {
+#define X(bp, sp) if (Bc == bp && spl == sp) return launch_bwd_cfg<bp / sp, sp>(a, kahan, grid, s);
     GABM_BATCH_CONFIGS(X)
 #undef X
     return cudaErrorInvalidValue;
@@ -652,8 +653,8 @@ int occupancy_fwd_b(int Bp, int spl, bool kahan) {
     return 1;
 }
 
-int occupancy_bwd_b(int Bp, int spl, bool kahan) {
-#define X(bp, sp) if (Bp == bp && spl == sp) return occ_cfg<bp / sp, sp>(false, kahan);
+int occupancy_bwd_b(int Bc, int spl, bool kahan) {
+#define X(bp, sp) if (Bc == bp && spl == sp) return occ_cfg<bp / sp, sp>(false, kahan);
     GABM_BATCH_CONFIGS(X)
 #undef X
     return 1;

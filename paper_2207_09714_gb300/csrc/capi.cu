@@ -32,6 +32,7 @@ struct gabm_ctx {
     bool batched = false;           // B > 1: the set-batched kernels over row-compressed edges
     bool kahan_b = false;           // batched sums: compensated (some row longer than kPlainSumMaxDegree)
     int spl_fwd = 2, spl_bwd = 2;   // batched schedules: sets per lane of the forward / backward day kernels
+    int bwd_chunk = 1;              // batched backward: sets per launch (a power of two dividing Bp)
     bool soft = false;              // fixed-noise soft relaxation instead of hard draws
     float *s_soft = nullptr, *nh = nullptr, *x2 = nullptr;      // [n_rows], [L][n_rows], [2][n_rows]
     float *s_hist = nullptr, *y_hist = nullptr;                 // [Tcap][n_rows] soft histories
@@ -57,7 +58,7 @@ struct gabm_ctx {
     // row-compressed edges (batched kernels): in-edges, and out-edges when not symmetric
     uint32_t *csr_rowptr = nullptr, *csr_col = nullptr, *t_csr_rowptr = nullptr, *t_csr_col = nullptr;
     float *csr_w = nullptr, *t_csr_w = nullptr;
-    uint32_t *rbits = nullptr;      // [2][ntiles] rows susceptible in some set (batched backward)
+    uint32_t *rbits = nullptr;      // [Bp/2][2][ntiles] rows susceptible in some set of a chunk (batched backward)
     double *Pc = nullptr;           // [Tcap][G][max_chunks][9][Bp] first-level gradient sums (batched)
     int max_chunks = 0, max_graph_tiles = 0;
     uint8_t *tile_new = nullptr;    // [Tcap][ntiles][Bp] exposures per tile, set and day (batched)
@@ -98,7 +99,7 @@ struct gabm_ctx {
 
     int grid_fwd = 0, grid_bwd = 0;
     bool smem_bits = false;         // forward keeps the infectious bitmap in shared memory
-    int *tile_ctr = nullptr;        // [2][Tcap] per-launch tile counters (forward, backward)
+    int *tile_ctr = nullptr;        // [1 + max chunks][Tcap] per-launch tile counters (forward, backward chunks)
     uint32_t *bits = nullptr;       // [Tcap][ntiles] per-day bitmaps of infectious rows
 
     size_t mem_cur = 0, mem_peak = 0;
@@ -392,6 +393,9 @@ HostGraph permute_graph(const HostGraph &h, const std::vector<uint32_t> &order) 
     return o;
 }
 
+// Launches per backward day at most (the batched backward may split a row's sets).
+int max_bwd_chunks(const gabm_ctx *c) { return c->batched ? std::max(1, c->Bp / 2) : 1; }
+
 gabm_status ensure_days(gabm_ctx *c, int T) {
     if (T <= c->Tcap) return GABM_OK;
     int cap = c->Tcap > 0 ? c->Tcap : 8;
@@ -431,7 +435,7 @@ gabm_status ensure_days(gabm_ctx *c, int T) {
     TRY(dalloc(c, &c->m, IT));
     TRY(dalloc(c, &c->dR_s, IT));
     TRY(dalloc(c, &c->dm_s, IT));
-    TRY(dalloc(c, &c->tile_ctr, (size_t)2 * cap));
+    TRY(dalloc(c, &c->tile_ctr, (size_t)(1 + max_bwd_chunks(c)) * cap));
     TRY(dalloc(c, &c->bits, (size_t)(cap + 1) * c->ntiles));
     TRY(dalloc(c, &c->sig, (size_t)c->G * (cap + 1)));
     TRY(dalloc(c, &c->emax, (size_t)c->G * (cap + 1)));
@@ -558,7 +562,8 @@ gabm_status forward_days_batched(gabm_ctx *c, int t0, int T, cudaStream_t s) {
 gabm_status backward_days_batched(gabm_ctx *c, int T, cudaStream_t s) {
     const int ld = c->Tcap;
     const size_t nb = (size_t)c->n_rows * c->Bp;
-    CK(cudaMemsetAsync(c->rbits, 0, sizeof(uint32_t) * 2 * (size_t)c->ntiles, s));
+    const int nch = c->Bp / c->bwd_chunk;
+    CK(cudaMemsetAsync(c->rbits, 0, sizeof(uint32_t) * 2 * (size_t)c->ntiles * nch, s));
     BwdBatchArgs a;
     a.m = csr_view(c, true);
     a.age = c->age;
@@ -582,19 +587,25 @@ gabm_status backward_days_batched(gabm_ctx *c, int T, cudaStream_t s) {
     a.sig = c->sig;
     a.emax = c->emax;
     a.ld_sig = ld + 1;
+    a.Bw = c->Bp;
     const int Lm1 = c->L - 1;
     for (int t = T - 1; t >= 0; --t) {
         a.t = t;
         a.lam_t = c->lam + (size_t)t * nb;
         a.r_next = c->r + (size_t)((t + 1) & 1) * nb;
         a.r_cur = c->r + (size_t)(t & 1) * nb;
-        a.rbits_next = c->rbits + (size_t)((t + 1) & 1) * c->ntiles;
-        a.rbits_cur = c->rbits + (size_t)(t & 1) * c->ntiles;
+
         a.P_t = c->P + (size_t)t * c->ntiles * kAges * c->Bp;
         for (int k = 0; k < kMaxL; ++k) a.ring_slot[k] = (k >= 1 && k < c->L) ? (t + k) % Lm1 : 0;
-        a.tile_ctr = c->tile_ctr + ld + t;
         prof_begin(c, 1);
-        LAUNCH(launch_bwd_day_b(a, c->Bp, c->spl_bwd, c->kahan_b, c->grid_bwd, s));
+        for (int ch = 0; ch < nch; ++ch) {   // the row's sets in launches of bwd_chunk sets
+            a.s0 = ch * c->bwd_chunk;
+            uint32_t *rb = c->rbits + (size_t)ch * 2 * c->ntiles;
+            a.rbits_next = rb + (size_t)((t + 1) & 1) * c->ntiles;
+            a.rbits_cur = rb + (size_t)(t & 1) * c->ntiles;
+            a.tile_ctr = c->tile_ctr + (size_t)(1 + ch) * ld + t;
+            LAUNCH(launch_bwd_day_b(a, c->bwd_chunk, c->spl_bwd, c->kahan_b, c->grid_bwd, s));
+        }
         prof_end(c, 1);
     }
     LAUNCH(launch_bwd_reduce_b(c->P, c->ntiles, c->d_tile0, c->d_ntiles, c->G, c->B, c->Bp, T, c->Pc, c->max_chunks,
@@ -825,7 +836,7 @@ gabm_status backward_core(gabm_ctx *c, int T) {
     cudaStream_t s = c->stream;
     CK(cudaMemsetAsync(c->r, 0, sizeof(float) * 2 * (size_t)c->n_rows * c->Bp, s));
     CK(cudaMemsetAsync(c->newRM_b, 0, sizeof(int32_t) * (size_t)c->I * ld, s));
-    CK(cudaMemsetAsync(c->tile_ctr + ld, 0, sizeof(int) * (size_t)ld, s));
+    CK(cudaMemsetAsync(c->tile_ctr + ld, 0, sizeof(int) * (size_t)ld * max_bwd_chunks(c), s));
     // sigma(T) = 0 and no stored exponent yet
     CK(cudaMemsetAsync(c->sig, 0, sizeof(int32_t) * (size_t)c->G * (ld + 1), s));
     CK(cudaMemsetAsync(c->emax, 0, sizeof(int32_t) * (size_t)c->G * (ld + 1), s));
@@ -845,7 +856,7 @@ void apply_schedule(gabm_ctx *c) {
         c->grid_bwd = c->num_sms * occupancy_bwd(mode);
     } else if (c->batched) {
         c->grid_fwd = c->num_sms * occupancy_fwd_b(c->Bp, c->spl_fwd, c->kahan_b);
-        c->grid_bwd = c->num_sms * occupancy_bwd_b(c->Bp, c->spl_bwd, c->kahan_b);
+        c->grid_bwd = c->num_sms * occupancy_bwd_b(c->bwd_chunk, c->spl_bwd, c->kahan_b);
     } else {
         const int bps = c->smem_bits ? occupancy_fwd(c->ntiles, true) : 0;
         if (c->smem_bits && bps <= 0) c->smem_bits = false;
@@ -1008,6 +1019,7 @@ gabm_status gabm_create(const gabm_graph_desc *graphs, int num_graphs, int sets_
     if (batched) {
         // widest vectors first: eight sets per lane keeps 32 / (Bp / 8) rows in flight per warp
         c->spl_fwd = c->spl_bwd = std::min(c->Bp, 8);
+        c->bwd_chunk = c->Bp;
         if (const char *f = getenv("GABM_BATCH_SPL")) {
             const int v = atoi(f);
             if (batch_config_ok(c->Bp, v)) c->spl_fwd = c->spl_bwd = v;
@@ -1130,7 +1142,7 @@ gabm_status gabm_create(const gabm_graph_desc *graphs, int num_graphs, int sets_
     CTRY(dalloc(c, &c->rows_e, nb));
     CTRY(dalloc(c, &c->stage_f, nb));
     if (batched) {
-        CTRY(dalloc(c, &c->rbits, (size_t)2 * ntiles));
+        CTRY(dalloc(c, &c->rbits, (size_t)2 * ntiles * std::max(1, c->Bp / 2)));
         CTRY(dalloc(c, &c->hist0, (size_t)c->I * (c->L + 2)));
     }
     if (c->soft) {
@@ -1361,6 +1373,7 @@ gabm_status gabm_get_schedule(const gabm_ctx *ctx, gabm_schedule *out) {
     if (!out) return GABM_EINVAL;
     out->fwd_sets_per_lane = ctx->batched ? ctx->spl_fwd : 0;
     out->bwd_sets_per_lane = ctx->batched ? ctx->spl_bwd : 0;
+    out->bwd_sets_per_launch = ctx->batched ? ctx->bwd_chunk : 0;
     out->fwd_smem_bitmap = ctx->batched ? 0 : (ctx->smem_bits ? 1 : 0);
     return GABM_OK;
 }
@@ -1370,10 +1383,15 @@ gabm_status gabm_set_schedule(gabm_ctx *ctx, const gabm_schedule *sched) {
     if (!c) return fail(nullptr, GABM_EINVAL, "ctx is NULL");
     if (!sched) return fail(c, GABM_EINVAL, "schedule is NULL");
     if (c->batched) {
-        if (!batch_config_ok(c->Bp, sched->fwd_sets_per_lane) || !batch_config_ok(c->Bp, sched->bwd_sets_per_lane))
-            return fail(c, GABM_EINVAL, "sets per lane must be 2, 4 or 8 and at most %d", c->Bp);
+        const int chunk = sched->bwd_sets_per_launch > 0 ? sched->bwd_sets_per_launch : c->Bp;
+        if (!batch_config_ok(c->Bp, sched->fwd_sets_per_lane))
+            return fail(c, GABM_EINVAL, "forward sets per lane must be 2, 4 or 8 and at most %d", c->Bp);
+        if (chunk > c->Bp || c->Bp % chunk != 0 || !batch_config_ok(chunk, sched->bwd_sets_per_lane))
+            return fail(c, GABM_EINVAL, "backward: sets per launch must be a power of two dividing %d, sets per lane "
+                        "2, 4 or 8 and at most that", c->Bp);
         c->spl_fwd = sched->fwd_sets_per_lane;
         c->spl_bwd = sched->bwd_sets_per_lane;
+        c->bwd_chunk = chunk;
     } else {
         if (sched->fwd_smem_bitmap && (c->soft || occupancy_fwd(c->ntiles, true) <= 0))
             return fail(c, GABM_EINVAL, "the infectious bitmap (%d words) does not fit in shared memory", c->ntiles);
@@ -1392,43 +1410,69 @@ gabm_status gabm_autotune(gabm_ctx *ctx, int repetitions) {
     const int T = c->T_last, ld = c->Tcap;
     cudaStream_t s = c->stream;
     if (!c->gD_staged) CK(cudaMemsetAsync(c->gD, 0, sizeof(double) * (size_t)c->I * ld, s));
-    std::vector<gabm_schedule> cands;
+    gabm_schedule cur{};
+    TRY(gabm_get_schedule(c, &cur));
+    // forward schedules (the backward schedule does not change the forward) ...
+    std::vector<gabm_schedule> fc, bc;
     if (c->batched) {
         for (int spl : {2, 4, 8})
-            if (batch_config_ok(c->Bp, spl)) cands.push_back(gabm_schedule{spl, spl, 0});
+            if (batch_config_ok(c->Bp, spl)) fc.push_back(gabm_schedule{spl, cur.bwd_sets_per_lane, 0, cur.bwd_sets_per_launch});
     } else {
-        cands.push_back(gabm_schedule{0, 0, 0});
-        if (!c->soft && occupancy_fwd(c->ntiles, true) > 0) cands.push_back(gabm_schedule{0, 0, 1});
+        fc.push_back(gabm_schedule{0, 0, 0, 0});
+        if (!c->soft && occupancy_fwd(c->ntiles, true) > 0) fc.push_back(gabm_schedule{0, 0, 1, 0});
     }
-    cudaEvent_t ev[4];
+    cudaEvent_t ev[2];
     for (auto &e : ev) CK(cudaEventCreate(&e));
     auto release = [&]() { for (auto &e : ev) cudaEventDestroy(e); };
-    float best_f = 1e30f, best_b = 1e30f;
-    gabm_schedule bf = cands[0], bb = cands[0];
-    for (const gabm_schedule &cand : cands) {
-        gabm_status st = gabm_set_schedule(c, &cand);
-        if (st == GABM_OK) st = forward_core(c, 0, T, true);   // warm-up (and graph capture)
-        if (st == GABM_OK) st = backward_core(c, T);
-        float tf = 0.f, tb = 0.f;
+    // mean time of `reps` runs of fn after one untimed run (which also captures the CUDA graph)
+    auto timed = [&](auto fn, float &ms) -> gabm_status {
+        gabm_status st = fn();
+        ms = 0.f;
         for (int r = 0; r < repetitions && st == GABM_OK; ++r) {
             cudaEventRecord(ev[0], s);
-            st = forward_core(c, 0, T, true);
+            st = fn();
             cudaEventRecord(ev[1], s);
-            if (st == GABM_OK) st = backward_core(c, T);
-            cudaEventRecord(ev[2], s);
-            if (cudaEventSynchronize(ev[2]) != cudaSuccess) st = fail(c, GABM_ECUDA, "autotune: %s", cudaGetErrorString(cudaGetLastError()));
-            float a = 0.f, b = 0.f;
+            if (cudaEventSynchronize(ev[1]) != cudaSuccess)
+                return fail(c, GABM_ECUDA, "autotune: %s", cudaGetErrorString(cudaGetLastError()));
+            float a = 0.f;
             cudaEventElapsedTime(&a, ev[0], ev[1]);
-            cudaEventElapsedTime(&b, ev[1], ev[2]);
-            tf += a;
-            tb += b;
+            ms += a;
         }
+        return st;
+    };
+    float best_f = 1e30f, best_b = 1e30f;
+    gabm_schedule bf = fc[0];
+    for (const gabm_schedule &cand : fc) {
+        float ms = 0.f;
+        gabm_status st = gabm_set_schedule(c, &cand);
+        if (st == GABM_OK) st = timed([&]() { return forward_core(c, 0, T, true); }, ms);
         if (st != GABM_OK) { release(); return st; }
-        if (tf < best_f) { best_f = tf; bf = cand; }
-        if (tb < best_b) { best_b = tb; bb = cand; }
+        if (ms < best_f) { best_f = ms; bf = cand; }
+    }
+    // ... then backward schedules after one forward with the best forward schedule
+    if (c->batched) {
+        for (int spl : {2, 4, 8})
+            for (int chunk = c->Bp; chunk >= 2 && chunk >= c->Bp / 4; chunk /= 2)
+                if (batch_config_ok(chunk, spl))
+                    bc.push_back(gabm_schedule{bf.fwd_sets_per_lane, spl, 0, chunk});
+    } else {
+        bc.push_back(bf);
+    }
+    gabm_schedule bb = bc[0];
+    {
+        gabm_status st = gabm_set_schedule(c, &bf);
+        if (st == GABM_OK) st = forward_core(c, 0, T, true);
+        if (st != GABM_OK) { release(); return st; }
+    }
+    for (const gabm_schedule &cand : bc) {
+        float ms = 0.f;
+        gabm_status st = gabm_set_schedule(c, &cand);
+        if (st == GABM_OK) st = timed([&]() { return backward_core(c, T); }, ms);
+        if (st != GABM_OK) { release(); return st; }
+        if (ms < best_b) { best_b = ms; bb = cand; }
     }
     release();
-    const gabm_schedule chosen{bf.fwd_sets_per_lane, bb.bwd_sets_per_lane, bf.fwd_smem_bitmap};
+    const gabm_schedule chosen{bf.fwd_sets_per_lane, bb.bwd_sets_per_lane, bf.fwd_smem_bitmap, bb.bwd_sets_per_launch};
     TRY(gabm_set_schedule(c, &chosen));
     // the last forward's outputs again (the trajectory does not depend on the schedule)
     TRY(forward_core(c, 0, T, true));

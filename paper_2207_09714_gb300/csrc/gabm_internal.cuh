@@ -251,14 +251,16 @@ struct BwdBatchArgs {
     int ring_slot[kMaxL];
     int32_t *sig, *emax;         // [G][ld_sig] per graph (shared by its sets)
     int ld_sig;
+    int Bw, s0;                  // row width of the per-agent arrays; first set of this launch
 };
 
 // Schedules: spl sets per lane (2, 4 or 8; Bp / spl lanes share a row).
 bool batch_config_ok(int Bp, int spl);
 cudaError_t launch_fwd_day_b(const FwdBatchArgs &a, int Bp, int spl, bool kahan, int grid, cudaStream_t s);
-cudaError_t launch_bwd_day_b(const BwdBatchArgs &a, int Bp, int spl, bool kahan, int grid, cudaStream_t s);
+// The backward runs the row's sets in launches of Bc sets (a.s0 .. a.s0 + Bc - 1).
+cudaError_t launch_bwd_day_b(const BwdBatchArgs &a, int Bc, int spl, bool kahan, int grid, cudaStream_t s);
 int occupancy_fwd_b(int Bp, int spl, bool kahan);
-int occupancy_bwd_b(int Bp, int spl, bool kahan);
+int occupancy_bwd_b(int Bc, int spl, bool kahan);
 // rows with 1 <= t0 - e < L in any set
 cudaError_t launch_infectious_bits_b(const int16_t *e, int Bp, int t0, int L, int ntiles, uint32_t *bits,
                                      cudaStream_t s);

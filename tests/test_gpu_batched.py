@@ -221,12 +221,23 @@ def test_schedules_are_bitwise_equal(B):
             assert np.abs(out["dR"]).max() > 0
         else:
             _assert_same(ref, out, f"spl={spl}")
+    # the backward in launches of fewer sets (each launch one column block of the rows)
+    for chunk in (Bp // 2, Bp // 4):
+        for spl in (2, 4, 8):
+            if chunk < 2 or spl > chunk:
+                continue
+            capi.gabm_set_schedule(ctx, 4 if Bp >= 4 else 2, spl, bwd_sets_per_launch=chunk)
+            assert capi.gabm_get_schedule(ctx)["bwd_sets_per_launch"] == chunk
+            _assert_same(ref, _run_all(ctx, T, R, m, S, [10] * B, y), f"chunk={chunk} spl={spl}")
+    with pytest.raises(capi.GabmError):
+        capi.gabm_set_schedule(ctx, 2, 2, bwd_sets_per_launch=3)
     # mixed schedules, then the autotuner: same results, state as after the last forward
     capi.gabm_set_schedule(ctx, 2, Bp if Bp <= 8 else 8)
     _assert_same(ref, _run_all(ctx, T, R, m, S, [10] * B, y), "mixed")
     e_before = capi.gabm_get_state(ctx)
     chosen = capi.gabm_autotune(ctx, 1)
     assert chosen["fwd_sets_per_lane"] in (2, 4, 8) and chosen["bwd_sets_per_lane"] in (2, 4, 8)
+    assert Bp % chosen["bwd_sets_per_launch"] == 0
     assert np.array_equal(capi.gabm_get_state(ctx), e_before)
     assert np.array_equal(capi.gabm_get_lambda(ctx, T // 2), ref["lam1"])
     (gDd,) = to_dev(np.stack([O.mse(ref["D"][b], y[b])[1] for b in range(B)]))
