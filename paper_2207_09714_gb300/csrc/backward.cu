@@ -60,8 +60,8 @@ __global__ void __launch_bounds__(kBlock, GABM_MINBLOCKS) k_bwd_day(const BwdDay
     };
 
     int cur_g = -1, cN = 0;
-    TileDispenser disp;
-    disp.init(a.tile_ctr, ntiles, gridDim.x * (kBlock / 32), lane);
+    BlockTiles disp;
+    disp.init(ntiles, lane);
     TileRows cur, nxt;
     load_tile_rows(a.m, E, a.gr.tile_graph, ntiles, disp.get(), lane, cur);
     load_tile_rows(a.m, E, a.gr.tile_graph, ntiles, disp.get(), lane, nxt);

@@ -99,7 +99,7 @@ struct gabm_ctx {
 
     int grid_fwd = 0, grid_bwd = 0;
     bool smem_bits = false;         // forward keeps the infectious bitmap in shared memory
-    int *tile_ctr = nullptr;        // [1 + max chunks][Tcap] per-launch tile counters (forward, backward chunks)
+    int *tile_ctr = nullptr;        // batched: [1 + max chunks][Tcap] per-launch tile counters (forward, backward chunks)
     uint32_t *bits = nullptr;       // [Tcap][ntiles] per-day bitmaps of infectious rows
 
     size_t mem_cur = 0, mem_peak = 0;
@@ -435,7 +435,7 @@ gabm_status ensure_days(gabm_ctx *c, int T) {
     TRY(dalloc(c, &c->m, IT));
     TRY(dalloc(c, &c->dR_s, IT));
     TRY(dalloc(c, &c->dm_s, IT));
-    TRY(dalloc(c, &c->tile_ctr, (size_t)(1 + max_bwd_chunks(c)) * cap));
+    if (c->batched) TRY(dalloc(c, &c->tile_ctr, (size_t)(1 + max_bwd_chunks(c)) * cap));
     TRY(dalloc(c, &c->bits, (size_t)(cap + 1) * c->ntiles));
     TRY(dalloc(c, &c->sig, (size_t)c->G * (cap + 1)));
     TRY(dalloc(c, &c->emax, (size_t)c->G * (cap + 1)));
@@ -636,7 +636,6 @@ gabm_status forward_days_plain(gabm_ctx *c, int t0, int T, cudaStream_t s) {
     for (int t = t0; t < T; ++t) {
         a.t = t;
         a.lam_out = c->policy == GABM_STORE_LAMBDA ? c->lam + (size_t)t * c->n_rows : nullptr;
-        a.tile_ctr = c->tile_ctr + t;
         a.bits_cur = c->bits + (size_t)t * c->ntiles;
         a.bits_next = c->bits + (size_t)(t + 1) * c->ntiles;
         prof_begin(c, 0);
@@ -695,7 +694,6 @@ gabm_status backward_days_plain(gabm_ctx *c, int T, cudaStream_t s) {
         a.r_cur = c->r + (size_t)(t & 1) * c->n_rows;
         a.P_t = c->P + (size_t)t * c->ntiles * kAges;
         for (int k = 0; k < kMaxL; ++k) a.ring_slot[k] = (k >= 1 && k < c->L) ? (t + k) % Lm1 : 0;
-        a.tile_ctr = c->tile_ctr + ld + t;
         prof_begin(c, 1);
         LAUNCH(launch_bwd_day(a, c->grid_bwd, s));
         prof_end(c, 1);
@@ -730,7 +728,6 @@ gabm_status forward_days_soft(gabm_ctx *c, int T, cudaStream_t s) {
         a.y_hist_t = c->y_hist + (size_t)t * n;
         a.lam_t = c->lam + (size_t)t * n;
         a.P_nrm_t = c->P_nrm + (size_t)t * c->ntiles;
-        a.tile_ctr = c->tile_ctr + t;
         prof_begin(c, 0);
         LAUNCH(launch_fwd_day_soft(a, c->grid_fwd, s));
         prof_end(c, 0);
@@ -795,7 +792,7 @@ gabm_status forward_core(gabm_ctx *c, int t0, int T, bool seeding) {
     CK(cudaMemsetAsync(c->counts, 0, sizeof(int32_t) * 4 * (size_t)c->I * ld, s));
     CK(cudaMemsetAsync(c->newRM, 0, sizeof(int32_t) * (size_t)c->I * ld, s));
     CK(cudaMemsetAsync(c->D, 0, sizeof(double) * (size_t)c->I * ld, s));
-    CK(cudaMemsetAsync(c->tile_ctr, 0, sizeof(int) * (size_t)ld, s));
+    if (c->batched) CK(cudaMemsetAsync(c->tile_ctr, 0, sizeof(int) * (size_t)ld, s));
 
     if (seeding) {
         CK(cudaMemcpyAsync(c->d_nseed, c->last_seeds.data(), sizeof(int32_t) * c->I, cudaMemcpyHostToDevice, s));
@@ -836,7 +833,7 @@ gabm_status backward_core(gabm_ctx *c, int T) {
     cudaStream_t s = c->stream;
     CK(cudaMemsetAsync(c->r, 0, sizeof(float) * 2 * (size_t)c->n_rows * c->Bp, s));
     CK(cudaMemsetAsync(c->newRM_b, 0, sizeof(int32_t) * (size_t)c->I * ld, s));
-    CK(cudaMemsetAsync(c->tile_ctr + ld, 0, sizeof(int) * (size_t)ld * max_bwd_chunks(c), s));
+    if (c->batched) CK(cudaMemsetAsync(c->tile_ctr + ld, 0, sizeof(int) * (size_t)ld * max_bwd_chunks(c), s));
     // sigma(T) = 0 and no stored exponent yet
     CK(cudaMemsetAsync(c->sig, 0, sizeof(int32_t) * (size_t)c->G * (ld + 1), s));
     CK(cudaMemsetAsync(c->emax, 0, sizeof(int32_t) * (size_t)c->G * (ld + 1), s));

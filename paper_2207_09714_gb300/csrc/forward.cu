@@ -1,7 +1,8 @@
 // forward.cu -- forward day step of the hard GradABM model on sm_103a.
 //
-// One launch per day (Sec. 3.1, Eq. 1-3; A1: one-day steps).  Warps take
-// 32-row tiles from a per-launch counter; each lane sums its own susceptible
+// One launch per day (Sec. 3.1, Eq. 1-3; A1: one-day steps).  Each block takes
+// a contiguous range of 32-row tiles, its warps one tile at a time (neighbours
+// stay in the SM's L1 this way); each lane sums its own susceptible
 // row over the in-edges (a pull gather, no atomics) read from the tile's
 // SELL-32 slice with coalesced loads: w_ji * c[t - e_j] for the neighbours
 // marked infectious in today's bitmap (an L1-resident bit array), whose
@@ -68,10 +69,10 @@ __global__ void __launch_bounds__(NT, MINB) k_fwd_day(const FwdDayArgs a) {
     int cur_g = -1;
     int cS = 0, cE = 0, cI = 0, cR = 0, cN = 0;
 
-    // Tiles come from a per-warp dispenser; each tile's row data is loaded one tile
-    // ahead of use (and, when enabled, its slice prefetched into L2).
-    TileDispenser disp;
-    disp.init(a.tile_ctr, ntiles, gridDim.x * NW, lane);
+    // Tiles come from the block's contiguous range; each tile's row data is loaded one
+    // tile ahead of use (and, when enabled, its slice prefetched into L2).
+    BlockTiles disp;
+    disp.init(ntiles, lane);
     TileRows cur, nxt;
     load_tile_rows(a.m, e, a.gr.tile_graph, ntiles, disp.get(), lane, cur);
     load_tile_rows(a.m, e, a.gr.tile_graph, ntiles, disp.get(), lane, nxt);
@@ -191,8 +192,8 @@ __global__ void __launch_bounds__(kBlock, GABM_MINBLOCKS) k_fwd_day_soft(const S
     const bool want[1] = {true};
     const size_t n_rows = (size_t)ntiles * kTile;
     const int slot_t = t % L;   // holds n(t - L) before this launch overwrites it with n(t)
-    TileDispenser disp;
-    disp.init(a.tile_ctr, ntiles, gridDim.x * (kBlock / 32), lane);
+    BlockTiles disp;
+    disp.init(ntiles, lane);
     for (int tile = disp.get(); tile < ntiles; tile = disp.get()) {
         const int row = tile * kTile + lane;
         const int ei = a.e[row];

@@ -114,7 +114,6 @@ struct FwdDayArgs {
     int ldP;              // per-instance stride of R (and m)
     int32_t *counts;      // [I][ldP][4]
     int32_t *newRM;       // [I][ldP]
-    int *tile_ctr;        // tile counter of this launch (zero before the launch)
     const uint32_t *bits_cur;   // [ntiles] bit i of word r/32: row r infectious on day t
     uint32_t *bits_next;        // [ntiles] the same for day t + 1 (written by this launch)
     int ntiles, t, tau_EI, L;
@@ -138,7 +137,6 @@ struct SoftDayArgs {
     const float *R, *S;
     int ldP;
     double *P_nrm_t;         // [ntiles] per-tile sums of n_i(t - L) (newRM of day t)
-    int *tile_ctr;
     int ntiles, t, L;
     uint64_t seed;
     float c[kMaxL];
@@ -162,7 +160,6 @@ struct BwdDayArgs {
     int ldP;
     double *P_t;               // [ntiles][9] partial sums of gl * Lam for day t
     int32_t *newRM;            // [I][ldP]
-    int *tile_ctr;             // tile counter of this launch (zero before the launch)
     int ntiles, t, T, tau_EI, L;
     int mode;                  // kBwdStore, kBwdFused or kBwdSplit
     uint64_t seed;

@@ -95,6 +95,39 @@ struct TileDispenser {
     }
 };
 
+// Hands each block one contiguous range of tiles, claimed tile by tile by its
+// warps through a shared-memory counter.  Rows are laid out breadth-first, so
+// the neighbours of a range's rows mostly lie in and around the same range:
+// the warps of a block gather from lines their own SM has just cached, where a
+// launch-wide counter would spread consecutive tiles over all SMs.  (Measured
+// on the 1M-agent typed graph: 10% shorter day kernels than the launch-wide
+// dispenser; handing the last eighth of the tiles out launch-wide to balance
+// the tail costs more locality than it gains.  The batched kernels, whose rows
+// carry up to 64 sets each, keep the launch-wide dispenser: there the ranges'
+// imbalance cost 7%.)  Called by every thread of the block (init holds a barrier).
+struct BlockTiles {
+    int *ctr;          // the block's counter (shared memory)
+    int end, ntiles, lane, pend;
+    __device__ __forceinline__ void init(int nt, int ln) {
+        __shared__ int s_ctr;
+        ntiles = nt;
+        lane = ln;
+        const int b0 = (int)(((long long)blockIdx.x * nt) / gridDim.x);
+        end = (int)(((long long)(blockIdx.x + 1) * nt) / gridDim.x);
+        if (threadIdx.x == 0) s_ctr = b0;
+        __syncthreads();
+        ctr = &s_ctr;
+        pend = (lane == 0) ? atomicAdd(ctr, 1) : 0;
+    }
+    // the next tile of this warp, or ntiles when the block's range is done
+    __device__ __forceinline__ int get() {
+        const int tile = __shfl_sync(0xffffffffu, pend, 0);
+        if (tile >= end) return ntiles;
+        if (lane == 0) pend = atomicAdd(ctr, 1);
+        return tile;
+    }
+};
+
 // Ask L2 to fetch one slice (entries [p0, p1) of both arrays) ahead of use.
 // Slices start on 128-byte boundaries and hold multiples of 32 entries.
 __device__ __forceinline__ void prefetch_slice(const Sell &m, uint32_t p0, uint32_t p1, int lane) {
