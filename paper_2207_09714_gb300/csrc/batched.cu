@@ -110,12 +110,38 @@ __device__ __forceinline__ float infect_lut(int e, const float *c_s, int t, unsi
     return c_s[min((unsigned)(t - e), L)];
 }
 
+// Row data of one pass (one row per group), loaded a pass ahead of use: the
+// lane's exposure words of its row, the row's entry range and the first chunk
+// of its entries (entry q for lane q of the group).
+template <int SPL>
+struct PassRow {
+    uint32_t ew[SPL / 2];
+    uint32_t p0, len;      // entries [p0, p0 + len)
+    uint32_t j0;           // column and weight of entry q, when q < len
+    float w0;
+};
+
+// Loads the pass row of tile row r (0..31) into pr; lane r holds the row bounds
+// (rowptr of tile row r and r + 1) in rp_lo / rp_hi.  Called by all 32 lanes.
+template <int SPL>
+__device__ __forceinline__ void load_pass_row(const Csr &m, const uint32_t *ew_ptr, uint32_t rp_lo, uint32_t rp_hi,
+                                              int r, int q, PassRow<SPL> &pr) {
+    pr.p0 = __shfl_sync(kFull, rp_lo, r);
+    pr.len = __shfl_sync(kFull, rp_hi, r) - pr.p0;
+    ld_words<SPL>(ew_ptr, true, pr.ew);
+    const bool v = (uint32_t)q < pr.len;
+    pr.j0 = ld_cs_if(m.col + pr.p0 + q, v);
+    pr.w0 = ld_cs_if(m.w + pr.p0 + q, v);
+}
+
 // For this lane's group row (entries [p0, p0 + len)), sum[h] = sum over the
 // entries whose column is marked in `bits` of w * x_h(j), in entry order, where
 // ld(j, ok, raw) gathers column j's values for this lane's sets (predicated by
-// ok) and val(raw, h) is set h's value.  Called by all 32 lanes.
+// ok) and val(raw, h) is set h's value.  (j0, w0) is the row's entry q, loaded
+// by the caller; each later chunk of LPR entries is in flight while the one
+// before it is used.  Called by all 32 lanes.
 template <int LPR, int SPL, bool KAHAN, class Raw, class Ld, class Val>
-__device__ __forceinline__ void group_row_sums(const Csr &m, uint32_t p0, uint32_t len,
+__device__ __forceinline__ void group_row_sums(const Csr &m, uint32_t p0, uint32_t len, uint32_t j0, float w0,
                                                const uint32_t *__restrict__ bits, int lane, Ld ld, Val val,
                                                float (&sum)[SPL]) {
     constexpr int U = (SPL == 8) ? 4 : 8;
@@ -125,11 +151,16 @@ __device__ __forceinline__ void group_row_sums(const Csr &m, uint32_t p0, uint32
 #pragma unroll
     for (int h = 0; h < SPL; ++h) sum[h] = comp[h] = 0.f;
     const uint32_t kmax = __reduce_max_sync(kFull, len);
+    uint32_t jn = j0;
+    float wn = w0;
     for (uint32_t k0 = 0; k0 < kmax; k0 += LPR) {
         const uint32_t kk = k0 + (uint32_t)q;
         const bool valid = kk < len;
-        const uint32_t j = ld_cs_if(m.col + p0 + kk, valid);
-        const float w = ld_cs_if(m.w + p0 + kk, valid);
+        const uint32_t j = jn;
+        const float w = wn;
+        const bool vn = kk + LPR < len;
+        jn = ld_cs_if(m.col + p0 + kk + LPR, vn);
+        wn = ld_cs_if(m.w + p0 + kk + LPR, vn);
         const bool mk = valid && marked(bits, j);
         unsigned mm = (__ballot_sync(kFull, mk) >> (grp * LPR)) & gmask;
         const int nmax = (int)__reduce_max_sync(kFull, (unsigned)__popc(mm));
@@ -213,7 +244,20 @@ __global__ void __launch_bounds__(kBlock, 2) k_fwd_day_b(const FwdBatchArgs a) {
     for (int h = 0; h < SPL; ++h) Rt[h] = 0.f;
     TileDispenser disp;
     disp.init(a.tile_ctr, ntiles, gridDim.x * NW, lane);
-    for (int tile = disp.get(); tile < ntiles; tile = disp.get()) {
+    // row bounds of the tile's 32 rows (lane r: rows r and r + 1), one tile ahead
+    int tile = disp.get();
+    uint32_t rp_lo = 0u, rp_hi = 0u;
+    if (tile < ntiles) {
+        rp_lo = a.m.rowptr[tile * kTile + lane];
+        rp_hi = a.m.rowptr[tile * kTile + lane + 1];
+    }
+    while (tile < ntiles) {
+        const int ntile = disp.get();
+        uint32_t nrp_lo = 0u, nrp_hi = 0u;
+        if (ntile < ntiles) {
+            nrp_lo = a.m.rowptr[ntile * kTile + lane];
+            nrp_hi = a.m.rowptr[ntile * kTile + lane + 1];
+        }
         const int g = a.gr.tile_graph ? (int)a.gr.tile_graph[tile] : 0;
         if (g != cur_g) {
             cur_g = g;
@@ -228,11 +272,17 @@ __global__ void __launch_bounds__(kBlock, 2) k_fwd_day_b(const FwdBatchArgs a) {
         int nnew[SPL];
 #pragma unroll
         for (int h = 0; h < SPL; ++h) nnew[h] = 0;
+        PassRow<SPL> nx;
+        load_pass_row<SPL>(a.m, e32 + (size_t)(tile * kTile + grp) * WPR + q * (SPL / 2), rp_lo, rp_hi, grp, q, nx);
         for (int pass = 0; pass < LPR; ++pass) {
             const int row = tile * kTile + pass * RPW + grp;
             uint32_t *mine_p = e32 + (size_t)row * WPR + q * (SPL / 2);
+            const PassRow<SPL> cu = nx;
+            if (pass + 1 < LPR)   // the next pass's row in flight while this one is summed
+                load_pass_row<SPL>(a.m, mine_p + (size_t)RPW * WPR, rp_lo, rp_hi, (pass + 1) * RPW + grp, q, nx);
             uint32_t ew[SPL / 2];
-            ld_words<SPL>(mine_p, true, ew);
+#pragma unroll
+            for (int k = 0; k < SPL / 2; ++k) ew[k] = cu.ew[k];
             bool sS[SPL];
             bool mine = false;
 #pragma unroll
@@ -240,11 +290,10 @@ __global__ void __launch_bounds__(kBlock, 2) k_fwd_day_b(const FwdBatchArgs a) {
                 sS[h] = half_of(ew[h >> 1], h & 1) == kNever;
                 mine |= sS[h];
             }
-            const uint32_t p0 = a.m.rowptr[row];
-            const uint32_t p1 = a.m.rowptr[row + 1];
             const bool act = (group_bits<LPR>(__ballot_sync(kFull, mine)) >> grp) & 1u;
             float sum[SPL];
-            group_row_sums<LPR, SPL, KAHAN, EWords<SPL>>(a.m, p0, act ? p1 - p0 : 0u, a.bits_cur, lane, ld, val, sum);
+            group_row_sums<LPR, SPL, KAHAN, EWords<SPL>>(a.m, cu.p0, act ? cu.len : 0u, cu.j0, cu.w0, a.bits_cur, lane,
+                                                         ld, val, sum);
 
             bool inf = false;
             if (mine) {
@@ -294,6 +343,9 @@ __global__ void __launch_bounds__(kBlock, 2) k_fwd_day_b(const FwdBatchArgs a) {
 #pragma unroll
             for (int h = 0; h < SPL; ++h) dst[h] = (uint8_t)nnew[h];
         }
+        tile = ntile;
+        rp_lo = nrp_lo;
+        rp_hi = nrp_hi;
     }
 }
 
@@ -338,7 +390,20 @@ __global__ void __launch_bounds__(kBlock, 2) k_bwd_day_b(const BwdBatchArgs a) {
     unsigned emax_w = 0u;          // largest exponent stored by this warp (+128)
     TileDispenser disp;
     disp.init(a.tile_ctr, ntiles, gridDim.x * NW, lane);
-    for (int tile = disp.get(); tile < ntiles; tile = disp.get()) {
+    // row bounds of the tile's 32 rows (lane r: rows r and r + 1), one tile ahead
+    int tile = disp.get();
+    uint32_t rp_lo = 0u, rp_hi = 0u;
+    if (tile < ntiles) {
+        rp_lo = a.m.rowptr[tile * kTile + lane];
+        rp_hi = a.m.rowptr[tile * kTile + lane + 1];
+    }
+    while (tile < ntiles) {
+        const int ntile = disp.get();
+        uint32_t nrp_lo = 0u, nrp_hi = 0u;
+        if (ntile < ntiles) {
+            nrp_lo = a.m.rowptr[ntile * kTile + lane];
+            nrp_hi = a.m.rowptr[ntile * kTile + lane + 1];
+        }
         const int g = a.gr.tile_graph ? (int)a.gr.tile_graph[tile] : 0;
         if (g != cur_g) {
             if (cur_g >= 0) {
@@ -362,11 +427,17 @@ __global__ void __launch_bounds__(kBlock, 2) k_bwd_day_b(const BwdBatchArgs a) {
         }
         const float inv_D = a.gr.inv_Dbar[g];
         uint32_t word = 0u;
+        PassRow<SPL> nx;
+        load_pass_row<SPL>(a.m, E32 + ((size_t)(tile * kTile + grp) * Bw + s0) / 2, rp_lo, rp_hi, grp, q, nx);
         for (int pass = 0; pass < LPR; ++pass) {
             const int row = tile * kTile + pass * RPW + grp;
             const size_t xo = (size_t)row * Bw + s0;   // this lane's first slot
+            const PassRow<SPL> cu = nx;
+            if (pass + 1 < LPR)   // the next pass's row in flight while this one is summed
+                load_pass_row<SPL>(a.m, E32 + (xo + (size_t)RPW * Bw) / 2, rp_lo, rp_hi, (pass + 1) * RPW + grp, q, nx);
             uint32_t ew[SPL / 2];
-            ld_words<SPL>(E32 + xo / 2, true, ew);
+#pragma unroll
+            for (int k = 0; k < SPL / 2; ++k) ew[k] = cu.ew[k];
             bool isS[SPL];
             bool needA_any = false, anyS = false;
 #pragma unroll
@@ -378,11 +449,10 @@ __global__ void __launch_bounds__(kBlock, 2) k_bwd_day_b(const BwdBatchArgs a) {
                 needA_any |= has_next && live && (never || Eh >= t + 2 - L);
                 anyS |= isS[h];
             }
-            const uint32_t p0 = a.m.rowptr[row];
-            const uint32_t p1 = a.m.rowptr[row + 1];
             const bool act = (group_bits<LPR>(__ballot_sync(kFull, needA_any)) >> grp) & 1u;
             float gx[SPL];
-            group_row_sums<LPR, SPL, KAHAN, FVec<SPL>>(a.m, p0, act ? p1 - p0 : 0u, a.rbits_next, lane, ld, val, gx);
+            group_row_sums<LPR, SPL, KAHAN, FVec<SPL>>(a.m, cu.p0, act ? cu.len : 0u, cu.j0, cu.w0, a.rbits_next, lane,
+                                                       ld, val, gx);
             if (needA_any) st_floats<SPL>(a.ring + (size_t)slot_k[1] * stride + xo, gx);
 
             float v[SPL];
@@ -472,6 +542,9 @@ __global__ void __launch_bounds__(kBlock, 2) k_bwd_day_b(const BwdBatchArgs a) {
         }
         __syncwarp();
         if (lane == 0) a.rbits_cur[tile] = word;
+        tile = ntile;
+        rp_lo = nrp_lo;
+        rp_hi = nrp_hi;
     }
     if (cur_g >= 0) flush_emax(a.emax + (size_t)cur_g * a.ld_sig + t, emax_w);
 }
