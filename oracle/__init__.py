@@ -67,11 +67,11 @@ def lib() -> ctypes.CDLL:
             L.orc_forward_hard.argtypes = [i64, P, P, P, P, P, i32, i32, P, u64, u32, i32, i32,
                                            P, P, P, i64, P, P, P, P, P, P, P, P]
             L.orc_backward_hard.argtypes = [i64, P, P, P, P, P, i32, i32, P, u64, u32, i32,
-                                            P, P, P, P, P, P, P, P, P]
+                                            P, P, P, P, P, P, P, P, P, P]
             L.orc_forward_soft.argtypes = [i64, P, P, P, P, P, i32, i32, P, u64, u32, i32,
                                            P, P, P, i64, P, P, P, P, P, P, P]
             L.orc_backward_soft.argtypes = [i64, P, P, P, P, i32, i32, P, i32, P, P, P, P,
-                                            P, P, P, P, P, P, P, P]
+                                            P, P, P, P, P, P, P, P, P, P]
             L.orc_mse.argtypes = [i32, P, P, P, P]
             L.orc_dy_dlambda.argtypes = [f64, f64]
             L.orc_dy_dlambda.restype = f64
@@ -186,18 +186,21 @@ def forward_hard(pop, model: Model, R, m, S_age, n_seed: int = 0, e0=None, t0: i
 
 
 def backward_hard(pop, model: Model, R, m, S_age, E, gD, inst: int = 0, orig_id=None, want_gl=False):
-    """Hard/straight-through adjoint of the trajectory encoded by the final state ``E``."""
+    """Hard/straight-through adjoint of the trajectory encoded by the final state ``E``.
+    ``dc`` [L] is dL/dc[k], the adjoint of the infectiousness table (dc[0] = 0: c[0] is fixed)."""
     keep, g = _graph_args(pop, orig_id)
     R = _arr(R, np.float32); m = _arr(m, np.float32); S = _arr(S_age, np.float32)
     E = _arr(E, np.int16); gD = _arr(gD, np.float64)
     T = int(R.size)
     dR = np.zeros(T); dm = np.zeros(T); dS = np.zeros(NUM_AGES)
     gl = np.zeros((T, pop.n)) if want_gl else None
+    dc = np.zeros(model.tau_EI + model.tau_IR)
     rc = lib().orc_backward_hard(*g, model.tau_EI, model.tau_IR, _p(model.c), model.seed, inst, T,
-                                 _p(R), _p(m), _p(S), _p(E), _p(gD), _p(dR), _p(dm), _p(dS), _p(gl))
+                                 _p(R), _p(m), _p(S), _p(E), _p(gD), _p(dR), _p(dm), _p(dS), _p(gl),
+                                 _p(dc))
     if rc:
         raise RuntimeError(f"orc_backward_hard failed ({rc})")
-    return dict(dR=dR, dm=dm, dS=dS, gl=gl)
+    return dict(dR=dR, dm=dm, dS=dS, gl=gl, dc=dc)
 
 
 def forward_soft(pop, model: Model, R, m, S_age, n_seed: int = 0, e0=None, inst: int = 0, orig_id=None):
@@ -217,8 +220,10 @@ def forward_soft(pop, model: Model, R, m, S_age, n_seed: int = 0, e0=None, inst:
     return dict(D=D, newRM=newRM, s_hist=s_hist, y_hist=y_hist, dydl_hist=dydl, Lam_hist=Lam)
 
 
-def backward_soft(pop, model: Model, R, m, S_age, gD, s_hist, y_hist, dydl_hist, Lam_hist, newRM):
-    """Adjoint of the relaxed model from its histories (hard values give the ST adjoint)."""
+def backward_soft(pop, model: Model, R, m, S_age, gD, s_hist, y_hist, dydl_hist, Lam_hist, newRM, e0=None):
+    """Adjoint of the relaxed model from its histories (hard values give the ST adjoint).
+    ``e0``: the initial exposure days (seeds negative), needed for the seeds' share of
+    ``dc`` [L] = dL/dc[k] (dc[0] = 0)."""
     rowptr = _arr(pop.rowptr, np.uint64); col = _arr(pop.col, np.uint32)
     w = _arr(pop.w, np.float32); age = _arr(pop.age, np.uint8)
     R = _arr(R, np.float32); m = _arr(m, np.float32); S = _arr(S_age, np.float32)
@@ -226,12 +231,14 @@ def backward_soft(pop, model: Model, R, m, S_age, gD, s_hist, y_hist, dydl_hist,
     arrs = [_arr(a, np.float64) for a in (s_hist, y_hist, dydl_hist, Lam_hist, newRM)]
     T = int(R.size)
     dR = np.zeros(T); dm = np.zeros(T); dS = np.zeros(NUM_AGES)
+    dc = np.zeros(model.tau_EI + model.tau_IR)
+    e0 = _arr(e0, np.int16)
     rc = lib().orc_backward_soft(pop.n, _p(rowptr), _p(col), _p(w), _p(age), model.tau_EI,
                                  model.tau_IR, _p(model.c), T, _p(R), _p(m), _p(S), _p(gD),
-                                 *[_p(a) for a in arrs], _p(dR), _p(dm), _p(dS))
+                                 *[_p(a) for a in arrs], _p(dR), _p(dm), _p(dS), _p(e0), _p(dc))
     if rc:
         raise RuntimeError(f"orc_backward_soft failed ({rc})")
-    return dict(dR=dR, dm=dm, dS=dS)
+    return dict(dR=dR, dm=dm, dS=dS, dc=dc)
 
 
 def mse(D, y):

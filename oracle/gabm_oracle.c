@@ -345,7 +345,7 @@ int orc_backward_hard(int64_t n, const uint64_t *rowptr, const uint32_t *col, co
                       const uint8_t *age, const uint32_t *orig_id, int tau_EI, int tau_IR,
                       const float *c, uint64_t seed, uint32_t inst, int T, const float *R,
                       const float *m, const float *S_age, const int16_t *E, const double *gD,
-                      double *dR, double *dm, double *dS, double *gl_hist)
+                      double *dR, double *dm, double *dS, double *gl_hist, double *dc)
 {
     orc_graph g = {n, rowptr, col, w, age, orig_id};
     const int L = tau_EI + tau_IR;
@@ -403,6 +403,21 @@ int orc_backward_hard(int64_t n, const uint64_t *rowptr, const uint32_t *col, co
             if (E[i] != ORC_NEVER && t - E[i] == L) nrm += 1;
         dm[t] = gD[t] * (double)nrm;
         if (gl_hist) memcpy(gl_hist + (size_t)t * n, gl, sizeof(double) * (size_t)n);
+    }
+    /* Adjoint of the infectiousness table: x_i(t) = sum_k c[k] n_i(t - k) with the
+     * hard n_i(d) = [E_i = d] (seeds at their negative exposure day), so
+     * dL/dc[k] = sum_i gx_i(E_i + k) over 0 <= E_i + k < T.  c[0] is fixed at 0 (A2). */
+    if (dc) {
+        for (int k = 0; k < L; ++k) dc[k] = 0.0;
+        for (int k = 1; k <= L - 1; ++k) {
+            double acc = 0.0;
+            for (int64_t i = 0; i < n; ++i) {
+                if (E[i] == ORC_NEVER) continue;
+                int t = (int)E[i] + k;
+                if (t >= 0 && t < T) acc += gx[(size_t)t * N + (size_t)i];
+            }
+            dc[k] = acc;
+        }
     }
     free(gx); free(A); free(gl); free(Lam);
     return 0;
@@ -493,7 +508,7 @@ int orc_backward_soft(int64_t n, const uint64_t *rowptr, const uint32_t *col, co
                       const float *R, const float *m, const float *S_age, const double *gD,
                       const double *s_hist, const double *y_hist, const double *dydl_hist,
                       const double *Lam_hist, const double *newRM, double *dR, double *dm,
-                      double *dS)
+                      double *dS, const int16_t *e0, double *dc)
 {
     const int L = tau_EI + tau_IR;
     size_t N = (size_t)(n > 0 ? n : 1);
@@ -529,6 +544,25 @@ int orc_backward_soft(int64_t n, const uint64_t *rowptr, const uint32_t *col, co
         }
         dR[t] = dRt;
         dm[t] = gD[t] * newRM[t];
+    }
+    /* Adjoint of the infectiousness table: dL/dc[k] = sum_t sum_i n_i(t - k) gx_i(t), with
+     * n_i(d) = s_i(d) y_i(d) for d >= 0 and, before day 0, the seeds' unit mass at their
+     * exposure day e0_i < 0 (no seeds when e0 is NULL).  c[0] is fixed at 0 (A2). */
+    if (dc) {
+        for (int k = 0; k < L; ++k) dc[k] = 0.0;
+        for (int k = 1; k <= L - 1; ++k) {
+            double acc = 0.0;
+            for (int t = 0; t < T; ++t) {
+                const int d = t - k;
+                for (int64_t i = 0; i < n; ++i) {
+                    double ni;
+                    if (d >= 0) ni = s_hist[(size_t)d * N + (size_t)i] * y_hist[(size_t)d * N + (size_t)i];
+                    else ni = (e0 && e0[i] == d) ? 1.0 : 0.0;
+                    if (ni != 0.0) acc += ni * gx[(size_t)t * N + (size_t)i];
+                }
+            }
+            dc[k] = acc;
+        }
     }
     free(gx); free(ds_next); free(gl);
     return 0;

@@ -328,13 +328,21 @@ def _soft_loss(pop, md, R, m, S, y):
     return O.mse(f["D"], y)[0]
 
 
+def _seed_days(pop, md, n_seed, inst=0):
+    """Initial exposure days of the seeded state: -tau_EI for the seeds, NEVER elsewhere."""
+    e0 = np.full(pop.n, NEVER, np.int16)
+    e0[O.select_seeds(pop.n, md.seed, inst, n_seed)] = -md.tau_EI
+    return e0
+
+
 def test_soft_adjoint_matches_central_differences():
     pop, md, R, m, S, y = _soft_setup()
     f = O.forward_soft(pop, md, R, m, S, n_seed=6)
     loss, gD = O.mse(f["D"], y)
     g = O.backward_soft(pop, md, R, m, S, gD, f["s_hist"], f["y_hist"], f["dydl_hist"],
-                        f["Lam_hist"], f["newRM"])
+                        f["Lam_hist"], f["newRM"], e0=_seed_days(pop, md, 6))
     assert np.abs(g["dR"]).max() > 0 and np.abs(g["dS"]).max() > 0
+    assert g["dc"][0] == 0.0 and np.abs(g["dc"][1:]).min() > 0
 
     # Central differences with Richardson extrapolation; the steps are powers of two that
     # are multiples of the parameter's fp32 spacing, so the perturbed fp32 inputs are exact.
@@ -356,6 +364,21 @@ def test_soft_adjoint_matches_central_differences():
             an = {"R": g["dR"], "m": g["dm"], "S": g["dS"]}[name][idx]
             ref = max(abs(an), 1e-9 * max(np.abs(g["dR"]).max(), 1.0))
             assert abs(est - an) <= 1e-6 * ref + 1e-12, (name, idx, est, an)
+
+    # the infectiousness table c[1..L-1] (c[0] = 0 is fixed by A2)
+    for k in range(1, md.L):
+        base = float(md.c[k])
+        h = 2.0 ** (math.floor(math.log2(max(1.0, abs(base)))) - 12)
+        def Lc_at(delta):
+            c = md.c.copy()
+            c[k] = np.float32(base + delta)
+            assert float(c[k]) == base + delta
+            return _soft_loss(pop, O.Model(md.tau_EI, md.tau_IR, c, seed=md.seed), R, m, S, y)
+        d1 = (Lc_at(h) - Lc_at(-h)) / (2 * h)
+        d2 = (Lc_at(2 * h) - Lc_at(-2 * h)) / (4 * h)
+        est = (4 * d1 - d2) / 3
+        an = g["dc"][k]
+        assert abs(est - an) <= 1e-6 * max(abs(an), 1e-9) + 1e-12, ("c", k, est, an)
 
 
 def test_hard_adjoint_is_soft_adjoint_at_hard_values():
@@ -384,8 +407,8 @@ def test_hard_adjoint_is_soft_adjoint_at_hard_values():
         dydl[t] = np.where(S_t, [O.dy_dlambda(a, b) if s else 0.0 for a, b, s in zip(lam, u, S_t)], 0.0)
     s_hist[T] = ~seeds & (E == NEVER)
     g = O.backward_soft(pop, md, R, m, S, gD, s_hist, y_hist, dydl, f["Lam_hist"],
-                        f["newRM"].astype(np.float64))
-    for k in ("dR", "dm", "dS"):
+                        f["newRM"].astype(np.float64), e0=np.where(seeds, E, NEVER))
+    for k in ("dR", "dm", "dS", "dc"):
         ref = np.abs(h[k]).max()
         assert ref > 0
         assert np.allclose(g[k], h[k], rtol=1e-10, atol=1e-12 * ref), k
