@@ -143,6 +143,13 @@ gabm_status gabm_forward(gabm_ctx *ctx, int T, const float *R, const float *m, c
  * GABM_ESTATE if no forward has run. */
 gabm_status gabm_mse_loss(gabm_ctx *ctx, const double *y, double *loss, double *gD, int mem_space);
 
+/* Replace the infectiousness table c [L] (host floats; c[0] = 0, every entry finite
+ * and >= 0, as at creation) for the forwards that follow, e.g. between the steps of a
+ * calibration that learns the stage factors or the profile behind c.  Waits for the
+ * ctx stream.  The last trajectory used the old table, so gabm_backward returns
+ * GABM_ESTATE until the next gabm_forward.  GABM_EINVAL for a NULL or invalid table. */
+gabm_status gabm_set_infectiousness(gabm_ctx *ctx, const float *c);
+
 /* Straight-through adjoint of the last forward (App. B): given gD = dL/dD_t
  * [I][T] (double), writes dR [I][T], dm [I][T] and dS_age [I][9] (double).
  * Cross-agent and cross-day sums are FP64 in a fixed order (bitwise
@@ -150,6 +157,19 @@ gabm_status gabm_mse_loss(gabm_ctx *ctx, const double *y, double *loss, double *
  * or with GABM_STORE_LAMBDA when the stored lambdas do not cover days 0..T-1. */
 gabm_status gabm_backward(gabm_ctx *ctx, const double *gD, double *dR, double *dm,
                           double *dS_age, int mem_space);
+
+/* gabm_backward that also writes dc [I][L] (double): the gradient of the loss with
+ * respect to the infectiousness table c[k] of the model (lambda is linear in each
+ * neighbour's c[t - e_j], Sec. 3.1 Eq. 3; adjoint of App. B).  With the hard
+ * trajectory, dc[i][k] = sum_j gx_j(E_j + k) over agents j exposed on day E_j (seeds at
+ * their negative exposure day) and days 0 <= E_j + k < T, where gx_j(t) is the adjoint of
+ * agent j's infectiousness on day t.  dc[i][0] = 0 (c[0] = 0 is fixed, A2 of App. A).
+ * Gradients of stage factors or profile parameters that define c (T_E, T_I, iota)
+ * follow by the chain rule on the caller's side.  Same preconditions as gabm_backward;
+ * GABM_EINVAL if dc is NULL; GABM_EUNSUPPORTED for contexts with several sets per
+ * graph or the soft relaxation. */
+gabm_status gabm_backward_table(gabm_ctx *ctx, const double *gD, double *dR, double *dm,
+                                double *dS_age, double *dc, int mem_space);
 
 /* Current exposure-day vector e [sets_per_graph][n_total] (int16; per set, the
  * graphs' agents concatenated in graph order, caller ids within each graph).

@@ -76,6 +76,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         L.gabm_forward.argtypes = [P, i32, P, P, P, P, P, P, i32]
         L.gabm_mse_loss.argtypes = [P, P, P, P, i32]
         L.gabm_backward.argtypes = [P, P, P, P, P, i32]
+        L.gabm_backward_table.argtypes = [P, P, P, P, P, P, i32]
+        L.gabm_set_infectiousness.argtypes = [P, P]
         L.gabm_get_state.argtypes = [P, P, i32]
         L.gabm_set_state.argtypes = [P, i32, P, i32]
         L.gabm_get_lambda.argtypes = [P, i32, P, i32]
@@ -96,7 +98,9 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         L.gabm_get_schedule.argtypes = [P, ctypes.POINTER(_Schedule)]
         L.gabm_set_schedule.argtypes = [P, ctypes.POINTER(_Schedule)]
         L.gabm_autotune.argtypes = [P, i32]
-        for name in ("gabm_create", "gabm_forward", "gabm_mse_loss", "gabm_backward", "gabm_get_state",
+        for name in ("gabm_create", "gabm_forward", "gabm_mse_loss", "gabm_backward", "gabm_backward_table",
+                     "gabm_set_infectiousness",
+                     "gabm_get_state",
                      "gabm_set_state", "gabm_get_lambda", "gabm_mem_stats", "gabm_set_profiling",
                      "gabm_get_profile", "gabm_philox", "gabm_get_schedule", "gabm_set_schedule",
                      "gabm_autotune"):
@@ -311,6 +315,44 @@ def gabm_backward(ctx: GabmCtx, gD, dR=None, dm=None, dS_age=None):
                                       _ptr(dm, np.float64), _ptr(dS_age, np.float64), ms)
     _check(st, ctx.handle)
     return dR, dm, dS_age
+
+
+def gabm_backward_table(ctx: GabmCtx, gD, dR=None, dm=None, dS_age=None, dc=None):
+    """``gabm_backward`` plus the adjoint of the infectiousness table; returns
+    (dR [I,T], dm [I,T], dS_age [I,9], dc [I,L]) in float64 (dc[:, 0] = 0)."""
+    ms = _space(gD, dR, dm, dS_age, dc)
+    cuda = ms == GABM_DEVICE
+    I, T = ctx.instances, (ctx.T if ctx.T is not None else int(gD.shape[-1]))
+    L = ctx.model.tau_EI + ctx.model.tau_IR
+    _shape(gD, (I, T), "gD")
+    _shape(dR, (I, T), "dR")
+    _shape(dm, (I, T), "dm")
+    _shape(dS_age, (I, GABM_NUM_AGES), "dS_age")
+    _shape(dc, (I, L), "dc")
+    if dR is None:
+        dR = _empty((I, T), np.float64, cuda, ctx.device)
+    if dm is None:
+        dm = _empty((I, T), np.float64, cuda, ctx.device)
+    if dS_age is None:
+        dS_age = _empty((I, GABM_NUM_AGES), np.float64, cuda, ctx.device)
+    if dc is None:
+        dc = _empty((I, L), np.float64, cuda, ctx.device)
+    st = load_library().gabm_backward_table(ctx.handle, _ptr(gD, np.float64), _ptr(dR, np.float64),
+                                            _ptr(dm, np.float64), _ptr(dS_age, np.float64),
+                                            _ptr(dc, np.float64), ms)
+    _check(st, ctx.handle)
+    return dR, dm, dS_age, dc
+
+
+def gabm_set_infectiousness(ctx: GabmCtx, c):
+    """Replace the model's infectiousness table c [L] (c[0] = 0) for the following forwards."""
+    L = ctx.model.tau_EI + ctx.model.tau_IR
+    c = np.ascontiguousarray(np.asarray(c, np.float32).reshape(-1))
+    if c.size != L:
+        raise ValueError(f"c must have {L} entries, got {c.size}")
+    st = load_library().gabm_set_infectiousness(ctx.handle, c.ctypes.data_as(ctypes.c_void_p))
+    _check(st, ctx.handle)
+    ctx.model = dataclasses.replace(ctx.model, c=c.copy())
 
 
 def gabm_get_state(ctx: GabmCtx, out=None, device: bool = False):

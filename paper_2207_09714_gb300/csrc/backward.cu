@@ -24,10 +24,34 @@ namespace gabm {
 
 namespace {
 
-template <int MODE>
+// Adds this tile's share of the table adjoint dL/dc[k] = sum_j gx_j(E_j + k): every lane
+// with `has` holds gx of its row for the day that is k = kd days after the row's
+// exposure, at scale 2^sigma of that day.  Rows with equal k are summed over the warp
+// (fp32, fixed tree), then added in FP64 to the tile's accumulator, whose only writer
+// is the warp holding the tile (days are sequential launches).  Called by all 32 lanes.
+__device__ __forceinline__ void dc_accumulate(double *dc_tile, int tile, bool has, int kd, float gx, int sigma,
+                                              int lane) {
+    unsigned pend = __ballot_sync(0xffffffffu, has);
+    if (!pend) return;
+    const double scale = ldexp(1.0, sigma);
+    while (pend) {
+        const int k0 = __shfl_sync(0xffffffffu, kd, __ffs(pend) - 1);
+        const bool sel = has && kd == k0;
+        float v = sel ? gx : 0.f;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) dc_tile[(size_t)tile * kMaxL + k0] += (double)v * scale;
+        pend &= ~__ballot_sync(0xffffffffu, sel);
+    }
+}
+
+// DC: accumulate the table adjoint (a.dc_tile); a separate instance, so the plain sweep
+// carries none of its code.
+template <int MODE, bool DC>
 __global__ void __launch_bounds__(kBlock, GABM_MINBLOCKS) k_bwd_day(const BwdDayArgs a) {
     constexpr int NARR = (MODE == kBwdFused) ? 2 : 1;
     constexpr bool SOFT = MODE == kBwdSoft;
+    static_assert(!(SOFT && DC), "the table adjoint is built for the hard sweep");
     __shared__ float c_s[kMaxL];
     __shared__ int slot_k[kMaxL];
     __shared__ int32_t red_s[kBlock / 32][2];
@@ -102,18 +126,23 @@ __global__ void __launch_bounds__(kBlock, GABM_MINBLOCKS) k_bwd_day(const BwdDay
         const bool isS = SOFT ? agent : live && (never || Ei >= t);
         const bool needA = has_next && (SOFT ? agent : live && (never || Ei >= t + 2 - L));
         if (!SOFT) cN += (agent && !never && t - Ei == L);
+        // table adjoint: rows infectious on day t+1 (k = t+1-E in [1, L-1]) add gx(t+1) to
+        // dc[k]; the non-seed ones are already gathered (needA), the seeds only for this
+        const int kd = t + 1 - Ei;
+        const bool dc_row = DC && has_next && agent && !never && kd >= 1 && kd <= L - 1;
 
         float sum[NARR];
         {
-            const bool act = (MODE == kBwdFused) ? (needA || isS) : needA;
+            const bool act = (MODE == kBwdFused) ? (needA || isS || dc_row) : (needA || dc_row);
             bool want[NARR];
-            want[0] = needA;
+            want[0] = needA || dc_row;
             if constexpr (NARR == 2) want[1] = isS;
             row_sums<NARR>(a.m, cur.p0, cur.len, act, lane, contrib, want, sum);
         }
         const float gx_mine = sum[0];
 
         if (needA) a.ring[(size_t)slot_k[1] * a.ring_stride + row] = gx_mine;
+        if constexpr (DC) dc_accumulate(a.dc_tile, tile, dc_row, kd, gx_mine, sg[t + 1], lane);
 
         float v = 0.f;
         int ai = 0;
@@ -243,6 +272,45 @@ __global__ void __launch_bounds__(kBlock) k_lam_day(Sell m, const int16_t *E, co
     }
 }
 
+// The seeds' share of the table adjoint through day 0: a seed exposed on day E < 0 is
+// infectious on day 0 with k = -E, and gx(0) = sum over its out-edges of w r(0) (r(0) at
+// scale 2^sigma(0)).  Only tiles holding a seed do any work.
+__global__ void __launch_bounds__(kBlock) k_dc_seeds(Sell m, const int16_t *E, const float *r0, GraphRef gr,
+                                                     const int32_t *sig, int ld_sig, int ntiles, int L,
+                                                     double *dc_tile) {
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int nwarps = gridDim.x * (kBlock / 32);
+    auto contrib = [&](uint32_t j, float w, bool valid, float (&out)[1]) { out[0] = w * ld_if(r0 + j, valid); };
+    const bool want[1] = {true};
+    for (int tile = blockIdx.x * (kBlock / 32) + wib; tile < ntiles; tile += nwarps) {
+        const int row = tile * kTile + lane;
+        const int Ei = E[row];
+        const bool seed = Ei != kPad && Ei < 0 && -Ei <= L - 1;
+        if (!__any_sync(0xffffffffu, seed)) continue;
+        float sum[1];
+        row_sums<1>(m, m.slice_ptr[tile], m.row_len[row], seed, lane, contrib, want, sum);
+        const int g = gr.tile_graph ? (int)gr.tile_graph[tile] : 0;
+        dc_accumulate(dc_tile, tile, seed, -Ei, sum[0], sig[(size_t)g * ld_sig], lane);
+    }
+}
+
+// dc[g][k] = sum over the graph's tiles of dc_tile[tile][k] (fixed order, FP64), k < L.
+__global__ void __launch_bounds__(256) k_dc_reduce(const double *dc_tile, const int32_t *graph_tile0,
+                                                   const int32_t *graph_ntiles, int L, double *dc) {
+    __shared__ double s[256];
+    const int g = blockIdx.x, k = blockIdx.y;
+    const int tile0 = graph_tile0[g], nt = graph_ntiles[g];
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < nt; i += blockDim.x) acc += dc_tile[(size_t)(tile0 + i) * kMaxL + k];
+    s[threadIdx.x] = acc;
+    __syncthreads();
+    for (int h = 128; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h) s[threadIdx.x] += s[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) dc[(size_t)g * L + k] = s[0];
+}
+
 // Q[inst][t][a] = sum over the graph's tiles of P[t][tile][a], fixed order, FP64.
 __global__ void __launch_bounds__(256) k_bwd_reduce(const double *P, int ntiles, const int32_t *graph_tile0,
                                                     const int32_t *graph_ntiles, int T, const int32_t *sig,
@@ -297,12 +365,34 @@ __global__ void __launch_bounds__(256) k_bwd_finalize(const double *Q, const flo
 }  // namespace
 
 cudaError_t launch_bwd_day(const BwdDayArgs &a, int grid, cudaStream_t s) {
+    const bool dc = a.dc_tile != nullptr;
     switch (a.mode) {
-        case kBwdStore: k_bwd_day<kBwdStore><<<grid, kBlock, 0, s>>>(a); break;
-        case kBwdFused: k_bwd_day<kBwdFused><<<grid, kBlock, 0, s>>>(a); break;
-        case kBwdSoft: k_bwd_day<kBwdSoft><<<grid, kBlock, 0, s>>>(a); break;
+        case kBwdStore:
+            if (dc) k_bwd_day<kBwdStore, true><<<grid, kBlock, 0, s>>>(a);
+            else k_bwd_day<kBwdStore, false><<<grid, kBlock, 0, s>>>(a);
+            break;
+        case kBwdFused:
+            if (dc) k_bwd_day<kBwdFused, true><<<grid, kBlock, 0, s>>>(a);
+            else k_bwd_day<kBwdFused, false><<<grid, kBlock, 0, s>>>(a);
+            break;
+        case kBwdSoft:
+            if (dc) return cudaErrorInvalidValue;
+            k_bwd_day<kBwdSoft, false><<<grid, kBlock, 0, s>>>(a);
+            break;
         default: return cudaErrorInvalidValue;
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dc_seeds(Sell m_out, const int16_t *E, const float *r0, GraphRef gr, const int32_t *sig,
+                            int ld_sig, int ntiles, int L, double *dc_tile, int grid, cudaStream_t s) {
+    k_dc_seeds<<<grid, kBlock, 0, s>>>(m_out, E, r0, gr, sig, ld_sig, ntiles, L, dc_tile);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dc_reduce(const double *dc_tile, const int32_t *graph_tile0, const int32_t *graph_ntiles, int G,
+                             int L, double *dc, cudaStream_t s) {
+    k_dc_reduce<<<dim3(G, L), 256, 0, s>>>(dc_tile, graph_tile0, graph_ntiles, L, dc);
     return cudaGetLastError();
 }
 
@@ -315,9 +405,9 @@ cudaError_t launch_lam_day(Sell m, const int16_t *E, const uint32_t *bits, Graph
 int occupancy_bwd(int mode) {
     int blocks = 0;
     switch (mode) {
-        case kBwdFused: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_bwd_day<kBwdFused>, kBlock, 0); break;
-        case kBwdSoft: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_bwd_day<kBwdSoft>, kBlock, 0); break;
-        default: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_bwd_day<kBwdStore>, kBlock, 0); break;
+        case kBwdFused: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_bwd_day<kBwdFused, false>, kBlock, 0); break;
+        case kBwdSoft: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_bwd_day<kBwdSoft, false>, kBlock, 0); break;
+        default: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_bwd_day<kBwdStore, false>, kBlock, 0); break;
     }
     return blocks > 0 ? blocks : 1;
 }

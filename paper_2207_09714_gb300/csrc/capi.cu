@@ -79,6 +79,9 @@ struct gabm_ctx {
     double *D = nullptr, *gD = nullptr, *y = nullptr, *P = nullptr, *Q = nullptr;
     float *R = nullptr, *m = nullptr, *S = nullptr;
     double *dR_s = nullptr, *dm_s = nullptr, *dS_s = nullptr, *loss_s = nullptr;
+    double *dc_tile = nullptr;      // [ntiles][kMaxL] table-adjoint accumulators (on request)
+    double *dc_s = nullptr;         // [I][L] staging of the table adjoint for host outputs
+    bool want_dc = false;           // the running backward accumulates the table adjoint
 
     SeedState *seedst = nullptr;
     uint32_t *hist = nullptr, *ties = nullptr;
@@ -111,6 +114,7 @@ struct gabm_ctx {
     struct LoopGraph {
         cudaGraphExec_t exec = nullptr;
         int t0 = -1, T = -1;
+        bool dc = false;           // captured with the table adjoint
         uint64_t generation = 0;
         uint64_t kernels = 0;      // kernel launches in the graph
     };
@@ -678,6 +682,7 @@ gabm_status backward_days_plain(gabm_ctx *c, int T, cudaStream_t s) {
     a.sig = c->sig;
     a.emax = c->emax;
     a.ld_sig = ld + 1;
+    a.dc_tile = c->want_dc ? c->dc_tile : nullptr;
     for (int t = T - 1; t >= 0; --t) {
         a.bits_t = (mode == kBwdFused || mode == kBwdSplit) ? c->bits + (size_t)t * c->ntiles : nullptr;
         a.t = t;
@@ -698,6 +703,9 @@ gabm_status backward_days_plain(gabm_ctx *c, int T, cudaStream_t s) {
         LAUNCH(launch_bwd_day(a, c->grid_bwd, s));
         prof_end(c, 1);
     }
+    if (a.dc_tile)   // the seeds' share through day 0 (r of day 0 is in slot 0)
+        LAUNCH(launch_dc_seeds(sell_view(c, true), c->e, c->r, graph_ref(c), c->sig, ld + 1, c->ntiles, c->L,
+                               c->dc_tile, c->grid_bwd, s));
     LAUNCH(launch_bwd_reduce(c->P, c->ntiles, ld, c->d_tile0, c->d_ntiles, T, c->I, c->sig, ld + 1, c->Q, s));
     return GABM_OK;
 }
@@ -753,7 +761,7 @@ void drop_graph(gabm_ctx::LoopGraph &g) {
 gabm_status run_day_loop(gabm_ctx *c, int which, int t0, int T) {
     if (!c->use_graphs || c->profiling) return day_loop(c, which, t0, T, c->stream);
     gabm_ctx::LoopGraph &g = c->loop_graph[which];
-    if (!g.exec || g.t0 != t0 || g.T != T || g.generation != c->buffer_generation) {
+    if (!g.exec || g.t0 != t0 || g.T != T || g.dc != c->want_dc || g.generation != c->buffer_generation) {
         drop_graph(g);
         if (!c->cap_stream) CK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
         CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
@@ -776,6 +784,7 @@ gabm_status run_day_loop(gabm_ctx *c, int which, int t0, int T) {
         }
         g.t0 = t0;
         g.T = T;
+        g.dc = c->want_dc;
         g.generation = c->buffer_generation;
         g.kernels = captured;
     }
@@ -1253,9 +1262,26 @@ gabm_status gabm_mse_loss(gabm_ctx *ctx, const double *y, double *loss, double *
     return GABM_OK;
 }
 
+static gabm_status backward_impl(gabm_ctx *c, const double *gD, double *dR, double *dm, double *dS_age, double *dc,
+                                 int mem_space);
+
 gabm_status gabm_backward(gabm_ctx *ctx, const double *gD, double *dR, double *dm, double *dS_age,
                           int mem_space) {
-    gabm_ctx *c = ctx;
+    return backward_impl(ctx, gD, dR, dm, dS_age, nullptr, mem_space);
+}
+
+gabm_status gabm_backward_table(gabm_ctx *ctx, const double *gD, double *dR, double *dm, double *dS_age,
+                                double *dc, int mem_space) {
+    if (!ctx) return fail(nullptr, GABM_EINVAL, "ctx is NULL");
+    if (!dc) return fail(ctx, GABM_EINVAL, "dc is required");
+    if (ctx->batched || ctx->soft)
+        return fail(ctx, GABM_EUNSUPPORTED, "the table adjoint is built for hard-mode contexts of one set per graph");
+    return backward_impl(ctx, gD, dR, dm, dS_age, dc, mem_space);
+}
+
+// gabm_backward, with the table adjoint accumulated into dc when dc is not NULL.
+static gabm_status backward_impl(gabm_ctx *c, const double *gD, double *dR, double *dm, double *dS_age, double *dc,
+                                 int mem_space) {
     if (!c) return fail(nullptr, GABM_EINVAL, "ctx is NULL");
     TRY(check_ms(c, mem_space));
     if (c->T_last < 1) return fail(c, GABM_ESTATE, "backward needs a forward first");
@@ -1266,8 +1292,17 @@ gabm_status gabm_backward(gabm_ctx *ctx, const double *gD, double *dR, double *d
     cudaStream_t s = c->stream;
     CK(cudaMemcpy2DAsync(c->gD, ld * sizeof(double), gD, T * sizeof(double), T * sizeof(double), c->I, h2d_kind(mem_space), s));
     c->gD_staged = true;
-    TRY(backward_core(c, T));
+    if (dc) {
+        if (!c->dc_tile) TRY(dalloc(c, &c->dc_tile, (size_t)c->ntiles * kMaxL));
+        if (!c->dc_s) TRY(dalloc(c, &c->dc_s, (size_t)c->I * c->L));
+        CK(cudaMemsetAsync(c->dc_tile, 0, sizeof(double) * (size_t)c->ntiles * kMaxL, s));
+    }
+    c->want_dc = dc != nullptr;
+    const gabm_status bst = backward_core(c, T);
+    c->want_dc = false;
+    TRY(bst);
     const bool dev = mem_space == GABM_DEVICE;
+    if (dc) LAUNCH(launch_dc_reduce(c->dc_tile, c->d_tile0, c->d_ntiles, c->G, c->L, dev ? dc : c->dc_s, s));
     LAUNCH(launch_bwd_finalize(c->Q, c->R, c->S, c->gD, c->batched ? c->newRM : c->newRM_b,
                                c->soft ? c->newRM_real : nullptr, ld, T, c->I,
                                dev ? dR : c->dR_s,
@@ -1276,6 +1311,7 @@ gabm_status gabm_backward(gabm_ctx *ctx, const double *gD, double *dR, double *d
         CK(cudaMemcpyAsync(dR, c->dR_s, sizeof(double) * (size_t)c->I * T, cudaMemcpyDeviceToHost, s));
         CK(cudaMemcpyAsync(dm, c->dm_s, sizeof(double) * (size_t)c->I * T, cudaMemcpyDeviceToHost, s));
         CK(cudaMemcpyAsync(dS_age, c->dS_s, sizeof(double) * (size_t)c->I * kAges, cudaMemcpyDeviceToHost, s));
+        if (dc) CK(cudaMemcpyAsync(dc, c->dc_s, sizeof(double) * (size_t)c->I * c->L, cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
     }
     return GABM_OK;
@@ -1372,6 +1408,21 @@ gabm_status gabm_get_schedule(const gabm_ctx *ctx, gabm_schedule *out) {
     out->bwd_sets_per_lane = ctx->batched ? ctx->spl_bwd : 0;
     out->bwd_sets_per_launch = ctx->batched ? ctx->bwd_chunk : 0;
     out->fwd_smem_bitmap = ctx->batched ? 0 : (ctx->smem_bits ? 1 : 0);
+    return GABM_OK;
+}
+
+gabm_status gabm_set_infectiousness(gabm_ctx *ctx, const float *c_in) {
+    gabm_ctx *c = ctx;
+    if (!c) return fail(nullptr, GABM_EINVAL, "ctx is NULL");
+    if (!c_in) return fail(c, GABM_EINVAL, "c is NULL");
+    if (c_in[0] != 0.0f) return fail(c, GABM_EINVAL, "c[0] must be 0 (no onward infection on the day of exposure)");
+    for (int k = 0; k < c->L; ++k)
+        if (!std::isfinite(c_in[k]) || c_in[k] < 0.0f) return fail(c, GABM_EINVAL, "c[%d] must be finite and >= 0", k);
+    CK(cudaStreamSynchronize(c->stream));   // launches in flight still read the old table
+    for (int k = 0; k < c->L; ++k) c->c[k] = c_in[k];
+    CK(cudaMemcpy(c->c_dev, c->c, sizeof(float) * kMaxL, cudaMemcpyHostToDevice));
+    for (auto &g : c->loop_graph) drop_graph(g);   // captured launches carry the table by value
+    c->T_last = -1;                                // the last trajectory used the old table
     return GABM_OK;
 }
 

@@ -167,6 +167,7 @@ struct BwdDayArgs {
     int ring_slot[kMaxL];      // ring slot holding day t + k, k = 1..L-1
     int32_t *sig, *emax;       // [G][ld_sig] scale exponent and largest stored exponent per day
     int ld_sig;
+    double *dc_tile;           // [ntiles][kMaxL] per-tile sums of the table adjoint over days, or nullptr
 };
 
 enum { kBwdStore = 0, kBwdFused = 1, kBwdSplit = 2, kBwdSoft = 3 };
@@ -332,6 +333,12 @@ cudaError_t launch_fwd_finalize(const int32_t *newRM, const int32_t *counts, con
 cudaError_t launch_mse(const double *D, int ldP, const double *y, int T, int I, double *loss,
                        double *gD_ctx, double *gD_out, cudaStream_t s);
 cudaError_t launch_bwd_day(const BwdDayArgs &a, int grid, cudaStream_t s);
+// Adjoint of the infectiousness table (hard mode, one set per graph): the seeds'
+// share through their day-0 infectiousness, then the per-graph sums of dc_tile.
+cudaError_t launch_dc_seeds(Sell m_out, const int16_t *E, const float *r0, GraphRef gr, const int32_t *sig,
+                            int ld_sig, int ntiles, int L, double *dc_tile, int grid, cudaStream_t s);
+cudaError_t launch_dc_reduce(const double *dc_tile, const int32_t *graph_tile0, const int32_t *graph_ntiles, int G,
+                             int L, double *dc, cudaStream_t s);
 cudaError_t launch_lam_day(Sell m, const int16_t *E, const uint32_t *bits, GraphRef gr, int t, int L, int ntiles,
                            const float *c, float *lam_out, int grid, cudaStream_t s);
 // Q[g][t][a] = 2^sigma_g(t) x (sum over graph g's tiles of P[t][tile][a]), FP64.

@@ -1,0 +1,101 @@
+"""The calibration workload (weekly-tied R and m, MSE on cumulative deaths, stage factors
+and infectiousness profile of the table) on the GPU.
+
+* Gradient parity: torch autograd through ``TableFunction`` against the FP64 oracle's
+  adjoint of the same trajectory, mapped to the unconstrained parameters by the chain
+  rule written out here in numpy (bar: the adjoint bar, 1e-3).
+* The Adam loop lowers the loss on a target simulated from known parameters.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2207_09714_gb300 import calibrate, capi, synth
+
+from helpers import EXACT_MARGIN, check_adjoint, ensure_built, model, to_dev, torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    ensure_built()
+    torch_cuda()
+
+
+def _table_chain(c, raw, dc, tau_EI):
+    """dL/dlog_T [2] and dL/dlog_iota [L-1] from dL/dc, for c = [0, raw / sum(raw)]."""
+    s = raw.sum()
+    d_raw = (dc[1:] - np.dot(dc[1:], c[1:])) / s
+    g_raw = d_raw * raw                  # d/dlog of each raw entry
+    k = np.arange(1, len(c))
+    return np.array([g_raw[k < tau_EI].sum(), g_raw[k >= tau_EI].sum()]), g_raw
+
+
+def test_calibration_gradient_matches_oracle():
+    torch = torch_cuda()
+    pop = synth.population_small(n=6000, seed=2)
+    T, n_seed = 28, 20
+    S = synth.SUSCEPTIBILITY.astype(np.float32)
+    y_cum = np.cumsum(synth.target_curve(T, pop.n, seed=3, level=5e-5))
+    p = calibrate.WeeklyParams(1, T, R0=2.6, m0=0.02, T_E=0.6, T_I=1.1)
+    with torch.no_grad():
+        p.log_R[0] += torch.tensor([0.0, 0.1, -0.05, 0.15], dtype=torch.float64, device="cuda")
+        p.logit_m[0] += torch.tensor([0.0, 0.2, -0.1, 0.1], dtype=torch.float64, device="cuda")
+    R, m, c = p()
+    R_np, m_np, c_np = (x.detach().cpu().numpy()[0] if x.dim() == 2 else x.detach().cpu().numpy()
+                        for x in (R, m, c))
+    # a Philox key whose trajectory has no near-tie draw, so the GPU reproduces it exactly
+    for seed in range(30):
+        md_o = O.Model(4, 7, c_np, seed=seed)
+        f = O.forward_hard(pop, md_o, R_np, m_np, S, n_seed=n_seed)
+        if f["margin"] > EXACT_MARGIN:
+            break
+    assert f["margin"] > EXACT_MARGIN
+
+    # oracle: loss on cumulative deaths, gD_t = sum_{s >= t} dL/dC_s, adjoint, chain rule
+    C = np.cumsum(f["D"])
+    dC = 2.0 * (C - y_cum) / T
+    gD = np.cumsum(dC[::-1])[::-1]
+    g = O.backward_hard(pop, md_o, R_np, m_np, S, f["e_final"], gD)
+    week = np.arange(T) // 7
+    R64 = np.exp(p.log_R.detach().cpu().numpy()[0])[week]
+    m64 = 1.0 / (1.0 + np.exp(-p.logit_m.detach().cpu().numpy()[0]))[week]
+    ref_R = np.bincount(week, g["dR"] * R64)
+    ref_m = np.bincount(week, g["dm"] * m64 * (1.0 - m64))
+    T_stage = np.where(np.arange(1, 11) < 4, np.exp(p.log_T[0].item()), np.exp(p.log_T[1].item()))
+    raw = T_stage * np.exp(p.log_iota.detach().cpu().numpy())
+    c64 = np.concatenate([[0.0], raw / raw.sum()])
+    ref_T, ref_iota = _table_chain(c64, raw, g["dc"], 4)
+
+    ctx = capi.gabm_create([pop], model(seed=seed))
+    (Sd,) = to_dev(S[None, :])
+    D = calibrate.TableFunction.apply(ctx, R, m, Sd, c, [n_seed])
+    assert np.array_equal(capi.gabm_get_state(ctx)[0], f["e_final"])
+    loss = calibrate.cumulative_mse(D, torch.as_tensor(y_cum[None, :], device="cuda"))
+    assert float(loss.detach()) == pytest.approx(np.mean((C - y_cum) ** 2), rel=1e-12)
+    loss.backward()
+    check_adjoint(p.log_R.grad.cpu().numpy()[0], ref_R, "log_R")
+    check_adjoint(p.logit_m.grad.cpu().numpy()[0], ref_m, "logit_m")
+    check_adjoint(p.log_T.grad.cpu().numpy(), ref_T, "log_T")
+    check_adjoint(p.log_iota.grad.cpu().numpy(), ref_iota, "log_iota")
+    assert np.abs(ref_T).min() > 0 and np.abs(ref_iota).max() > 0
+
+
+def test_adam_calibration_lowers_the_loss():
+    torch = torch_cuda()
+    pop = synth.population_small(n=20000, seed=5)
+    T, n_seed = 42, 30
+    S = synth.SUSCEPTIBILITY.astype(np.float32)
+    (Sd,) = to_dev(S[None, :])
+    ctx = capi.gabm_create([pop], model(seed=7))
+    # target: a run at known weekly parameters
+    truth = calibrate.WeeklyParams(1, T, R0=3.0, m0=0.03, T_E=0.4, T_I=1.2)
+    with torch.no_grad():
+        truth.log_R[0] += torch.linspace(0.2, -0.3, truth.log_R.shape[1], dtype=torch.float64, device="cuda")
+        R, m, c = truth()
+        y_cum = torch.cumsum(calibrate.TableFunction.apply(ctx, R, m, Sd, c, [n_seed]), dim=-1)
+    p = calibrate.WeeklyParams(1, T, R0=2.0, m0=0.01)
+    losses = calibrate.calibrate(ctx, p, y_cum, Sd, [n_seed], steps=40, lr=0.08)
+    assert all(np.isfinite(losses))
+    assert min(losses[-5:]) < 0.2 * losses[0], losses[::5]
