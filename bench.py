@@ -415,6 +415,47 @@ def cpu_baseline(pop, c, y):
                       f"edges, {DAYS} days), FP64, {dt:.1f} s"}
 
 
+def bench_calibration(ctx, stream, S, y_np, dist, steps=5):
+    """One Adam step of the calibration workload on the bench graph: weekly-tied R and m,
+    the stage factors and profile of the infectiousness table, MSE on cumulative deaths.
+    A step is the forward, the adjoint including dL/dc, the torch parameter maps and the
+    update; the table changes every step, so both day loops are re-captured each step."""
+    import torch
+    from paper_2207_09714_gb300 import calibrate
+
+    with torch.cuda.stream(stream):
+        p = calibrate.WeeklyParams(1, DAYS, R0=R0, m0=MORTALITY)
+        opt = torch.optim.Adam(p.parameters(), lr=0.02)
+        y_cum = torch.cumsum(torch.from_numpy(y_np).cuda(), dim=-1)
+        losses = []
+
+        def cstep():
+            opt.zero_grad()
+            R, m, c = p()
+            D = calibrate.TableFunction.apply(ctx, R, m, S, c, [N_SEED])
+            loss = calibrate.cumulative_mse(D, y_cum)
+            loss.backward()
+            opt.step()
+            losses.append(loss.detach())
+
+        for _ in range(3):
+            cstep()
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            cstep()
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = max_over_ranks(e0.elapsed_time(e1), dist, "cuda") / steps
+    return {"workload": f"calibration on the same graph: {DAYS} days, weekly-tied R and m, T_E, T_I and "
+                        f"the infectiousness profile; MSE on cumulative deaths; Adam",
+            "ms_per_step": ms, "steps": steps,
+            "loss_first_last": [float(losses[0]), float(losses[-1])]}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -586,6 +627,7 @@ def main():
     d2h = (Dh.numel() * 8 + lh.numel() * 8 + gDh.numel() * 8 + dRh.numel() * 8 + dmh.numel() * 8 + dSh.numel() * 8)
 
     cur, peak_mem = capi.gabm_mem_stats(ctx)
+    calib = bench_calibration(ctx, stream, S, y_np, dist)
     del ctx
     batched = None
     if not args.no_batched:
@@ -619,6 +661,7 @@ def main():
         "clocks": clk.summary(),
         "peak_hbm_bytes": peak_mem,
         "cpu_baseline": cpu,
+        "calibration": calib,
         "batched": batched,
     }
     print(json.dumps(line), flush=True)

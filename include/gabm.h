@@ -165,9 +165,9 @@ gabm_status gabm_backward(gabm_ctx *ctx, const double *gD, double *dR, double *d
  * their negative exposure day) and days 0 <= E_j + k < T, where gx_j(t) is the adjoint of
  * agent j's infectiousness on day t.  dc[i][0] = 0 (c[0] = 0 is fixed, A2 of App. A).
  * Gradients of stage factors or profile parameters that define c (T_E, T_I, iota)
- * follow by the chain rule on the caller's side.  Same preconditions as gabm_backward;
- * GABM_EINVAL if dc is NULL; GABM_EUNSUPPORTED for contexts with several sets per
- * graph or the soft relaxation. */
+ * follow by the chain rule on the caller's side.  With several sets per graph, each
+ * instance i = graph * sets_per_graph + set gets its own dc[i].  Same preconditions as
+ * gabm_backward; GABM_EINVAL if dc is NULL; GABM_EUNSUPPORTED for the soft relaxation. */
 gabm_status gabm_backward_table(gabm_ctx *ctx, const double *gD, double *dR, double *dm,
                                 double *dS_age, double *dc, int mem_space);
 

@@ -353,11 +353,15 @@ __global__ void __launch_bounds__(kBlock, 2) k_fwd_day_b(const FwdBatchArgs a) {
 // Reverse day t for every set: the transpose gather of day t+1 and the
 // straight-through adjoint of day t's draws (the per-set steps of backward.cu).
 // ---------------------------------------------------------------------------
-template <int LPR, int SPL, bool KAHAN>
+// DC: also accumulate the adjoint of the infectiousness table (a.dc_tile), a separate
+// instance so that the plain sweep carries none of its code.
+template <int LPR, int SPL, bool KAHAN, bool DC>
 __global__ void __launch_bounds__(kBlock, 2) k_bwd_day_b(const BwdBatchArgs a) {
     constexpr int RPW = 32 / LPR;
     constexpr int Bc = LPR * SPL;        // sets of this launch (a chunk of the row's Bw)
     constexpr int NW = kBlock / 32;
+    // DC: per-warp tile sums [L][Bc] of gx at the rows' infectious days, by k = t + 1 - E
+    extern __shared__ float dcs_all[];
     __shared__ float c_s[kMaxL];
     __shared__ int slot_k[kMaxL];
     __shared__ float pacc[NW][kAges][Bc];   // per-warp tile sums of gl * Lam by age and set
@@ -368,6 +372,9 @@ __global__ void __launch_bounds__(kBlock, 2) k_bwd_day_b(const BwdBatchArgs a) {
     }
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     for (int i = lane; i < kAges * Bc; i += 32) (&pacc[wib][0][0])[i] = 0.f;
+    float *dcs = dcs_all + (size_t)wib * a.L * Bc;
+    if constexpr (DC)
+        for (int i = lane; i < a.L * Bc; i += 32) dcs[i] = 0.f;
     __syncthreads();
 
     const int grp = lane / LPR, q = lane % LPR;
@@ -388,6 +395,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_bwd_day_b(const BwdBatchArgs a) {
     const int32_t *sg = nullptr;   // scale exponents of the current graph (shared by its sets)
     int sig_t = 0;
     unsigned emax_w = 0u;          // largest exponent stored by this warp (+128)
+    uint32_t touched = 0u;         // DC: the k rows of dcs this lane added to in the current tile
     TileDispenser disp;
     disp.init(a.tile_ctr, ntiles, gridDim.x * NW, lane);
     // row bounds of the tile's 32 rows (lane r: rows r and r + 1), one tile ahead
@@ -449,11 +457,37 @@ __global__ void __launch_bounds__(kBlock, 2) k_bwd_day_b(const BwdBatchArgs a) {
                 needA_any |= has_next && live && (never || Eh >= t + 2 - L);
                 anyS |= isS[h];
             }
-            const bool act = (group_bits<LPR>(__ballot_sync(kFull, needA_any)) >> grp) & 1u;
+            // table adjoint: sets in which the row is infectious on day t+1 (k = t+1-E in
+            // [1, L-1]) add gx(t+1) to dc[k]; seeds are gathered for this alone
+            bool dch[SPL];
+            int kdh[SPL];
+            bool dc_any = false;
+#pragma unroll
+            for (int h = 0; h < SPL; ++h) {
+                const int Eh = half_of(ew[h >> 1], h & 1);
+                kdh[h] = t + 1 - Eh;
+                dch[h] = DC && has_next && Eh != kPad && Eh != kNever && kdh[h] >= 1 && kdh[h] <= L - 1;
+                dc_any |= dch[h];
+            }
+            const bool act = (group_bits<LPR>(__ballot_sync(kFull, needA_any || dc_any)) >> grp) & 1u;
             float gx[SPL];
             group_row_sums<LPR, SPL, KAHAN, FVec<SPL>>(a.m, cu.p0, act ? cu.len : 0u, cu.j0, cu.w0, a.rbits_next, lane,
                                                        ld, val, gx);
             if (needA_any) st_floats<SPL>(a.ring + (size_t)slot_k[1] * stride + xo, gx);
+            if constexpr (DC) {
+                // the groups add their rows in a fixed order
+#pragma unroll
+                for (int gi = 0; gi < RPW; ++gi) {
+                    if (grp == gi)
+#pragma unroll
+                        for (int h = 0; h < SPL; ++h)
+                            if (dch[h]) {
+                                dcs[kdh[h] * Bc + q * SPL + h] += gx[h];
+                                touched |= 1u << kdh[h];
+                            }
+                    __syncwarp();
+                }
+            }
 
             float v[SPL];
             int ai = 0;
@@ -542,6 +576,28 @@ __global__ void __launch_bounds__(kBlock, 2) k_bwd_day_b(const BwdBatchArgs a) {
         }
         __syncwarp();
         if (lane == 0) a.rbits_cur[tile] = word;
+        if constexpr (DC) {
+            // the tile's sums of the table adjoint, at the scale of day t+1, into FP64 (the
+            // warp holding the tile is the only writer of its accumulators on this day)
+            uint32_t tm = __reduce_or_sync(kFull, touched);
+            touched = 0u;
+            if (tm) {
+                const double scale = ldexp(1.0, sg[t + 1]);
+                double *dt = a.dc_tile + (size_t)tile * L * Bw + a.s0;
+                while (tm) {
+                    const int k = __ffs(tm) - 1;
+                    tm &= tm - 1u;
+                    for (int i = lane; i < Bc; i += 32) {
+                        const float v = dcs[k * Bc + i];
+                        if (v != 0.f) {
+                            dt[(size_t)k * Bw + i] += (double)v * scale;
+                            dcs[k * Bc + i] = 0.f;
+                        }
+                    }
+                }
+                __syncwarp();
+            }
+        }
         tile = ntile;
         rp_lo = nrp_lo;
         rp_hi = nrp_hi;
@@ -659,6 +715,48 @@ __global__ void k_reduce_b2(const double *Pc, int G, int B, int Bp, int T, int m
     }
 }
 
+// The seeds' share of the table adjoint through day 0, one thread per (tile, set): a
+// seed exposed on day E < 0 is infectious on day 0 with k = -E, and gx(0) = sum over its
+// out-edges of w r(0) (r(0) at scale 2^sigma(0) of its graph).  The thread adds its
+// tile's seeds in row order, so the sums do not depend on scheduling.
+__global__ void k_dc_seeds_b(Csr m, const int16_t *E, const float *r0, GraphRef gr, const int32_t *sig,
+                             int ld_sig, int ntiles, int L, int B, int Bp, double *dc_tile) {
+    const int64_t total = (int64_t)ntiles * B;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int tile = (int)(idx / B), s = (int)(idx - (int64_t)tile * B);
+        const int g = gr.tile_graph ? (int)gr.tile_graph[tile] : 0;
+        const double scale = ldexp(1.0, sig[(size_t)g * ld_sig]);
+        for (int r = 0; r < kTile; ++r) {
+            const int row = tile * kTile + r;
+            const int Eh = E[(size_t)row * Bp + s];
+            if (Eh == kPad || Eh >= 0 || -Eh > L - 1) continue;
+            float gx = 0.f;
+            for (uint32_t p = m.rowptr[row]; p < m.rowptr[row + 1]; ++p)
+                gx = __fmaf_rn(m.w[p], r0[(size_t)m.col[p] * Bp + s], gx);
+            dc_tile[((size_t)tile * L - Eh) * Bp + s] += (double)gx * scale;
+        }
+    }
+}
+
+// dc[g*B+s][k] = sum over the tiles of graph g of dc_tile[tile][k][s] (fixed order, FP64).
+__global__ void __launch_bounds__(256) k_dc_reduce_b(const double *dc_tile, const int32_t *graph_tile0,
+                                                     const int32_t *graph_ntiles, int B, int Bp, int L, double *dc) {
+    __shared__ double sh[256];
+    const int inst = blockIdx.x, k = blockIdx.y;
+    const int g = inst / B, s = inst - g * B;
+    const int tile0 = graph_tile0[g], nt = graph_ntiles[g];
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < nt; i += blockDim.x) acc += dc_tile[((size_t)(tile0 + i) * L + k) * Bp + s];
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int h = 128; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h) sh[threadIdx.x] += sh[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) dc[(size_t)inst * L + k] = (k == 0) ? 0.0 : sh[0];
+}
+
 // ---- dispatch over (lanes per row, sets per lane) -------------------------
 template <int LPR, int SPL>
 cudaError_t launch_fwd_cfg(const FwdBatchArgs &a, bool kahan, int grid, cudaStream_t s) {
@@ -667,10 +765,24 @@ cudaError_t launch_fwd_cfg(const FwdBatchArgs &a, bool kahan, int grid, cudaStre
     return cudaGetLastError();
 }
 
+template <int LPR, int SPL, bool KAHAN>
+cudaError_t launch_bwd_dc(const BwdBatchArgs &a, int grid, cudaStream_t s) {
+    const size_t bytes = sizeof(float) * (size_t)(kBlock / 32) * a.L * (LPR * SPL);
+    if (bytes > 48 * 1024) {
+        const cudaError_t e =
+            cudaFuncSetAttribute(k_bwd_day_b<LPR, SPL, KAHAN, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)bytes);
+        if (e != cudaSuccess) return e;
+    }
+    k_bwd_day_b<LPR, SPL, KAHAN, true><<<grid, kBlock, bytes, s>>>(a);
+    return cudaGetLastError();
+}
+
 template <int LPR, int SPL>
 cudaError_t launch_bwd_cfg(const BwdBatchArgs &a, bool kahan, int grid, cudaStream_t s) {
-    if (kahan) k_bwd_day_b<LPR, SPL, true><<<grid, kBlock, 0, s>>>(a);
-    else k_bwd_day_b<LPR, SPL, false><<<grid, kBlock, 0, s>>>(a);
+    if (a.dc_tile) return kahan ? launch_bwd_dc<LPR, SPL, true>(a, grid, s) : launch_bwd_dc<LPR, SPL, false>(a, grid, s);
+    if (kahan) k_bwd_day_b<LPR, SPL, true, false><<<grid, kBlock, 0, s>>>(a);
+    else k_bwd_day_b<LPR, SPL, false, false><<<grid, kBlock, 0, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -684,7 +796,7 @@ int blocks_of(K kernel) {
 template <int LPR, int SPL>
 int occ_cfg(bool fwd, bool kahan) {
     if (fwd) return kahan ? blocks_of(k_fwd_day_b<LPR, SPL, true>) : blocks_of(k_fwd_day_b<LPR, SPL, false>);
-    return kahan ? blocks_of(k_bwd_day_b<LPR, SPL, true>) : blocks_of(k_bwd_day_b<LPR, SPL, false>);
+    return kahan ? blocks_of(k_bwd_day_b<LPR, SPL, true, false>) : blocks_of(k_bwd_day_b<LPR, SPL, false, false>);
 }
 
 // The (Bp, SPL) pairs built: SPL in {2, 4, 8} with Bp / SPL lanes per row (1..32).
@@ -774,6 +886,20 @@ cudaError_t launch_bwd_reduce_b(const double *P, int ntiles, const int32_t *d_ti
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_reduce_b2<<<dim3(T, G), threads, 0, s>>>(scratch, G, B, Bp, T, max_chunks, sig, ld_sig, Q);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dc_seeds_b(Csr m_out, const int16_t *E, const float *r0, GraphRef gr, const int32_t *sig,
+                              int ld_sig, int ntiles, int L, int B, int Bp, double *dc_tile, cudaStream_t s) {
+    const int64_t total = (int64_t)ntiles * B;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, 65535));
+    k_dc_seeds_b<<<grid, 256, 0, s>>>(m_out, E, r0, gr, sig, ld_sig, ntiles, L, B, Bp, dc_tile);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dc_reduce_b(const double *dc_tile, const int32_t *graph_tile0, const int32_t *graph_ntiles, int G,
+                               int B, int Bp, int L, double *dc, cudaStream_t s) {
+    k_dc_reduce_b<<<dim3(G * B, L), 256, 0, s>>>(dc_tile, graph_tile0, graph_ntiles, B, Bp, L, dc);
     return cudaGetLastError();
 }
 

@@ -592,6 +592,7 @@ gabm_status backward_days_batched(gabm_ctx *c, int T, cudaStream_t s) {
     a.emax = c->emax;
     a.ld_sig = ld + 1;
     a.Bw = c->Bp;
+    a.dc_tile = c->want_dc ? c->dc_tile : nullptr;
     const int Lm1 = c->L - 1;
     for (int t = T - 1; t >= 0; --t) {
         a.t = t;
@@ -612,6 +613,9 @@ gabm_status backward_days_batched(gabm_ctx *c, int T, cudaStream_t s) {
         }
         prof_end(c, 1);
     }
+    if (a.dc_tile)   // the seeds' share through day 0 (r of day 0 is in slot 0)
+        LAUNCH(launch_dc_seeds_b(csr_view(c, true), c->e, c->r, graph_ref(c), c->sig, ld + 1, c->ntiles, c->L, c->B,
+                                 c->Bp, c->dc_tile, s));
     LAUNCH(launch_bwd_reduce_b(c->P, c->ntiles, c->d_tile0, c->d_ntiles, c->G, c->B, c->Bp, T, c->Pc, c->max_chunks,
                                c->sig, ld + 1, c->Q, s));
     return GABM_OK;
@@ -1274,8 +1278,7 @@ gabm_status gabm_backward_table(gabm_ctx *ctx, const double *gD, double *dR, dou
                                 double *dc, int mem_space) {
     if (!ctx) return fail(nullptr, GABM_EINVAL, "ctx is NULL");
     if (!dc) return fail(ctx, GABM_EINVAL, "dc is required");
-    if (ctx->batched || ctx->soft)
-        return fail(ctx, GABM_EUNSUPPORTED, "the table adjoint is built for hard-mode contexts of one set per graph");
+    if (ctx->soft) return fail(ctx, GABM_EUNSUPPORTED, "the table adjoint is built for the hard (straight-through) mode");
     return backward_impl(ctx, gD, dR, dm, dS_age, dc, mem_space);
 }
 
@@ -1292,17 +1295,23 @@ static gabm_status backward_impl(gabm_ctx *c, const double *gD, double *dR, doub
     cudaStream_t s = c->stream;
     CK(cudaMemcpy2DAsync(c->gD, ld * sizeof(double), gD, T * sizeof(double), T * sizeof(double), c->I, h2d_kind(mem_space), s));
     c->gD_staged = true;
+    // table-adjoint accumulators: [ntiles][kMaxL] (one set per graph) or [ntiles][L][Bp]
+    const size_t dc_len = c->batched ? (size_t)c->ntiles * c->L * c->Bp : (size_t)c->ntiles * kMaxL;
     if (dc) {
-        if (!c->dc_tile) TRY(dalloc(c, &c->dc_tile, (size_t)c->ntiles * kMaxL));
+        if (!c->dc_tile) TRY(dalloc(c, &c->dc_tile, dc_len));
         if (!c->dc_s) TRY(dalloc(c, &c->dc_s, (size_t)c->I * c->L));
-        CK(cudaMemsetAsync(c->dc_tile, 0, sizeof(double) * (size_t)c->ntiles * kMaxL, s));
+        CK(cudaMemsetAsync(c->dc_tile, 0, sizeof(double) * dc_len, s));
     }
     c->want_dc = dc != nullptr;
     const gabm_status bst = backward_core(c, T);
     c->want_dc = false;
     TRY(bst);
     const bool dev = mem_space == GABM_DEVICE;
-    if (dc) LAUNCH(launch_dc_reduce(c->dc_tile, c->d_tile0, c->d_ntiles, c->G, c->L, dev ? dc : c->dc_s, s));
+    if (dc) {
+        double *out = dev ? dc : c->dc_s;
+        if (c->batched) LAUNCH(launch_dc_reduce_b(c->dc_tile, c->d_tile0, c->d_ntiles, c->G, c->B, c->Bp, c->L, out, s));
+        else LAUNCH(launch_dc_reduce(c->dc_tile, c->d_tile0, c->d_ntiles, c->G, c->L, out, s));
+    }
     LAUNCH(launch_bwd_finalize(c->Q, c->R, c->S, c->gD, c->batched ? c->newRM : c->newRM_b,
                                c->soft ? c->newRM_real : nullptr, ld, T, c->I,
                                dev ? dR : c->dR_s,

@@ -250,6 +250,7 @@ struct BwdBatchArgs {
     int32_t *sig, *emax;         // [G][ld_sig] per graph (shared by its sets)
     int ld_sig;
     int Bw, s0;                  // row width of the per-agent arrays; first set of this launch
+    double *dc_tile;             // [ntiles][L][Bw] per-tile sums of the table adjoint over days, or nullptr
 };
 
 // Schedules: spl sets per lane (2, 4 or 8; Bp / spl lanes share a row).
@@ -339,6 +340,10 @@ cudaError_t launch_dc_seeds(Sell m_out, const int16_t *E, const float *r0, Graph
                             int ld_sig, int ntiles, int L, double *dc_tile, int grid, cudaStream_t s);
 cudaError_t launch_dc_reduce(const double *dc_tile, const int32_t *graph_tile0, const int32_t *graph_ntiles, int G,
                              int L, double *dc, cudaStream_t s);
+cudaError_t launch_dc_seeds_b(Csr m_out, const int16_t *E, const float *r0, GraphRef gr, const int32_t *sig,
+                              int ld_sig, int ntiles, int L, int B, int Bp, double *dc_tile, cudaStream_t s);
+cudaError_t launch_dc_reduce_b(const double *dc_tile, const int32_t *graph_tile0, const int32_t *graph_ntiles, int G,
+                               int B, int Bp, int L, double *dc, cudaStream_t s);
 cudaError_t launch_lam_day(Sell m, const int16_t *E, const uint32_t *bits, GraphRef gr, int t, int L, int ntiles,
                            const float *c, float *lam_out, int grid, cudaStream_t s);
 // Q[g][t][a] = 2^sigma_g(t) x (sum over graph g's tiles of P[t][tile][a]), FP64.

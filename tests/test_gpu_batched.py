@@ -147,6 +147,10 @@ def _adjoint_case(pops, B, T, seed, rng_seed):
     e = capi.gabm_get_state(ctx)
     (gDd,) = to_dev(np.stack(gDs))
     dR, dm, dS = [x.cpu().numpy() for x in capi.gabm_backward(ctx, gDd)]
+    tab = [x.cpu().numpy() for x in capi.gabm_backward_table(ctx, gDd)]
+    for a, b in zip((dR, dm, dS), tab[:3]):   # the table adjoint leaves the others unchanged
+        assert np.array_equal(a, b)
+    dc = tab[3]
     checked = 0
     off = np.concatenate([[0], np.cumsum([p.n for p in pops])])
     i = 0
@@ -158,6 +162,8 @@ def _adjoint_case(pops, B, T, seed, rng_seed):
                 check_adjoint(dR[i], gs[i]["dR"], f"dR[{i}]")
                 check_adjoint(dm[i], gs[i]["dm"], f"dm[{i}]")
                 check_adjoint(dS[i], gs[i]["dS"], f"dS[{i}]")
+                assert dc[i, 0] == 0.0
+                check_adjoint(dc[i, 1:], gs[i]["dc"][1:], f"dc[{i}]")
                 assert np.abs(gs[i]["dR"]).max() > 0
                 checked += 1
             assert np.all(np.isfinite(dR[i])) and np.all(np.isfinite(dS[i]))
@@ -185,8 +191,9 @@ def _run_all(ctx, T, R, m, S, n_seed, y):
     lam = [capi.gabm_get_lambda(ctx, t) for t in (0, T // 2, T - 1)]
     loss, gD = capi.gabm_mse_loss(ctx, yd)
     dR, dm, dS = capi.gabm_backward(ctx, gD)
+    dc = capi.gabm_backward_table(ctx, gD)[3]
     out = dict(D=D.cpu().numpy(), counts=counts.cpu().numpy(), e=capi.gabm_get_state(ctx),
-               dR=dR.cpu().numpy(), dm=dm.cpu().numpy(), dS=dS.cpu().numpy())
+               dR=dR.cpu().numpy(), dm=dm.cpu().numpy(), dS=dS.cpu().numpy(), dc=dc.cpu().numpy())
     for k, v in enumerate(lam):
         out[f"lam{k}"] = v
     return out

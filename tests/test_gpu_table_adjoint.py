@@ -3,7 +3,8 @@ against the FP64 oracle, on the oracle's own trajectories.
 
 Bar: the adjoint bar of the other parameters, |gpu - oracle| <= 1e-3 * max(|oracle|,
 1e-3 * max|oracle|) for k = 1..L-1, and dc[0] = 0 exactly.  dR, dm and dS from the same
-call are bitwise those of gabm_backward.
+call are bitwise those of gabm_backward.  Contexts with several sets per graph are
+checked by the batched adjoint tests (test_gpu_batched.py), per instance.
 """
 import numpy as np
 import pytest
@@ -130,14 +131,15 @@ def test_table_adjoint_long_horizon_and_short_horizon():
         _check_table(dc, g["dc"])
 
 
-def test_table_adjoint_unsupported_contexts():
+def test_table_adjoint_unsupported_for_the_soft_relaxation():
     pop = synth.population_small(n=1000, seed=1)
-    ctx_b = capi.gabm_create([pop], model(seed=0), sets_per_graph=4)
+    md = capi.ModelDesc(tau_EI=4, tau_IR=7, c=synth.infectiousness_table(), seed=0, relax_mode=capi.GABM_SOFT)
+    ctx = capi.gabm_create([pop], md)
     T = 5
-    Rd, md_, Sd = to_dev(np.full((4, T), 2.5, np.float32), np.full((4, T), 0.01, np.float32),
-                         np.repeat(synth.SUSCEPTIBILITY[None, :], 4, axis=0).astype(np.float32))
-    capi.gabm_forward(ctx_b, T, Rd, md_, Sd, [5] * 4)
-    (gDd,) = to_dev(np.ones((4, T)))
+    Rd, md_, Sd = to_dev(np.full((1, T), 2.5, np.float32), np.full((1, T), 0.01, np.float32),
+                         synth.SUSCEPTIBILITY[None, :].astype(np.float32))
+    capi.gabm_forward(ctx, T, Rd, md_, Sd, [5])
+    (gDd,) = to_dev(np.ones((1, T)))
     with pytest.raises(capi.GabmError) as ei:
-        capi.gabm_backward_table(ctx_b, gDd)
+        capi.gabm_backward_table(ctx, gDd)
     assert ei.value.status == capi.GABM_EUNSUPPORTED
