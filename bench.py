@@ -353,6 +353,15 @@ def bench_batched(args, stream, peak, peak_kind):
     return result
 
 
+def workload_config(pop, policy: str) -> dict:
+    """The bench workload's config (both arms)."""
+    return {"workload": f"1M-agent typed contact graph (households, schools, workplaces, random), "
+                        f"{DAYS} days, forward + MSE + hand-written backward",
+            "n_agents": pop.n, "nnz": pop.nnz, "days": DAYS, "instances_per_gpu": 1,
+            "lambda_policy": policy, "R": R0, "n_seed": N_SEED,
+            "l2": f"inputs larger than L2 (edge arrays {pop.nnz * 8 / 1e6:.0f} MB > 129 MB), no flush"}
+
+
 def run_reference(args, world, rank):
     """The FP64 CPU oracle as it stands, on a bounded sample of the workload."""
     if rank != 0:
@@ -380,14 +389,14 @@ def run_reference(args, world, rank):
         step()
     dt = (time.perf_counter() - t0) / max(args.steps, 1)
     value = pop.n * DAYS / dt
-    sample = (f"{pop.n} agents of the same generator ({pop.nnz} directed edges), {DAYS} days, "
-              f"forward + MSE + backward per step")
+    sample = (f"each step a bounded sample of the workload: {pop.n} agents of the same generator "
+              f"({pop.nnz} directed edges), {DAYS} days, forward + MSE + backward; value in agent-days/s "
+              f"of the sample")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "agent-days/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"typed contact graph, {DAYS} days, fwd+bwd (CPU oracle sample)",
-                   "n_agents": pop.n, "nnz": pop.nnz, "days": DAYS},
+        "config": workload_config(synth.population_typed(N_AGENTS, seed=0), args.policy),
         "cpu_baseline": {"value": value, "unit": "agent-days/s", "cores": O.num_threads(), "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": "agent-days/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -641,11 +650,7 @@ def main():
         "metric": METRIC, "value": value, "unit": "agent-days/s", "n_gpus": world, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"1M-agent typed contact graph (households, schools, workplaces, random), "
-                               f"{DAYS} days, forward + MSE + hand-written backward",
-                   "n_agents": pop.n, "nnz": pop.nnz, "days": DAYS, "instances_per_gpu": 1,
-                   "lambda_policy": args.policy, "R": R0, "n_seed": N_SEED,
-                   "l2": f"inputs larger than L2 (edge arrays {pop.nnz * 8 / 1e6:.0f} MB > 129 MB), no flush"},
+        "config": workload_config(pop, args.policy),
         "fwd_agent_days_per_s": fwd_value,
         "ms_per_step_profiled": ms_per_step_profiled,
         "edge_updates_per_s": world * pop.nnz * DAYS / (ms_per_step / 1e3),
