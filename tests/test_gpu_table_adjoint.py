@@ -143,3 +143,40 @@ def test_table_adjoint_unsupported_for_the_soft_relaxation():
     with pytest.raises(capi.GabmError) as ei:
         capi.gabm_backward_table(ctx, gDd)
     assert ei.value.status == capi.GABM_EUNSUPPORTED
+
+
+def test_set_infectiousness_validation_and_state():
+    """An invalid table is refused and leaves the ctx as it was; a valid one invalidates the
+    last trajectory until the next forward, which then uses the new table (it equals a
+    ctx created with that table, bitwise)."""
+    pop = synth.population_small(n=2000, seed=9)
+    T = 15
+    Rd, md_, Sd = to_dev(np.full((1, T), 2.8, np.float32), np.full((1, T), 0.02, np.float32),
+                         synth.SUSCEPTIBILITY[None, :].astype(np.float32))
+    ctx = capi.gabm_create([pop], model(seed=2))
+    capi.gabm_forward(ctx, T, Rd, md_, Sd, [10])
+    e0 = capi.gabm_get_state(ctx)
+    (gDd,) = to_dev(np.ones((1, T)))
+    c = synth.infectiousness_table().copy()
+    for bad in (np.r_[0.1, c[1:]], np.r_[c[:3], -0.5, c[4:]], np.r_[c[:5], np.nan, c[6:]]):
+        with pytest.raises(capi.GabmError) as ei:
+            capi.gabm_set_infectiousness(ctx, bad.astype(np.float32))
+        assert ei.value.status == capi.GABM_EINVAL
+    with pytest.raises(ValueError):
+        capi.gabm_set_infectiousness(ctx, c[:5])
+    capi.gabm_backward(ctx, gDd)                          # the refused tables changed nothing
+    c2 = synth.infectiousness_table(T_E=0.2, T_I=1.3)
+    capi.gabm_set_infectiousness(ctx, c2)
+    with pytest.raises(capi.GabmError) as ei:
+        capi.gabm_backward(ctx, gDd)
+    assert ei.value.status == capi.GABM_ESTATE
+    D1, _ = capi.gabm_forward(ctx, T, Rd, md_, Sd, [10])
+    ref = capi.gabm_create([pop], model(c=c2, seed=2))
+    D2, _ = capi.gabm_forward(ref, T, Rd, md_, Sd, [10])
+    assert np.array_equal(D1.cpu().numpy(), D2.cpu().numpy())
+    assert np.array_equal(capi.gabm_get_state(ctx), capi.gabm_get_state(ref))
+    assert not np.array_equal(capi.gabm_get_state(ctx), e0)
+    a = [x.cpu().numpy() for x in capi.gabm_backward_table(ctx, gDd)]
+    b = [x.cpu().numpy() for x in capi.gabm_backward_table(ref, gDd)]
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
