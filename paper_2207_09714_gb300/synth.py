@@ -270,6 +270,74 @@ def permute(pop: Population, perm: np.ndarray) -> Population:
                       age=age, name=pop.name + "_perm")
 
 
+@dataclasses.dataclass
+class Bipartite:
+    """Agents and locations, the heterogeneous contact structure of GradABM-JUNE (Sec. 5):
+    agent i attends location l with weight w_il (agent-sorted incidence).  Two agents
+    interact through every location they share: the one-hop weight of the pair is
+    W_ij = sum_l w_il w_jl (i != j)."""
+
+    n: int               # agents
+    n_loc: int           # locations
+    rowptr: np.ndarray   # uint64 [n+1]: agent i's locations are loc[rowptr[i]:rowptr[i+1]]
+    loc: np.ndarray      # uint32 [nnz]
+    w: np.ndarray        # float32 [nnz] attendance weight w_il
+    age: np.ndarray      # uint8 [n]
+    name: str = ""
+
+    @property
+    def nnz(self) -> int:
+        return int(self.loc.shape[0])
+
+
+def population_bipartite(n: int = 20_000, seed: int = 0, school=(100, 400), work=(5, 60),
+                         venues_per_agent: float = 1.5, venue_size: float = 40.0) -> Bipartite:
+    """Agents attending locations: one household each (sizes geometric(p = 0.4) up to 6), a
+    school (age bins 0-1, sizes U{school}) or a workplace (bins 2-6, U{work}), and a
+    Poisson(venues_per_agent) number of shared venues (shops, transport) drawn uniformly
+    among n / venue_size venues.  Weight = type scale (household 1.0, school 0.6, workplace
+    0.4, venue 0.2) x U[0.5, 1.5].  Locations are numbered households, schools,
+    workplaces, venues; each agent's list is sorted by location."""
+    rng = _rng([seed, 800])
+    age = rng.integers(0, NUM_AGE_BINS, size=n).astype(np.uint8)
+    agents, locs, ws = [], [], []
+    base = 0
+    hs = _cut_sizes(rng, n, 1, 6, "geometric", p=0.4)
+    agents.append(np.arange(n, dtype=np.int64))
+    locs.append(np.repeat(np.arange(hs.size, dtype=np.int64), hs))
+    ws.append(TYPE_WEIGHT["household"] * rng.uniform(0.5, 1.5, n))
+    base += hs.size
+    for kind, bins, (lo, hi) in (("school", (0, 1), school), ("workplace", (2, 3, 4, 5, 6), work)):
+        elig = np.flatnonzero(np.isin(age, bins)).astype(np.int64)
+        rng.shuffle(elig)
+        gs = _cut_sizes(rng, elig.size, lo, hi, "uniform")
+        agents.append(elig)
+        locs.append(base + np.repeat(np.arange(gs.size, dtype=np.int64), gs))
+        ws.append(TYPE_WEIGHT[kind] * rng.uniform(0.5, 1.5, elig.size))
+        base += gs.size
+    n_venue = max(1, int(n / venue_size))
+    k = rng.poisson(venues_per_agent, size=n)
+    va = np.repeat(np.arange(n, dtype=np.int64), k)
+    vl = base + rng.integers(0, n_venue, size=va.size)
+    agents.append(va)
+    locs.append(vl)
+    ws.append(TYPE_WEIGHT["random"] * rng.uniform(0.5, 1.5, va.size))
+    base += n_venue
+    a = np.concatenate(agents)
+    l = np.concatenate(locs)
+    w = np.concatenate(ws)
+    key = a * np.int64(base) + l
+    order = np.argsort(key, kind="stable")
+    key, w = key[order], w[order]
+    uniq, start = np.unique(key, return_index=True)          # repeated visits add up
+    wsum = np.add.reduceat(w, start)
+    a, l = uniq // base, uniq % base
+    rowptr = np.zeros(n + 1, np.uint64)
+    np.cumsum(np.bincount(a, minlength=n), out=rowptr[1:])
+    return Bipartite(n=n, n_loc=int(base), rowptr=rowptr, loc=l.astype(np.uint32), w=wsum.astype(np.float32),
+                     age=age, name=f"bipartite_n{n}")
+
+
 def uneven_counties(num: int = 32, lo: float = 5e4, hi: float = 2e6, seed: int = 0, scale: float = 1.0):
     """County graphs with agent counts log-uniform in [lo, hi] (times ``scale``)."""
     rng = _rng([seed, 400])

@@ -11,6 +11,7 @@ import os
 
 import numpy as np
 import pytest
+import scipy.sparse as sp
 
 import oracle as O
 from oracle import brute, meanfield
@@ -413,3 +414,27 @@ def test_hard_adjoint_is_soft_adjoint_at_hard_values():
         assert ref > 0
         assert np.allclose(g[k], h[k], rtol=1e-10, atol=1e-12 * ref), k
     assert np.array_equal(h["dm"], gD * f["newRM"])
+
+
+def test_agent_location_expansion():
+    """The one-hop weights of an agent-location graph, checked by hand on a small case:
+    agents 0, 1, 2 share location A (weights 1, 2, 3), agents 1 and 2 also share B
+    (weights 0.5, 4); agent 3 is alone at C."""
+    from oracle import bipartite as OB
+    bip = synth.Bipartite(n=4, n_loc=3, rowptr=np.array([0, 1, 3, 5, 6], np.uint64),
+                          loc=np.array([0, 0, 1, 0, 1, 2], np.uint32),
+                          w=np.array([1.0, 2.0, 0.5, 3.0, 4.0, 7.0], np.float32), age=np.zeros(4, np.uint8))
+    W = OB.expand(bip)
+    dense = np.zeros((4, 4))
+    for i in range(4):
+        for p in range(int(W.rowptr[i]), int(W.rowptr[i + 1])):
+            dense[i, W.col[p]] = W.w64[p]
+    ref = np.array([[0, 2, 3, 0], [2, 0, 6 + 2, 0], [3, 8, 0, 0], [0, 0, 0, 0]], np.float64)
+    assert np.array_equal(dense, ref)
+    assert OB.mean_weighted_degree(bip) == pytest.approx(ref.sum() / 4, rel=1e-15)
+    # on a generated population: symmetric, no self pairs, Dbar from the incidence alone
+    big = synth.population_bipartite(3000, seed=2)
+    Wb = OB.expand(big)
+    A = sp.csr_matrix((Wb.w64, Wb.col.astype(np.int64), Wb.rowptr.astype(np.int64)), shape=(big.n, big.n))
+    assert abs(A - A.T).max() < 1e-12 and A.diagonal().max() == 0
+    assert OB.mean_weighted_degree(big) == pytest.approx(Wb.w64.sum() / big.n, rel=1e-12)
