@@ -118,10 +118,37 @@ typedef struct {
  * any CUDA call), builds the device CSR and its transpose (aliased when the
  * weights are symmetric), and allocates the per-agent state.  cuda_stream is a
  * cudaStream_t (NULL = legacy default stream).  num_graphs >= 1 graphs are
- * concatenated block-diagonally (uneven batch); sets_per_graph must be 1 in
- * this build.  On success *out owns everything; release with gabm_destroy. */
+ * concatenated block-diagonally (uneven batch); sets_per_graph = B in 1..64
+ * parameter sets share each graph (instance i = graph * B + set; B > 1 needs
+ * GABM_STORE_LAMBDA).  On success *out owns everything; release with gabm_destroy. */
 gabm_status gabm_create(const gabm_graph_desc *graphs, int num_graphs, int sets_per_graph,
                         const gabm_model_desc *model, void *cuda_stream, gabm_ctx **out);
+
+/* An agent-location graph, the heterogeneous contact structure of GradABM-JUNE
+ * (Sec. 5): agent i attends location loc[p] with weight w[p] for p in
+ * [rowptr[i], rowptr[i+1]).  Two agents interact through every location they
+ * share, so the model is that of Sec. 3.1 (Eq. 3) on the agent graph with pair
+ * weights W_ij = sum_l w_il w_jl (i != j), and Dbar is W's mean weighted degree.
+ * Each day is computed in two hops over the attendance entries -- location
+ * pressures P_l(t) = sum_{j at l} w_jl x_j(t), then
+ * lambda_i(t) = R_t S[a_i] (1/Dbar) sum_l w_il P_l(t) -- and the adjoint likewise,
+ * so W, whose size grows with the square of the location sizes, is never formed.
+ * (An agent's own term drops out: x_i = 0 while i is susceptible.)  Host memory. */
+typedef struct {
+    int64_t n_agents, n_locations, nnz;
+    const uint64_t *rowptr;  /* [n_agents+1] */
+    const uint32_t *loc;     /* [nnz] location of each attendance, < n_locations */
+    const float *w;          /* [nnz] attendance weight, finite and >= 0 (repeats add) */
+    const uint8_t *age;      /* [n_agents] age bins 0..8 */
+} gabm_bipartite_desc;
+
+/* Build a ctx over one agent-location graph (copied; GABM_EINVAL on bad data,
+ * before any CUDA call).  It then works as a gabm_create ctx of one graph and one
+ * set: agents are the rows, in input order within degree windows (agent_order is
+ * not used).  The model must use GABM_HARD_ST and GABM_STORE_LAMBDA
+ * (GABM_EUNSUPPORTED otherwise). */
+gabm_status gabm_create_bipartite(const gabm_bipartite_desc *graph, const gabm_model_desc *model,
+                                  void *cuda_stream, gabm_ctx **out);
 
 /* Forward over days t0..T-1 (Sec. 3.1, Eq. 1-3, K = T steps).  t0 = 0 after
  * create (seeding from n_seed), or the day given to the last gabm_set_state.

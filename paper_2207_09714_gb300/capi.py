@@ -45,6 +45,12 @@ class _GraphDesc(ctypes.Structure):
                 ("mem_space", ctypes.c_int)]
 
 
+class _BipartiteDesc(ctypes.Structure):
+    _fields_ = [("n_agents", ctypes.c_int64), ("n_locations", ctypes.c_int64), ("nnz", ctypes.c_int64),
+                ("rowptr", ctypes.c_void_p), ("loc", ctypes.c_void_p), ("w", ctypes.c_void_p),
+                ("age", ctypes.c_void_p)]
+
+
 class _ModelDesc(ctypes.Structure):
     _fields_ = [("tau_EI", ctypes.c_int), ("tau_IR", ctypes.c_int), ("c", ctypes.c_void_p),
                 ("gumbel_tau", ctypes.c_float), ("relax_mode", ctypes.c_int),
@@ -74,6 +80,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         L.gabm_create.argtypes = [ctypes.POINTER(_GraphDesc), i32, i32, ctypes.POINTER(_ModelDesc), P,
                                   ctypes.POINTER(P)]
         L.gabm_forward.argtypes = [P, i32, P, P, P, P, P, P, i32]
+        L.gabm_create_bipartite.argtypes = [ctypes.POINTER(_BipartiteDesc), ctypes.POINTER(_ModelDesc), P,
+                                            ctypes.POINTER(P)]
         L.gabm_mse_loss.argtypes = [P, P, P, P, i32]
         L.gabm_backward.argtypes = [P, P, P, P, P, i32]
         L.gabm_backward_table.argtypes = [P, P, P, P, P, P, i32]
@@ -98,7 +106,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         L.gabm_get_schedule.argtypes = [P, ctypes.POINTER(_Schedule)]
         L.gabm_set_schedule.argtypes = [P, ctypes.POINTER(_Schedule)]
         L.gabm_autotune.argtypes = [P, i32]
-        for name in ("gabm_create", "gabm_forward", "gabm_mse_loss", "gabm_backward", "gabm_backward_table",
+        for name in ("gabm_create", "gabm_create_bipartite", "gabm_forward", "gabm_mse_loss", "gabm_backward", "gabm_backward_table",
                      "gabm_set_infectiousness",
                      "gabm_get_state",
                      "gabm_set_state", "gabm_get_lambda", "gabm_mem_stats", "gabm_set_profiling",
@@ -218,6 +226,35 @@ def gabm_version() -> str:
     return load_library().gabm_version().decode()
 
 
+def _model_struct(model: ModelDesc, c: np.ndarray) -> _ModelDesc:
+    return _ModelDesc(int(model.tau_EI), int(model.tau_IR), _ptr(c, np.float32), float(model.gumbel_tau),
+                      int(model.relax_mode), int(model.lambda_policy), int(model.seed), int(model.agent_order))
+
+
+def gabm_create_bipartite(graph, model: ModelDesc, stream=None) -> GabmCtx:
+    """Create a ctx over an agent-location graph (an object with n, n_loc, rowptr [n+1],
+    loc, w, age as host numpy arrays): agents interact through shared locations, the
+    pair weight being sum_l w_il w_jl.  One graph, one set; store-lambda hard mode."""
+    L = load_library()
+    rowptr = np.ascontiguousarray(graph.rowptr, np.uint64)
+    loc = np.ascontiguousarray(graph.loc, np.uint32)
+    w = np.ascontiguousarray(graph.w, np.float32)
+    age = np.ascontiguousarray(graph.age, np.uint8)
+    desc = _BipartiteDesc(int(graph.n), int(graph.n_loc), int(loc.shape[0]), _ptr(rowptr, np.uint64),
+                          _ptr(loc, np.uint32), _ptr(w, np.float32), _ptr(age, np.uint8))
+    c = np.ascontiguousarray(model.c, dtype=np.float32)
+    md = _model_struct(model, c)
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    s = ctypes.c_void_p(int(getattr(stream, "cuda_stream", stream)))
+    device = getattr(stream, "device", None) or torch.device("cuda", torch.cuda.current_device())
+    out = ctypes.c_void_p()
+    st = L.gabm_create_bipartite(ctypes.byref(desc), ctypes.byref(md), s, ctypes.byref(out))
+    _check(st, None)
+    return GabmCtx(out, [graph], 1, model, device, stream)
+
+
 def gabm_create(graphs, model: ModelDesc, sets_per_graph: int = 1, stream=None) -> GabmCtx:
     """Create a ctx from graphs (objects with n, rowptr, col, w, age) and a ModelDesc."""
     L = load_library()
@@ -232,8 +269,7 @@ def gabm_create(graphs, model: ModelDesc, sets_per_graph: int = 1, stream=None) 
                               _ptr(g.w, np.float32), _ptr(g.age, np.uint8), ms)
         keep.append(g)
     c = np.ascontiguousarray(model.c, dtype=np.float32)
-    md = _ModelDesc(int(model.tau_EI), int(model.tau_IR), _ptr(c, np.float32), float(model.gumbel_tau),
-                    int(model.relax_mode), int(model.lambda_policy), int(model.seed), int(model.agent_order))
+    md = _model_struct(model, c)
     s = None
     if stream is not None:
         s = ctypes.c_void_p(int(getattr(stream, "cuda_stream", stream)))

@@ -139,7 +139,8 @@ __global__ void __launch_bounds__(kBlock, GABM_MINBLOCKS) k_bwd_day(const BwdDay
             if constexpr (NARR == 2) want[1] = isS;
             row_sums<NARR>(a.m, cur.p0, cur.len, act, lane, contrib, want, sum);
         }
-        const float gx_mine = sum[0];
+        float gx_mine = sum[0];
+        if (a.self_q) gx_mine = __fmaf_rn(-a.self_q[row], a.self_r[row], gx_mine);
 
         if (needA) a.ring[(size_t)slot_k[1] * a.ring_stride + row] = gx_mine;
         if constexpr (DC) dc_accumulate(a.dc_tile, tile, dc_row, kd, gx_mine, sg[t + 1], lane);

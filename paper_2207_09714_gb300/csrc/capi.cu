@@ -102,6 +102,14 @@ struct gabm_ctx {
 
     int grid_fwd = 0, grid_bwd = 0;
     bool smem_bits = false;         // forward keeps the infectious bitmap in shared memory
+    // agent-location graphs: the location hop (SELL-32 of locations -> members) and its values
+    bool two_hop = false;
+    int64_t n_loc = 0;
+    int loc_ntiles = 0, grid_loc = 0;
+    uint32_t *loc_slice_ptr = nullptr, *loc_row_len = nullptr, *loc_col = nullptr;
+    float *loc_w = nullptr;
+    float *locv = nullptr;          // [loc_ntiles * 32] location pressures (forward) or adjoints (backward)
+    float *self_q = nullptr;        // [n_rows] sum over the agent's locations of w_il^2
     int *tile_ctr = nullptr;        // batched: [1 + max chunks][Tcap] per-launch tile counters (forward, backward chunks)
     uint32_t *bits = nullptr;       // [Tcap][ntiles] per-day bitmaps of infectious rows
 
@@ -493,6 +501,15 @@ Sell sell_view(const gabm_ctx *c, bool out_edges) {
     return m;
 }
 
+Sell loc_sell_view(const gabm_ctx *c) {
+    Sell m;
+    m.slice_ptr = c->loc_slice_ptr;
+    m.row_len = c->loc_row_len;
+    m.col = c->loc_col;
+    m.w = c->loc_w;
+    return m;
+}
+
 GraphRef graph_ref(const gabm_ctx *c) {
     GraphRef gr;
     gr.row0 = c->d_row0;
@@ -646,7 +663,13 @@ gabm_status forward_days_plain(gabm_ctx *c, int t0, int T, cudaStream_t s) {
         a.lam_out = c->policy == GABM_STORE_LAMBDA ? c->lam + (size_t)t * c->n_rows : nullptr;
         a.bits_cur = c->bits + (size_t)t * c->ntiles;
         a.bits_next = c->bits + (size_t)(t + 1) * c->ntiles;
+        a.pull = nullptr;
         prof_begin(c, 0);
+        if (c->two_hop) {   // location pressures of day t, then the agents' pull over their locations
+            LAUNCH(launch_loc_pressure(loc_sell_view(c), c->loc_ntiles, c->e, a.bits_cur, t, c->L, c->c_dev, c->locv,
+                                       c->grid_loc, s));
+            a.pull = c->locv;
+        }
         LAUNCH(launch_fwd_day(a, c->grid_fwd, c->smem_bits, s));
         prof_end(c, 0);
     }
@@ -687,6 +710,7 @@ gabm_status backward_days_plain(gabm_ctx *c, int T, cudaStream_t s) {
     a.emax = c->emax;
     a.ld_sig = ld + 1;
     a.dc_tile = c->want_dc ? c->dc_tile : nullptr;
+    a.self_r = a.self_q = nullptr;
     for (int t = T - 1; t >= 0; --t) {
         a.bits_t = (mode == kBwdFused || mode == kBwdSplit) ? c->bits + (size_t)t * c->ntiles : nullptr;
         a.t = t;
@@ -701,15 +725,27 @@ gabm_status backward_days_plain(gabm_ctx *c, int T, cudaStream_t s) {
                                   c->ntiles, c->c_dev, c->lam_tmp, c->grid_bwd, s));
         a.r_next = c->r + (size_t)((t + 1) & 1) * c->n_rows;
         a.r_cur = c->r + (size_t)(t & 1) * c->n_rows;
+        if (c->two_hop) {   // the location hop of the transpose gather: gP = sum over members of w r(t+1)
+            LAUNCH(launch_loc_adjoint(loc_sell_view(c), c->loc_ntiles, a.r_next, c->c_dev, c->locv, c->grid_loc, s));
+            a.self_r = a.r_next;
+            a.self_q = c->self_q;
+            a.r_next = c->locv;
+        }
         a.P_t = c->P + (size_t)t * c->ntiles * kAges;
         for (int k = 0; k < kMaxL; ++k) a.ring_slot[k] = (k >= 1 && k < c->L) ? (t + k) % Lm1 : 0;
         prof_begin(c, 1);
         LAUNCH(launch_bwd_day(a, c->grid_bwd, s));
         prof_end(c, 1);
     }
-    if (a.dc_tile)   // the seeds' share through day 0 (r of day 0 is in slot 0)
-        LAUNCH(launch_dc_seeds(sell_view(c, true), c->e, c->r, graph_ref(c), c->sig, ld + 1, c->ntiles, c->L,
+    if (a.dc_tile) {   // the seeds' share through day 0 (r of day 0 is in slot 0)
+        const float *r0 = c->r;
+        if (c->two_hop) {
+            LAUNCH(launch_loc_adjoint(loc_sell_view(c), c->loc_ntiles, c->r, c->c_dev, c->locv, c->grid_loc, s));
+            r0 = c->locv;
+        }
+        LAUNCH(launch_dc_seeds(sell_view(c, true), c->e, r0, graph_ref(c), c->sig, ld + 1, c->ntiles, c->L,
                                c->dc_tile, c->grid_bwd, s));
+    }
     LAUNCH(launch_bwd_reduce(c->P, c->ntiles, ld, c->d_tile0, c->d_ntiles, T, c->I, c->sig, ld + 1, c->Q, s));
     return GABM_OK;
 }
@@ -873,6 +909,10 @@ void apply_schedule(gabm_ctx *c) {
         c->grid_fwd = c->num_sms * (c->smem_bits ? bps : occupancy_fwd(c->ntiles, false));
         c->grid_bwd = c->num_sms * occupancy_bwd(mode);
     }
+    if (c->two_hop) {
+        c->smem_bits = false;
+        c->grid_loc = std::min(c->num_sms * occupancy_loc(), std::max(1, (c->loc_ntiles + kBlock / 32 - 1) / (kBlock / 32)));
+    }
     const int max_grid = (c->ntiles + kBlock / 32 - 1) / (kBlock / 32);
     if (!c->smem_bits && c->grid_fwd > max_grid) c->grid_fwd = max_grid;
     if (c->grid_bwd > max_grid) c->grid_bwd = max_grid;
@@ -897,116 +937,40 @@ const char *gabm_version(void) { return "gabm-gb300 0.1 (sm_103a)"; }
 
 const char *gabm_last_error(const gabm_ctx *ctx) { return ctx ? ctx->err.c_str() : g_create_error.c_str(); }
 
-gabm_status gabm_create(const gabm_graph_desc *graphs, int num_graphs, int sets_per_graph,
-                        const gabm_model_desc *model, void *cuda_stream, gabm_ctx **out) {
-    g_create_error.clear();
-    if (!out) return fail(nullptr, GABM_EINVAL, "out is NULL");
-    *out = nullptr;
-    if (!graphs || num_graphs < 1 || num_graphs > 65535) return fail(nullptr, GABM_EINVAL, "need 1..65535 graphs");
-    if (sets_per_graph < 1) return fail(nullptr, GABM_EINVAL, "sets_per_graph must be >= 1");
-    if (sets_per_graph > kMaxSets) return fail(nullptr, GABM_EUNSUPPORTED, "sets_per_graph > %d", kMaxSets);
-    TRY(validate_model(model));
-    if (sets_per_graph > 1 && model->lambda_policy != GABM_STORE_LAMBDA)
-        return fail(nullptr, GABM_EUNSUPPORTED, "sets_per_graph > 1 needs GABM_STORE_LAMBDA in this build");
-    if (model->relax_mode == GABM_SOFT && (sets_per_graph > 1 || model->lambda_policy != GABM_STORE_LAMBDA))
-        return fail(nullptr, GABM_EUNSUPPORTED, "GABM_SOFT needs sets_per_graph = 1 and GABM_STORE_LAMBDA in this build");
-
-    // ---- host side: validate, concatenate, transpose ----
-    std::vector<HostGraph> hg((size_t)num_graphs);
-    bool any_device = false;
-    for (int g = 0; g < num_graphs; ++g) any_device |= (graphs[g].mem_space == GABM_DEVICE);
-    for (int g = 0; g < num_graphs; ++g) TRY(fetch_graph(graphs[g], g, hg[g]));
-    (void)any_device;
-
-    std::vector<int32_t> row0(num_graphs), rows(num_graphs), tile0(num_graphs), ntl(num_graphs);
-    std::vector<double> Dbar(num_graphs);
-    int64_t n_rows = 0, nnz = 0, n_total = 0;
-    for (int g = 0; g < num_graphs; ++g) {
-        row0[g] = (int32_t)n_rows;
-        rows[g] = (int32_t)hg[g].n;
-        tile0[g] = (int32_t)(n_rows / kTile);
-        const int64_t padded = (int64_t)round_up((size_t)hg[g].n, kTile);
-        ntl[g] = (int32_t)(padded / kTile);
-        n_rows += padded;
-        nnz += hg[g].nnz;
-        n_total += hg[g].n;
-        double s = 0.0;
-        for (int64_t p = 0; p < hg[g].nnz; ++p) s += (double)hg[g].w[p];
-        Dbar[g] = hg[g].n > 0 ? s / (double)hg[g].n : 0.0;
-    }
-    // device layout: optionally relabel each graph's agents (D-bar above uses the caller's order)
-    std::vector<std::vector<uint32_t>> orders((size_t)num_graphs);
-    const bool reorder = true;
-    int sigma = 1024;
-    if (const char *f = getenv("GABM_SELL_SIGMA")) sigma = std::max(1, atoi(f));
-    for (int g = 0; g < num_graphs; ++g) {
-        if (model->agent_order == GABM_ORDER_BFS) {
-            orders[g] = bfs_order(hg[g]);
-        } else {
-            orders[g].resize((size_t)hg[g].n);
-            for (int64_t i = 0; i < hg[g].n; ++i) orders[g][i] = (uint32_t)i;
-        }
-        sort_windows_by_degree(hg[g], orders[g], sigma);
-        hg[g] = permute_graph(hg[g], orders[g]);
-    }
-    if (n_rows >= ((int64_t)1 << 31) - 64) return fail(nullptr, GABM_EUNSUPPORTED, "total rows >= 2^31");
-    if (nnz >= ((int64_t)1 << 32) - 64) return fail(nullptr, GABM_EUNSUPPORTED, "total nnz >= 2^32");
-    if (n_rows == 0) n_rows = kTile;  // keep one (padding) tile so every buffer is non-empty
-    const int64_t nnz_pad = (int64_t)round_up((size_t)(nnz > 0 ? nnz : 1), 4);
-    const int ntiles = (int)(n_rows / kTile);
-
-    std::vector<uint32_t> h_rowptr((size_t)n_rows + 1), h_col((size_t)nnz_pad, 0u);
-    std::vector<float> h_w((size_t)nnz_pad, 0.f);
-    std::vector<uint8_t> h_age((size_t)n_rows, 0);
-    std::vector<uint32_t> t_rowptr((size_t)n_rows + 1), t_col((size_t)nnz_pad, 0u);
-    std::vector<float> t_w((size_t)nnz_pad, 0.f);
-    std::vector<uint16_t> tile_graph((size_t)ntiles, 0);
-    std::vector<uint32_t> h_orig(reorder ? (size_t)n_rows : 0, 0u);
-    std::vector<int64_t> goff((size_t)num_graphs, 0);
-    for (int g = 1; g < num_graphs; ++g) goff[g] = goff[g - 1] + hg[g - 1].n;
-    bool symmetric = true;
-    {
-        int64_t e0 = 0;
-        for (int g = 0; g < num_graphs; ++g) {
-            const HostGraph &h = hg[g];
-            std::vector<uint64_t> trp;
-            std::vector<uint32_t> tc;
-            std::vector<float> tw;
-            transpose_graph(h, trp, tc, tw);
-            const int64_t padded = (int64_t)ntl[g] * kTile;
-            for (int64_t i = 0; i < padded; ++i) {
-                const int64_t r = row0[g] + i;
-                h_rowptr[r] = (uint32_t)(e0 + (int64_t)h.rowptr[i < h.n ? i : h.n]);
-                t_rowptr[r] = (uint32_t)(e0 + (int64_t)trp[i < h.n ? i : h.n]);
-                if (i < h.n) h_age[r] = h.age[i];
-                if (reorder && i < h.n) h_orig[r] = orders[g][i];
-            }
-            for (int64_t p = 0; p < h.nnz; ++p) {
-                h_col[e0 + p] = h.col[p] + (uint32_t)row0[g];
-                h_w[e0 + p] = h.w[p];
-                t_col[e0 + p] = tc[p] + (uint32_t)row0[g];
-                t_w[e0 + p] = tw[p];
-            }
-            for (int k = 0; k < ntl[g]; ++k) tile_graph[tile0[g] + k] = (uint16_t)g;
-            e0 += h.nnz;
-        }
-        h_rowptr[n_rows] = (uint32_t)e0;
-        t_rowptr[n_rows] = (uint32_t)e0;
-        symmetric = (h_rowptr == t_rowptr) && (h_col == t_col) &&
-                    (memcmp(h_w.data(), t_w.data(), sizeof(float) * h_w.size()) == 0);
-    }
+// Host-side layout of a ctx's graphs, ready for upload (built by gabm_create and
+// gabm_create_bipartite).
+struct HostLayout {
     HostSell sell_in, sell_out;
-    const bool batched = sets_per_graph > 1;
-    if (!batched && (!build_sell(h_rowptr, h_col, h_w, n_rows, sell_in) ||
-                     (!symmetric && !build_sell(t_rowptr, t_col, t_w, n_rows, sell_out))))
-        return fail(nullptr, GABM_EUNSUPPORTED, "SELL-32 layout needs >= 2^32 entries");
+    std::vector<uint32_t> h_rowptr, h_col, t_rowptr, t_col;
+    std::vector<float> h_w, t_w;
+    std::vector<uint8_t> h_age;
+    std::vector<uint16_t> tile_graph;
+    std::vector<uint32_t> h_orig;
+    std::vector<int64_t> goff;
+    std::vector<int32_t> row0, rows, tile0, ntl;
+    std::vector<double> Dbar;
+    bool symmetric = true, batched = false, reorder = true;
     uint32_t max_degree = 0;
-    for (int64_t r = 0; r < n_rows; ++r) {
-        max_degree = std::max(max_degree, h_rowptr[r + 1] - h_rowptr[r]);
-        max_degree = std::max(max_degree, t_rowptr[r + 1] - t_rowptr[r]);
-    }
+    int64_t n_rows = 0, nnz = 0, nnz_pad = 0, n_total = 0;
+    int ntiles = 0, sigma = 1024, num_graphs = 1;
+};
 
-    // ---- device side ----
+// Device side of ctx creation: upload the layout, allocate the state and buffers.
+static gabm_status create_on_device(const HostLayout &H, const gabm_model_desc *model, int sets_per_graph,
+                                    void *cuda_stream, gabm_ctx **out) {
+    const HostSell &sell_in = H.sell_in, &sell_out = H.sell_out;
+    const std::vector<uint32_t> &h_rowptr = H.h_rowptr, &h_col = H.h_col, &t_rowptr = H.t_rowptr, &t_col = H.t_col;
+    const std::vector<float> &h_w = H.h_w, &t_w = H.t_w;
+    const std::vector<uint8_t> &h_age = H.h_age;
+    const std::vector<uint16_t> &tile_graph = H.tile_graph;
+    const std::vector<uint32_t> &h_orig = H.h_orig;
+    const std::vector<int64_t> &goff = H.goff;
+    const std::vector<int32_t> &row0 = H.row0, &rows = H.rows, &tile0 = H.tile0, &ntl = H.ntl;
+    const std::vector<double> &Dbar = H.Dbar;
+    const bool symmetric = H.symmetric, batched = H.batched, reorder = H.reorder;
+    const uint32_t max_degree = H.max_degree;
+    const int64_t n_rows = H.n_rows, nnz = H.nnz, nnz_pad = H.nnz_pad, n_total = H.n_total;
+    const int ntiles = H.ntiles, sigma = H.sigma, num_graphs = H.num_graphs;
     gabm_ctx *c = new gabm_ctx();
     c->stream = (cudaStream_t)cuda_stream;
     c->G = num_graphs;
@@ -1187,6 +1151,330 @@ gabm_status gabm_create(const gabm_graph_desc *graphs, int num_graphs, int sets_
     CCK(cudaStreamSynchronize(c->stream));
 #undef CTRY
 #undef CCK
+    *out = c;
+    return GABM_OK;
+}
+
+gabm_status gabm_create(const gabm_graph_desc *graphs, int num_graphs, int sets_per_graph,
+                        const gabm_model_desc *model, void *cuda_stream, gabm_ctx **out) {
+    g_create_error.clear();
+    if (!out) return fail(nullptr, GABM_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!graphs || num_graphs < 1 || num_graphs > 65535) return fail(nullptr, GABM_EINVAL, "need 1..65535 graphs");
+    if (sets_per_graph < 1) return fail(nullptr, GABM_EINVAL, "sets_per_graph must be >= 1");
+    if (sets_per_graph > kMaxSets) return fail(nullptr, GABM_EUNSUPPORTED, "sets_per_graph > %d", kMaxSets);
+    TRY(validate_model(model));
+    if (sets_per_graph > 1 && model->lambda_policy != GABM_STORE_LAMBDA)
+        return fail(nullptr, GABM_EUNSUPPORTED, "sets_per_graph > 1 needs GABM_STORE_LAMBDA in this build");
+    if (model->relax_mode == GABM_SOFT && (sets_per_graph > 1 || model->lambda_policy != GABM_STORE_LAMBDA))
+        return fail(nullptr, GABM_EUNSUPPORTED, "GABM_SOFT needs sets_per_graph = 1 and GABM_STORE_LAMBDA in this build");
+
+    // ---- host side: validate, concatenate, transpose ----
+    std::vector<HostGraph> hg((size_t)num_graphs);
+    bool any_device = false;
+    for (int g = 0; g < num_graphs; ++g) any_device |= (graphs[g].mem_space == GABM_DEVICE);
+    for (int g = 0; g < num_graphs; ++g) TRY(fetch_graph(graphs[g], g, hg[g]));
+    (void)any_device;
+
+    std::vector<int32_t> row0(num_graphs), rows(num_graphs), tile0(num_graphs), ntl(num_graphs);
+    std::vector<double> Dbar(num_graphs);
+    int64_t n_rows = 0, nnz = 0, n_total = 0;
+    for (int g = 0; g < num_graphs; ++g) {
+        row0[g] = (int32_t)n_rows;
+        rows[g] = (int32_t)hg[g].n;
+        tile0[g] = (int32_t)(n_rows / kTile);
+        const int64_t padded = (int64_t)round_up((size_t)hg[g].n, kTile);
+        ntl[g] = (int32_t)(padded / kTile);
+        n_rows += padded;
+        nnz += hg[g].nnz;
+        n_total += hg[g].n;
+        double s = 0.0;
+        for (int64_t p = 0; p < hg[g].nnz; ++p) s += (double)hg[g].w[p];
+        Dbar[g] = hg[g].n > 0 ? s / (double)hg[g].n : 0.0;
+    }
+    // device layout: optionally relabel each graph's agents (D-bar above uses the caller's order)
+    std::vector<std::vector<uint32_t>> orders((size_t)num_graphs);
+    const bool reorder = true;
+    int sigma = 1024;
+    if (const char *f = getenv("GABM_SELL_SIGMA")) sigma = std::max(1, atoi(f));
+    for (int g = 0; g < num_graphs; ++g) {
+        if (model->agent_order == GABM_ORDER_BFS) {
+            orders[g] = bfs_order(hg[g]);
+        } else {
+            orders[g].resize((size_t)hg[g].n);
+            for (int64_t i = 0; i < hg[g].n; ++i) orders[g][i] = (uint32_t)i;
+        }
+        sort_windows_by_degree(hg[g], orders[g], sigma);
+        hg[g] = permute_graph(hg[g], orders[g]);
+    }
+    if (n_rows >= ((int64_t)1 << 31) - 64) return fail(nullptr, GABM_EUNSUPPORTED, "total rows >= 2^31");
+    if (nnz >= ((int64_t)1 << 32) - 64) return fail(nullptr, GABM_EUNSUPPORTED, "total nnz >= 2^32");
+    if (n_rows == 0) n_rows = kTile;  // keep one (padding) tile so every buffer is non-empty
+    const int64_t nnz_pad = (int64_t)round_up((size_t)(nnz > 0 ? nnz : 1), 4);
+    const int ntiles = (int)(n_rows / kTile);
+
+    std::vector<uint32_t> h_rowptr((size_t)n_rows + 1), h_col((size_t)nnz_pad, 0u);
+    std::vector<float> h_w((size_t)nnz_pad, 0.f);
+    std::vector<uint8_t> h_age((size_t)n_rows, 0);
+    std::vector<uint32_t> t_rowptr((size_t)n_rows + 1), t_col((size_t)nnz_pad, 0u);
+    std::vector<float> t_w((size_t)nnz_pad, 0.f);
+    std::vector<uint16_t> tile_graph((size_t)ntiles, 0);
+    std::vector<uint32_t> h_orig(reorder ? (size_t)n_rows : 0, 0u);
+    std::vector<int64_t> goff((size_t)num_graphs, 0);
+    for (int g = 1; g < num_graphs; ++g) goff[g] = goff[g - 1] + hg[g - 1].n;
+    bool symmetric = true;
+    {
+        int64_t e0 = 0;
+        for (int g = 0; g < num_graphs; ++g) {
+            const HostGraph &h = hg[g];
+            std::vector<uint64_t> trp;
+            std::vector<uint32_t> tc;
+            std::vector<float> tw;
+            transpose_graph(h, trp, tc, tw);
+            const int64_t padded = (int64_t)ntl[g] * kTile;
+            for (int64_t i = 0; i < padded; ++i) {
+                const int64_t r = row0[g] + i;
+                h_rowptr[r] = (uint32_t)(e0 + (int64_t)h.rowptr[i < h.n ? i : h.n]);
+                t_rowptr[r] = (uint32_t)(e0 + (int64_t)trp[i < h.n ? i : h.n]);
+                if (i < h.n) h_age[r] = h.age[i];
+                if (reorder && i < h.n) h_orig[r] = orders[g][i];
+            }
+            for (int64_t p = 0; p < h.nnz; ++p) {
+                h_col[e0 + p] = h.col[p] + (uint32_t)row0[g];
+                h_w[e0 + p] = h.w[p];
+                t_col[e0 + p] = tc[p] + (uint32_t)row0[g];
+                t_w[e0 + p] = tw[p];
+            }
+            for (int k = 0; k < ntl[g]; ++k) tile_graph[tile0[g] + k] = (uint16_t)g;
+            e0 += h.nnz;
+        }
+        h_rowptr[n_rows] = (uint32_t)e0;
+        t_rowptr[n_rows] = (uint32_t)e0;
+        symmetric = (h_rowptr == t_rowptr) && (h_col == t_col) &&
+                    (memcmp(h_w.data(), t_w.data(), sizeof(float) * h_w.size()) == 0);
+    }
+    HostSell sell_in, sell_out;
+    const bool batched = sets_per_graph > 1;
+    if (!batched && (!build_sell(h_rowptr, h_col, h_w, n_rows, sell_in) ||
+                     (!symmetric && !build_sell(t_rowptr, t_col, t_w, n_rows, sell_out))))
+        return fail(nullptr, GABM_EUNSUPPORTED, "SELL-32 layout needs >= 2^32 entries");
+    uint32_t max_degree = 0;
+    for (int64_t r = 0; r < n_rows; ++r) {
+        max_degree = std::max(max_degree, h_rowptr[r + 1] - h_rowptr[r]);
+        max_degree = std::max(max_degree, t_rowptr[r + 1] - t_rowptr[r]);
+    }
+
+    HostLayout H;
+    H.sell_in = std::move(sell_in);
+    H.sell_out = std::move(sell_out);
+    H.h_rowptr = std::move(h_rowptr);
+    H.h_col = std::move(h_col);
+    H.h_w = std::move(h_w);
+    H.t_rowptr = std::move(t_rowptr);
+    H.t_col = std::move(t_col);
+    H.t_w = std::move(t_w);
+    H.h_age = std::move(h_age);
+    H.tile_graph = std::move(tile_graph);
+    H.h_orig = std::move(h_orig);
+    H.goff = std::move(goff);
+    H.row0 = row0;
+    H.rows = rows;
+    H.tile0 = tile0;
+    H.ntl = ntl;
+    H.Dbar = Dbar;
+    H.symmetric = symmetric;
+    H.batched = batched;
+    H.reorder = reorder;
+    H.max_degree = max_degree;
+    H.n_rows = n_rows;
+    H.nnz = nnz;
+    H.nnz_pad = nnz_pad;
+    H.ntiles = ntiles;
+    H.n_total = n_total;
+    H.sigma = sigma;
+    H.num_graphs = num_graphs;
+    return create_on_device(H, model, sets_per_graph, cuda_stream, out);
+}
+
+gabm_status gabm_create_bipartite(const gabm_bipartite_desc *bip, const gabm_model_desc *model, void *cuda_stream,
+                                  gabm_ctx **out) {
+    g_create_error.clear();
+    if (!out) return fail(nullptr, GABM_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!bip) return fail(nullptr, GABM_EINVAL, "graph is NULL");
+    TRY(validate_model(model));
+    if (model->relax_mode != GABM_HARD_ST || model->lambda_policy != GABM_STORE_LAMBDA)
+        return fail(nullptr, GABM_EUNSUPPORTED, "agent-location graphs need GABM_HARD_ST and GABM_STORE_LAMBDA in this build");
+    const int64_t n = bip->n_agents, nl = bip->n_locations, nnz = bip->nnz;
+    if (n < 1 || nl < 1 || nnz < 0) return fail(nullptr, GABM_EINVAL, "need n_agents >= 1, n_locations >= 1 and nnz >= 0");
+    if (!bip->rowptr || !bip->age || (nnz > 0 && (!bip->loc || !bip->w)))
+        return fail(nullptr, GABM_EINVAL, "rowptr, loc, w and age are required");
+    if (n >= ((int64_t)1 << 31) - 64 || nl >= ((int64_t)1 << 31) - 64 || nnz >= ((int64_t)1 << 32) - 64)
+        return fail(nullptr, GABM_EUNSUPPORTED, "agents, locations and attendances must stay below 2^31, 2^31, 2^32");
+    if (bip->rowptr[0] != 0 || (int64_t)bip->rowptr[n] != nnz) return fail(nullptr, GABM_EINVAL, "rowptr[0] must be 0 and rowptr[n] = nnz");
+    for (int64_t i = 0; i < n; ++i) {
+        if (bip->rowptr[i + 1] < bip->rowptr[i]) return fail(nullptr, GABM_EINVAL, "rowptr decreases at agent %lld", (long long)i);
+        if (bip->age[i] >= kAges) return fail(nullptr, GABM_EINVAL, "age[%lld] = %d out of 0..8", (long long)i, (int)bip->age[i]);
+    }
+    for (int64_t p = 0; p < nnz; ++p) {
+        if ((int64_t)bip->loc[p] >= nl) return fail(nullptr, GABM_EINVAL, "loc[%lld] = %u out of range", (long long)p, bip->loc[p]);
+        if (!std::isfinite(bip->w[p]) || bip->w[p] < 0.0f) return fail(nullptr, GABM_EINVAL, "w[%lld] not finite and >= 0", (long long)p);
+    }
+    int sigma = 1024;
+    if (const char *f = getenv("GABM_SELL_SIGMA")) sigma = std::max(1, atoi(f));
+
+    // each agent's attendances by location, repeats merged (their weights add)
+    std::vector<uint64_t> arow((size_t)n + 1, 0);
+    std::vector<uint32_t> aloc;
+    std::vector<float> aw;
+    aloc.reserve((size_t)nnz);
+    aw.reserve((size_t)nnz);
+    {
+        std::vector<std::pair<uint32_t, float>> tmp;
+        for (int64_t i = 0; i < n; ++i) {
+            tmp.clear();
+            for (uint64_t p = bip->rowptr[i]; p < bip->rowptr[i + 1]; ++p) tmp.emplace_back(bip->loc[p], bip->w[p]);
+            std::stable_sort(tmp.begin(), tmp.end(), [](const std::pair<uint32_t, float> &a, const std::pair<uint32_t, float> &b) {
+                return a.first < b.first;
+            });
+            for (size_t k = 0; k < tmp.size(); ++k) {
+                if (!aloc.empty() && arow[i] < aloc.size() && aloc.back() == tmp[k].first) aw.back() += tmp[k].second;
+                else { aloc.push_back(tmp[k].first); aw.push_back(tmp[k].second); }
+            }
+            arow[i + 1] = aloc.size();
+        }
+    }
+    const int64_t m = (int64_t)aloc.size();
+    // Dbar of the one-hop weights W_ij = sum_l w_il w_jl (i != j): (1/n) sum_l [(sum_i w_il)^2 - sum_i w_il^2]
+    double Dbar = 0.0;
+    {
+        std::vector<double> s1((size_t)nl, 0.0), s2((size_t)nl, 0.0);
+        for (int64_t p = 0; p < m; ++p) {
+            s1[aloc[p]] += (double)aw[p];
+            s2[aloc[p]] += (double)aw[p] * (double)aw[p];
+        }
+        for (int64_t l = 0; l < nl; ++l) Dbar += s1[l] * s1[l] - s2[l];
+        Dbar /= (double)n;
+    }
+    // agents: input order, sorted by attendance count within windows; locations: by member count
+    HostGraph h;
+    h.n = n;
+    h.nnz = m;
+    h.rowptr = arow;
+    std::vector<uint32_t> order((size_t)n);
+    for (int64_t i = 0; i < n; ++i) order[i] = (uint32_t)i;
+    sort_windows_by_degree(h, order, sigma);
+    std::vector<uint32_t> lcnt((size_t)nl, 0), lorder((size_t)nl), linv((size_t)nl);
+    for (int64_t p = 0; p < m; ++p) lcnt[aloc[p]]++;
+    for (int64_t l = 0; l < nl; ++l) lorder[l] = (uint32_t)l;
+    for (size_t w0 = 0; w0 < (size_t)nl; w0 += (size_t)sigma) {
+        const size_t w1 = std::min((size_t)nl, w0 + (size_t)sigma);
+        std::stable_sort(lorder.begin() + w0, lorder.begin() + w1, [&](uint32_t a, uint32_t b) { return lcnt[a] > lcnt[b]; });
+    }
+    for (int64_t k = 0; k < nl; ++k) linv[lorder[k]] = (uint32_t)k;
+
+    HostLayout H;
+    const int64_t n_rows = (int64_t)round_up((size_t)n, kTile);
+    const int ntiles = (int)(n_rows / kTile);
+    const int64_t nnz_pad = (int64_t)round_up((size_t)(m > 0 ? m : 1), 4);
+    H.h_rowptr.assign((size_t)n_rows + 1, 0u);
+    H.h_col.assign((size_t)nnz_pad, 0u);
+    H.h_w.assign((size_t)nnz_pad, 0.f);
+    H.h_age.assign((size_t)n_rows, 0);
+    H.h_orig.assign((size_t)n_rows, 0u);
+    uint32_t max_degree = 0;
+    {
+        std::vector<std::pair<uint32_t, float>> tmp;
+        uint32_t q = 0;
+        for (int64_t k = 0; k < n_rows; ++k) {
+            H.h_rowptr[k] = q;
+            if (k >= n) continue;
+            const uint32_t v = order[k];
+            tmp.clear();
+            for (uint64_t p = arow[v]; p < arow[v + 1]; ++p) tmp.emplace_back(linv[aloc[p]], aw[p]);
+            std::sort(tmp.begin(), tmp.end(), [](const std::pair<uint32_t, float> &a, const std::pair<uint32_t, float> &b) {
+                return a.first < b.first;
+            });
+            for (const auto &e : tmp) { H.h_col[q] = e.first; H.h_w[q] = e.second; ++q; }
+            max_degree = std::max(max_degree, (uint32_t)tmp.size());
+            H.h_age[k] = bip->age[v];
+            H.h_orig[k] = v;
+        }
+        H.h_rowptr[n_rows] = q;
+    }
+    // locations -> members (agent rows ascending), padded to whole tiles
+    const int64_t nl_rows = (int64_t)round_up((size_t)nl, kTile);
+    std::vector<uint32_t> lrow((size_t)nl_rows + 1, 0u), lcol((size_t)nnz_pad, 0u);
+    std::vector<float> lw((size_t)nnz_pad, 0.f);
+    for (int64_t p = 0; p < m; ++p) lrow[H.h_col[p] + 1]++;
+    for (int64_t k = 0; k < nl_rows; ++k) lrow[k + 1] += lrow[k];
+    {
+        std::vector<uint32_t> pos(lrow.begin(), lrow.end() - 1);
+        for (int64_t k = 0; k < n; ++k)
+            for (uint32_t p = H.h_rowptr[k]; p < H.h_rowptr[k + 1]; ++p) {
+                const uint32_t q = pos[H.h_col[p]]++;
+                lcol[q] = (uint32_t)k;
+                lw[q] = H.h_w[p];
+            }
+    }
+    HostSell loc_sell;
+    if (!build_sell(H.h_rowptr, H.h_col, H.h_w, n_rows, H.sell_in) || !build_sell(lrow, lcol, lw, nl_rows, loc_sell))
+        return fail(nullptr, GABM_EUNSUPPORTED, "SELL-32 layout needs >= 2^32 entries");
+    H.t_rowptr = H.h_rowptr;
+    H.t_col = H.h_col;
+    H.t_w = H.h_w;
+    H.tile_graph.assign((size_t)ntiles, 0);
+    H.goff = {0};
+    H.row0 = {0};
+    H.rows = {(int32_t)n};
+    H.tile0 = {0};
+    H.ntl = {ntiles};
+    H.Dbar = {Dbar};
+    H.symmetric = true;
+    H.batched = false;
+    H.reorder = true;
+    H.max_degree = max_degree;
+    H.n_rows = n_rows;
+    H.nnz = m;
+    H.nnz_pad = nnz_pad;
+    H.ntiles = ntiles;
+    H.n_total = n;
+    H.sigma = sigma;
+    H.num_graphs = 1;
+    gabm_ctx *c = nullptr;
+    TRY(create_on_device(H, model, 1, cuda_stream, &c));
+    auto bail = [&](gabm_status st) {
+        g_create_error = c->err;
+        destroy_all(c);
+        delete c;
+        return st;
+    };
+    // the location hop: its SELL-32 and one value per location
+    c->two_hop = true;
+    c->n_loc = nl;
+    c->loc_ntiles = (int)(nl_rows / kTile);
+    gabm_status st = GABM_OK;
+    auto up = [&](auto *&dst, const auto &src) -> gabm_status {
+        TRY(dalloc(c, &dst, src.size()));
+        CK(cudaMemcpy(dst, src.data(), sizeof(src[0]) * src.size(), cudaMemcpyHostToDevice));
+        return GABM_OK;
+    };
+    if (st == GABM_OK) st = up(c->loc_slice_ptr, loc_sell.slice_ptr);
+    if (st == GABM_OK) st = up(c->loc_row_len, loc_sell.row_len);
+    if (st == GABM_OK) st = up(c->loc_col, loc_sell.col);
+    if (st == GABM_OK) st = up(c->loc_w, loc_sell.w);
+    if (st == GABM_OK) st = dalloc(c, &c->locv, (size_t)nl_rows);
+    {
+        std::vector<float> q((size_t)n_rows, 0.f);
+        for (int64_t k = 0; k < n; ++k) {
+            double acc = 0.0;
+            for (uint32_t p = H.h_rowptr[k]; p < H.h_rowptr[k + 1]; ++p) acc += (double)H.h_w[p] * (double)H.h_w[p];
+            q[k] = (float)acc;
+        }
+        if (st == GABM_OK) st = up(c->self_q, q);
+    }
+    if (st != GABM_OK) return bail(st);
+    apply_schedule(c);
     *out = c;
     return GABM_OK;
 }
@@ -1450,7 +1738,7 @@ gabm_status gabm_set_schedule(gabm_ctx *ctx, const gabm_schedule *sched) {
         c->spl_bwd = sched->bwd_sets_per_lane;
         c->bwd_chunk = chunk;
     } else {
-        if (sched->fwd_smem_bitmap && (c->soft || occupancy_fwd(c->ntiles, true) <= 0))
+        if (sched->fwd_smem_bitmap && (c->soft || c->two_hop || occupancy_fwd(c->ntiles, true) <= 0))
             return fail(c, GABM_EINVAL, "the infectious bitmap (%d words) does not fit in shared memory", c->ntiles);
         c->smem_bits = sched->fwd_smem_bitmap != 0;
     }
@@ -1476,7 +1764,7 @@ gabm_status gabm_autotune(gabm_ctx *ctx, int repetitions) {
             if (batch_config_ok(c->Bp, spl)) fc.push_back(gabm_schedule{spl, cur.bwd_sets_per_lane, 0, cur.bwd_sets_per_launch});
     } else {
         fc.push_back(gabm_schedule{0, 0, 0, 0});
-        if (!c->soft && occupancy_fwd(c->ntiles, true) > 0) fc.push_back(gabm_schedule{0, 0, 1, 0});
+        if (!c->soft && !c->two_hop && occupancy_fwd(c->ntiles, true) > 0) fc.push_back(gabm_schedule{0, 0, 1, 0});
     }
     cudaEvent_t ev[2];
     for (auto &e : ev) CK(cudaEventCreate(&e));

@@ -43,7 +43,10 @@ __device__ __forceinline__ void flush_counts_warp(int32_t *counts, int32_t *newR
 // SMEM_BITS: today's infectious bitmap is copied into shared memory (one large
 // block per SM), so the per-edge test is a shared-memory lookup instead of a
 // scattered L1 load; otherwise it is read through L1 from global memory.
-template <bool SMEM_BITS, int NT, int MINB>
+// PULL (agent-location graphs): the row's entries are the agent's locations, and each
+// contributes w_il * P_l from the day's location pressures (a.pull) instead of a marked
+// neighbour's infectiousness.
+template <bool SMEM_BITS, int NT, int MINB, bool PULL = false>
 __global__ void __launch_bounds__(NT, MINB) k_fwd_day(const FwdDayArgs a) {
     constexpr int NW = NT / 32;
     extern __shared__ uint32_t bits_s[];
@@ -60,9 +63,13 @@ __global__ void __launch_bounds__(NT, MINB) k_fwd_day(const FwdDayArgs a) {
     const uint32_t *bits = a.bits_cur;
     // only neighbours marked infectious today contribute; their exposure day is gathered
     auto contrib = [&](uint32_t j, float w, bool valid, float (&out)[1]) {
-        const bool mk = valid && (SMEM_BITS ? ((bits_s[j >> 5] >> (j & 31u)) & 1u) : marked(bits, j));
-        const int ej = ld_if(e + j, mk, kNever);
-        out[0] = mk ? w * infectiousness(ej, c_s, t, L) : 0.f;
+        if constexpr (PULL) {
+            out[0] = w * ld_if(a.pull + j, valid);
+        } else {
+            const bool mk = valid && (SMEM_BITS ? ((bits_s[j >> 5] >> (j & 31u)) & 1u) : marked(bits, j));
+            const int ej = ld_if(e + j, mk, kNever);
+            out[0] = mk ? w * infectiousness(ej, c_s, t, L) : 0.f;
+        }
     };
     const bool want[1] = {true};
 
@@ -573,9 +580,11 @@ cudaError_t launch_seed_ties(const SeedArgs &a, int I, cudaStream_t s) {
 constexpr int kBitsBlock = 768;   // one block of 24 warps per SM when the bitmap lives in shared memory
 
 cudaError_t launch_fwd_day(const FwdDayArgs &a, int grid, bool smem_bits, cudaStream_t s) {
-    if (smem_bits) {
+    if (smem_bits && !a.pull) {
         const size_t bytes = (size_t)a.ntiles * sizeof(uint32_t);
         k_fwd_day<true, kBitsBlock, 1><<<grid, kBitsBlock, bytes, s>>>(a);
+    } else if (a.pull) {
+        k_fwd_day<false, kBlock, GABM_MINBLOCKS, true><<<grid, kBlock, 0, s>>>(a);
     } else {
         k_fwd_day<false, kBlock, GABM_MINBLOCKS><<<grid, kBlock, 0, s>>>(a);
     }

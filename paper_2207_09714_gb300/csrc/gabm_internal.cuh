@@ -116,6 +116,8 @@ struct FwdDayArgs {
     int32_t *newRM;       // [I][ldP]
     const uint32_t *bits_cur;   // [ntiles] bit i of word r/32: row r infectious on day t
     uint32_t *bits_next;        // [ntiles] the same for day t + 1 (written by this launch)
+    const float *pull;          // agent-location graphs: location pressures P [locations] (m lists
+                                // each agent's locations), gathered in place of marked neighbours
     int ntiles, t, tau_EI, L;
     uint64_t seed;
     float c[kMaxL];
@@ -168,6 +170,10 @@ struct BwdDayArgs {
     int32_t *sig, *emax;       // [G][ld_sig] scale exponent and largest stored exponent per day
     int ld_sig;
     double *dc_tile;           // [ntiles][kMaxL] per-tile sums of the table adjoint over days, or nullptr
+    // agent-location graphs: r_next is the location adjoint gP; the agent's own share of its
+    // locations, self_q[i] * self_r[i] with self_q = sum_l w_il^2 and self_r = r(t+1), is
+    // removed from the gather (the pair weights have no self term)
+    const float *self_r, *self_q;
 };
 
 enum { kBwdStore = 0, kBwdFused = 1, kBwdSplit = 2, kBwdSoft = 3 };
@@ -344,6 +350,12 @@ cudaError_t launch_dc_seeds_b(Csr m_out, const int16_t *E, const float *r0, Grap
                               int ld_sig, int ntiles, int L, int B, int Bp, double *dc_tile, cudaStream_t s);
 cudaError_t launch_dc_reduce_b(const double *dc_tile, const int32_t *graph_tile0, const int32_t *graph_ntiles, int G,
                                int B, int Bp, int L, double *dc, cudaStream_t s);
+// Location hop of agent-location graphs (twohop.cu): pressures of day t and adjoints.
+cudaError_t launch_loc_pressure(Sell ml, int nloc_tiles, const int16_t *e, const uint32_t *bits, int t, int L,
+                                const float *c, float *P, int grid, cudaStream_t s);
+cudaError_t launch_loc_adjoint(Sell ml, int nloc_tiles, const float *r, const float *c, float *gP, int grid,
+                               cudaStream_t s);
+int occupancy_loc();
 cudaError_t launch_lam_day(Sell m, const int16_t *E, const uint32_t *bits, GraphRef gr, int t, int L, int ntiles,
                            const float *c, float *lam_out, int grid, cudaStream_t s);
 // Q[g][t][a] = 2^sigma_g(t) x (sum over graph g's tiles of P[t][tile][a]), FP64.
