@@ -424,6 +424,48 @@ def cpu_baseline(pop, c, y):
                       f"edges, {DAYS} days), FP64, {dt:.1f} s"}
 
 
+def bench_twohop(stream, dist, steps=5, n=1_000_000):
+    """The agent-location workload (GradABM-JUNE, Sec. 5): one forward + MSE + backward
+    step over 60 days on a synthetic agent-location graph of n agents (households,
+    schools of 100-400, workplaces of 5-60, shared venues), computed in two hops over the
+    attendance entries.  Reports the pair count the two hops avoid forming."""
+    import torch
+    from paper_2207_09714_gb300 import capi, synth
+
+    bip = synth.population_bipartite(n, seed=0)
+    sizes = np.bincount(bip.loc.astype(np.int64), minlength=bip.n_loc).astype(np.int64)
+    pairs = int((sizes * (sizes - 1)).sum())
+    with torch.cuda.stream(stream):
+        ctx = capi.gabm_create_bipartite(bip, capi.ModelDesc(TAU_EI, TAU_IR, synth.infectiousness_table(TAU_EI, TAU_IR),
+                                                             seed=0), stream=stream)
+        R = torch.full((1, DAYS), R0, dtype=torch.float32, device="cuda")
+        m = torch.full((1, DAYS), MORTALITY, dtype=torch.float32, device="cuda")
+        S = torch.from_numpy(synth.SUSCEPTIBILITY[None, :].copy()).cuda()
+        y = torch.from_numpy(synth.target_curve(DAYS, n)[None, :]).cuda()
+
+        def step():
+            capi.gabm_forward(ctx, DAYS, R, m, S, [N_SEED])
+            _, gD = capi.gabm_mse_loss(ctx, y)
+            capi.gabm_backward(ctx, gD)
+
+        for _ in range(3):
+            step()
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = max_over_ranks(e0.elapsed_time(e1), dist, "cuda") / steps
+    return {"workload": f"agent-location graph, {n} agents, {bip.n_loc} locations, {DAYS} days, "
+                        f"forward + MSE + backward in two hops", "n_agents": n, "attendances": bip.nnz,
+            "pair_entries_avoided": pairs, "ms_per_step": ms, "steps": steps,
+            "value": n * DAYS / (ms / 1e3), "unit": "agent-days/s"}
+
+
 def bench_calibration(ctx, stream, S, y_np, dist, steps=5):
     """One Adam step of the calibration workload on the bench graph: weekly-tied R and m,
     the stage factors and profile of the infectiousness table, MSE on cumulative deaths.
@@ -638,6 +680,7 @@ def main():
     cur, peak_mem = capi.gabm_mem_stats(ctx)
     calib = bench_calibration(ctx, stream, S, y_np, dist)
     del ctx
+    twohop = bench_twohop(stream, dist)
     batched = None
     if not args.no_batched:
         batched = bench_batched(args, stream, peak, peak_kind)
@@ -667,6 +710,7 @@ def main():
         "peak_hbm_bytes": peak_mem,
         "cpu_baseline": cpu,
         "calibration": calib,
+        "agent_location": twohop,
         "batched": batched,
     }
     print(json.dumps(line), flush=True)

@@ -110,6 +110,9 @@ struct gabm_ctx {
     float *loc_w = nullptr;
     float *locv = nullptr;          // [loc_ntiles * 32] location pressures (forward) or adjoints (backward)
     float *self_q = nullptr;        // [n_rows] sum over the agent's locations of w_il^2
+    uint32_t *big_rowptr = nullptr, *big_col = nullptr;   // locations of more than 32 members (CSR)
+    float *big_w = nullptr;
+    int n_big = 0;
     int *tile_ctr = nullptr;        // batched: [1 + max chunks][Tcap] per-launch tile counters (forward, backward chunks)
     uint32_t *bits = nullptr;       // [Tcap][ntiles] per-day bitmaps of infectious rows
 
@@ -510,6 +513,16 @@ Sell loc_sell_view(const gabm_ctx *c) {
     return m;
 }
 
+LocCsr loc_big_view(const gabm_ctx *c) {
+    LocCsr b;
+    b.rowptr = c->big_rowptr;
+    b.col = c->big_col;
+    b.w = c->big_w;
+    b.n = c->n_big;
+    b.base = c->loc_ntiles * kTile;
+    return b;
+}
+
 GraphRef graph_ref(const gabm_ctx *c) {
     GraphRef gr;
     gr.row0 = c->d_row0;
@@ -666,7 +679,7 @@ gabm_status forward_days_plain(gabm_ctx *c, int t0, int T, cudaStream_t s) {
         a.pull = nullptr;
         prof_begin(c, 0);
         if (c->two_hop) {   // location pressures of day t, then the agents' pull over their locations
-            LAUNCH(launch_loc_pressure(loc_sell_view(c), c->loc_ntiles, c->e, a.bits_cur, t, c->L, c->c_dev, c->locv,
+            LAUNCH(launch_loc_pressure(loc_sell_view(c), c->loc_ntiles, loc_big_view(c), c->e, a.bits_cur, t, c->L, c->c_dev, c->locv,
                                        c->grid_loc, s));
             a.pull = c->locv;
         }
@@ -726,7 +739,8 @@ gabm_status backward_days_plain(gabm_ctx *c, int T, cudaStream_t s) {
         a.r_next = c->r + (size_t)((t + 1) & 1) * c->n_rows;
         a.r_cur = c->r + (size_t)(t & 1) * c->n_rows;
         if (c->two_hop) {   // the location hop of the transpose gather: gP = sum over members of w r(t+1)
-            LAUNCH(launch_loc_adjoint(loc_sell_view(c), c->loc_ntiles, a.r_next, c->c_dev, c->locv, c->grid_loc, s));
+            LAUNCH(launch_loc_adjoint(loc_sell_view(c), c->loc_ntiles, loc_big_view(c), a.r_next, c->c_dev, c->locv,
+                                      c->grid_loc, s));
             a.self_r = a.r_next;
             a.self_q = c->self_q;
             a.r_next = c->locv;
@@ -740,7 +754,8 @@ gabm_status backward_days_plain(gabm_ctx *c, int T, cudaStream_t s) {
     if (a.dc_tile) {   // the seeds' share through day 0 (r of day 0 is in slot 0)
         const float *r0 = c->r;
         if (c->two_hop) {
-            LAUNCH(launch_loc_adjoint(loc_sell_view(c), c->loc_ntiles, c->r, c->c_dev, c->locv, c->grid_loc, s));
+            LAUNCH(launch_loc_adjoint(loc_sell_view(c), c->loc_ntiles, loc_big_view(c), c->r, c->c_dev, c->locv,
+                                      c->grid_loc, s));
             r0 = c->locv;
         }
         LAUNCH(launch_dc_seeds(sell_view(c, true), c->e, r0, graph_ref(c), c->sig, ld + 1, c->ntiles, c->L,
@@ -911,7 +926,8 @@ void apply_schedule(gabm_ctx *c) {
     }
     if (c->two_hop) {
         c->smem_bits = false;
-        c->grid_loc = std::min(c->num_sms * occupancy_loc(), std::max(1, (c->loc_ntiles + kBlock / 32 - 1) / (kBlock / 32)));
+        const int units = std::max(c->loc_ntiles, c->n_big);   // warp work units of the larger launch
+        c->grid_loc = std::min(c->num_sms * occupancy_loc(), std::max(1, (units + kBlock / 32 - 1) / (kBlock / 32)));
     }
     const int max_grid = (c->ntiles + kBlock / 32 - 1) / (kBlock / 32);
     if (!c->smem_bits && c->grid_fwd > max_grid) c->grid_fwd = max_grid;
@@ -1364,14 +1380,21 @@ gabm_status gabm_create_bipartite(const gabm_bipartite_desc *bip, const gabm_mod
     std::vector<uint32_t> order((size_t)n);
     for (int64_t i = 0; i < n; ++i) order[i] = (uint32_t)i;
     sort_windows_by_degree(h, order, sigma);
-    std::vector<uint32_t> lcnt((size_t)nl, 0), lorder((size_t)nl), linv((size_t)nl);
+    // locations of up to 32 members: SELL-32 tiles, sorted by member count within windows;
+    // larger ones: a CSR taken one warp per location, sorted by member count
+    constexpr uint32_t kSmallLoc = 32;
+    std::vector<uint32_t> lcnt((size_t)nl, 0), lsmall, lbig, linv((size_t)nl);
     for (int64_t p = 0; p < m; ++p) lcnt[aloc[p]]++;
-    for (int64_t l = 0; l < nl; ++l) lorder[l] = (uint32_t)l;
-    for (size_t w0 = 0; w0 < (size_t)nl; w0 += (size_t)sigma) {
-        const size_t w1 = std::min((size_t)nl, w0 + (size_t)sigma);
-        std::stable_sort(lorder.begin() + w0, lorder.begin() + w1, [&](uint32_t a, uint32_t b) { return lcnt[a] > lcnt[b]; });
+    for (int64_t l = 0; l < nl; ++l) (lcnt[l] <= kSmallLoc ? lsmall : lbig).push_back((uint32_t)l);
+    for (size_t w0 = 0; w0 < lsmall.size(); w0 += (size_t)sigma) {
+        const size_t w1 = std::min(lsmall.size(), w0 + (size_t)sigma);
+        std::stable_sort(lsmall.begin() + w0, lsmall.begin() + w1, [&](uint32_t a, uint32_t b) { return lcnt[a] > lcnt[b]; });
     }
-    for (int64_t k = 0; k < nl; ++k) linv[lorder[k]] = (uint32_t)k;
+    std::stable_sort(lbig.begin(), lbig.end(), [&](uint32_t a, uint32_t b) { return lcnt[a] > lcnt[b]; });
+    const int64_t ns_rows = (int64_t)round_up(lsmall.size(), kTile);
+    const int64_t n_big = (int64_t)lbig.size();
+    for (size_t k = 0; k < lsmall.size(); ++k) linv[lsmall[k]] = (uint32_t)k;
+    for (int64_t k = 0; k < n_big; ++k) linv[lbig[k]] = (uint32_t)(ns_rows + k);
 
     HostLayout H;
     const int64_t n_rows = (int64_t)round_up((size_t)n, kTile);
@@ -1402,23 +1425,29 @@ gabm_status gabm_create_bipartite(const gabm_bipartite_desc *bip, const gabm_mod
         }
         H.h_rowptr[n_rows] = q;
     }
-    // locations -> members (agent rows ascending), padded to whole tiles
-    const int64_t nl_rows = (int64_t)round_up((size_t)nl, kTile);
-    std::vector<uint32_t> lrow((size_t)nl_rows + 1, 0u), lcol((size_t)nnz_pad, 0u);
-    std::vector<float> lw((size_t)nnz_pad, 0.f);
-    for (int64_t p = 0; p < m; ++p) lrow[H.h_col[p] + 1]++;
-    for (int64_t k = 0; k < nl_rows; ++k) lrow[k + 1] += lrow[k];
+    // locations -> members (agent rows ascending): small ones padded to whole tiles, large ones a CSR
+    std::vector<uint32_t> lrow((size_t)ns_rows + 1, 0u), brow((size_t)n_big + 1, 0u);
+    for (int64_t p = 0; p < m; ++p) {
+        const uint32_t l = H.h_col[p];
+        if (l < (uint32_t)ns_rows) lrow[l + 1]++;
+        else brow[l - ns_rows + 1]++;
+    }
+    for (int64_t k = 0; k < ns_rows; ++k) lrow[k + 1] += lrow[k];
+    for (int64_t k = 0; k < n_big; ++k) brow[k + 1] += brow[k];
+    std::vector<uint32_t> lcol((size_t)std::max<uint32_t>(lrow.back(), 1), 0u), bcol((size_t)std::max<uint32_t>(brow.back(), 1), 0u);
+    std::vector<float> lw(lcol.size(), 0.f), bw(bcol.size(), 0.f);
     {
-        std::vector<uint32_t> pos(lrow.begin(), lrow.end() - 1);
+        std::vector<uint32_t> pos(lrow.begin(), lrow.end() - 1), bpos(brow.begin(), brow.end() - 1);
         for (int64_t k = 0; k < n; ++k)
             for (uint32_t p = H.h_rowptr[k]; p < H.h_rowptr[k + 1]; ++p) {
-                const uint32_t q = pos[H.h_col[p]]++;
-                lcol[q] = (uint32_t)k;
-                lw[q] = H.h_w[p];
+                const uint32_t l = H.h_col[p];
+                const uint32_t q = (l < (uint32_t)ns_rows) ? pos[l]++ : bpos[l - ns_rows]++;
+                (l < (uint32_t)ns_rows ? lcol : bcol)[q] = (uint32_t)k;
+                (l < (uint32_t)ns_rows ? lw : bw)[q] = H.h_w[p];
             }
     }
     HostSell loc_sell;
-    if (!build_sell(H.h_rowptr, H.h_col, H.h_w, n_rows, H.sell_in) || !build_sell(lrow, lcol, lw, nl_rows, loc_sell))
+    if (!build_sell(H.h_rowptr, H.h_col, H.h_w, n_rows, H.sell_in) || !build_sell(lrow, lcol, lw, ns_rows, loc_sell))
         return fail(nullptr, GABM_EUNSUPPORTED, "SELL-32 layout needs >= 2^32 entries");
     H.t_rowptr = H.h_rowptr;
     H.t_col = H.h_col;
@@ -1452,7 +1481,8 @@ gabm_status gabm_create_bipartite(const gabm_bipartite_desc *bip, const gabm_mod
     // the location hop: its SELL-32 and one value per location
     c->two_hop = true;
     c->n_loc = nl;
-    c->loc_ntiles = (int)(nl_rows / kTile);
+    c->loc_ntiles = (int)(ns_rows / kTile);
+    c->n_big = (int)n_big;
     gabm_status st = GABM_OK;
     auto up = [&](auto *&dst, const auto &src) -> gabm_status {
         TRY(dalloc(c, &dst, src.size()));
@@ -1463,7 +1493,10 @@ gabm_status gabm_create_bipartite(const gabm_bipartite_desc *bip, const gabm_mod
     if (st == GABM_OK) st = up(c->loc_row_len, loc_sell.row_len);
     if (st == GABM_OK) st = up(c->loc_col, loc_sell.col);
     if (st == GABM_OK) st = up(c->loc_w, loc_sell.w);
-    if (st == GABM_OK) st = dalloc(c, &c->locv, (size_t)nl_rows);
+    if (st == GABM_OK) st = up(c->big_rowptr, brow);
+    if (st == GABM_OK) st = up(c->big_col, bcol);
+    if (st == GABM_OK) st = up(c->big_w, bw);
+    if (st == GABM_OK) st = dalloc(c, &c->locv, (size_t)std::max<int64_t>(1, ns_rows + n_big));
     {
         std::vector<float> q((size_t)n_rows, 0.f);
         for (int64_t k = 0; k < n; ++k) {

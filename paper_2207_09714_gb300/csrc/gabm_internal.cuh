@@ -350,11 +350,19 @@ cudaError_t launch_dc_seeds_b(Csr m_out, const int16_t *E, const float *r0, Grap
                               int ld_sig, int ntiles, int L, int B, int Bp, double *dc_tile, cudaStream_t s);
 cudaError_t launch_dc_reduce_b(const double *dc_tile, const int32_t *graph_tile0, const int32_t *graph_ntiles, int G,
                                int B, int Bp, int L, double *dc, cudaStream_t s);
-// Location hop of agent-location graphs (twohop.cu): pressures of day t and adjoints.
-cudaError_t launch_loc_pressure(Sell ml, int nloc_tiles, const int16_t *e, const uint32_t *bits, int t, int L,
-                                const float *c, float *P, int grid, cudaStream_t s);
-cudaError_t launch_loc_adjoint(Sell ml, int nloc_tiles, const float *r, const float *c, float *gP, int grid,
-                               cudaStream_t s);
+// Location hop of agent-location graphs (twohop.cu): pressures of day t and adjoints.  Small
+// locations are SELL-32 tiles (values at [0, 32 * nloc_tiles)); large ones a CSR of their
+// members (values at [base, base + n)).
+struct LocCsr {
+    const uint32_t *rowptr;   // [n+1]
+    const uint32_t *col;      // member rows
+    const float *w;           // attendance weights
+    int n, base;
+};
+cudaError_t launch_loc_pressure(Sell ml, int nloc_tiles, LocCsr big, const int16_t *e, const uint32_t *bits, int t,
+                                int L, const float *c, float *P, int grid, cudaStream_t s);
+cudaError_t launch_loc_adjoint(Sell ml, int nloc_tiles, LocCsr big, const float *r, const float *c, float *gP,
+                               int grid, cudaStream_t s);
 int occupancy_loc();
 cudaError_t launch_lam_day(Sell m, const int16_t *E, const uint32_t *bits, GraphRef gr, int t, int L, int ntiles,
                            const float *c, float *lam_out, int grid, cudaStream_t s);
