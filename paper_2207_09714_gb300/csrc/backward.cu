@@ -47,8 +47,15 @@ __device__ __forceinline__ void dc_accumulate(double *dc_tile, int tile, bool ha
 
 // DC: accumulate the table adjoint (a.dc_tile); a separate instance, so the plain sweep
 // carries none of its code.
+// Four resident blocks (64 registers) for the plain store sweep: the gathers of r want
+// the warps (79 vs 82 us per day on the 1M-agent graph at three).  The fused, soft and
+// table-adjoint instances, which spill at 64 registers, keep three.
+#ifndef GABM_BWD_MINBLOCKS
+#define GABM_BWD_MINBLOCKS 4
+#endif
 template <int MODE, bool DC>
-__global__ void __launch_bounds__(kBlock, GABM_MINBLOCKS) k_bwd_day(const BwdDayArgs a) {
+__global__ void __launch_bounds__(kBlock, (MODE == kBwdStore && !DC) ? GABM_BWD_MINBLOCKS : GABM_MINBLOCKS)
+    k_bwd_day(const BwdDayArgs a) {
     constexpr int NARR = (MODE == kBwdFused) ? 2 : 1;
     constexpr bool SOFT = MODE == kBwdSoft;
     static_assert(!(SOFT && DC), "the table adjoint is built for the hard sweep");
