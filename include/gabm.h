@@ -142,13 +142,14 @@ typedef struct {
     const uint8_t *age;      /* [n_agents] age bins 0..8 */
 } gabm_bipartite_desc;
 
-/* Build a ctx over one agent-location graph (copied; GABM_EINVAL on bad data,
- * before any CUDA call).  It then works as a gabm_create ctx of one graph and one
- * set: agents are the rows, in input order within degree windows (agent_order is
- * not used).  The model must use GABM_HARD_ST and GABM_STORE_LAMBDA
- * (GABM_EUNSUPPORTED otherwise). */
-gabm_status gabm_create_bipartite(const gabm_bipartite_desc *graph, const gabm_model_desc *model,
-                                  void *cuda_stream, gabm_ctx **out);
+/* Build a ctx over num_graphs >= 1 agent-location graphs (copied; GABM_EINVAL on
+ * bad data, before any CUDA call).  It then works as a gabm_create ctx of that many
+ * graphs and one set per graph (instance g = graph g, with its own Dbar): agents are
+ * the rows, in input order within degree windows (agent_order is not used), and no
+ * location is shared between graphs.  The model must use GABM_HARD_ST and
+ * GABM_STORE_LAMBDA (GABM_EUNSUPPORTED otherwise). */
+gabm_status gabm_create_bipartite(const gabm_bipartite_desc *graphs, int num_graphs,
+                                  const gabm_model_desc *model, void *cuda_stream, gabm_ctx **out);
 
 /* Forward over days t0..T-1 (Sec. 3.1, Eq. 1-3, K = T steps).  t0 = 0 after
  * create (seeding from n_seed), or the day given to the last gabm_set_state.

@@ -80,7 +80,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         L.gabm_create.argtypes = [ctypes.POINTER(_GraphDesc), i32, i32, ctypes.POINTER(_ModelDesc), P,
                                   ctypes.POINTER(P)]
         L.gabm_forward.argtypes = [P, i32, P, P, P, P, P, P, i32]
-        L.gabm_create_bipartite.argtypes = [ctypes.POINTER(_BipartiteDesc), ctypes.POINTER(_ModelDesc), P,
+        L.gabm_create_bipartite.argtypes = [ctypes.POINTER(_BipartiteDesc), i32, ctypes.POINTER(_ModelDesc), P,
                                             ctypes.POINTER(P)]
         L.gabm_mse_loss.argtypes = [P, P, P, P, i32]
         L.gabm_backward.argtypes = [P, P, P, P, P, i32]
@@ -231,17 +231,23 @@ def _model_struct(model: ModelDesc, c: np.ndarray) -> _ModelDesc:
                       int(model.relax_mode), int(model.lambda_policy), int(model.seed), int(model.agent_order))
 
 
-def gabm_create_bipartite(graph, model: ModelDesc, stream=None) -> GabmCtx:
-    """Create a ctx over an agent-location graph (an object with n, n_loc, rowptr [n+1],
-    loc, w, age as host numpy arrays): agents interact through shared locations, the
-    pair weight being sum_l w_il w_jl.  One graph, one set; store-lambda hard mode."""
+def gabm_create_bipartite(graphs, model: ModelDesc, stream=None) -> GabmCtx:
+    """Create a ctx over agent-location graphs (one, or a list; objects with n, n_loc,
+    rowptr [n+1], loc, w, age as host numpy arrays): agents interact through shared
+    locations, the pair weight being sum_l w_il w_jl.  One set per graph; store-lambda
+    hard mode."""
     L = load_library()
-    rowptr = np.ascontiguousarray(graph.rowptr, np.uint64)
-    loc = np.ascontiguousarray(graph.loc, np.uint32)
-    w = np.ascontiguousarray(graph.w, np.float32)
-    age = np.ascontiguousarray(graph.age, np.uint8)
-    desc = _BipartiteDesc(int(graph.n), int(graph.n_loc), int(loc.shape[0]), _ptr(rowptr, np.uint64),
-                          _ptr(loc, np.uint32), _ptr(w, np.float32), _ptr(age, np.uint8))
+    graphs = list(graphs) if isinstance(graphs, (list, tuple)) else [graphs]
+    descs = (_BipartiteDesc * len(graphs))()
+    keep = []
+    for i, graph in enumerate(graphs):
+        rowptr = np.ascontiguousarray(graph.rowptr, np.uint64)
+        loc = np.ascontiguousarray(graph.loc, np.uint32)
+        w = np.ascontiguousarray(graph.w, np.float32)
+        age = np.ascontiguousarray(graph.age, np.uint8)
+        keep.append((rowptr, loc, w, age))
+        descs[i] = _BipartiteDesc(int(graph.n), int(graph.n_loc), int(loc.shape[0]), _ptr(rowptr, np.uint64),
+                                  _ptr(loc, np.uint32), _ptr(w, np.float32), _ptr(age, np.uint8))
     c = np.ascontiguousarray(model.c, dtype=np.float32)
     md = _model_struct(model, c)
     import torch
@@ -250,9 +256,9 @@ def gabm_create_bipartite(graph, model: ModelDesc, stream=None) -> GabmCtx:
     s = ctypes.c_void_p(int(getattr(stream, "cuda_stream", stream)))
     device = getattr(stream, "device", None) or torch.device("cuda", torch.cuda.current_device())
     out = ctypes.c_void_p()
-    st = L.gabm_create_bipartite(ctypes.byref(desc), ctypes.byref(md), s, ctypes.byref(out))
+    st = L.gabm_create_bipartite(descs, len(graphs), ctypes.byref(md), s, ctypes.byref(out))
     _check(st, None)
-    return GabmCtx(out, [graph], 1, model, device, stream)
+    return GabmCtx(out, graphs, 1, model, device, stream)
 
 
 def gabm_create(graphs, model: ModelDesc, sets_per_graph: int = 1, stream=None) -> GabmCtx:

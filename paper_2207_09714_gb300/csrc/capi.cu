@@ -1312,40 +1312,55 @@ gabm_status gabm_create(const gabm_graph_desc *graphs, int num_graphs, int sets_
     return create_on_device(H, model, sets_per_graph, cuda_stream, out);
 }
 
-gabm_status gabm_create_bipartite(const gabm_bipartite_desc *bip, const gabm_model_desc *model, void *cuda_stream,
-                                  gabm_ctx **out) {
+gabm_status gabm_create_bipartite(const gabm_bipartite_desc *graphs, int num_graphs, const gabm_model_desc *model,
+                                  void *cuda_stream, gabm_ctx **out) {
     g_create_error.clear();
     if (!out) return fail(nullptr, GABM_EINVAL, "out is NULL");
     *out = nullptr;
-    if (!bip) return fail(nullptr, GABM_EINVAL, "graph is NULL");
+    if (!graphs || num_graphs < 1 || num_graphs > 65535) return fail(nullptr, GABM_EINVAL, "need 1..65535 graphs");
     TRY(validate_model(model));
     if (model->relax_mode != GABM_HARD_ST || model->lambda_policy != GABM_STORE_LAMBDA)
         return fail(nullptr, GABM_EUNSUPPORTED, "agent-location graphs need GABM_HARD_ST and GABM_STORE_LAMBDA in this build");
-    const int64_t n = bip->n_agents, nl = bip->n_locations, nnz = bip->nnz;
-    if (n < 1 || nl < 1 || nnz < 0) return fail(nullptr, GABM_EINVAL, "need n_agents >= 1, n_locations >= 1 and nnz >= 0");
-    if (!bip->rowptr || !bip->age || (nnz > 0 && (!bip->loc || !bip->w)))
-        return fail(nullptr, GABM_EINVAL, "rowptr, loc, w and age are required");
-    if (n >= ((int64_t)1 << 31) - 64 || nl >= ((int64_t)1 << 31) - 64 || nnz >= ((int64_t)1 << 32) - 64)
-        return fail(nullptr, GABM_EUNSUPPORTED, "agents, locations and attendances must stay below 2^31, 2^31, 2^32");
-    if (bip->rowptr[0] != 0 || (int64_t)bip->rowptr[n] != nnz) return fail(nullptr, GABM_EINVAL, "rowptr[0] must be 0 and rowptr[n] = nnz");
-    for (int64_t i = 0; i < n; ++i) {
-        if (bip->rowptr[i + 1] < bip->rowptr[i]) return fail(nullptr, GABM_EINVAL, "rowptr decreases at agent %lld", (long long)i);
-        if (bip->age[i] >= kAges) return fail(nullptr, GABM_EINVAL, "age[%lld] = %d out of 0..8", (long long)i, (int)bip->age[i]);
-    }
-    for (int64_t p = 0; p < nnz; ++p) {
-        if ((int64_t)bip->loc[p] >= nl) return fail(nullptr, GABM_EINVAL, "loc[%lld] = %u out of range", (long long)p, bip->loc[p]);
-        if (!std::isfinite(bip->w[p]) || bip->w[p] < 0.0f) return fail(nullptr, GABM_EINVAL, "w[%lld] not finite and >= 0", (long long)p);
-    }
     int sigma = 1024;
     if (const char *f = getenv("GABM_SELL_SIGMA")) sigma = std::max(1, atoi(f));
+    const int G = num_graphs;
 
-    // each agent's attendances by location, repeats merged (their weights add)
-    std::vector<uint64_t> arow((size_t)n + 1, 0);
-    std::vector<uint32_t> aloc;
-    std::vector<float> aw;
-    aloc.reserve((size_t)nnz);
-    aw.reserve((size_t)nnz);
-    {
+    // per graph: validate; each agent's attendances by location, repeats merged (their
+    // weights add); Dbar of W_ij = sum_l w_il w_jl (i != j) = (1/n) sum_l [(sum_i w_il)^2 - sum_i w_il^2];
+    // agents in input order sorted by attendance count within windows.  Locations of all
+    // graphs form one pool (graph g's location l is loc_off[g] + l): no location is shared
+    // between graphs, so the graphs stay independent.
+    std::vector<std::vector<uint64_t>> arow((size_t)G);
+    std::vector<std::vector<uint32_t>> aloc((size_t)G), order((size_t)G);
+    std::vector<std::vector<float>> aw((size_t)G);
+    std::vector<double> Dbar((size_t)G);
+    std::vector<int64_t> loc_off((size_t)G + 1, 0);
+    int64_t n_total = 0, m_total = 0, n_rows = 0;
+    std::vector<int32_t> row0((size_t)G), rows((size_t)G), tile0((size_t)G), ntl((size_t)G);
+    for (int g = 0; g < G; ++g) {
+        const gabm_bipartite_desc *bip = graphs + g;
+        const int64_t n = bip->n_agents, nl = bip->n_locations, nnz = bip->nnz;
+        if (n < 1 || nl < 1 || nnz < 0) return fail(nullptr, GABM_EINVAL, "graph %d: need n_agents >= 1, n_locations >= 1 and nnz >= 0", g);
+        if (!bip->rowptr || !bip->age || (nnz > 0 && (!bip->loc || !bip->w)))
+            return fail(nullptr, GABM_EINVAL, "graph %d: rowptr, loc, w and age are required", g);
+        if (n >= ((int64_t)1 << 31) - 64 || nl >= ((int64_t)1 << 31) - 64 || nnz >= ((int64_t)1 << 32) - 64)
+            return fail(nullptr, GABM_EUNSUPPORTED, "graph %d: agents, locations and attendances must stay below 2^31, 2^31, 2^32", g);
+        if (bip->rowptr[0] != 0 || (int64_t)bip->rowptr[n] != nnz)
+            return fail(nullptr, GABM_EINVAL, "graph %d: rowptr[0] must be 0 and rowptr[n] = nnz", g);
+        for (int64_t i = 0; i < n; ++i) {
+            if (bip->rowptr[i + 1] < bip->rowptr[i]) return fail(nullptr, GABM_EINVAL, "graph %d: rowptr decreases at agent %lld", g, (long long)i);
+            if (bip->age[i] >= kAges) return fail(nullptr, GABM_EINVAL, "graph %d: age[%lld] = %d out of 0..8", g, (long long)i, (int)bip->age[i]);
+        }
+        for (int64_t p = 0; p < nnz; ++p) {
+            if ((int64_t)bip->loc[p] >= nl) return fail(nullptr, GABM_EINVAL, "graph %d: loc[%lld] = %u out of range", g, (long long)p, bip->loc[p]);
+            if (!std::isfinite(bip->w[p]) || bip->w[p] < 0.0f) return fail(nullptr, GABM_EINVAL, "graph %d: w[%lld] not finite and >= 0", g, (long long)p);
+        }
+        std::vector<uint64_t> &ar = arow[g];
+        std::vector<uint32_t> &al = aloc[g];
+        std::vector<float> &awg = aw[g];
+        ar.assign((size_t)n + 1, 0);
+        al.reserve((size_t)nnz);
+        awg.reserve((size_t)nnz);
         std::vector<std::pair<uint32_t, float>> tmp;
         for (int64_t i = 0; i < n; ++i) {
             tmp.clear();
@@ -1354,37 +1369,44 @@ gabm_status gabm_create_bipartite(const gabm_bipartite_desc *bip, const gabm_mod
                 return a.first < b.first;
             });
             for (size_t k = 0; k < tmp.size(); ++k) {
-                if (!aloc.empty() && arow[i] < aloc.size() && aloc.back() == tmp[k].first) aw.back() += tmp[k].second;
-                else { aloc.push_back(tmp[k].first); aw.push_back(tmp[k].second); }
+                if (ar[i] < al.size() && al.back() == tmp[k].first) awg.back() += tmp[k].second;
+                else { al.push_back(tmp[k].first); awg.push_back(tmp[k].second); }
             }
-            arow[i + 1] = aloc.size();
+            ar[i + 1] = al.size();
         }
-    }
-    const int64_t m = (int64_t)aloc.size();
-    // Dbar of the one-hop weights W_ij = sum_l w_il w_jl (i != j): (1/n) sum_l [(sum_i w_il)^2 - sum_i w_il^2]
-    double Dbar = 0.0;
-    {
         std::vector<double> s1((size_t)nl, 0.0), s2((size_t)nl, 0.0);
-        for (int64_t p = 0; p < m; ++p) {
-            s1[aloc[p]] += (double)aw[p];
-            s2[aloc[p]] += (double)aw[p] * (double)aw[p];
+        for (size_t p = 0; p < al.size(); ++p) {
+            s1[al[p]] += (double)awg[p];
+            s2[al[p]] += (double)awg[p] * (double)awg[p];
         }
-        for (int64_t l = 0; l < nl; ++l) Dbar += s1[l] * s1[l] - s2[l];
-        Dbar /= (double)n;
+        double D = 0.0;
+        for (int64_t l = 0; l < nl; ++l) D += s1[l] * s1[l] - s2[l];
+        Dbar[g] = D / (double)n;
+        HostGraph h;
+        h.n = n;
+        h.nnz = (int64_t)al.size();
+        h.rowptr = ar;
+        order[g].resize((size_t)n);
+        for (int64_t i = 0; i < n; ++i) order[g][i] = (uint32_t)i;
+        sort_windows_by_degree(h, order[g], sigma);
+        loc_off[g + 1] = loc_off[g] + nl;
+        row0[g] = (int32_t)n_rows;
+        rows[g] = (int32_t)n;
+        tile0[g] = (int32_t)(n_rows / kTile);
+        ntl[g] = (int32_t)(round_up((size_t)n, kTile) / kTile);
+        n_rows += (int64_t)ntl[g] * kTile;
+        n_total += n;
+        m_total += (int64_t)al.size();
     }
-    // agents: input order, sorted by attendance count within windows; locations: by member count
-    HostGraph h;
-    h.n = n;
-    h.nnz = m;
-    h.rowptr = arow;
-    std::vector<uint32_t> order((size_t)n);
-    for (int64_t i = 0; i < n; ++i) order[i] = (uint32_t)i;
-    sort_windows_by_degree(h, order, sigma);
+    if (n_rows >= ((int64_t)1 << 31) - 64 || loc_off[G] >= ((int64_t)1 << 31) - 64 || m_total >= ((int64_t)1 << 32) - 64)
+        return fail(nullptr, GABM_EUNSUPPORTED, "total agents, locations and attendances must stay below 2^31, 2^31, 2^32");
+    const int64_t nl = loc_off[G], m = m_total, n = n_total;
     // locations of up to 32 members: SELL-32 tiles, sorted by member count within windows;
     // larger ones: a CSR taken one warp per location, sorted by member count
     constexpr uint32_t kSmallLoc = 32;
     std::vector<uint32_t> lcnt((size_t)nl, 0), lsmall, lbig, linv((size_t)nl);
-    for (int64_t p = 0; p < m; ++p) lcnt[aloc[p]]++;
+    for (int g = 0; g < G; ++g)
+        for (uint32_t l : aloc[g]) lcnt[loc_off[g] + l]++;
     for (int64_t l = 0; l < nl; ++l) (lcnt[l] <= kSmallLoc ? lsmall : lbig).push_back((uint32_t)l);
     for (size_t w0 = 0; w0 < lsmall.size(); w0 += (size_t)sigma) {
         const size_t w1 = std::min(lsmall.size(), w0 + (size_t)sigma);
@@ -1397,7 +1419,6 @@ gabm_status gabm_create_bipartite(const gabm_bipartite_desc *bip, const gabm_mod
     for (int64_t k = 0; k < n_big; ++k) linv[lbig[k]] = (uint32_t)(ns_rows + k);
 
     HostLayout H;
-    const int64_t n_rows = (int64_t)round_up((size_t)n, kTile);
     const int ntiles = (int)(n_rows / kTile);
     const int64_t nnz_pad = (int64_t)round_up((size_t)(m > 0 ? m : 1), 4);
     H.h_rowptr.assign((size_t)n_rows + 1, 0u);
@@ -1405,23 +1426,31 @@ gabm_status gabm_create_bipartite(const gabm_bipartite_desc *bip, const gabm_mod
     H.h_w.assign((size_t)nnz_pad, 0.f);
     H.h_age.assign((size_t)n_rows, 0);
     H.h_orig.assign((size_t)n_rows, 0u);
+    H.tile_graph.assign((size_t)ntiles, 0);
+    H.goff.assign((size_t)G, 0);
+    for (int g = 1; g < G; ++g) H.goff[g] = H.goff[g - 1] + rows[g - 1];
     uint32_t max_degree = 0;
     {
         std::vector<std::pair<uint32_t, float>> tmp;
         uint32_t q = 0;
-        for (int64_t k = 0; k < n_rows; ++k) {
-            H.h_rowptr[k] = q;
-            if (k >= n) continue;
-            const uint32_t v = order[k];
-            tmp.clear();
-            for (uint64_t p = arow[v]; p < arow[v + 1]; ++p) tmp.emplace_back(linv[aloc[p]], aw[p]);
-            std::sort(tmp.begin(), tmp.end(), [](const std::pair<uint32_t, float> &a, const std::pair<uint32_t, float> &b) {
-                return a.first < b.first;
-            });
-            for (const auto &e : tmp) { H.h_col[q] = e.first; H.h_w[q] = e.second; ++q; }
-            max_degree = std::max(max_degree, (uint32_t)tmp.size());
-            H.h_age[k] = bip->age[v];
-            H.h_orig[k] = v;
+        for (int g = 0; g < G; ++g) {
+            const gabm_bipartite_desc *bip = graphs + g;
+            for (int32_t k = 0; k < ntl[g] * kTile; ++k) {
+                const int64_t r = row0[g] + k;
+                H.h_rowptr[r] = q;
+                if (k >= rows[g]) continue;
+                const uint32_t v = order[g][k];
+                tmp.clear();
+                for (uint64_t p = arow[g][v]; p < arow[g][v + 1]; ++p) tmp.emplace_back(linv[loc_off[g] + aloc[g][p]], aw[g][p]);
+                std::sort(tmp.begin(), tmp.end(), [](const std::pair<uint32_t, float> &a, const std::pair<uint32_t, float> &b) {
+                    return a.first < b.first;
+                });
+                for (const auto &e : tmp) { H.h_col[q] = e.first; H.h_w[q] = e.second; ++q; }
+                max_degree = std::max(max_degree, (uint32_t)tmp.size());
+                H.h_age[r] = bip->age[v];
+                H.h_orig[r] = v;
+            }
+            for (int k = 0; k < ntl[g]; ++k) H.tile_graph[tile0[g] + k] = (uint16_t)g;
         }
         H.h_rowptr[n_rows] = q;
     }
@@ -1438,7 +1467,7 @@ gabm_status gabm_create_bipartite(const gabm_bipartite_desc *bip, const gabm_mod
     std::vector<float> lw(lcol.size(), 0.f), bw(bcol.size(), 0.f);
     {
         std::vector<uint32_t> pos(lrow.begin(), lrow.end() - 1), bpos(brow.begin(), brow.end() - 1);
-        for (int64_t k = 0; k < n; ++k)
+        for (int64_t k = 0; k < n_rows; ++k)
             for (uint32_t p = H.h_rowptr[k]; p < H.h_rowptr[k + 1]; ++p) {
                 const uint32_t l = H.h_col[p];
                 const uint32_t q = (l < (uint32_t)ns_rows) ? pos[l]++ : bpos[l - ns_rows]++;
@@ -1452,13 +1481,11 @@ gabm_status gabm_create_bipartite(const gabm_bipartite_desc *bip, const gabm_mod
     H.t_rowptr = H.h_rowptr;
     H.t_col = H.h_col;
     H.t_w = H.h_w;
-    H.tile_graph.assign((size_t)ntiles, 0);
-    H.goff = {0};
-    H.row0 = {0};
-    H.rows = {(int32_t)n};
-    H.tile0 = {0};
-    H.ntl = {ntiles};
-    H.Dbar = {Dbar};
+    H.row0 = row0;
+    H.rows = rows;
+    H.tile0 = tile0;
+    H.ntl = ntl;
+    H.Dbar = Dbar;
     H.symmetric = true;
     H.batched = false;
     H.reorder = true;
@@ -1469,7 +1496,7 @@ gabm_status gabm_create_bipartite(const gabm_bipartite_desc *bip, const gabm_mod
     H.ntiles = ntiles;
     H.n_total = n;
     H.sigma = sigma;
-    H.num_graphs = 1;
+    H.num_graphs = G;
     gabm_ctx *c = nullptr;
     TRY(create_on_device(H, model, 1, cuda_stream, &c));
     auto bail = [&](gabm_status st) {
@@ -1499,7 +1526,7 @@ gabm_status gabm_create_bipartite(const gabm_bipartite_desc *bip, const gabm_mod
     if (st == GABM_OK) st = dalloc(c, &c->locv, (size_t)std::max<int64_t>(1, ns_rows + n_big));
     {
         std::vector<float> q((size_t)n_rows, 0.f);
-        for (int64_t k = 0; k < n; ++k) {
+        for (int64_t k = 0; k < n_rows; ++k) {
             double acc = 0.0;
             for (uint32_t p = H.h_rowptr[k]; p < H.h_rowptr[k + 1]; ++p) acc += (double)H.h_w[p] * (double)H.h_w[p];
             q[k] = (float)acc;

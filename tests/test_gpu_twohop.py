@@ -124,3 +124,35 @@ def test_invalid_and_unsupported(bip):
     with pytest.raises(capi.GabmError) as ei:
         capi.gabm_create_bipartite(b, model(seed=0, policy=capi.GABM_RECOMPUTE))
     assert ei.value.status == capi.GABM_EUNSUPPORTED
+
+
+def test_several_agent_location_graphs():
+    """Three counties as agent-location graphs in one ctx: each follows the oracle's run of
+    its own expanded graph (its own Dbar and Philox instance)."""
+    bips = [synth.population_bipartite(n, seed=10 + i) for i, n in enumerate((3000, 777, 4500))]
+    Ws = [OB.expand(b) for b in bips]
+    G, T, n_seed = len(bips), 24, 10
+    rng = np.random.default_rng(12)
+    R = rng.uniform(1.8, 2.6, (G, T)).astype(np.float32)
+    m = rng.uniform(0.01, 0.03, (G, T)).astype(np.float32)
+    S = np.repeat(synth.SUSCEPTIBILITY[None, :], G, axis=0).astype(np.float32)
+    md_o = O.Model(4, 7, synth.infectiousness_table(), seed=6)
+    refs = [O.forward_hard(Ws[g], md_o, R[g], m[g], S[g], n_seed=n_seed, inst=g) for g in range(G)]
+    gD = np.stack([O.mse(refs[g]["D"], synth.target_curve(T, bips[g].n, seed=g, level=5e-5))[1] for g in range(G)])
+    ctx = capi.gabm_create_bipartite(bips, model(seed=6))
+    Rd, md_, Sd, gDd = to_dev(R, m, S, gD)
+    D, _ = capi.gabm_forward(ctx, T, Rd, md_, Sd, [n_seed] * G)
+    e = capi.gabm_get_state(ctx)[0]
+    dR, dm, dS = [x.cpu().numpy() for x in capi.gabm_backward(ctx, gDd)]
+    off = np.concatenate([[0], np.cumsum([b.n for b in bips])])
+    checked = 0
+    for g in range(G):
+        if refs[g]["margin"] <= EXACT_MARGIN:
+            continue
+        assert np.array_equal(e[off[g]:off[g + 1]], refs[g]["e_final"]), g
+        assert np.allclose(D.cpu().numpy()[g], refs[g]["D"], rtol=1e-15, atol=0)
+        ref = O.backward_hard(Ws[g], md_o, R[g], m[g], S[g], refs[g]["e_final"], gD[g], inst=g)
+        check_adjoint(dR[g], ref["dR"], f"dR[{g}]")
+        check_adjoint(dS[g], ref["dS"], f"dS[{g}]")
+        checked += 1
+    assert checked >= 2
