@@ -33,16 +33,22 @@ __device__ __forceinline__ void dc_accumulate(double *dc_tile, int tile, bool ha
                                               int lane) {
     unsigned pend = __ballot_sync(0xffffffffu, has);
     if (!pend) return;
-    const double scale = ldexp(1.0, sigma);
+    // lane k keeps the sum for k (k < L <= 32), so the read-modify-writes of all k go out together
+    float mine = 0.f;
+    bool touched = false;
     while (pend) {
         const int k0 = __shfl_sync(0xffffffffu, kd, __ffs(pend) - 1);
         const bool sel = has && kd == k0;
         float v = sel ? gx : 0.f;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) dc_tile[(size_t)tile * kMaxL + k0] += (double)v * scale;
+        if (lane == k0) {
+            mine = v;
+            touched = true;
+        }
         pend &= ~__ballot_sync(0xffffffffu, sel);
     }
+    if (touched) dc_tile[(size_t)tile * kMaxL + lane] += (double)mine * ldexp(1.0, sigma);
 }
 
 // DC: accumulate the table adjoint (a.dc_tile); a separate instance, so the plain sweep
@@ -410,12 +416,18 @@ cudaError_t launch_lam_day(Sell m, const int16_t *E, const uint32_t *bits, Graph
     return cudaGetLastError();
 }
 
-int occupancy_bwd(int mode) {
+int occupancy_bwd(int mode, bool dc) {
     int blocks = 0;
     switch (mode) {
-        case kBwdFused: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_bwd_day<kBwdFused, false>, kBlock, 0); break;
+        case kBwdFused:
+            if (dc) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_bwd_day<kBwdFused, true>, kBlock, 0);
+            else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_bwd_day<kBwdFused, false>, kBlock, 0);
+            break;
         case kBwdSoft: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_bwd_day<kBwdSoft, false>, kBlock, 0); break;
-        default: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_bwd_day<kBwdStore, false>, kBlock, 0); break;
+        default:
+            if (dc) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_bwd_day<kBwdStore, true>, kBlock, 0);
+            else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_bwd_day<kBwdStore, false>, kBlock, 0);
+            break;
     }
     return blocks > 0 ? blocks : 1;
 }

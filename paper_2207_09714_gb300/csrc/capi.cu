@@ -100,7 +100,7 @@ struct gabm_ctx {
     int T_last = -1;
     int lam_from = -1;
 
-    int grid_fwd = 0, grid_bwd = 0;
+    int grid_fwd = 0, grid_bwd = 0, grid_bwd_dc = 0;   // grid_bwd_dc: the table-adjoint instance
     bool smem_bits = false;         // forward keeps the infectious bitmap in shared memory
     // agent-location graphs: the location hop (SELL-32 of locations -> members) and its values
     bool two_hop = false;
@@ -748,7 +748,7 @@ gabm_status backward_days_plain(gabm_ctx *c, int T, cudaStream_t s) {
         a.P_t = c->P + (size_t)t * c->ntiles * kAges;
         for (int k = 0; k < kMaxL; ++k) a.ring_slot[k] = (k >= 1 && k < c->L) ? (t + k) % Lm1 : 0;
         prof_begin(c, 1);
-        LAUNCH(launch_bwd_day(a, c->grid_bwd, s));
+        LAUNCH(launch_bwd_day(a, a.dc_tile ? c->grid_bwd_dc : c->grid_bwd, s));
         prof_end(c, 1);
     }
     if (a.dc_tile) {   // the seeds' share through day 0 (r of day 0 is in slot 0)
@@ -923,6 +923,7 @@ void apply_schedule(gabm_ctx *c) {
         if (c->smem_bits && bps <= 0) c->smem_bits = false;
         c->grid_fwd = c->num_sms * (c->smem_bits ? bps : occupancy_fwd(c->ntiles, false));
         c->grid_bwd = c->num_sms * occupancy_bwd(mode);
+        c->grid_bwd_dc = c->num_sms * occupancy_bwd(mode, true);
     }
     if (c->two_hop) {
         c->smem_bits = false;
@@ -932,6 +933,7 @@ void apply_schedule(gabm_ctx *c) {
     const int max_grid = (c->ntiles + kBlock / 32 - 1) / (kBlock / 32);
     if (!c->smem_bits && c->grid_fwd > max_grid) c->grid_fwd = max_grid;
     if (c->grid_bwd > max_grid) c->grid_bwd = max_grid;
+    if (c->grid_bwd_dc > max_grid) c->grid_bwd_dc = max_grid;
     for (auto &g : c->loop_graph) drop_graph(g);   // captured launches carry the old schedule
 }
 

@@ -401,6 +401,6 @@ cudaError_t launch_rows_to_caller_f32(const float *src, float *dst, GraphRef gr,
 cudaError_t launch_caller_to_rows_i16(const int16_t *src, int16_t *dst, GraphRef gr, const int32_t *rows,
                                       const int64_t *goff, int64_t n_rows, SetLayout sl, cudaStream_t s);
 int occupancy_fwd(int ntiles, bool smem_bits);
-int occupancy_bwd(int mode);
+int occupancy_bwd(int mode, bool dc = false);
 
 }  // namespace gabm
