@@ -425,7 +425,7 @@ def cpu_baseline(pop, c, y):
 
 
 def bench_twohop(stream, dist, steps=5, n=1_000_000):
-    """The agent-location workload (GradABM-JUNE, Sec. 5): one forward + MSE + backward
+    """The agent-location workload (GradABM-JUNE, Sec. 6): one forward + MSE + backward
     step over 60 days on a synthetic agent-location graph of n agents (households,
     schools of 100-400, workplaces of 5-60, shared venues), computed in two hops over the
     attendance entries.  Reports the pair count the two hops avoid forming."""

@@ -125,7 +125,7 @@ gabm_status gabm_create(const gabm_graph_desc *graphs, int num_graphs, int sets_
                         const gabm_model_desc *model, void *cuda_stream, gabm_ctx **out);
 
 /* An agent-location graph, the heterogeneous contact structure of GradABM-JUNE
- * (Sec. 5): agent i attends location loc[p] with weight w[p] for p in
+ * (Sec. 6): agent i attends location loc[p] with weight w[p] for p in
  * [rowptr[i], rowptr[i+1]).  Two agents interact through every location they
  * share, so the model is that of Sec. 3.1 (Eq. 3) on the agent graph with pair
  * weights W_ij = sum_l w_il w_jl (i != j), and Dbar is W's mean weighted degree.

@@ -2,7 +2,7 @@
 
 TEST INFRASTRUCTURE ONLY, like the rest of ``oracle``.
 
-GradABM-JUNE (Sec. 5) represents contacts as a heterogeneous graph of agents and
+GradABM-JUNE (Sec. 6) represents contacts as a heterogeneous graph of agents and
 locations.  Two agents interact through every location they share, so the model
 on the agent-location graph is the one-hop model of Sec. 3.1 on the agent graph
 with pair weights W_ij = sum_l w_il w_jl (i != j): the force of infection

@@ -1,4 +1,4 @@
-// twohop.cu -- the location hop of agent-location graphs (GradABM-JUNE, Sec. 5).
+// twohop.cu -- the location hop of agent-location graphs (GradABM-JUNE, Sec. 6).
 //
 // Agents interact through shared locations: with attendance weights w_il the pair
 // weight is W_ij = sum_l w_il w_jl, and each sum over W is computed in two hops over

@@ -272,7 +272,7 @@ def permute(pop: Population, perm: np.ndarray) -> Population:
 
 @dataclasses.dataclass
 class Bipartite:
-    """Agents and locations, the heterogeneous contact structure of GradABM-JUNE (Sec. 5):
+    """Agents and locations, the heterogeneous contact structure of GradABM-JUNE (Sec. 6):
     agent i attends location l with weight w_il (agent-sorted incidence).  Two agents
     interact through every location they share: the one-hop weight of the pair is
     W_ij = sum_l w_il w_jl (i != j)."""

@@ -1,4 +1,4 @@
-"""Agent-location graphs (GradABM-JUNE, Sec. 5) on the GPU against the oracle.
+"""Agent-location graphs (GradABM-JUNE, Sec. 6) on the GPU against the oracle.
 
 The GPU computes every day in two hops over the attendance entries (location
 pressures, then the agents' pull over their locations; the adjoint likewise).  The
