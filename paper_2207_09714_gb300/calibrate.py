@@ -1,10 +1,10 @@
 """Calibration of the simulator's parameters by gradient descent through the day loop:
 C-GradABM (Sec. 3.2, Stages 2-4, and the C-GradABM baseline of Sec. 4.2), and DC- / JDC-
-GradABM, where a calibration network (CalibNN, App. D) maps feature time series to the
+GradABM, where a calibration network (CalibNN, App. C) maps feature time series to the
 parameters and is trained through the simulator (one network per county, or one shared by
 all the counties of a multi-graph context).
 
-* Parameters are tied within weeks: every day of week w uses R_w and m_w (App. C: one
+* Parameters are tied within weeks: every day of week w uses R_w and m_w (App. D: one
   parameter set for every 7 days).
 * The loss is the mean-squared error of the cumulative deaths (Sec. 3.2, Stage 3).
 * Gradients come from the library's straight-through adjoint (App. B): R_t, m_t, S_a,
@@ -108,7 +108,7 @@ class WeeklyParams(torch.nn.Module):
 
 
 class CalibNN(torch.nn.Module):
-    """The calibration network of App. D: a GRU encodes the feature series x^t (t0..tN)
+    """The calibration network of App. C: a GRU encodes the feature series x^t (t0..tN)
     into h^t; scaled dot-product self-attention over the h^t, summed over t, gives the
     context u; a GRU decoder started from u reads the positional codes tau_k = k/K
     (k = 1..K) and a feed-forward head maps each output o^k to parameters bounded as
