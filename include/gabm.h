@@ -194,8 +194,10 @@ gabm_status gabm_backward(gabm_ctx *ctx, const double *gD, double *dR, double *d
  * agent j's infectiousness on day t.  dc[i][0] = 0 (c[0] = 0 is fixed, A2 of App. A).
  * Gradients of stage factors or profile parameters that define c (T_E, T_I, iota)
  * follow by the chain rule on the caller's side.  With several sets per graph, each
- * instance i = graph * sets_per_graph + set gets its own dc[i].  Same preconditions as
- * gabm_backward; GABM_EINVAL if dc is NULL; GABM_EUNSUPPORTED for the soft relaxation. */
+ * instance i = graph * sets_per_graph + set gets its own dc[i].  Under GABM_SOFT the
+ * exposed mass replaces the indicator: dc[i][k] = sum_t sum_j n_j(t - k) gx_j(t) with
+ * n_j(d) = s_j(d) y_j(d), the seeds' unit mass before day 0.  Same preconditions as
+ * gabm_backward; GABM_EINVAL if dc is NULL. */
 gabm_status gabm_backward_table(gabm_ctx *ctx, const double *gD, double *dR, double *dm,
                                 double *dS_age, double *dc, int mem_space);
 

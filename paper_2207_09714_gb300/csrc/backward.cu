@@ -64,7 +64,6 @@ __global__ void __launch_bounds__(kBlock, (MODE == kBwdStore && !DC) ? GABM_BWD_
     k_bwd_day(const BwdDayArgs a) {
     constexpr int NARR = (MODE == kBwdFused) ? 2 : 1;
     constexpr bool SOFT = MODE == kBwdSoft;
-    static_assert(!(SOFT && DC), "the table adjoint is built for the hard sweep");
     __shared__ float c_s[kMaxL];
     __shared__ int slot_k[kMaxL];
     __shared__ int32_t red_s[kBlock / 32][2];
@@ -142,7 +141,7 @@ __global__ void __launch_bounds__(kBlock, (MODE == kBwdStore && !DC) ? GABM_BWD_
         // table adjoint: rows infectious on day t+1 (k = t+1-E in [1, L-1]) add gx(t+1) to
         // dc[k]; the non-seed ones are already gathered (needA), the seeds only for this
         const int kd = t + 1 - Ei;
-        const bool dc_row = DC && has_next && agent && !never && kd >= 1 && kd <= L - 1;
+        const bool dc_row = DC && !SOFT && has_next && agent && !never && kd >= 1 && kd <= L - 1;
 
         float sum[NARR];
         {
@@ -156,7 +155,28 @@ __global__ void __launch_bounds__(kBlock, (MODE == kBwdStore && !DC) ? GABM_BWD_
         if (a.self_q) gx_mine = __fmaf_rn(-a.self_q[row], a.self_r[row], gx_mine);
 
         if (needA) a.ring[(size_t)slot_k[1] * a.ring_stride + row] = gx_mine;
-        if constexpr (DC) dc_accumulate(a.dc_tile, tile, dc_row, kd, gx_mine, sg[t + 1], lane);
+        if constexpr (DC && !SOFT) dc_accumulate(a.dc_tile, tile, dc_row, kd, gx_mine, sg[t + 1], lane);
+        if constexpr (DC && SOFT) {
+            // soft: every agent's mass exposed k days before t+1 counts, n_j(d) = s_j(d) y_j(d)
+            // for d >= 0 and the seeds' unit mass on their day E_j < 0 (lane k keeps k's sum)
+            const bool on = has_next && agent;
+            if (__any_sync(0xffffffffu, on)) {
+                float mine = 0.f;
+                for (int k = 1; k < L; ++k) {
+                    const int d = t + 1 - k;
+                    float nk = 0.f;
+                    if (on)
+                        nk = (d >= 0) ? a.s_hist[(size_t)d * a.hist_stride + row] * a.y_hist[(size_t)d * a.hist_stride + row]
+                                      : (Ei == d ? 1.f : 0.f);
+                    float v = nk * gx_mine;
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                    if (lane == k) mine = v;
+                }
+                if (lane >= 1 && lane < L && mine != 0.f)
+                    a.dc_tile[(size_t)tile * kMaxL + lane] += (double)mine * ldexp(1.0, sg[t + 1]);
+            }
+        }
 
         float v = 0.f;
         int ai = 0;
@@ -390,8 +410,8 @@ cudaError_t launch_bwd_day(const BwdDayArgs &a, int grid, cudaStream_t s) {
             else k_bwd_day<kBwdFused, false><<<grid, kBlock, 0, s>>>(a);
             break;
         case kBwdSoft:
-            if (dc) return cudaErrorInvalidValue;
-            k_bwd_day<kBwdSoft, false><<<grid, kBlock, 0, s>>>(a);
+            if (dc) k_bwd_day<kBwdSoft, true><<<grid, kBlock, 0, s>>>(a);
+            else k_bwd_day<kBwdSoft, false><<<grid, kBlock, 0, s>>>(a);
             break;
         default: return cudaErrorInvalidValue;
     }
@@ -423,7 +443,10 @@ int occupancy_bwd(int mode, bool dc) {
             if (dc) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_bwd_day<kBwdFused, true>, kBlock, 0);
             else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_bwd_day<kBwdFused, false>, kBlock, 0);
             break;
-        case kBwdSoft: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_bwd_day<kBwdSoft, false>, kBlock, 0); break;
+        case kBwdSoft:
+            if (dc) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_bwd_day<kBwdSoft, true>, kBlock, 0);
+            else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_bwd_day<kBwdSoft, false>, kBlock, 0);
+            break;
         default:
             if (dc) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_bwd_day<kBwdStore, true>, kBlock, 0);
             else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_bwd_day<kBwdStore, false>, kBlock, 0);

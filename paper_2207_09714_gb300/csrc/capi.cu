@@ -719,6 +719,9 @@ gabm_status backward_days_plain(gabm_ctx *c, int T, cudaStream_t s) {
     if (mode == kBwdFused || mode == kBwdSplit)   // every day's infectious rows, from the final state
         LAUNCH(launch_infectious_bits(c->e, 0, T, c->L, c->ntiles, c->bits, (size_t)c->ntiles, s));
     a.s_hist_t = a.y_hist_t = nullptr;
+    a.s_hist = c->s_hist;
+    a.y_hist = c->y_hist;
+    a.hist_stride = (size_t)c->n_rows;
     a.sig = c->sig;
     a.emax = c->emax;
     a.ld_sig = ld + 1;
@@ -915,6 +918,7 @@ void apply_schedule(gabm_ctx *c) {
         c->smem_bits = false;
         c->grid_fwd = c->num_sms * occupancy_fwd_soft();
         c->grid_bwd = c->num_sms * occupancy_bwd(mode);
+        c->grid_bwd_dc = c->num_sms * occupancy_bwd(mode, true);
     } else if (c->batched) {
         c->grid_fwd = c->num_sms * occupancy_fwd_b(c->Bp, c->spl_fwd, c->kahan_b);
         c->grid_bwd = c->num_sms * occupancy_bwd_b(c->bwd_chunk, c->spl_bwd, c->kahan_b);
@@ -1628,7 +1632,6 @@ gabm_status gabm_backward_table(gabm_ctx *ctx, const double *gD, double *dR, dou
                                 double *dc, int mem_space) {
     if (!ctx) return fail(nullptr, GABM_EINVAL, "ctx is NULL");
     if (!dc) return fail(ctx, GABM_EINVAL, "dc is required");
-    if (ctx->soft) return fail(ctx, GABM_EUNSUPPORTED, "the table adjoint is built for the hard (straight-through) mode");
     return backward_impl(ctx, gD, dR, dm, dS_age, dc, mem_space);
 }
 

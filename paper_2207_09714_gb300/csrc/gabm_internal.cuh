@@ -157,6 +157,8 @@ struct BwdDayArgs {
     size_t ring_stride;
     float *A;                  // [n_rows] adjoint of s carried back from the infection day (soft: dL/ds(t+1))
     const float *s_hist_t, *y_hist_t;   // soft mode: s_i(t), y_i(t)
+    const float *s_hist, *y_hist;       // soft mode, table adjoint: all days [T][hist_stride]
+    size_t hist_stride;
     const float *R, *m_t, *S;  // R and mortality [I][ldP], susceptibility [I][9]
     const double *gD;          // [I][ldP]
     int ldP;

@@ -132,3 +132,35 @@ def test_soft_multi_graph_and_schedule_calls():
     capi.gabm_autotune(ctx, 1)
     D2, _ = capi.gabm_forward(ctx, T, Rd, md_, Sd, [4, 7])
     assert np.array_equal(D2.cpu().numpy(), D)
+
+
+def test_soft_table_adjoint():
+    """dL/dc[k] of the soft relaxation: against the oracle's soft adjoint (1e-3) and
+    against Richardson central differences of the oracle's soft loss in c[k] (1e-2)."""
+    pop, R, m, S, y = _case(n=2500, T=22, seed=6, graph_seed=9)
+    md = O.Model(4, 7, synth.infectiousness_table(), seed=13)
+    f = O.forward_soft(pop, md, R, m, S, n_seed=5)
+    _, gD = O.mse(f["D"], y)
+    e0 = np.full(pop.n, capi.GABM_NEVER, np.int16)
+    e0[O.select_seeds(pop.n, 13, 0, 5)] = -4
+    g = O.backward_soft(pop, md, R, m, S, gD, f["s_hist"], f["y_hist"], f["dydl_hist"], f["Lam_hist"],
+                        f["newRM"], e0=e0)
+    ctx = capi.gabm_create([pop], _soft_model(13))
+    Rd, md_, Sd, yd = to_dev(R[None], m[None], S[None], y[None])
+    capi.gabm_forward(ctx, R.size, Rd, md_, Sd, [5])
+    _, gDd = capi.gabm_mse_loss(ctx, yd)
+    dc = capi.gabm_backward_table(ctx, gDd)[3].cpu().numpy()[0]
+    assert dc[0] == 0.0 and np.abs(g["dc"][1:]).min() > 0
+    check_adjoint(dc[1:], g["dc"][1:], "dc")
+    for k in range(1, 11):
+        base = float(md.c[k])
+        h = 2.0 ** (math.floor(math.log2(max(1.0, abs(base)))) - 12)
+
+        def L_at(delta):
+            c = md.c.copy()
+            c[k] = np.float32(base + delta)
+            return O.mse(O.forward_soft(pop, O.Model(4, 7, c, seed=13), R, m, S, n_seed=5)["D"], y)[0]
+        d1 = (L_at(h) - L_at(-h)) / (2 * h)
+        d2 = (L_at(2 * h) - L_at(-2 * h)) / (4 * h)
+        fd = (4 * d1 - d2) / 3
+        assert abs(dc[k] - fd) <= 1e-2 * max(abs(fd), 1e-3 * np.abs(dc).max()), (k, dc[k], fd)

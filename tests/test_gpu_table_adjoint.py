@@ -131,20 +131,6 @@ def test_table_adjoint_long_horizon_and_short_horizon():
         _check_table(dc, g["dc"])
 
 
-def test_table_adjoint_unsupported_for_the_soft_relaxation():
-    pop = synth.population_small(n=1000, seed=1)
-    md = capi.ModelDesc(tau_EI=4, tau_IR=7, c=synth.infectiousness_table(), seed=0, relax_mode=capi.GABM_SOFT)
-    ctx = capi.gabm_create([pop], md)
-    T = 5
-    Rd, md_, Sd = to_dev(np.full((1, T), 2.5, np.float32), np.full((1, T), 0.01, np.float32),
-                         synth.SUSCEPTIBILITY[None, :].astype(np.float32))
-    capi.gabm_forward(ctx, T, Rd, md_, Sd, [5])
-    (gDd,) = to_dev(np.ones((1, T)))
-    with pytest.raises(capi.GabmError) as ei:
-        capi.gabm_backward_table(ctx, gDd)
-    assert ei.value.status == capi.GABM_EUNSUPPORTED
-
-
 def test_set_infectiousness_validation_and_state():
     """An invalid table is refused and leaves the ctx as it was; a valid one invalidates the
     last trajectory until the next forward, which then uses the new table (it equals a
