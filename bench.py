@@ -489,22 +489,40 @@ def bench_calibration(ctx, stream, S, y_np, dist, steps=5):
             opt.step()
             losses.append(loss.detach())
 
-        for _ in range(3):
-            cstep()
-        torch.cuda.synchronize()
-        if dist is not None:
-            dist.barrier()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(steps):
-            cstep()
-        e1.record(stream)
-        torch.cuda.synchronize()
-    ms = max_over_ranks(e0.elapsed_time(e1), dist, "cuda") / steps
+        def timed(fn):
+            for _ in range(3):
+                fn()
+            torch.cuda.synchronize()
+            if dist is not None:
+                dist.barrier()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(steps):
+                fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            return max_over_ranks(e0.elapsed_time(e1), dist, "cuda") / steps
+
+        ms = timed(cstep)
+        first_last = [float(losses[0]), float(losses[-1])]
+        # DC-GradABM: the weekly parameters from CalibNN over synthetic features
+        torch.manual_seed(0)
+        x = torch.as_tensor(calibrate.synthetic_features(np.full((1, DAYS), R0), t_N=DAYS, F=5, seed=0),
+                            device="cuda")
+        net = calibrate.DeepCalibration(5, DAYS, hidden=32).cuda()
+        opt_dc = torch.optim.Adam([q for q in net.parameters() if q.requires_grad], lr=0.004)
+
+        def dcstep():
+            opt_dc.zero_grad()
+            R, m, c = net(x)
+            calibrate.cumulative_mse(calibrate.TableFunction.apply(ctx, R, m, S, c, [N_SEED]), y_cum).backward()
+            opt_dc.step()
+
+        ms_dc = timed(dcstep)
     return {"workload": f"calibration on the same graph: {DAYS} days, weekly-tied R and m, T_E, T_I and "
                         f"the infectiousness profile; MSE on cumulative deaths; Adam",
-            "ms_per_step": ms, "steps": steps,
-            "loss_first_last": [float(losses[0]), float(losses[-1])]}
+            "ms_per_step": ms, "steps": steps, "loss_first_last": first_last,
+            "dc_calibnn_ms_per_step": ms_dc}
 
 
 def main():
