@@ -300,8 +300,9 @@ def bench_batched(args, stream, peak, peak_kind):
     del ctx
     units = B * pop.n * T
     dom = "k_bwd_day_b" if b_ms >= f_ms else "k_fwd_day_b"
-    traffic = _ncu_traffic(dom, _kernel_source_sha(["batched.cu", "rowsum.cuh", "gabm_internal.cuh"]),
-                           f"typed500k_B{B}_T{T}_store")
+    src = ["batched_bwd.cu" if dom == "k_bwd_day_b" else "batched.cu", "batched_common.cuh", "rowsum.cuh",
+           "gabm_internal.cuh"]
+    traffic = _ncu_traffic(dom, _kernel_source_sha(src), f"typed500k_B{B}_T{T}_store")
     result = {
         "workload": f"one shared {pop.n}-agent typed contact graph, {B} parameter sets (R ~ U[1.5, 4.0], "
                     f"m ~ U[0.005, 0.05]), {T} days, forward + MSE + backward of every set",
