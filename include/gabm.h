@@ -119,8 +119,9 @@ typedef struct {
  * weights are symmetric), and allocates the per-agent state.  cuda_stream is a
  * cudaStream_t (NULL = legacy default stream).  num_graphs >= 1 graphs are
  * concatenated block-diagonally (uneven batch); sets_per_graph = B in 1..64
- * parameter sets share each graph (instance i = graph * B + set; B > 1 needs
- * GABM_STORE_LAMBDA).  On success *out owns everything; release with gabm_destroy. */
+ * parameter sets share each graph (instance i = graph * B + set; B > 1 with
+ * GABM_RECOMPUTE needs symmetric weights, else GABM_EUNSUPPORTED).  On success *out
+ * owns everything; release with gabm_destroy. */
 gabm_status gabm_create(const gabm_graph_desc *graphs, int num_graphs, int sets_per_graph,
                         const gabm_model_desc *model, void *cuda_stream, gabm_ctx **out);
 
@@ -182,7 +183,11 @@ gabm_status gabm_set_infectiousness(gabm_ctx *ctx, const float *c);
  * [I][T] (double), writes dR [I][T], dm [I][T] and dS_age [I][9] (double).
  * Cross-agent and cross-day sums are FP64 in a fixed order (bitwise
  * reproducible).  GABM_ESTATE without a forward (or set_state) of the same T,
- * or with GABM_STORE_LAMBDA when the stored lambdas do not cover days 0..T-1. */
+ * with GABM_STORE_LAMBDA when the stored lambdas do not cover days 0..T-1, or with
+ * several sets per graph when the last forward did not start at day 0.  Several sets
+ * under GABM_RECOMPUTE: each day's lambda is summed again from the final state over the
+ * same entries in the same order as the forward, so the result is bitwise that of
+ * GABM_STORE_LAMBDA. */
 gabm_status gabm_backward(gabm_ctx *ctx, const double *gD, double *dR, double *dm,
                           double *dS_age, int mem_space);
 
@@ -197,7 +202,8 @@ gabm_status gabm_backward(gabm_ctx *ctx, const double *gD, double *dR, double *d
  * instance i = graph * sets_per_graph + set gets its own dc[i].  Under GABM_SOFT the
  * exposed mass replaces the indicator: dc[i][k] = sum_t sum_j n_j(t - k) gx_j(t) with
  * n_j(d) = s_j(d) y_j(d), the seeds' unit mass before day 0.  Same preconditions as
- * gabm_backward; GABM_EINVAL if dc is NULL. */
+ * gabm_backward; GABM_EINVAL if dc is NULL; GABM_EUNSUPPORTED for several sets per graph
+ * under GABM_RECOMPUTE. */
 gabm_status gabm_backward_table(gabm_ctx *ctx, const double *gD, double *dR, double *dm,
                                 double *dS_age, double *dc, int mem_space);
 
@@ -209,7 +215,9 @@ gabm_status gabm_get_state(gabm_ctx *ctx, int16_t *e_out, int mem_space);
 /* Replace the state with e [sets_per_graph][n_total] as the start of day `day` (0 <= day <=
  * GABM_MAX_DAYS).  The next gabm_forward then runs days day..T-1 without
  * seeding; a gabm_forward with T == day only records its parameters, after
- * which gabm_backward (GABM_RECOMPUTE) replays the trajectory e encodes.
+ * which gabm_backward (GABM_RECOMPUTE, one set per graph) replays the trajectory e
+ * encodes.  With several sets per graph a backward needs a forward over days 0..T-1
+ * (GABM_ESTATE after a forward from a set state at day > 0).
  * Values must be GABM_NEVER or in [-GABM_MAX_L, day). */
 gabm_status gabm_set_state(gabm_ctx *ctx, int day, const int16_t *e_in, int mem_space);
 
@@ -217,7 +225,8 @@ gabm_status gabm_set_state(gabm_ctx *ctx, int day, const int16_t *e_in, int mem_
  * susceptible on day t (GABM_SOFT: 0 for the seeds, which hold no susceptible mass).
  * GABM_STORE_LAMBDA: the stored value; t must have been run by the last forward.
  * GABM_RECOMPUTE: recomputed from the current state, which fixes every earlier day
- * (no reinfection); 0 <= t < the last forward's T.  GABM_ESTATE otherwise. */
+ * (no reinfection); 0 <= t < the last forward's T; one-hop graphs of one set per graph
+ * (GABM_EUNSUPPORTED otherwise).  GABM_ESTATE otherwise. */
 gabm_status gabm_get_lambda(gabm_ctx *ctx, int t, float *lam_out, int mem_space);
 
 /* Kernel schedule of a ctx.  Schedules change how rows and parameter sets map

@@ -13,15 +13,18 @@ namespace {
 // straight-through adjoint of day t's draws (the per-set steps of backward.cu).
 // ---------------------------------------------------------------------------
 // DC: also accumulate the adjoint of the infectiousness table (a.dc_tile), a separate
-// instance so that the plain sweep carries none of its code.
-template <int LPR, int SPL, bool KAHAN, bool DC>
+// instance so that the plain sweep carries none of its code.  REC (recompute policy,
+// symmetric weights): lambda is not stored but summed again from the final exposure
+// days over the same entries, with the forward's marking (a.bits_t) and order, so it
+// is bitwise the forward's.
+template <int LPR, int SPL, bool KAHAN, bool DC, bool REC = false>
 __global__ void __launch_bounds__(kBlock, 2) k_bwd_day_b(const BwdBatchArgs a) {
     constexpr int RPW = 32 / LPR;
     constexpr int Bc = LPR * SPL;        // sets of this launch (a chunk of the row's Bw)
     constexpr int NW = kBlock / 32;
     // DC: per-warp tile sums [L][Bc] of gx at the rows' infectious days, by k = t + 1 - E
     extern __shared__ float dcs_all[];
-    __shared__ float c_s[kMaxL];
+    __shared__ float c_s[kMaxL + 1];    // c_s[k] = 0 for k >= L (the clamped lookup)
     __shared__ int slot_k[kMaxL];
     __shared__ float pacc[NW][kAges][Bc];   // per-warp tile sums of gl * Lam by age and set
     __shared__ float fac_s[NW][kMaxL];       // 2^(sigma(t+k) - sigma(t)) of the warp's graph
@@ -29,6 +32,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_bwd_day_b(const BwdBatchArgs a) {
         c_s[threadIdx.x] = a.c[threadIdx.x];
         slot_k[threadIdx.x] = a.ring_slot[threadIdx.x];
     }
+    if (threadIdx.x == kMaxL) c_s[kMaxL] = 0.f;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     for (int i = lane; i < kAges * Bc; i += 32) (&pacc[wib][0][0])[i] = 0.f;
     float *dcs = dcs_all + (size_t)wib * a.L * Bc;
@@ -148,6 +152,22 @@ __global__ void __launch_bounds__(kBlock, 2) k_bwd_day_b(const BwdBatchArgs a) {
                 }
             }
 
+            // REC: the day's lambda sums of the row's susceptible sets, from the final state
+            float Lrec[SPL];
+            if constexpr (REC) {
+                const bool actl = (group_bits<LPR>(__ballot_sync(kFull, anyS)) >> grp) & 1u;
+                auto lde = [&](uint32_t j, bool ok, EWords<SPL> &rw) {
+                    ld_words<SPL>(E32 + ((size_t)j * Bw + s0) / 2, ok, rw.w);
+                };
+                auto vale = [&](const EWords<SPL> &rw, int h) {
+                    return infect_lut(half_of(rw.w[h >> 1], h & 1), c_s, t, (unsigned)L);
+                };
+                group_row_sums<LPR, SPL, KAHAN, EWords<SPL>>(a.m, cu.p0, actl ? cu.len : 0u, cu.j0, cu.w0, a.bits_t,
+                                                             lane, lde, vale, Lrec);
+#pragma unroll
+                for (int h = 0; h < SPL; ++h) Lrec[h] = Lrec[h] * inv_D;
+            }
+
             float v[SPL];
             int ai = 0;
 #pragma unroll
@@ -166,7 +186,12 @@ __global__ void __launch_bounds__(kBlock, 2) k_bwd_day_b(const BwdBatchArgs a) {
                 float Av[SPL];
                 ld_floats<SPL>(a.A + xo, readA || writeA, Av);
                 float Lv[SPL];
-                ld_floats<SPL>(a.lam_t + xo, true, Lv);
+                if constexpr (REC) {
+#pragma unroll
+                    for (int h = 0; h < SPL; ++h) Lv[h] = Lrec[h];
+                } else {
+                    ld_floats<SPL>(a.lam_t + xo, true, Lv);
+                }
                 float G[SPL];
 #pragma unroll
                 for (int h = 0; h < SPL; ++h)
@@ -279,6 +304,12 @@ cudaError_t launch_bwd_dc(const BwdBatchArgs &a, int grid, cudaStream_t s) {
 
 template <int LPR, int SPL>
 cudaError_t launch_bwd_cfg(const BwdBatchArgs &a, bool kahan, int grid, cudaStream_t s) {
+    if (!a.lam_t) {   // recompute policy (no table adjoint)
+        if (a.dc_tile) return cudaErrorInvalidValue;
+        if (kahan) k_bwd_day_b<LPR, SPL, true, false, true><<<grid, kBlock, 0, s>>>(a);
+        else k_bwd_day_b<LPR, SPL, false, false, true><<<grid, kBlock, 0, s>>>(a);
+        return cudaGetLastError();
+    }
     if (a.dc_tile) return kahan ? launch_bwd_dc<LPR, SPL, true>(a, grid, s) : launch_bwd_dc<LPR, SPL, false>(a, grid, s);
     if (kahan) k_bwd_day_b<LPR, SPL, true, false><<<grid, kBlock, 0, s>>>(a);
     else k_bwd_day_b<LPR, SPL, false, false><<<grid, kBlock, 0, s>>>(a);

@@ -99,6 +99,7 @@ struct gabm_ctx {
     std::vector<int32_t> last_seeds;  // n_seed of the last seeded forward
     int T_last = -1;
     int lam_from = -1;
+    int bits_from = -1;             // first day whose infectious bitmap the last forward wrote
 
     int grid_fwd = 0, grid_bwd = 0, grid_bwd_dc = 0;   // grid_bwd_dc: the table-adjoint instance
     bool smem_bits = false;         // forward keeps the infectious bitmap in shared memory
@@ -623,10 +624,12 @@ gabm_status backward_days_batched(gabm_ctx *c, int T, cudaStream_t s) {
     a.ld_sig = ld + 1;
     a.Bw = c->Bp;
     a.dc_tile = c->want_dc ? c->dc_tile : nullptr;
+    const bool rec = c->policy != GABM_STORE_LAMBDA;   // the last forward wrote every day's bitmap
     const int Lm1 = c->L - 1;
     for (int t = T - 1; t >= 0; --t) {
         a.t = t;
-        a.lam_t = c->lam + (size_t)t * nb;
+        a.lam_t = rec ? nullptr : c->lam + (size_t)t * nb;
+        a.bits_t = c->bits + (size_t)t * c->ntiles;
         a.r_next = c->r + (size_t)((t + 1) & 1) * nb;
         a.r_cur = c->r + (size_t)(t & 1) * nb;
 
@@ -905,6 +908,7 @@ gabm_status backward_core(gabm_ctx *c, int T) {
     CK(cudaMemsetAsync(c->sig, 0, sizeof(int32_t) * (size_t)c->G * (ld + 1), s));
     CK(cudaMemsetAsync(c->emax, 0, sizeof(int32_t) * (size_t)c->G * (ld + 1), s));
     if (c->soft) CK(cudaMemsetAsync(c->A, 0, sizeof(float) * (size_t)c->n_rows, s));   // dL/ds(T) = 0
+
     if (!c->batched && c->policy != GABM_STORE_LAMBDA && !c->symmetric && !c->lam_tmp)
         TRY(dalloc(c, &c->lam_tmp, (size_t)c->n_rows));
     return run_day_loop(c, kLoopBackward, 0, T);
@@ -1186,8 +1190,6 @@ gabm_status gabm_create(const gabm_graph_desc *graphs, int num_graphs, int sets_
     if (sets_per_graph < 1) return fail(nullptr, GABM_EINVAL, "sets_per_graph must be >= 1");
     if (sets_per_graph > kMaxSets) return fail(nullptr, GABM_EUNSUPPORTED, "sets_per_graph > %d", kMaxSets);
     TRY(validate_model(model));
-    if (sets_per_graph > 1 && model->lambda_policy != GABM_STORE_LAMBDA)
-        return fail(nullptr, GABM_EUNSUPPORTED, "sets_per_graph > 1 needs GABM_STORE_LAMBDA in this build");
     if (model->relax_mode == GABM_SOFT && (sets_per_graph > 1 || model->lambda_policy != GABM_STORE_LAMBDA))
         return fail(nullptr, GABM_EUNSUPPORTED, "GABM_SOFT needs sets_per_graph = 1 and GABM_STORE_LAMBDA in this build");
 
@@ -1277,6 +1279,8 @@ gabm_status gabm_create(const gabm_graph_desc *graphs, int num_graphs, int sets_
     }
     HostSell sell_in, sell_out;
     const bool batched = sets_per_graph > 1;
+    if (batched && model->lambda_policy != GABM_STORE_LAMBDA && !symmetric)
+        return fail(nullptr, GABM_EUNSUPPORTED, "sets_per_graph > 1 with GABM_RECOMPUTE needs symmetric weights in this build");
     if (!batched && (!build_sell(h_rowptr, h_col, h_w, n_rows, sell_in) ||
                      (!symmetric && !build_sell(t_rowptr, t_col, t_w, n_rows, sell_out))))
         return fail(nullptr, GABM_EUNSUPPORTED, "SELL-32 layout needs >= 2^32 entries");
@@ -1586,6 +1590,7 @@ gabm_status gabm_forward(gabm_ctx *ctx, int T, const float *R, const float *m, c
                                    dev ? counts : nullptr, s));
     c->T_last = T;
     c->lam_from = c->policy == GABM_STORE_LAMBDA ? t0 : -1;
+    c->bits_from = t0;
     c->last_from_seeding = !c->resumed;
     c->resumed = false;
     c->t0_next = 0;
@@ -1632,6 +1637,8 @@ gabm_status gabm_backward_table(gabm_ctx *ctx, const double *gD, double *dR, dou
                                 double *dc, int mem_space) {
     if (!ctx) return fail(nullptr, GABM_EINVAL, "ctx is NULL");
     if (!dc) return fail(ctx, GABM_EINVAL, "dc is required");
+    if (ctx->batched && ctx->policy != GABM_STORE_LAMBDA)
+        return fail(ctx, GABM_EUNSUPPORTED, "the table adjoint of several sets per graph needs GABM_STORE_LAMBDA in this build");
     return backward_impl(ctx, gD, dR, dm, dS_age, dc, mem_space);
 }
 
@@ -1641,6 +1648,9 @@ static gabm_status backward_impl(gabm_ctx *c, const double *gD, double *dR, doub
     if (!c) return fail(nullptr, GABM_EINVAL, "ctx is NULL");
     TRY(check_ms(c, mem_space));
     if (c->T_last < 1) return fail(c, GABM_ESTATE, "backward needs a forward first");
+    if (c->batched && c->bits_from != 0)
+        return fail(c, GABM_ESTATE, "several sets per graph: the backward needs a forward over days 0..T-1 "
+                    "(its day bitmaps and counts)");
     if (c->policy == GABM_STORE_LAMBDA && c->lam_from != 0)
         return fail(c, GABM_ESTATE, "stored lambdas do not cover days 0..T-1 (use GABM_RECOMPUTE to replay a set state)");
     if (!gD || !dR || !dm || !dS_age) return fail(c, GABM_EINVAL, "gD, dR, dm and dS_age are required");
@@ -1741,6 +1751,8 @@ gabm_status gabm_get_lambda(gabm_ctx *ctx, int t, float *lam_out, int mem_space)
         lam_t = c->lam + (size_t)t * c->n_rows * c->Bp;
     } else {
         // recomputed from the current state, which (no reinfection) fixes every earlier day
+        if (c->batched || c->two_hop)
+            return fail(c, GABM_EUNSUPPORTED, "lambda on request under GABM_RECOMPUTE is built for one-hop graphs of one set");
         if (c->T_last < 1 || t < 0 || t >= c->T_last)
             return fail(c, GABM_ESTATE, "day %d is not before the last forward's horizon", t);
         if (!c->lam_tmp) TRY(dalloc(c, &c->lam_tmp, (size_t)c->n_rows));

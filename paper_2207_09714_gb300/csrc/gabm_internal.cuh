@@ -259,6 +259,7 @@ struct BwdBatchArgs {
     int ld_sig;
     int Bw, s0;                  // row width of the per-agent arrays; first set of this launch
     double *dc_tile;             // [ntiles][L][Bw] per-tile sums of the table adjoint over days, or nullptr
+    const uint32_t *bits_t;      // recompute policy (lam_t == nullptr): [ntiles] rows infectious on day t in any set
 };
 
 // Schedules: spl sets per lane (2, 4 or 8; Bp / spl lanes share a row).

@@ -78,9 +78,10 @@ def test_create_rejects_bad_models(lib):
     _expect(capi.GABM_EINVAL, [pop], _md(lambda_policy=7))
     _expect(capi.GABM_EINVAL, [pop], _md(), sets=0)
     _expect(capi.GABM_EINVAL, [], _md())
-    # parameter sets per graph: up to 64, with the lambda store
+    # parameter sets per graph: up to 64; without the lambda store only on symmetric weights
     _expect(capi.GABM_EUNSUPPORTED, [pop], _md(), sets=65)
-    _expect(capi.GABM_EUNSUPPORTED, [pop], _md(lambda_policy=capi.GABM_RECOMPUTE), sets=4)
+    _expect(capi.GABM_EUNSUPPORTED, [synth.random_directed(64, 4.0, seed=3)],
+            _md(lambda_policy=capi.GABM_RECOMPUTE), sets=4)
 
 
 def test_null_handles_are_safe(lib):

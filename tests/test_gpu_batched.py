@@ -303,3 +303,36 @@ def test_batched_long_horizon_beyond_fp32_range():
         check_adjoint(dS[s], g["dS"], f"dS[{s}]")
         checked += 1
     assert checked >= 2
+
+
+@pytest.mark.parametrize("B", [6, 64])
+def test_recompute_policy_is_bitwise_the_store_policy(B):
+    """Several sets per graph without the lambda store: the backward sums lambda again
+    from the final exposure days, bitwise the forward's, so the adjoint is bitwise that of
+    the store policy.  A backward needs a forward over days 0..T-1 (after a forward from a
+    set state it is refused)."""
+    pop = synth.population_small(n=5000, seed=13)
+    T = 24
+    R, m, S = _params(B, T, 90 + B)
+    y = np.stack([synth.target_curve(T, pop.n, seed=s, level=5e-5) for s in range(B)])
+    outs = {}
+    for policy in (capi.GABM_STORE_LAMBDA, capi.GABM_RECOMPUTE):
+        ctx = capi.gabm_create([pop], model(seed=3, policy=policy), sets_per_graph=B)
+        Rd, md_, Sd, yd = to_dev(R, m, S, y)
+        D, _ = capi.gabm_forward(ctx, T, Rd, md_, Sd, [10] * B)
+        _, gD = capi.gabm_mse_loss(ctx, yd)
+        outs[policy] = [D.cpu().numpy()] + [x.cpu().numpy() for x in capi.gabm_backward(ctx, gD)]
+        if policy == capi.GABM_RECOMPUTE:
+            again = [x.cpu().numpy() for x in capi.gabm_backward(ctx, gD)]   # a second sweep, same result
+            for a, b in zip(outs[policy][1:], again):
+                assert np.array_equal(a, b)
+            with pytest.raises(capi.GabmError) as ei:
+                capi.gabm_backward_table(ctx, gD)
+            assert ei.value.status == capi.GABM_EUNSUPPORTED
+            capi.gabm_set_state(ctx, T, capi.gabm_get_state(ctx))
+            capi.gabm_forward(ctx, T, Rd, md_, Sd)
+            with pytest.raises(capi.GabmError) as ei:
+                capi.gabm_backward(ctx, gD)
+            assert ei.value.status == capi.GABM_ESTATE
+    for a, b in zip(outs[capi.GABM_STORE_LAMBDA], outs[capi.GABM_RECOMPUTE]):
+        assert np.array_equal(a, b)
