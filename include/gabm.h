@@ -101,7 +101,8 @@ typedef struct {
  * T_s stage transmissibility folded into c; App. D: infectiousness profile). */
 typedef struct {
     int tau_EI, tau_IR;   /* days E->I and I->RM; 1 <= each, L = sum <= GABM_MAX_L */
-    const float *c;       /* host [L]: infectiousness by days since exposure, c[0] = 0, c >= 0 */
+    const float *c;       /* host [L]: infectiousness by days since exposure, c[0] = 0, c >= 0
+                           * (with tau_IM > 0: L = tau_EI + max(tau_IR, tau_IM)) */
     float gumbel_tau;     /* relaxation temperature; this build supports 1.0 */
     int relax_mode;       /* GABM_HARD_ST, or GABM_SOFT (sets_per_graph = 1 and GABM_STORE_LAMBDA):
                            * the fixed-noise soft relaxation -- every agent draws every day
@@ -112,6 +113,18 @@ typedef struct {
     int lambda_policy;    /* GABM_STORE_LAMBDA or GABM_RECOMPUTE */
     uint64_t seed;        /* Philox key */
     int agent_order;      /* GABM_ORDER_INPUT or GABM_ORDER_BFS (device layout only) */
+    int tau_IM;           /* 0: the single RM exit at L with expected deaths D_t = m_t newRM(t)
+                           * (Sec. 3.1 Aggregate).  > 0: the sampled R/M split -- the mortality
+                           * stage M with its own I->M time (Sec. 3.1 lists tau_IM in theta_P):
+                           * an agent exposed on day d draws its fate on its I-entry day
+                           * t_I = d + tau_EI (day 0 for exposures before -tau_EI): M iff v <
+                           * m_{t_I}, v the Philox uniform of (caller id, t_I, instance, stream 1).
+                           * It is infectious for 1 <= t - d < tau_EI + tau_IR (R) or
+                           * tau_EI + tau_IM (M), and D_t counts the M entries
+                           * (t - d = tau_EI + tau_IM).  The adjoint relaxes the fate draw like the
+                           * infection draw (straight-through, tau = 1), so dm comes from the
+                           * fates.  Needs GABM_HARD_ST, sets_per_graph = 1, GABM_STORE_LAMBDA and
+                           * a one-hop graph; no table adjoint (GABM_EUNSUPPORTED otherwise). */
 } gabm_model_desc;
 
 /* Build a ctx: validates and copies the graphs (GABM_EINVAL on bad data, before

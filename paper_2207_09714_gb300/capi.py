@@ -54,7 +54,8 @@ class _BipartiteDesc(ctypes.Structure):
 class _ModelDesc(ctypes.Structure):
     _fields_ = [("tau_EI", ctypes.c_int), ("tau_IR", ctypes.c_int), ("c", ctypes.c_void_p),
                 ("gumbel_tau", ctypes.c_float), ("relax_mode", ctypes.c_int),
-                ("lambda_policy", ctypes.c_int), ("seed", ctypes.c_uint64), ("agent_order", ctypes.c_int)]
+                ("lambda_policy", ctypes.c_int), ("seed", ctypes.c_uint64), ("agent_order", ctypes.c_int),
+                ("tau_IM", ctypes.c_int)]
 
 
 class _Schedule(ctypes.Structure):
@@ -191,6 +192,11 @@ class ModelDesc:
     gumbel_tau: float = 1.0
     relax_mode: int = GABM_HARD_ST
     agent_order: int = GABM_ORDER_BFS
+    tau_IM: int = 0          # > 0: the sampled R/M split (c then has tau_EI + max(tau_IR, tau_IM) entries)
+
+    @property
+    def L(self) -> int:
+        return int(self.tau_EI) + max(int(self.tau_IR), int(self.tau_IM))
 
 
 class GabmCtx:
@@ -227,8 +233,11 @@ def gabm_version() -> str:
 
 
 def _model_struct(model: ModelDesc, c: np.ndarray) -> _ModelDesc:
+    if c.size != model.L:
+        raise ValueError(f"c must have tau_EI + max(tau_IR, tau_IM) = {model.L} entries, got {c.size}")
     return _ModelDesc(int(model.tau_EI), int(model.tau_IR), _ptr(c, np.float32), float(model.gumbel_tau),
-                      int(model.relax_mode), int(model.lambda_policy), int(model.seed), int(model.agent_order))
+                      int(model.relax_mode), int(model.lambda_policy), int(model.seed), int(model.agent_order),
+                      int(model.tau_IM))
 
 
 def gabm_create_bipartite(graphs, model: ModelDesc, stream=None) -> GabmCtx:
@@ -365,7 +374,7 @@ def gabm_backward_table(ctx: GabmCtx, gD, dR=None, dm=None, dS_age=None, dc=None
     ms = _space(gD, dR, dm, dS_age, dc)
     cuda = ms == GABM_DEVICE
     I, T = ctx.instances, (ctx.T if ctx.T is not None else int(gD.shape[-1]))
-    L = ctx.model.tau_EI + ctx.model.tau_IR
+    L = ctx.model.L
     _shape(gD, (I, T), "gD")
     _shape(dR, (I, T), "dR")
     _shape(dm, (I, T), "dm")
@@ -388,7 +397,7 @@ def gabm_backward_table(ctx: GabmCtx, gD, dR=None, dm=None, dS_age=None, dc=None
 
 def gabm_set_infectiousness(ctx: GabmCtx, c):
     """Replace the model's infectiousness table c [L] (c[0] = 0) for the following forwards."""
-    L = ctx.model.tau_EI + ctx.model.tau_IR
+    L = ctx.model.L
     c = np.ascontiguousarray(np.asarray(c, np.float32).reshape(-1))
     if c.size != L:
         raise ValueError(f"c must have {L} entries, got {c.size}")

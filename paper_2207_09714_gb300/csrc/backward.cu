@@ -59,8 +59,13 @@ __device__ __forceinline__ void dc_accumulate(double *dc_tile, int tile, bool ha
 #ifndef GABM_BWD_MINBLOCKS
 #define GABM_BWD_MINBLOCKS 4
 #endif
-template <int MODE, bool DC>
-__global__ void __launch_bounds__(kBlock, (MODE == kBwdStore && !DC) ? GABM_BWD_MINBLOCKS : GABM_MINBLOCKS)
+// FATE (sampled R/M split, store policy): G of an exposure today takes the fate it would
+// draw (window L_R or L_M; the death term gD_{t+L_M} only if M-fated), and the rows exposed
+// today add H dphi/dm to day t + tau_EI's dL/dm, H = dL/dphi = sum over the days between
+// the two exits of +-c[k] gx(t+k) plus gD_{t+L_M}.  Rows exposed before day 0 keep their
+// gx in the ring for k_fate_seeds.
+template <int MODE, bool DC, bool FATE = false>
+__global__ void __launch_bounds__(kBlock, (MODE == kBwdStore && !DC && !FATE) ? GABM_BWD_MINBLOCKS : GABM_MINBLOCKS)
     k_bwd_day(const BwdDayArgs a) {
     constexpr int NARR = (MODE == kBwdFused) ? 2 : 1;
     constexpr bool SOFT = MODE == kBwdSoft;
@@ -124,7 +129,10 @@ __global__ void __launch_bounds__(kBlock, (MODE == kBwdStore && !DC) ? GABM_BWD_
                 fac_s[wib][lane] = (lane >= 1 && lane < L && t + lane <= T) ? exp2i(sg[t + lane] - sig_t) : 0.f;
             {
                 const size_t pg = (size_t)g * a.ldP;
-                gtail = (t + L < T) ? a.m_t[pg + t + L] * (float)a.gD[pg + t + L] * exp2i(-sig_t) : 0.f;
+                if constexpr (FATE)   // deaths are counted: dL/d(one M entry on day t + L_M)
+                    gtail = (t + a.fate.L_M < T) ? (float)a.gD[pg + t + a.fate.L_M] * exp2i(-sig_t) : 0.f;
+                else
+                    gtail = (t + L < T) ? a.m_t[pg + t + L] * (float)a.gD[pg + t + L] * exp2i(-sig_t) : 0.f;
             }
             __syncwarp();
             cur_g = g;
@@ -136,7 +144,9 @@ __global__ void __launch_bounds__(kBlock, (MODE == kBwdStore && !DC) ? GABM_BWD_
         const bool live = agent && (never || Ei >= 0);           // seeds are constants
         // soft relaxation: every agent carries susceptible mass and draws every day
         const bool isS = SOFT ? agent : live && (never || Ei >= t);
-        const bool needA = has_next && (SOFT ? agent : live && (never || Ei >= t + 2 - L));
+        // FATE: rows exposed before day 0 keep gx while day t+1 is inside their window
+        const bool needA = has_next && (SOFT ? agent : (live && (never || Ei >= t + 2 - L)) ||
+                                                       (FATE && agent && !never && Ei < 0 && t + 1 - Ei < L));
         if (!SOFT) cN += (agent && !never && t - Ei == L);
         // table adjoint: rows infectious on day t+1 (k = t+1-E in [1, L-1]) add gx(t+1) to
         // dc[k]; the non-seed ones are already gathered (needA), the seeds only for this
@@ -178,7 +188,7 @@ __global__ void __launch_bounds__(kBlock, (MODE == kBwdStore && !DC) ? GABM_BWD_
             }
         }
 
-        float v = 0.f;
+        float v = 0.f, pm = 0.f;
         int ai = 0;
         if (isS) {
             ai = a.age[row];
@@ -191,7 +201,21 @@ __global__ void __launch_bounds__(kBlock, (MODE == kBwdStore && !DC) ? GABM_BWD_
             float Lam;
             if constexpr (MODE == kBwdFused) Lam = sum[NARR - 1] * a.gr.inv_Dbar[g];
             else Lam = a.lam_t[row];
-            float G = gtail;
+            // FATE: the fate an exposure today would draw on day t + tau_EI
+            bool phi = false;
+            float vf = 0.5f;
+            int Lx = L;
+            if constexpr (FATE) {
+                if (t + a.tau_EI < T) {
+                    vf = fate_uniform(a.fate, caller_id(a.gr, row, g), t + a.tau_EI, g);
+                    phi = vf < a.m_t[(size_t)g * a.ldP + t + a.tau_EI];
+                }
+                Lx = phi ? a.fate.L_M : a.fate.L_R;
+            }
+            const int Lmin = FATE ? min(a.fate.L_R, a.fate.L_M) : L;
+            const float sgn = (FATE && a.fate.L_M > a.fate.L_R) ? 1.f : -1.f;
+            float G = (FATE && !phi) ? 0.f : gtail;
+            float H = gtail;
             if (has_next) G = __fmaf_rn(c_s[1], gx_mine * fac_s[wib][1], G);
             for (int k0 = 2; k0 < L; k0 += 8) {
                 float rv[8];
@@ -204,7 +228,19 @@ __global__ void __launch_bounds__(kBlock, (MODE == kBwdStore && !DC) ? GABM_BWD_
 #pragma unroll
                 for (int u = 0; u < 8; ++u) {
                     const int k = k0 + u;
-                    if (k < L && t + k < T) G = __fmaf_rn(c_s[k], rv[u] * fac_s[wib][k], G);
+                    if (k < L && t + k < T) {
+                        const float gk = rv[u] * fac_s[wib][k];
+                        if (!FATE || k < Lx) G = __fmaf_rn(c_s[k], gk, G);
+                        if (FATE && k >= Lmin) H = __fmaf_rn(sgn * c_s[k], gk, H);
+                    }
+                }
+            }
+            if constexpr (FATE) {
+                // the fate draw of today's exposure: dphi_soft/dm = v (1-v) / (m (1-v) + (1-m) v)^2
+                if (Ei == t && t + a.tau_EI < T) {
+                    const float mI = a.m_t[(size_t)g * a.ldP + t + a.tau_EI];
+                    const float den = __fmaf_rn(mI, 1.f - vf, (1.f - mI) * vf);
+                    pm = H * ((vf * (1.f - vf)) / (den * den));
                 }
             }
             float dy;
@@ -253,6 +289,12 @@ __global__ void __launch_bounds__(kBlock, (MODE == kBwdStore && !DC) ? GABM_BWD_
             outv = (double)mine;
         }
         if (lane < kAges) a.P_t[(size_t)tile * kAges + lane] = outv;
+        if constexpr (FATE) {
+            // dL/dm of day t + tau_EI from this tile's exposures today (fixed tree, FP64 out)
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) pm += __shfl_xor_sync(0xffffffffu, pm, o);
+            if (lane == 0 && t + a.tau_EI < T) a.Pm_t[tile] = ldexp((double)pm, sig_t);
+        }
 
         cur = nxt;
         nxt = nn;
@@ -328,6 +370,75 @@ __global__ void __launch_bounds__(kBlock) k_dc_seeds(Sell m, const int16_t *E, c
     }
 }
 
+// Sampled R/M split: the fate draws of agents exposed before day 0 (E < 0, drawn on day
+// t_I = max(E + tau_EI, 0)).  H = gD_{E+L_M} + sum over k between the two exits of
+// +-c[k] gx(E + k) over days 0..T-1: gx(0) gathered from r(0), later days from the ring
+// (day d in slot d mod (L-1), written while the sweep ran).  Each tile adds its seeds'
+// H dphi/dm per day t_I < tau_EI (warp tree in FP64) to Pm[t_I][tile], zeroed beforehand.
+__global__ void __launch_bounds__(kBlock) k_fate_seeds(Sell m, const int16_t *E, const float *r0, const float *ring,
+                                                       size_t ring_stride, int Lm1, GraphRef gr, FateRef f,
+                                                       const double *gD, const int32_t *sig, int ld_sig, int ntiles,
+                                                       int T, const float *c, double *Pm) {
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int nwarps = gridDim.x * (kBlock / 32);
+    const int L = Lm1 + 1;
+    const int Lmin = min(f.L_R, f.L_M);
+    const double sgn = f.L_M > f.L_R ? 1.0 : -1.0;
+    auto contrib = [&](uint32_t j, float w, bool valid, float (&out)[1]) { out[0] = w * ld_if(r0 + j, valid); };
+    const bool want[1] = {true};
+    for (int tile = blockIdx.x * (kBlock / 32) + wib; tile < ntiles; tile += nwarps) {
+        const int row = tile * kTile + lane;
+        const int Ei = E[row];
+        const int tI = max(Ei + f.tau_EI, 0);
+        const bool seed = Ei != kPad && Ei != kNever && Ei < 0 && tI < T;
+        if (!__any_sync(0xffffffffu, seed)) continue;
+        const int g = gr.tile_graph ? (int)gr.tile_graph[tile] : 0;
+        const int32_t *sg = sig + (size_t)g * ld_sig;
+        // gx(0), needed when day 0 lies between the two exits
+        const bool at0 = seed && -Ei >= Lmin && -Ei < L;
+        float sum[1];
+        row_sums<1>(m, m.slice_ptr[tile], m.row_len[row], at0, lane, contrib, want, sum);
+        double pm = 0.0;
+        if (seed) {
+            const size_t pg = (size_t)g * f.ldP;
+            double H = (Ei + f.L_M >= 0 && Ei + f.L_M < T) ? gD[pg + Ei + f.L_M] : 0.0;
+            for (int k = Lmin; k < L; ++k) {
+                const int d = Ei + k;
+                if (d < 0 || d >= T) continue;
+                const float gxs = d == 0 ? sum[0] : ring[(size_t)(d % Lm1) * ring_stride + row];
+                H += sgn * (double)c[k] * ldexp((double)gxs, sg[d]);
+            }
+            const float vf = fate_uniform(f, caller_id(gr, row, g), tI, g);
+            const double mI = (double)f.mort[pg + tI], v = (double)vf;
+            const double den = mI * (1.0 - v) + (1.0 - mI) * v;
+            pm = H * (v * (1.0 - v) / (den * den));
+        }
+        for (int d = 0; d < f.tau_EI && d < T; ++d) {
+            double x = (seed && tI == d) ? pm : 0.0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+            if (lane == 0 && x != 0.0) Pm[(size_t)d * ntiles + tile] = x;
+        }
+    }
+}
+
+// dm[g][t] = sum over the graph's tiles of Pm[t][tile] (fixed order, FP64).
+__global__ void __launch_bounds__(256) k_fate_dm(const double *Pm, int ntiles, const int32_t *graph_tile0,
+                                                 const int32_t *graph_ntiles, int T, double *dm) {
+    __shared__ double s[256];
+    const int t = blockIdx.x, g = blockIdx.y;
+    const int tile0 = graph_tile0[g], nt = graph_ntiles[g];
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < nt; i += blockDim.x) acc += Pm[(size_t)t * ntiles + tile0 + i];
+    s[threadIdx.x] = acc;
+    __syncthreads();
+    for (int h = 128; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h) s[threadIdx.x] += s[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) dm[(size_t)g * T + t] = s[0];
+}
+
 // dc[g][k] = sum over the graph's tiles of dc_tile[tile][k] (fixed order, FP64), k < L.
 __global__ void __launch_bounds__(256) k_dc_reduce(const double *dc_tile, const int32_t *graph_tile0,
                                                    const int32_t *graph_ntiles, int L, double *dc) {
@@ -374,7 +485,8 @@ __global__ void __launch_bounds__(256) k_bwd_reduce(const double *P, int ntiles,
         Q[((size_t)inst * T + t) * kAges + threadIdx.x] = ldexp(s[0][threadIdx.x], sig[(size_t)g * ld_sig + t]);
 }
 
-// dR_t = sum_a S_a Q[t][a];  dS_a = sum_t R_t Q[t][a];  dm_t = gD_t newRM(t).
+// dR_t = sum_a S_a Q[t][a];  dS_a = sum_t R_t Q[t][a];  dm_t = gD_t newRM(t) (not written
+// when both counts are NULL: the sampled R/M split's dm comes from k_fate_dm).
 __global__ void __launch_bounds__(256) k_bwd_finalize(const double *Q, const float *R, const float *S,
                                                       const double *gD, const int32_t *newRM,
                                                       const double *newRM_real, int ldP, int T, double *dR,
@@ -386,7 +498,7 @@ __global__ void __launch_bounds__(256) k_bwd_finalize(const double *Q, const flo
         for (int b = 0; b < kAges; ++b) acc += (double)S[inst * kAges + b] * q[b];
         dR[(size_t)inst * T + t] = acc;
         const size_t pi = (size_t)inst * ldP + t;
-        dm[(size_t)inst * T + t] = gD[pi] * (newRM_real ? newRM_real[pi] : (double)newRM[pi]);
+        if (newRM_real || newRM) dm[(size_t)inst * T + t] = gD[pi] * (newRM_real ? newRM_real[pi] : (double)newRM[pi]);
     }
     if (threadIdx.x < kAges) {
         const int b = threadIdx.x;
@@ -400,6 +512,11 @@ __global__ void __launch_bounds__(256) k_bwd_finalize(const double *Q, const flo
 
 cudaError_t launch_bwd_day(const BwdDayArgs &a, int grid, cudaStream_t s) {
     const bool dc = a.dc_tile != nullptr;
+    if (a.fate.L_M > 0) {   // store policy, plain instance only (checked at creation)
+        if (a.mode != kBwdStore || dc) return cudaErrorInvalidValue;
+        k_bwd_day<kBwdStore, false, true><<<grid, kBlock, 0, s>>>(a);
+        return cudaGetLastError();
+    }
     switch (a.mode) {
         case kBwdStore:
             if (dc) k_bwd_day<kBwdStore, true><<<grid, kBlock, 0, s>>>(a);
@@ -424,6 +541,19 @@ cudaError_t launch_dc_seeds(Sell m_out, const int16_t *E, const float *r0, Graph
     return cudaGetLastError();
 }
 
+cudaError_t launch_fate_seeds(Sell m_out, const int16_t *E, const float *r0, const float *ring, size_t ring_stride,
+                              int Lm1, GraphRef gr, FateRef f, const double *gD, const int32_t *sig, int ld_sig,
+                              int ntiles, int T, const float *c, double *Pm, int grid, cudaStream_t s) {
+    k_fate_seeds<<<grid, kBlock, 0, s>>>(m_out, E, r0, ring, ring_stride, Lm1, gr, f, gD, sig, ld_sig, ntiles, T, c, Pm);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fate_dm(const double *Pm, int ntiles, const int32_t *graph_tile0, const int32_t *graph_ntiles,
+                           int G, int T, double *dm, cudaStream_t s) {
+    if (T > 0) k_fate_dm<<<dim3(T, G), 256, 0, s>>>(Pm, ntiles, graph_tile0, graph_ntiles, T, dm);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_dc_reduce(const double *dc_tile, const int32_t *graph_tile0, const int32_t *graph_ntiles, int G,
                              int L, double *dc, cudaStream_t s) {
     k_dc_reduce<<<dim3(G, L), 256, 0, s>>>(dc_tile, graph_tile0, graph_ntiles, L, dc);
@@ -436,8 +566,12 @@ cudaError_t launch_lam_day(Sell m, const int16_t *E, const uint32_t *bits, Graph
     return cudaGetLastError();
 }
 
-int occupancy_bwd(int mode, bool dc) {
+int occupancy_bwd(int mode, bool dc, bool fate) {
     int blocks = 0;
+    if (fate) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_bwd_day<kBwdStore, false, true>, kBlock, 0);
+        return blocks > 0 ? blocks : 1;
+    }
     switch (mode) {
         case kBwdFused:
             if (dc) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_bwd_day<kBwdFused, true>, kBlock, 0);

@@ -38,7 +38,10 @@ struct gabm_ctx {
     float *s_hist = nullptr, *y_hist = nullptr;                 // [Tcap][n_rows] soft histories
     double *P_nrm = nullptr, *newRM_real = nullptr;             // [Tcap][ntiles], [I][Tcap]
     int32_t *sig = nullptr, *emax = nullptr;   // [G][Tcap+1] reverse-sweep scale exponents per graph and day
-    int tau_EI = 0, tau_IR = 0, L = 0;
+    int tau_EI = 0, tau_IR = 0, L = 0;   // L: the table's length, the longest infectious window
+    int tau_IM = 0, L_R = 0, L_M = 0;    // sampled R/M split (tau_IM > 0): exits at L_R and L_M
+    bool fate = false;
+    double *Pm = nullptr;                // [Tcap][ntiles] fate-draw shares of dL/dm by draw day
     float c[kMaxL] = {0};
     uint64_t seed = 0;
     int policy = GABM_STORE_LAMBDA;
@@ -102,6 +105,7 @@ struct gabm_ctx {
     int bits_from = -1;             // first day whose infectious bitmap the last forward wrote
 
     int grid_fwd = 0, grid_bwd = 0, grid_bwd_dc = 0;   // grid_bwd_dc: the table-adjoint instance
+    int grid_bwd_fate = 0;                              // the sampled R/M split's instance
     bool smem_bits = false;         // forward keeps the infectious bitmap in shared memory
     // agent-location graphs: the location hop (SELL-32 of locations -> members) and its values
     bool two_hop = false;
@@ -224,8 +228,9 @@ struct HostGraph {
 gabm_status validate_model(const gabm_model_desc *md) {
     if (!md) return fail(nullptr, GABM_EINVAL, "model descriptor is NULL");
     if (md->tau_EI < 1 || md->tau_IR < 1) return fail(nullptr, GABM_EINVAL, "tau_EI and tau_IR must be >= 1");
-    const int L = md->tau_EI + md->tau_IR;
-    if (L > kMaxL) return fail(nullptr, GABM_EINVAL, "tau_EI + tau_IR = %d exceeds %d", L, kMaxL);
+    if (md->tau_IM < 0) return fail(nullptr, GABM_EINVAL, "tau_IM must be >= 0 (0: a single RM exit)");
+    const int L = md->tau_EI + std::max(md->tau_IR, md->tau_IM);
+    if (L > kMaxL) return fail(nullptr, GABM_EINVAL, "tau_EI + max(tau_IR, tau_IM) = %d exceeds %d", L, kMaxL);
     if (!md->c) return fail(nullptr, GABM_EINVAL, "infectiousness table c is NULL");
     if (md->c[0] != 0.0f) return fail(nullptr, GABM_EINVAL, "c[0] must be 0 (no onward infection on the day of exposure)");
     for (int k = 0; k < L; ++k)
@@ -424,7 +429,7 @@ gabm_status ensure_days(gabm_ctx *c, int T) {
     dfree(c, c->dR_s); dfree(c, c->dm_s); dfree(c, c->tile_ctr); dfree(c, c->bits); dfree(c, c->Pc);
     dfree(c, c->tile_new); dfree(c, c->newinf);
     dfree(c, c->s_hist); dfree(c, c->y_hist); dfree(c, c->P_nrm); dfree(c, c->newRM_real);
-    dfree(c, c->sig); dfree(c, c->emax);
+    dfree(c, c->sig); dfree(c, c->emax); dfree(c, c->Pm);
     c->Tcap = 0;
     const size_t IT = (size_t)c->I * cap;
     if (c->policy == GABM_STORE_LAMBDA) TRY(dalloc(c, &c->lam, (size_t)cap * c->n_rows * c->Bp));
@@ -435,6 +440,7 @@ gabm_status ensure_days(gabm_ctx *c, int T) {
     TRY(dalloc(c, &c->gD, IT));
     TRY(dalloc(c, &c->y, IT));
     TRY(dalloc(c, &c->P, (size_t)cap * c->ntiles * kAges * c->Bp));
+    if (c->fate) TRY(dalloc(c, &c->Pm, (size_t)cap * c->ntiles));
     if (c->soft) {
         TRY(dalloc(c, &c->s_hist, (size_t)cap * c->n_rows));
         TRY(dalloc(c, &c->y_hist, (size_t)cap * c->n_rows));
@@ -531,6 +537,18 @@ GraphRef graph_ref(const gabm_ctx *c) {
     gr.inv_Dbar = c->d_inv_Dbar;
     gr.orig_id = c->d_orig_id;
     return gr;
+}
+
+// The sampled R/M split's constants and the staged mortality (L_M = 0: the single RM exit).
+FateRef fate_ref(const gabm_ctx *c) {
+    FateRef f;
+    f.mort = c->m;
+    f.ldP = c->Tcap;
+    f.tau_EI = c->tau_EI;
+    f.L_R = c->fate ? c->L_R : 0;
+    f.L_M = c->fate ? c->L_M : 0;
+    f.seed = c->seed;
+    return f;
 }
 
 gabm_status check_ms(gabm_ctx *c, int ms) {
@@ -671,9 +689,13 @@ gabm_status forward_days_plain(gabm_ctx *c, int t0, int T, cudaStream_t s) {
     a.tau_EI = c->tau_EI;
     a.L = c->L;
     a.seed = c->seed;
+    a.fate = fate_ref(c);
     for (int k = 0; k < kMaxL; ++k) a.c[k] = k < c->L ? c->c[k] : 0.f;
-    if (t0 < T) LAUNCH(launch_infectious_bits(c->e, t0, 1, c->L, c->ntiles, c->bits + (size_t)t0 * c->ntiles,
-                                              (size_t)c->ntiles, s));
+    if (t0 < T && c->fate)
+        LAUNCH(launch_infectious_bits_fate(c->e, graph_ref(c), a.fate, t0, c->ntiles, c->bits + (size_t)t0 * c->ntiles, s));
+    else if (t0 < T)
+        LAUNCH(launch_infectious_bits(c->e, t0, 1, c->L, c->ntiles, c->bits + (size_t)t0 * c->ntiles,
+                                      (size_t)c->ntiles, s));
     for (int t = t0; t < T; ++t) {
         a.t = t;
         a.lam_out = c->policy == GABM_STORE_LAMBDA ? c->lam + (size_t)t * c->n_rows : nullptr;
@@ -730,6 +752,11 @@ gabm_status backward_days_plain(gabm_ctx *c, int T, cudaStream_t s) {
     a.ld_sig = ld + 1;
     a.dc_tile = c->want_dc ? c->dc_tile : nullptr;
     a.self_r = a.self_q = nullptr;
+    a.fate = fate_ref(c);
+    a.Pm_t = nullptr;
+    const int grid = c->fate ? c->grid_bwd_fate : (a.dc_tile ? c->grid_bwd_dc : c->grid_bwd);
+    if (c->fate)   // draw days 0..tau_EI-1 hold only the seeds' shares (k_fate_seeds)
+        CK(cudaMemsetAsync(c->Pm, 0, sizeof(double) * (size_t)std::min(c->tau_EI, T) * c->ntiles, s));
     for (int t = T - 1; t >= 0; --t) {
         a.bits_t = (mode == kBwdFused || mode == kBwdSplit) ? c->bits + (size_t)t * c->ntiles : nullptr;
         a.t = t;
@@ -752,11 +779,15 @@ gabm_status backward_days_plain(gabm_ctx *c, int T, cudaStream_t s) {
             a.r_next = c->locv;
         }
         a.P_t = c->P + (size_t)t * c->ntiles * kAges;
+        if (c->fate) a.Pm_t = (t + c->tau_EI < T) ? c->Pm + (size_t)(t + c->tau_EI) * c->ntiles : nullptr;
         for (int k = 0; k < kMaxL; ++k) a.ring_slot[k] = (k >= 1 && k < c->L) ? (t + k) % Lm1 : 0;
         prof_begin(c, 1);
-        LAUNCH(launch_bwd_day(a, a.dc_tile ? c->grid_bwd_dc : c->grid_bwd, s));
+        LAUNCH(launch_bwd_day(a, grid, s));
         prof_end(c, 1);
     }
+    if (c->fate)   // the fate draws of agents exposed before day 0 (r of day 0 is in slot 0)
+        LAUNCH(launch_fate_seeds(sell_view(c, true), c->e, c->r, c->ring, (size_t)c->n_rows, Lm1, graph_ref(c), a.fate,
+                                 c->gD, c->sig, ld + 1, c->ntiles, T, c->c_dev, c->Pm, c->grid_bwd, s));
     if (a.dc_tile) {   // the seeds' share through day 0 (r of day 0 is in slot 0)
         const float *r0 = c->r;
         if (c->two_hop) {
@@ -927,11 +958,13 @@ void apply_schedule(gabm_ctx *c) {
         c->grid_fwd = c->num_sms * occupancy_fwd_b(c->Bp, c->spl_fwd, c->kahan_b);
         c->grid_bwd = c->num_sms * occupancy_bwd_b(c->bwd_chunk, c->spl_bwd, c->kahan_b);
     } else {
+        if (c->fate) c->smem_bits = false;   // the split's forward reads the bitmap from global memory
         const int bps = c->smem_bits ? occupancy_fwd(c->ntiles, true) : 0;
         if (c->smem_bits && bps <= 0) c->smem_bits = false;
         c->grid_fwd = c->num_sms * (c->smem_bits ? bps : occupancy_fwd(c->ntiles, false));
         c->grid_bwd = c->num_sms * occupancy_bwd(mode);
         c->grid_bwd_dc = c->num_sms * occupancy_bwd(mode, true);
+        c->grid_bwd_fate = c->num_sms * occupancy_bwd(mode, false, true);
     }
     if (c->two_hop) {
         c->smem_bits = false;
@@ -942,6 +975,7 @@ void apply_schedule(gabm_ctx *c) {
     if (!c->smem_bits && c->grid_fwd > max_grid) c->grid_fwd = max_grid;
     if (c->grid_bwd > max_grid) c->grid_bwd = max_grid;
     if (c->grid_bwd_dc > max_grid) c->grid_bwd_dc = max_grid;
+    if (c->grid_bwd_fate > max_grid) c->grid_bwd_fate = max_grid;
     for (auto &g : c->loop_graph) drop_graph(g);   // captured launches carry the old schedule
 }
 
@@ -1027,7 +1061,11 @@ static gabm_status create_on_device(const HostLayout &H, const gabm_model_desc *
     }
     c->tau_EI = model->tau_EI;
     c->tau_IR = model->tau_IR;
-    c->L = model->tau_EI + model->tau_IR;
+    c->tau_IM = model->tau_IM;
+    c->fate = model->tau_IM > 0;
+    c->L_R = model->tau_EI + model->tau_IR;
+    c->L_M = model->tau_EI + model->tau_IM;
+    c->L = model->tau_EI + std::max(model->tau_IR, model->tau_IM);
     for (int k = 0; k < c->L; ++k) c->c[k] = model->c[k];
     c->seed = model->seed;
     c->policy = model->lambda_policy;
@@ -1192,6 +1230,10 @@ gabm_status gabm_create(const gabm_graph_desc *graphs, int num_graphs, int sets_
     TRY(validate_model(model));
     if (model->relax_mode == GABM_SOFT && (sets_per_graph > 1 || model->lambda_policy != GABM_STORE_LAMBDA))
         return fail(nullptr, GABM_EUNSUPPORTED, "GABM_SOFT needs sets_per_graph = 1 and GABM_STORE_LAMBDA in this build");
+    if (model->tau_IM > 0 && (model->relax_mode != GABM_HARD_ST || sets_per_graph > 1 ||
+                              model->lambda_policy != GABM_STORE_LAMBDA))
+        return fail(nullptr, GABM_EUNSUPPORTED, "the sampled R/M split (tau_IM > 0) needs GABM_HARD_ST, "
+                    "sets_per_graph = 1 and GABM_STORE_LAMBDA in this build");
 
     // ---- host side: validate, concatenate, transpose ----
     std::vector<HostGraph> hg((size_t)num_graphs);
@@ -1329,8 +1371,9 @@ gabm_status gabm_create_bipartite(const gabm_bipartite_desc *graphs, int num_gra
     *out = nullptr;
     if (!graphs || num_graphs < 1 || num_graphs > 65535) return fail(nullptr, GABM_EINVAL, "need 1..65535 graphs");
     TRY(validate_model(model));
-    if (model->relax_mode != GABM_HARD_ST || model->lambda_policy != GABM_STORE_LAMBDA)
-        return fail(nullptr, GABM_EUNSUPPORTED, "agent-location graphs need GABM_HARD_ST and GABM_STORE_LAMBDA in this build");
+    if (model->relax_mode != GABM_HARD_ST || model->lambda_policy != GABM_STORE_LAMBDA || model->tau_IM > 0)
+        return fail(nullptr, GABM_EUNSUPPORTED, "agent-location graphs need GABM_HARD_ST, GABM_STORE_LAMBDA and "
+                    "tau_IM = 0 in this build");
     int sigma = 1024;
     if (const char *f = getenv("GABM_SELL_SIGMA")) sigma = std::max(1, atoi(f));
     const int G = num_graphs;
@@ -1586,7 +1629,7 @@ gabm_status gabm_forward(gabm_ctx *ctx, int T, const float *R, const float *m, c
         LAUNCH(launch_soft_finalize(c->P_nrm, c->ntiles, c->d_tile0, c->d_ntiles, c->m, ld, T, c->G, c->newRM_real,
                                     c->D, dev ? D : nullptr, s));
     else
-        LAUNCH(launch_fwd_finalize(c->newRM, c->counts, c->m, ld, t0, T, c->I, c->D, dev ? D : nullptr,
+        LAUNCH(launch_fwd_finalize(c->newRM, c->counts, c->fate ? nullptr : c->m, ld, t0, T, c->I, c->D, dev ? D : nullptr,
                                    dev ? counts : nullptr, s));
     c->T_last = T;
     c->lam_from = c->policy == GABM_STORE_LAMBDA ? t0 : -1;
@@ -1639,6 +1682,7 @@ gabm_status gabm_backward_table(gabm_ctx *ctx, const double *gD, double *dR, dou
     if (!dc) return fail(ctx, GABM_EINVAL, "dc is required");
     if (ctx->batched && ctx->policy != GABM_STORE_LAMBDA)
         return fail(ctx, GABM_EUNSUPPORTED, "the table adjoint of several sets per graph needs GABM_STORE_LAMBDA in this build");
+    if (ctx->fate) return fail(ctx, GABM_EUNSUPPORTED, "the table adjoint of the sampled R/M split is not built");
     return backward_impl(ctx, gD, dR, dm, dS_age, dc, mem_space);
 }
 
@@ -1675,10 +1719,12 @@ static gabm_status backward_impl(gabm_ctx *c, const double *gD, double *dR, doub
         if (c->batched) LAUNCH(launch_dc_reduce_b(c->dc_tile, c->d_tile0, c->d_ntiles, c->G, c->B, c->Bp, c->L, out, s));
         else LAUNCH(launch_dc_reduce(c->dc_tile, c->d_tile0, c->d_ntiles, c->G, c->L, out, s));
     }
-    LAUNCH(launch_bwd_finalize(c->Q, c->R, c->S, c->gD, c->batched ? c->newRM : c->newRM_b,
+    LAUNCH(launch_bwd_finalize(c->Q, c->R, c->S, c->gD,
+                               c->fate ? nullptr : (c->batched ? c->newRM : c->newRM_b),
                                c->soft ? c->newRM_real : nullptr, ld, T, c->I,
                                dev ? dR : c->dR_s,
                                dev ? dm : c->dm_s, dev ? dS_age : c->dS_s, s));
+    if (c->fate) LAUNCH(launch_fate_dm(c->Pm, c->ntiles, c->d_tile0, c->d_ntiles, c->G, T, dev ? dm : c->dm_s, s));
     if (!dev) {
         CK(cudaMemcpyAsync(dR, c->dR_s, sizeof(double) * (size_t)c->I * T, cudaMemcpyDeviceToHost, s));
         CK(cudaMemcpyAsync(dm, c->dm_s, sizeof(double) * (size_t)c->I * T, cudaMemcpyDeviceToHost, s));
@@ -1815,7 +1861,7 @@ gabm_status gabm_set_schedule(gabm_ctx *ctx, const gabm_schedule *sched) {
         c->spl_bwd = sched->bwd_sets_per_lane;
         c->bwd_chunk = chunk;
     } else {
-        if (sched->fwd_smem_bitmap && (c->soft || c->two_hop || occupancy_fwd(c->ntiles, true) <= 0))
+        if (sched->fwd_smem_bitmap && (c->soft || c->two_hop || c->fate || occupancy_fwd(c->ntiles, true) <= 0))
             return fail(c, GABM_EINVAL, "the infectious bitmap (%d words) does not fit in shared memory", c->ntiles);
         c->smem_bits = sched->fwd_smem_bitmap != 0;
     }
@@ -1841,7 +1887,7 @@ gabm_status gabm_autotune(gabm_ctx *ctx, int repetitions) {
             if (batch_config_ok(c->Bp, spl)) fc.push_back(gabm_schedule{spl, cur.bwd_sets_per_lane, 0, cur.bwd_sets_per_launch});
     } else {
         fc.push_back(gabm_schedule{0, 0, 0, 0});
-        if (!c->soft && !c->two_hop && occupancy_fwd(c->ntiles, true) > 0) fc.push_back(gabm_schedule{0, 0, 1, 0});
+        if (!c->soft && !c->two_hop && !c->fate && occupancy_fwd(c->ntiles, true) > 0) fc.push_back(gabm_schedule{0, 0, 1, 0});
     }
     cudaEvent_t ev[2];
     for (auto &e : ev) CK(cudaEventCreate(&e));
@@ -1902,7 +1948,7 @@ gabm_status gabm_autotune(gabm_ctx *ctx, int repetitions) {
         LAUNCH(launch_soft_finalize(c->P_nrm, c->ntiles, c->d_tile0, c->d_ntiles, c->m, ld, T, c->G, c->newRM_real,
                                     c->D, nullptr, s));
     else
-        LAUNCH(launch_fwd_finalize(c->newRM, c->counts, c->m, ld, 0, T, c->I, c->D, nullptr, nullptr, s));
+        LAUNCH(launch_fwd_finalize(c->newRM, c->counts, c->fate ? nullptr : c->m, ld, 0, T, c->I, c->D, nullptr, nullptr, s));
     CK(cudaStreamSynchronize(s));
     return GABM_OK;
 }

@@ -46,7 +46,10 @@ __device__ __forceinline__ void flush_counts_warp(int32_t *counts, int32_t *newR
 // PULL (agent-location graphs): the row's entries are the agent's locations, and each
 // contributes w_il * P_l from the day's location pressures (a.pull) instead of a marked
 // neighbour's infectiousness.
-template <bool SMEM_BITS, int NT, int MINB, bool PULL = false>
+// FATE (sampled R/M split): a row's exit from I is L_R or L_M after exposure by its fate,
+// drawn again where needed (the day before the earlier exit through the later one), and
+// the deaths counted are the M entries.
+template <bool SMEM_BITS, int NT, int MINB, bool PULL = false, bool FATE = false>
 __global__ void __launch_bounds__(NT, MINB) k_fwd_day(const FwdDayArgs a) {
     constexpr int NW = NT / 32;
     extern __shared__ uint32_t bits_s[];
@@ -97,10 +100,19 @@ __global__ void __launch_bounds__(NT, MINB) k_fwd_day(const FwdDayArgs a) {
         }
         const int row = tile * kTile + lane;
         const bool isS = (ei == kNever);
+        int Lx = L;   // this row's exit from I
+        if constexpr (FATE) {
+            const int k = t - ei;
+            bool phi = false;
+            if (ei != kPad && !isS && k + 1 >= min(a.fate.L_R, a.fate.L_M) && k <= L)
+                phi = fate_M(a.fate, caller_id(a.gr, row, g), ei, g, t + 1);
+            Lx = phi ? a.fate.L_M : a.fate.L_R;
+            if (ei != kPad && !isS) cN += (phi && k == a.fate.L_M);
+        }
         if (ei != kPad && !isS) {
             const int k = t - ei;
-            if (k < tau_EI) ++cE; else if (k < L) ++cI; else ++cR;
-            cN += (k == L);
+            if (k < tau_EI) ++cE; else if (k < Lx) ++cI; else ++cR;
+            if (!FATE) cN += (k == L);
         }
         cS += isS;
 
@@ -123,7 +135,7 @@ __global__ void __launch_bounds__(NT, MINB) k_fwd_day(const FwdDayArgs a) {
         }
         // rows infectious tomorrow (susceptible and padding rows fall outside the window)
         const int kn = t + 1 - e_next;
-        const unsigned inf_next = __ballot_sync(0xffffffffu, (unsigned)(kn - 1) < (unsigned)(L - 1));
+        const unsigned inf_next = __ballot_sync(0xffffffffu, (unsigned)(kn - 1) < (unsigned)(Lx - 1));
         if (lane == 0) a.bits_next[tile] = inf_next;
 
         cur = nxt;
@@ -267,6 +279,23 @@ __global__ void __launch_bounds__(256) k_soft_finalize(const double *P_nrm, int 
 
 // One warp per tile: for every day d of the range, the ballot of rows with
 // 1 <= d - e < L.
+__global__ void k_infectious_bits_fate(const int16_t *e, GraphRef gr, FateRef f, int t, int ntiles, uint32_t *bits) {
+    const int lane = threadIdx.x & 31;
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    for (int tile = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; tile < ntiles; tile += warps) {
+        const int row = tile * kTile + lane;
+        const int ei = e[row];
+        const int k = t - ei;
+        int Lx = f.L_R;
+        if (ei != kPad && ei != kNever && k >= min(f.L_R, f.L_M) && k < max(f.L_R, f.L_M)) {
+            const int g = gr.tile_graph ? (int)gr.tile_graph[tile] : 0;
+            Lx = fate_M(f, caller_id(gr, row, g), ei, g, t + 1) ? f.L_M : f.L_R;
+        }
+        const unsigned b = __ballot_sync(0xffffffffu, (unsigned)(k - 1) < (unsigned)(Lx - 1));
+        if (lane == 0) bits[tile] = b;
+    }
+}
+
 __global__ void k_infectious_bits(const int16_t *e, int t0, int ndays, int L, int ntiles, uint32_t *bits,
                                   size_t day_stride) {
     const int lane = threadIdx.x & 31;
@@ -468,7 +497,8 @@ __global__ void k_caller_to_rows(const T *src, T *dst, GraphRef gr, const int32_
     }
 }
 
-// D_t = m_t * newRM(t) in FP64 (Aggregate, Sec. 3.1); copies counts out.
+// D_t = m_t * newRM(t) in FP64 (Aggregate, Sec. 3.1), or the counted M entries when m is
+// NULL (sampled R/M split); copies counts out.
 __global__ void k_fwd_finalize(const int32_t *newRM, const int32_t *counts, const float *m, int ldP,
                                int t0, int T, int I, double *D_ctx, double *D_out, int32_t *counts_out) {
     const int total = I * T;
@@ -476,7 +506,7 @@ __global__ void k_fwd_finalize(const int32_t *newRM, const int32_t *counts, cons
         const int inst = idx / T, t = idx - inst * T;
         if (t < t0) continue;
         const size_t src = (size_t)inst * ldP + t;
-        const double d = (double)m[src] * (double)newRM[src];
+        const double d = m ? (double)m[src] * (double)newRM[src] : (double)newRM[src];
         D_ctx[src] = d;
         if (D_out) D_out[idx] = d;
         if (counts_out)
@@ -546,6 +576,14 @@ cudaError_t launch_infectious_bits(const int16_t *e, int t0, int ndays, int L, i
     return cudaGetLastError();
 }
 
+cudaError_t launch_infectious_bits_fate(const int16_t *e, GraphRef gr, FateRef f, int t, int ntiles, uint32_t *bits,
+                                        cudaStream_t s) {
+    int grid = (ntiles + 7) / 8;
+    if (grid > 65535) grid = 65535;
+    k_infectious_bits_fate<<<grid > 0 ? grid : 1, 256, 0, s>>>(e, gr, f, t, ntiles, bits);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_init_state(int16_t *e, const int32_t *row0, const int32_t *rows, int G,
                               int64_t n_rows, int B, int Bp, int grid, cudaStream_t s) {
     k_init_state<<<grid, 256, 0, s>>>(e, row0, rows, G, n_rows, B, Bp);
@@ -580,7 +618,9 @@ cudaError_t launch_seed_ties(const SeedArgs &a, int I, cudaStream_t s) {
 constexpr int kBitsBlock = 768;   // one block of 24 warps per SM when the bitmap lives in shared memory
 
 cudaError_t launch_fwd_day(const FwdDayArgs &a, int grid, bool smem_bits, cudaStream_t s) {
-    if (smem_bits && !a.pull) {
+    if (a.fate.L_M > 0) {
+        k_fwd_day<false, kBlock, GABM_MINBLOCKS, false, true><<<grid, kBlock, 0, s>>>(a);
+    } else if (smem_bits && !a.pull) {
         const size_t bytes = (size_t)a.ntiles * sizeof(uint32_t);
         k_fwd_day<true, kBitsBlock, 1><<<grid, kBitsBlock, bytes, s>>>(a);
     } else if (a.pull) {

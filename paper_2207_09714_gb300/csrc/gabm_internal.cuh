@@ -95,6 +95,30 @@ __device__ __forceinline__ uint32_t caller_id(const GraphRef &gr, int row, int g
     return gr.orig_id ? gr.orig_id[row] : (uint32_t)(row - gr.row0[g]);
 }
 
+// Sampled R/M split (Sec. 3.1 names a mortality stage M with its own I->M time tau_IM):
+// an agent exposed on day d draws its fate on its I-entry day t_I = d + tau_EI (day 0 for
+// exposures before -tau_EI) -- M with probability m_{t_I}, else R -- and leaves I at
+// L_M = tau_EI + tau_IM or L_R = tau_EI + tau_IR days after exposure.  Deaths are the
+// M entries.  L_M = 0 selects the base model's single RM exit.
+struct FateRef {
+    const float *mort;   // mortality m [I][ldP]
+    int ldP, tau_EI, L_R, L_M;
+    uint64_t seed;
+};
+
+// The fate's uniform v: Philox stream 1 of the agent's caller id on day t_I (stream 0 is
+// the infection draw); M iff v < m_{t_I}.
+__device__ __forceinline__ float fate_uniform(const FateRef &f, uint32_t id, int tI, int inst) {
+    return uniform_from_word(philox_word(f.seed, id, (uint32_t)tI, (uint32_t)inst, 1u));
+}
+
+// Whether agent `id`'s exposure on day d is M-fated; draws on or after day T are not made.
+__device__ __forceinline__ bool fate_M(const FateRef &f, uint32_t id, int d, int inst, int T) {
+    const int tI = max(d + f.tau_EI, 0);
+    if (tI >= T) return false;
+    return fate_uniform(f, id, tI, inst) < f.mort[(size_t)inst * f.ldP + tI];
+}
+
 // Edges of one orientation in SELL-32 layout (one slice per 32-row tile).
 struct Sell {
     const uint32_t *slice_ptr;  // [ntiles+1] first entry of each slice
@@ -118,8 +142,9 @@ struct FwdDayArgs {
     uint32_t *bits_next;        // [ntiles] the same for day t + 1 (written by this launch)
     const float *pull;          // agent-location graphs: location pressures P [locations] (m lists
                                 // each agent's locations), gathered in place of marked neighbours
-    int ntiles, t, tau_EI, L;
+    int ntiles, t, tau_EI, L;   // L: the longest infectious window (the table's length)
     uint64_t seed;
+    FateRef fate;               // sampled R/M split (fate.L_M > 0) or the single RM exit
     float c[kMaxL];
 };
 
@@ -176,6 +201,10 @@ struct BwdDayArgs {
     // locations, self_q[i] * self_r[i] with self_q = sum_l w_il^2 and self_r = r(t+1), is
     // removed from the gather (the pair weights have no self term)
     const float *self_r, *self_q;
+    // sampled R/M split (fate.L_M > 0): Pm_t [ntiles] receives, per tile, the fate-draw share
+    // of dL/dm on day t + tau_EI of the agents exposed on day t
+    FateRef fate;
+    double *Pm_t;
 };
 
 enum { kBwdStore = 0, kBwdFused = 1, kBwdSplit = 2, kBwdSoft = 3 };
@@ -335,6 +364,13 @@ cudaError_t launch_seed_mark(const SeedArgs &a, int I, int grid_x, cudaStream_t 
 cudaError_t launch_seed_ties(const SeedArgs &a, int I, cudaStream_t s);
 cudaError_t launch_fwd_day(const FwdDayArgs &a, int grid, bool smem_bits, cudaStream_t s);
 // bits[d][tile] for days t0 .. t0 + ndays - 1: rows with 1 <= t - e < L (infectious on day t).
+cudaError_t launch_infectious_bits_fate(const int16_t *e, GraphRef gr, FateRef f, int t, int ntiles, uint32_t *bits,
+                                        cudaStream_t s);
+cudaError_t launch_fate_seeds(Sell m_out, const int16_t *E, const float *r0, const float *ring, size_t ring_stride,
+                              int Lm1, GraphRef gr, FateRef f, const double *gD, const int32_t *sig, int ld_sig,
+                              int ntiles, int T, const float *c, double *Pm, int grid, cudaStream_t s);
+cudaError_t launch_fate_dm(const double *Pm, int ntiles, const int32_t *graph_tile0, const int32_t *graph_ntiles,
+                           int G, int T, double *dm, cudaStream_t s);
 cudaError_t launch_infectious_bits(const int16_t *e, int t0, int ndays, int L, int ntiles, uint32_t *bits,
                                    size_t day_stride, cudaStream_t s);
 cudaError_t launch_fwd_finalize(const int32_t *newRM, const int32_t *counts, const float *m, int ldP,
@@ -404,6 +440,6 @@ cudaError_t launch_rows_to_caller_f32(const float *src, float *dst, GraphRef gr,
 cudaError_t launch_caller_to_rows_i16(const int16_t *src, int16_t *dst, GraphRef gr, const int32_t *rows,
                                       const int64_t *goff, int64_t n_rows, SetLayout sl, cudaStream_t s);
 int occupancy_fwd(int ntiles, bool smem_bits);
-int occupancy_bwd(int mode, bool dc = false);
+int occupancy_bwd(int mode, bool dc = false, bool fate = false);
 
 }  // namespace gabm

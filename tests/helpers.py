@@ -58,6 +58,8 @@ def check_adjoint(gpu, orc, what=""):
     tol = ADJ_RTOL * np.maximum(np.abs(orc), ADJ_FLOOR * scale)
     bad = np.abs(gpu - orc) > tol
     assert not bad.any(), (what, np.flatnonzero(bad)[:10], gpu[bad][:5], orc[bad][:5])
+    if scale == 0.0:   # an identically zero adjoint: matched exactly above
+        return 0.0
     return float(np.max(np.abs(gpu - orc) / np.maximum(np.abs(orc), ADJ_FLOOR * scale)))
 
 
