@@ -467,6 +467,64 @@ def bench_twohop(stream, dist, steps=5, n=1_000_000):
             "value": n * DAYS / (ms / 1e3), "unit": "agent-days/s"}
 
 
+TAU_IM = 10   # I->M days of the sampled R/M split workload (the paper gives no value)
+
+
+def bench_rm_split(pop, stream, S, y_np, dist, peak, peak_kind, steps=5):
+    """The sampled R/M split (tau_IM > 0): the bench graph and parameters, fates drawn at I
+    entry, deaths counted; one forward + MSE + backward step, then the same steps with
+    events around every day launch for the per-kernel rates (the algorithmic bytes of the
+    base model's day kernels with the longer window, L = tau_EI + max(tau_IR, tau_IM))."""
+    import torch
+    from paper_2207_09714_gb300 import capi, synth
+
+    L = TAU_EI + max(TAU_IR, TAU_IM)
+    with torch.cuda.stream(stream):
+        ctx = capi.gabm_create([pop], capi.ModelDesc(TAU_EI, TAU_IR, synth.infectiousness_table(TAU_EI, max(TAU_IR, TAU_IM)),
+                                                     seed=0, tau_IM=TAU_IM), stream=stream)
+        R = torch.full((1, DAYS), R0, dtype=torch.float32, device="cuda")
+        m = torch.full((1, DAYS), MORTALITY, dtype=torch.float32, device="cuda")
+        y = torch.from_numpy(y_np).cuda()
+
+        def step():
+            capi.gabm_forward(ctx, DAYS, R, m, S, [N_SEED])
+            _, gD = capi.gabm_mse_loss(ctx, y)
+            capi.gabm_backward(ctx, gD)
+
+        for _ in range(3):
+            step()
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = max_over_ranks(e0.elapsed_time(e1), dist, "cuda") / steps
+        capi.gabm_set_profiling(ctx, True)
+        for _ in range(steps):
+            step()
+        torch.cuda.synchronize()
+        f_ms, f_n = capi.gabm_get_profile(ctx, 0)
+        b_ms, b_n = capi.gabm_get_profile(ctx, 1)
+        capi.gabm_set_profiling(ctx, False)
+        E = capi.gabm_get_state(ctx)[0]
+        D = capi.gabm_forward(ctx, DAYS, R, m, S, [N_SEED])[0].cpu().numpy()[0]
+    n_rows = ((pop.n + 31) // 32) * 32
+    fwd_b, bwd_b, _, _ = trajectory_bytes(E, pop.degrees().astype(np.float64), DAYS, L, n_rows, True)
+    f_gbs = fwd_b.sum() * steps / (f_ms / 1e3) / 1e9
+    b_gbs = bwd_b.sum() * steps / (b_ms / 1e3) / 1e9
+    return {"workload": f"sampled R/M split on the bench graph: tau_EI {TAU_EI}, tau_IR {TAU_IR}, tau_IM {TAU_IM}, "
+                        f"m = {MORTALITY}, {DAYS} days, forward + MSE + backward",
+            "ms_per_step": ms, "steps": steps, "value": pop.n * DAYS / (ms / 1e3), "unit": "agent-days/s",
+            "deaths_counted": float(D.sum()),
+            "fwd_day": {"avg_launch_ms": f_ms / f_n, "achieved_gbs": f_gbs, "frac": f_gbs / peak},
+            "bwd_day": {"avg_launch_ms": b_ms / b_n, "achieved_gbs": b_gbs, "frac": b_gbs / peak},
+            "peak": peak, "peak_source": peak_kind}
+
+
 def bench_calibration(ctx, stream, S, y_np, dist, steps=5):
     """One Adam step of the calibration workload on the bench graph: weekly-tied R and m,
     the stage factors and profile of the infectiousness table, MSE on cumulative deaths.
@@ -700,6 +758,7 @@ def main():
     calib = bench_calibration(ctx, stream, S, y_np, dist)
     del ctx
     twohop = bench_twohop(stream, dist)
+    rm_split = bench_rm_split(pop, stream, S, y_np, dist, peak, peak_kind)
     batched = None
     if not args.no_batched:
         batched = bench_batched(args, stream, peak, peak_kind)
@@ -730,6 +789,7 @@ def main():
         "cpu_baseline": cpu,
         "calibration": calib,
         "agent_location": twohop,
+        "rm_split": rm_split,
         "batched": batched,
     }
     print(json.dumps(line), flush=True)
