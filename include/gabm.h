@@ -125,6 +125,16 @@ typedef struct {
                            * infection draw (straight-through, tau = 1), so dm comes from the
                            * fates.  Needs GABM_HARD_ST, sets_per_graph = 1, GABM_STORE_LAMBDA and
                            * a one-hop graph; no table adjoint (GABM_EUNSUPPORTED otherwise). */
+    const float *p_IR;    /* NULL: every agent stays tau_IR days in I.  Else host [tau_IR], the pmf
+                           * of a per-agent I-stage duration (stochastic progression, Sec. 6):
+                           * p_IR[j-1] = P(j days), finite and >= 0 with some mass.  An exposure
+                           * on day d stays j days in I, j the first with u < F_j (F_j = p_IR[0] +
+                           * ... + p_IR[j-1] summed in order in double; tau_IR if none), u the
+                           * Philox uniform of (caller id, max(d, 0), instance, stream 2); it is
+                           * infectious for 1 <= t - d < tau_EI + j and enters RM at tau_EI + j,
+                           * where the expected deaths m_t newRM(t) count it.  The adjoint takes
+                           * each row's drawn window.  Same restrictions as tau_IM > 0, and not
+                           * together with it (GABM_EUNSUPPORTED).  Read during gabm_create only. */
 } gabm_model_desc;
 
 /* Build a ctx: validates and copies the graphs (GABM_EINVAL on bad data, before

@@ -64,18 +64,26 @@ __device__ __forceinline__ void dc_accumulate(double *dc_tile, int tile, bool ha
 // today add H dphi/dm to day t + tau_EI's dL/dm, H = dL/dphi = sum over the days between
 // the two exits of +-c[k] gx(t+k) plus gD_{t+L_M}.  Rows exposed before day 0 keep their
 // gx in the ring for k_fate_seeds.
-template <int MODE, bool DC, bool FATE = false>
-__global__ void __launch_bounds__(kBlock, (MODE == kBwdStore && !DC && !FATE) ? GABM_BWD_MINBLOCKS : GABM_MINBLOCKS)
+// EXIT = kExitDur (stochastic I-stage durations, store policy): G of an exposure today
+// sums over the window L_i it would draw and takes the death term m gD of its own exit
+// day; the exits recounted for dm are at each row's drawn L_i.
+template <int MODE, bool DC, int EXIT = kExitBase>
+__global__ void __launch_bounds__(kBlock, (MODE == kBwdStore && !DC && EXIT == kExitBase) ? GABM_BWD_MINBLOCKS
+                                                                                           : GABM_MINBLOCKS)
     k_bwd_day(const BwdDayArgs a) {
+    constexpr bool FATE = EXIT == kExitFate;
+    constexpr bool DUR = EXIT == kExitDur;
     constexpr int NARR = (MODE == kBwdFused) ? 2 : 1;
     constexpr bool SOFT = MODE == kBwdSoft;
     __shared__ float c_s[kMaxL];
     __shared__ int slot_k[kMaxL];
     __shared__ int32_t red_s[kBlock / 32][2];
     __shared__ float fac_s[kBlock / 32][kMaxL];   // 2^(sigma(t+k) - sigma(t)) of the warp's graph
+    __shared__ double F_s[kMaxL];
     if (threadIdx.x < kMaxL) {
         c_s[threadIdx.x] = a.c[threadIdx.x];
         slot_k[threadIdx.x] = a.ring_slot[threadIdx.x];
+        if (DUR) F_s[threadIdx.x] = a.dur.F[threadIdx.x];
     }
     __syncthreads();
 
@@ -147,7 +155,14 @@ __global__ void __launch_bounds__(kBlock, (MODE == kBwdStore && !DC && !FATE) ? 
         // FATE: rows exposed before day 0 keep gx while day t+1 is inside their window
         const bool needA = has_next && (SOFT ? agent : (live && (never || Ei >= t + 2 - L)) ||
                                                        (FATE && agent && !never && Ei < 0 && t + 1 - Ei < L));
-        if (!SOFT) cN += (agent && !never && t - Ei == L);
+        if constexpr (DUR) {
+            // exits at the row's drawn L_i (its first possible day is tau_EI + 1)
+            const int k = t - Ei;
+            if (agent && !never && k > a.tau_EI && k <= L)
+                cN += (k == dur_exit(a.dur, F_s, caller_id(a.gr, row, g), Ei, g));
+        } else if (!SOFT) {
+            cN += (agent && !never && t - Ei == L);
+        }
         // table adjoint: rows infectious on day t+1 (k = t+1-E in [1, L-1]) add gx(t+1) to
         // dc[k]; the non-seed ones are already gathered (needA), the seeds only for this
         const int kd = t + 1 - Ei;
@@ -214,6 +229,12 @@ __global__ void __launch_bounds__(kBlock, (MODE == kBwdStore && !DC && !FATE) ? 
             }
             const int Lmin = FATE ? min(a.fate.L_R, a.fate.L_M) : L;
             const float sgn = (FATE && a.fate.L_M > a.fate.L_R) ? 1.f : -1.f;
+            if constexpr (DUR) {
+                // the window an exposure today would draw, and the death term of its exit day
+                Lx = dur_exit(a.dur, F_s, caller_id(a.gr, row, g), t, g);
+                const size_t pg = (size_t)g * a.ldP;
+                gtail = (t + Lx < T) ? a.m_t[pg + t + Lx] * (float)a.gD[pg + t + Lx] * exp2i(-sig_t) : 0.f;
+            }
             float G = (FATE && !phi) ? 0.f : gtail;
             float H = gtail;
             if (has_next) G = __fmaf_rn(c_s[1], gx_mine * fac_s[wib][1], G);
@@ -230,7 +251,7 @@ __global__ void __launch_bounds__(kBlock, (MODE == kBwdStore && !DC && !FATE) ? 
                     const int k = k0 + u;
                     if (k < L && t + k < T) {
                         const float gk = rv[u] * fac_s[wib][k];
-                        if (!FATE || k < Lx) G = __fmaf_rn(c_s[k], gk, G);
+                        if (!(FATE || DUR) || k < Lx) G = __fmaf_rn(c_s[k], gk, G);
                         if (FATE && k >= Lmin) H = __fmaf_rn(sgn * c_s[k], gk, H);
                     }
                 }
@@ -512,9 +533,10 @@ __global__ void __launch_bounds__(256) k_bwd_finalize(const double *Q, const flo
 
 cudaError_t launch_bwd_day(const BwdDayArgs &a, int grid, cudaStream_t s) {
     const bool dc = a.dc_tile != nullptr;
-    if (a.fate.L_M > 0) {   // store policy, plain instance only (checked at creation)
+    if (a.fate.L_M > 0 || a.dur.n > 0) {   // store policy, plain instance only (checked at creation)
         if (a.mode != kBwdStore || dc) return cudaErrorInvalidValue;
-        k_bwd_day<kBwdStore, false, true><<<grid, kBlock, 0, s>>>(a);
+        if (a.fate.L_M > 0) k_bwd_day<kBwdStore, false, kExitFate><<<grid, kBlock, 0, s>>>(a);
+        else k_bwd_day<kBwdStore, false, kExitDur><<<grid, kBlock, 0, s>>>(a);
         return cudaGetLastError();
     }
     switch (a.mode) {
@@ -566,10 +588,13 @@ cudaError_t launch_lam_day(Sell m, const int16_t *E, const uint32_t *bits, Graph
     return cudaGetLastError();
 }
 
-int occupancy_bwd(int mode, bool dc, bool fate) {
+int occupancy_bwd(int mode, bool dc, int exit_mode) {
     int blocks = 0;
-    if (fate) {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_bwd_day<kBwdStore, false, true>, kBlock, 0);
+    if (exit_mode != kExitBase) {
+        if (exit_mode == kExitFate)
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_bwd_day<kBwdStore, false, kExitFate>, kBlock, 0);
+        else
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_bwd_day<kBwdStore, false, kExitDur>, kBlock, 0);
         return blocks > 0 ? blocks : 1;
     }
     switch (mode) {

@@ -42,6 +42,7 @@ struct gabm_ctx {
     int tau_IM = 0, L_R = 0, L_M = 0;    // sampled R/M split (tau_IM > 0): exits at L_R and L_M
     bool fate = false;
     double *Pm = nullptr;                // [Tcap][ntiles] fate-draw shares of dL/dm by draw day
+    DurRef dur{};                        // stochastic I-stage durations (dur.n > 0)
     float c[kMaxL] = {0};
     uint64_t seed = 0;
     int policy = GABM_STORE_LAMBDA;
@@ -229,6 +230,15 @@ gabm_status validate_model(const gabm_model_desc *md) {
     if (!md) return fail(nullptr, GABM_EINVAL, "model descriptor is NULL");
     if (md->tau_EI < 1 || md->tau_IR < 1) return fail(nullptr, GABM_EINVAL, "tau_EI and tau_IR must be >= 1");
     if (md->tau_IM < 0) return fail(nullptr, GABM_EINVAL, "tau_IM must be >= 0 (0: a single RM exit)");
+    if (md->p_IR) {
+        double sum = 0.0;
+        for (int j = 0; j < md->tau_IR && j < kMaxL; ++j) {
+            if (!std::isfinite(md->p_IR[j]) || md->p_IR[j] < 0.0f)
+                return fail(nullptr, GABM_EINVAL, "p_IR[%d] must be finite and >= 0", j);
+            sum += md->p_IR[j];
+        }
+        if (!(sum > 0.0)) return fail(nullptr, GABM_EINVAL, "p_IR has no mass");
+    }
     const int L = md->tau_EI + std::max(md->tau_IR, md->tau_IM);
     if (L > kMaxL) return fail(nullptr, GABM_EINVAL, "tau_EI + max(tau_IR, tau_IM) = %d exceeds %d", L, kMaxL);
     if (!md->c) return fail(nullptr, GABM_EINVAL, "infectiousness table c is NULL");
@@ -690,8 +700,11 @@ gabm_status forward_days_plain(gabm_ctx *c, int t0, int T, cudaStream_t s) {
     a.L = c->L;
     a.seed = c->seed;
     a.fate = fate_ref(c);
+    a.dur = c->dur;
     for (int k = 0; k < kMaxL; ++k) a.c[k] = k < c->L ? c->c[k] : 0.f;
-    if (t0 < T && c->fate)
+    if (t0 < T && c->dur.n > 0)
+        LAUNCH(launch_infectious_bits_dur(c->e, graph_ref(c), c->dur, t0, c->ntiles, c->bits + (size_t)t0 * c->ntiles, s));
+    else if (t0 < T && c->fate)
         LAUNCH(launch_infectious_bits_fate(c->e, graph_ref(c), a.fate, t0, c->ntiles, c->bits + (size_t)t0 * c->ntiles, s));
     else if (t0 < T)
         LAUNCH(launch_infectious_bits(c->e, t0, 1, c->L, c->ntiles, c->bits + (size_t)t0 * c->ntiles,
@@ -754,7 +767,8 @@ gabm_status backward_days_plain(gabm_ctx *c, int T, cudaStream_t s) {
     a.self_r = a.self_q = nullptr;
     a.fate = fate_ref(c);
     a.Pm_t = nullptr;
-    const int grid = c->fate ? c->grid_bwd_fate : (a.dc_tile ? c->grid_bwd_dc : c->grid_bwd);
+    a.dur = c->dur;
+    const int grid = (c->fate || c->dur.n > 0) ? c->grid_bwd_fate : (a.dc_tile ? c->grid_bwd_dc : c->grid_bwd);
     if (c->fate)   // draw days 0..tau_EI-1 hold only the seeds' shares (k_fate_seeds)
         CK(cudaMemsetAsync(c->Pm, 0, sizeof(double) * (size_t)std::min(c->tau_EI, T) * c->ntiles, s));
     for (int t = T - 1; t >= 0; --t) {
@@ -958,13 +972,13 @@ void apply_schedule(gabm_ctx *c) {
         c->grid_fwd = c->num_sms * occupancy_fwd_b(c->Bp, c->spl_fwd, c->kahan_b);
         c->grid_bwd = c->num_sms * occupancy_bwd_b(c->bwd_chunk, c->spl_bwd, c->kahan_b);
     } else {
-        if (c->fate) c->smem_bits = false;   // the split's forward reads the bitmap from global memory
+        if (c->fate || c->dur.n > 0) c->smem_bits = false;   // these forwards read the bitmap from global memory
         const int bps = c->smem_bits ? occupancy_fwd(c->ntiles, true) : 0;
         if (c->smem_bits && bps <= 0) c->smem_bits = false;
         c->grid_fwd = c->num_sms * (c->smem_bits ? bps : occupancy_fwd(c->ntiles, false));
         c->grid_bwd = c->num_sms * occupancy_bwd(mode);
         c->grid_bwd_dc = c->num_sms * occupancy_bwd(mode, true);
-        c->grid_bwd_fate = c->num_sms * occupancy_bwd(mode, false, true);
+        c->grid_bwd_fate = c->num_sms * occupancy_bwd(mode, false, c->fate ? kExitFate : kExitDur);
     }
     if (c->two_hop) {
         c->smem_bits = false;
@@ -1066,6 +1080,17 @@ static gabm_status create_on_device(const HostLayout &H, const gabm_model_desc *
     c->L_R = model->tau_EI + model->tau_IR;
     c->L_M = model->tau_EI + model->tau_IM;
     c->L = model->tau_EI + std::max(model->tau_IR, model->tau_IM);
+    c->dur = DurRef{};
+    if (model->p_IR) {   // running sums of the duration pmf, in order, in FP64
+        c->dur.n = model->tau_IR;
+        c->dur.tau_EI = model->tau_EI;
+        c->dur.seed = model->seed;
+        double acc = 0.0;
+        for (int j = 0; j < model->tau_IR; ++j) {
+            acc += (double)model->p_IR[j];
+            c->dur.F[j] = acc;
+        }
+    }
     for (int k = 0; k < c->L; ++k) c->c[k] = model->c[k];
     c->seed = model->seed;
     c->policy = model->lambda_policy;
@@ -1230,10 +1255,12 @@ gabm_status gabm_create(const gabm_graph_desc *graphs, int num_graphs, int sets_
     TRY(validate_model(model));
     if (model->relax_mode == GABM_SOFT && (sets_per_graph > 1 || model->lambda_policy != GABM_STORE_LAMBDA))
         return fail(nullptr, GABM_EUNSUPPORTED, "GABM_SOFT needs sets_per_graph = 1 and GABM_STORE_LAMBDA in this build");
-    if (model->tau_IM > 0 && (model->relax_mode != GABM_HARD_ST || sets_per_graph > 1 ||
-                              model->lambda_policy != GABM_STORE_LAMBDA))
-        return fail(nullptr, GABM_EUNSUPPORTED, "the sampled R/M split (tau_IM > 0) needs GABM_HARD_ST, "
-                    "sets_per_graph = 1 and GABM_STORE_LAMBDA in this build");
+    if ((model->tau_IM > 0 || model->p_IR) && (model->relax_mode != GABM_HARD_ST || sets_per_graph > 1 ||
+                                               model->lambda_policy != GABM_STORE_LAMBDA))
+        return fail(nullptr, GABM_EUNSUPPORTED, "the sampled R/M split (tau_IM > 0) and stochastic durations (p_IR) "
+                    "need GABM_HARD_ST, sets_per_graph = 1 and GABM_STORE_LAMBDA in this build");
+    if (model->tau_IM > 0 && model->p_IR)
+        return fail(nullptr, GABM_EUNSUPPORTED, "tau_IM > 0 with p_IR is not built");
 
     // ---- host side: validate, concatenate, transpose ----
     std::vector<HostGraph> hg((size_t)num_graphs);
@@ -1371,9 +1398,10 @@ gabm_status gabm_create_bipartite(const gabm_bipartite_desc *graphs, int num_gra
     *out = nullptr;
     if (!graphs || num_graphs < 1 || num_graphs > 65535) return fail(nullptr, GABM_EINVAL, "need 1..65535 graphs");
     TRY(validate_model(model));
-    if (model->relax_mode != GABM_HARD_ST || model->lambda_policy != GABM_STORE_LAMBDA || model->tau_IM > 0)
-        return fail(nullptr, GABM_EUNSUPPORTED, "agent-location graphs need GABM_HARD_ST, GABM_STORE_LAMBDA and "
-                    "tau_IM = 0 in this build");
+    if (model->relax_mode != GABM_HARD_ST || model->lambda_policy != GABM_STORE_LAMBDA || model->tau_IM > 0 ||
+        model->p_IR)
+        return fail(nullptr, GABM_EUNSUPPORTED, "agent-location graphs need GABM_HARD_ST, GABM_STORE_LAMBDA, "
+                    "tau_IM = 0 and p_IR = NULL in this build");
     int sigma = 1024;
     if (const char *f = getenv("GABM_SELL_SIGMA")) sigma = std::max(1, atoi(f));
     const int G = num_graphs;
@@ -1682,7 +1710,8 @@ gabm_status gabm_backward_table(gabm_ctx *ctx, const double *gD, double *dR, dou
     if (!dc) return fail(ctx, GABM_EINVAL, "dc is required");
     if (ctx->batched && ctx->policy != GABM_STORE_LAMBDA)
         return fail(ctx, GABM_EUNSUPPORTED, "the table adjoint of several sets per graph needs GABM_STORE_LAMBDA in this build");
-    if (ctx->fate) return fail(ctx, GABM_EUNSUPPORTED, "the table adjoint of the sampled R/M split is not built");
+    if (ctx->fate || ctx->dur.n > 0)
+        return fail(ctx, GABM_EUNSUPPORTED, "the table adjoint of the sampled R/M split or stochastic durations is not built");
     return backward_impl(ctx, gD, dR, dm, dS_age, dc, mem_space);
 }
 
@@ -1861,7 +1890,8 @@ gabm_status gabm_set_schedule(gabm_ctx *ctx, const gabm_schedule *sched) {
         c->spl_bwd = sched->bwd_sets_per_lane;
         c->bwd_chunk = chunk;
     } else {
-        if (sched->fwd_smem_bitmap && (c->soft || c->two_hop || c->fate || occupancy_fwd(c->ntiles, true) <= 0))
+        if (sched->fwd_smem_bitmap && (c->soft || c->two_hop || c->fate || c->dur.n > 0 ||
+                                       occupancy_fwd(c->ntiles, true) <= 0))
             return fail(c, GABM_EINVAL, "the infectious bitmap (%d words) does not fit in shared memory", c->ntiles);
         c->smem_bits = sched->fwd_smem_bitmap != 0;
     }
@@ -1887,7 +1917,8 @@ gabm_status gabm_autotune(gabm_ctx *ctx, int repetitions) {
             if (batch_config_ok(c->Bp, spl)) fc.push_back(gabm_schedule{spl, cur.bwd_sets_per_lane, 0, cur.bwd_sets_per_launch});
     } else {
         fc.push_back(gabm_schedule{0, 0, 0, 0});
-        if (!c->soft && !c->two_hop && !c->fate && occupancy_fwd(c->ntiles, true) > 0) fc.push_back(gabm_schedule{0, 0, 1, 0});
+        if (!c->soft && !c->two_hop && !c->fate && c->dur.n == 0 && occupancy_fwd(c->ntiles, true) > 0)
+            fc.push_back(gabm_schedule{0, 0, 1, 0});
     }
     cudaEvent_t ev[2];
     for (auto &e : ev) CK(cudaEventCreate(&e));

@@ -46,16 +46,21 @@ __device__ __forceinline__ void flush_counts_warp(int32_t *counts, int32_t *newR
 // PULL (agent-location graphs): the row's entries are the agent's locations, and each
 // contributes w_il * P_l from the day's location pressures (a.pull) instead of a marked
 // neighbour's infectiousness.
-// FATE (sampled R/M split): a row's exit from I is L_R or L_M after exposure by its fate,
-// drawn again where needed (the day before the earlier exit through the later one), and
-// the deaths counted are the M entries.
-template <bool SMEM_BITS, int NT, int MINB, bool PULL = false, bool FATE = false>
+// EXIT = kExitFate (sampled R/M split): a row's exit from I is L_R or L_M after exposure by
+// its fate, drawn again where needed (the day before the earlier exit through the later
+// one), and the deaths counted are the M entries.  EXIT = kExitDur (stochastic I-stage
+// durations): the exit is the row's drawn L_i (drawn again from its first possible day
+// on); deaths stay m_t newRM(t).
+template <bool SMEM_BITS, int NT, int MINB, bool PULL = false, int EXIT = kExitBase>
 __global__ void __launch_bounds__(NT, MINB) k_fwd_day(const FwdDayArgs a) {
     constexpr int NW = NT / 32;
     extern __shared__ uint32_t bits_s[];
+    constexpr bool FATE = EXIT == kExitFate;
     __shared__ float c_s[kMaxL];
+    __shared__ double F_s[kMaxL];
     __shared__ int32_t red_s[NW][6];
     if (threadIdx.x < kMaxL) c_s[threadIdx.x] = a.c[threadIdx.x];
+    if (EXIT == kExitDur && threadIdx.x < kMaxL) F_s[threadIdx.x] = a.dur.F[threadIdx.x];
     if (SMEM_BITS)
         for (int i = threadIdx.x; i < a.ntiles; i += NT) bits_s[i] = __ldcg(a.bits_cur + i);
     __syncthreads();
@@ -109,10 +114,14 @@ __global__ void __launch_bounds__(NT, MINB) k_fwd_day(const FwdDayArgs a) {
             Lx = phi ? a.fate.L_M : a.fate.L_R;
             if (ei != kPad && !isS) cN += (phi && k == a.fate.L_M);
         }
+        if constexpr (EXIT == kExitDur) {
+            const int k = t - ei;
+            if (ei != kPad && !isS && k >= tau_EI && k <= L) Lx = dur_exit(a.dur, F_s, caller_id(a.gr, row, g), ei, g);
+        }
         if (ei != kPad && !isS) {
             const int k = t - ei;
             if (k < tau_EI) ++cE; else if (k < Lx) ++cI; else ++cR;
-            if (!FATE) cN += (k == L);
+            if (!FATE) cN += (k == Lx);
         }
         cS += isS;
 
@@ -279,6 +288,27 @@ __global__ void __launch_bounds__(256) k_soft_finalize(const double *P_nrm, int 
 
 // One warp per tile: for every day d of the range, the ballot of rows with
 // 1 <= d - e < L.
+__global__ void k_infectious_bits_dur(const int16_t *e, GraphRef gr, const DurRef d, int t, int ntiles, uint32_t *bits) {
+    __shared__ double F_s[kMaxL];
+    if (threadIdx.x < kMaxL) F_s[threadIdx.x] = d.F[threadIdx.x];
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    const int L = d.tau_EI + d.n;
+    for (int tile = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; tile < ntiles; tile += warps) {
+        const int row = tile * kTile + lane;
+        const int ei = e[row];
+        const int k = t - ei;
+        int Lx = L;
+        if (ei != kPad && ei != kNever && k > d.tau_EI && k < L) {
+            const int g = gr.tile_graph ? (int)gr.tile_graph[tile] : 0;
+            Lx = dur_exit(d, F_s, caller_id(gr, row, g), ei, g);
+        }
+        const unsigned b = __ballot_sync(0xffffffffu, (unsigned)(k - 1) < (unsigned)(Lx - 1));
+        if (lane == 0) bits[tile] = b;
+    }
+}
+
 __global__ void k_infectious_bits_fate(const int16_t *e, GraphRef gr, FateRef f, int t, int ntiles, uint32_t *bits) {
     const int lane = threadIdx.x & 31;
     const int warps = (gridDim.x * blockDim.x) >> 5;
@@ -576,6 +606,14 @@ cudaError_t launch_infectious_bits(const int16_t *e, int t0, int ndays, int L, i
     return cudaGetLastError();
 }
 
+cudaError_t launch_infectious_bits_dur(const int16_t *e, GraphRef gr, const DurRef &d, int t, int ntiles,
+                                       uint32_t *bits, cudaStream_t s) {
+    int grid = (ntiles + 7) / 8;
+    if (grid > 65535) grid = 65535;
+    k_infectious_bits_dur<<<grid > 0 ? grid : 1, 256, 0, s>>>(e, gr, d, t, ntiles, bits);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_infectious_bits_fate(const int16_t *e, GraphRef gr, FateRef f, int t, int ntiles, uint32_t *bits,
                                         cudaStream_t s) {
     int grid = (ntiles + 7) / 8;
@@ -619,7 +657,9 @@ constexpr int kBitsBlock = 768;   // one block of 24 warps per SM when the bitma
 
 cudaError_t launch_fwd_day(const FwdDayArgs &a, int grid, bool smem_bits, cudaStream_t s) {
     if (a.fate.L_M > 0) {
-        k_fwd_day<false, kBlock, GABM_MINBLOCKS, false, true><<<grid, kBlock, 0, s>>>(a);
+        k_fwd_day<false, kBlock, GABM_MINBLOCKS, false, kExitFate><<<grid, kBlock, 0, s>>>(a);
+    } else if (a.dur.n > 0) {
+        k_fwd_day<false, kBlock, GABM_MINBLOCKS, false, kExitDur><<<grid, kBlock, 0, s>>>(a);
     } else if (smem_bits && !a.pull) {
         const size_t bytes = (size_t)a.ntiles * sizeof(uint32_t);
         k_fwd_day<true, kBitsBlock, 1><<<grid, kBitsBlock, bytes, s>>>(a);

@@ -119,6 +119,27 @@ __device__ __forceinline__ bool fate_M(const FateRef &f, uint32_t id, int d, int
     return fate_uniform(f, id, tI, inst) < f.mort[(size_t)inst * f.ldP + tI];
 }
 
+// Stochastic I-stage durations (Sec. 6 names stochastic progression): an exposure of
+// day d stays in I for j days, j the first with u < F[j-1] (F: the pmf's running sums in
+// FP64, tau_IR if none), u the Philox uniform of (caller id, max(d, 0), instance, stream 2);
+// it leaves I at L_i = tau_EI + j days after exposure.  n = 0: every agent stays tau_IR days.
+struct DurRef {
+    int n;               // pmf entries (tau_IR) or 0
+    int tau_EI;
+    uint64_t seed;
+    double F[kMaxL];     // running sums of the pmf
+};
+
+// Exit offset L_i of agent `id`'s exposure on day d (F_s: the running sums, e.g. in shared memory).
+__device__ __forceinline__ int dur_exit(const DurRef &dr, const double *F_s, uint32_t id, int d, int inst) {
+    const double u = (double)uniform_from_word(philox_word(dr.seed, id, (uint32_t)max(d, 0), (uint32_t)inst, 2u));
+    int j = 1;
+    while (j < dr.n && !(u < F_s[j - 1])) ++j;
+    return dr.tau_EI + j;
+}
+
+enum { kExitBase = 0, kExitFate = 1, kExitDur = 2 };
+
 // Edges of one orientation in SELL-32 layout (one slice per 32-row tile).
 struct Sell {
     const uint32_t *slice_ptr;  // [ntiles+1] first entry of each slice
@@ -145,6 +166,7 @@ struct FwdDayArgs {
     int ntiles, t, tau_EI, L;   // L: the longest infectious window (the table's length)
     uint64_t seed;
     FateRef fate;               // sampled R/M split (fate.L_M > 0) or the single RM exit
+    DurRef dur;                 // stochastic I-stage durations (dur.n > 0)
     float c[kMaxL];
 };
 
@@ -205,6 +227,7 @@ struct BwdDayArgs {
     // of dL/dm on day t + tau_EI of the agents exposed on day t
     FateRef fate;
     double *Pm_t;
+    DurRef dur;                // stochastic I-stage durations (dur.n > 0)
 };
 
 enum { kBwdStore = 0, kBwdFused = 1, kBwdSplit = 2, kBwdSoft = 3 };
@@ -366,6 +389,8 @@ cudaError_t launch_fwd_day(const FwdDayArgs &a, int grid, bool smem_bits, cudaSt
 // bits[d][tile] for days t0 .. t0 + ndays - 1: rows with 1 <= t - e < L (infectious on day t).
 cudaError_t launch_infectious_bits_fate(const int16_t *e, GraphRef gr, FateRef f, int t, int ntiles, uint32_t *bits,
                                         cudaStream_t s);
+cudaError_t launch_infectious_bits_dur(const int16_t *e, GraphRef gr, const DurRef &d, int t, int ntiles,
+                                       uint32_t *bits, cudaStream_t s);
 cudaError_t launch_fate_seeds(Sell m_out, const int16_t *E, const float *r0, const float *ring, size_t ring_stride,
                               int Lm1, GraphRef gr, FateRef f, const double *gD, const int32_t *sig, int ld_sig,
                               int ntiles, int T, const float *c, double *Pm, int grid, cudaStream_t s);
@@ -440,6 +465,6 @@ cudaError_t launch_rows_to_caller_f32(const float *src, float *dst, GraphRef gr,
 cudaError_t launch_caller_to_rows_i16(const int16_t *src, int16_t *dst, GraphRef gr, const int32_t *rows,
                                       const int64_t *goff, int64_t n_rows, SetLayout sl, cudaStream_t s);
 int occupancy_fwd(int ntiles, bool smem_bits);
-int occupancy_bwd(int mode, bool dc = false, bool fate = false);
+int occupancy_bwd(int mode, bool dc = false, int exit_mode = kExitBase);
 
 }  // namespace gabm
