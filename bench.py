@@ -468,20 +468,30 @@ def bench_twohop(stream, dist, steps=5, n=1_000_000):
 
 
 TAU_IM = 10   # I->M days of the sampled R/M split workload (the paper gives no value)
+# I-stage duration pmf of the stochastic-duration workload (1..9 days; mean 5.7)
+P_IR = np.array([0.02, 0.05, 0.13, 0.2, 0.2, 0.15, 0.12, 0.08, 0.05], np.float32)
 
 
-def bench_rm_split(pop, stream, S, y_np, dist, peak, peak_kind, steps=5):
-    """The sampled R/M split (tau_IM > 0): the bench graph and parameters, fates drawn at I
-    entry, deaths counted; one forward + MSE + backward step, then the same steps with
-    events around every day launch for the per-kernel rates (the algorithmic bytes of the
-    base model's day kernels with the longer window, L = tau_EI + max(tau_IR, tau_IM))."""
+def bench_progression_variant(pop, stream, S, y_np, dist, peak, peak_kind, variant, steps=5):
+    """A progression variant on the bench graph and parameters: ``rm_split`` (tau_IM > 0,
+    fates drawn at I entry, deaths counted) or ``durations`` (per-agent I-stage durations
+    from P_IR).  One forward + MSE + backward step, then the same steps with events around
+    every day launch for the per-kernel rates (the algorithmic bytes of the base model's
+    day kernels with the longest window L)."""
     import torch
     from paper_2207_09714_gb300 import capi, synth
 
-    L = TAU_EI + max(TAU_IR, TAU_IM)
+    if variant == "rm_split":
+        L = TAU_EI + max(TAU_IR, TAU_IM)
+        md = capi.ModelDesc(TAU_EI, TAU_IR, synth.infectiousness_table(TAU_EI, max(TAU_IR, TAU_IM)), seed=0,
+                            tau_IM=TAU_IM)
+        what = f"sampled R/M split: tau_EI {TAU_EI}, tau_IR {TAU_IR}, tau_IM {TAU_IM}"
+    else:
+        L = TAU_EI + P_IR.size
+        md = capi.ModelDesc(TAU_EI, P_IR.size, synth.infectiousness_table(TAU_EI, P_IR.size), seed=0, p_IR=P_IR)
+        what = f"stochastic I-stage durations: tau_EI {TAU_EI}, I days ~ pmf {P_IR.round(2).tolist()} over 1..{P_IR.size}"
     with torch.cuda.stream(stream):
-        ctx = capi.gabm_create([pop], capi.ModelDesc(TAU_EI, TAU_IR, synth.infectiousness_table(TAU_EI, max(TAU_IR, TAU_IM)),
-                                                     seed=0, tau_IM=TAU_IM), stream=stream)
+        ctx = capi.gabm_create([pop], md, stream=stream)
         R = torch.full((1, DAYS), R0, dtype=torch.float32, device="cuda")
         m = torch.full((1, DAYS), MORTALITY, dtype=torch.float32, device="cuda")
         y = torch.from_numpy(y_np).cuda()
@@ -516,10 +526,9 @@ def bench_rm_split(pop, stream, S, y_np, dist, peak, peak_kind, steps=5):
     fwd_b, bwd_b, _, _ = trajectory_bytes(E, pop.degrees().astype(np.float64), DAYS, L, n_rows, True)
     f_gbs = fwd_b.sum() * steps / (f_ms / 1e3) / 1e9
     b_gbs = bwd_b.sum() * steps / (b_ms / 1e3) / 1e9
-    return {"workload": f"sampled R/M split on the bench graph: tau_EI {TAU_EI}, tau_IR {TAU_IR}, tau_IM {TAU_IM}, "
-                        f"m = {MORTALITY}, {DAYS} days, forward + MSE + backward",
+    return {"workload": f"{what}, on the bench graph, m = {MORTALITY}, {DAYS} days, forward + MSE + backward",
             "ms_per_step": ms, "steps": steps, "value": pop.n * DAYS / (ms / 1e3), "unit": "agent-days/s",
-            "deaths_counted": float(D.sum()),
+            "deaths": float(D.sum()),
             "fwd_day": {"avg_launch_ms": f_ms / f_n, "achieved_gbs": f_gbs, "frac": f_gbs / peak},
             "bwd_day": {"avg_launch_ms": b_ms / b_n, "achieved_gbs": b_gbs, "frac": b_gbs / peak},
             "peak": peak, "peak_source": peak_kind}
@@ -758,7 +767,8 @@ def main():
     calib = bench_calibration(ctx, stream, S, y_np, dist)
     del ctx
     twohop = bench_twohop(stream, dist)
-    rm_split = bench_rm_split(pop, stream, S, y_np, dist, peak, peak_kind)
+    rm_split = bench_progression_variant(pop, stream, S, y_np, dist, peak, peak_kind, "rm_split")
+    durations = bench_progression_variant(pop, stream, S, y_np, dist, peak, peak_kind, "durations")
     batched = None
     if not args.no_batched:
         batched = bench_batched(args, stream, peak, peak_kind)
@@ -790,6 +800,7 @@ def main():
         "calibration": calib,
         "agent_location": twohop,
         "rm_split": rm_split,
+        "stochastic_durations": durations,
         "batched": batched,
     }
     print(json.dumps(line), flush=True)

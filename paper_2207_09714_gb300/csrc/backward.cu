@@ -59,11 +59,11 @@ __device__ __forceinline__ void dc_accumulate(double *dc_tile, int tile, bool ha
 #ifndef GABM_BWD_MINBLOCKS
 #define GABM_BWD_MINBLOCKS 4
 #endif
-// FATE (sampled R/M split, store policy): G of an exposure today takes the fate it would
-// draw (window L_R or L_M; the death term gD_{t+L_M} only if M-fated), and the rows exposed
-// today add H dphi/dm to day t + tau_EI's dL/dm, H = dL/dphi = sum over the days between
-// the two exits of +-c[k] gx(t+k) plus gD_{t+L_M}.  Rows exposed before day 0 keep their
-// gx in the ring for k_fate_seeds.
+// EXIT = kExitFate (sampled R/M split, store policy): G of an exposure today takes the
+// fate it would draw (window L_R or L_M; the death term gD_{t+L_M} only if M-fated), and
+// the rows exposed today add H dphi/dm to day t + tau_EI's dL/dm, H = dL/dphi = sum over
+// the days between the two exits of +-c[k] gx(t+k) plus gD_{t+L_M}.  Rows exposed before
+// day 0 keep their gx in the ring for k_fate_seeds.
 // EXIT = kExitDur (stochastic I-stage durations, store policy): G of an exposure today
 // sums over the window L_i it would draw and takes the death term m gD of its own exit
 // day; the exits recounted for dm are at each row's drawn L_i.
@@ -152,7 +152,7 @@ __global__ void __launch_bounds__(kBlock, (MODE == kBwdStore && !DC && EXIT == k
         const bool live = agent && (never || Ei >= 0);           // seeds are constants
         // soft relaxation: every agent carries susceptible mass and draws every day
         const bool isS = SOFT ? agent : live && (never || Ei >= t);
-        // FATE: rows exposed before day 0 keep gx while day t+1 is inside their window
+        // R/M split: rows exposed before day 0 keep gx while day t+1 is inside their window
         const bool needA = has_next && (SOFT ? agent : (live && (never || Ei >= t + 2 - L)) ||
                                                        (FATE && agent && !never && Ei < 0 && t + 1 - Ei < L));
         if constexpr (DUR) {
@@ -216,7 +216,7 @@ __global__ void __launch_bounds__(kBlock, (MODE == kBwdStore && !DC && EXIT == k
             float Lam;
             if constexpr (MODE == kBwdFused) Lam = sum[NARR - 1] * a.gr.inv_Dbar[g];
             else Lam = a.lam_t[row];
-            // FATE: the fate an exposure today would draw on day t + tau_EI
+            // R/M split: the fate an exposure today would draw on day t + tau_EI
             bool phi = false;
             float vf = 0.5f;
             int Lx = L;
