@@ -131,3 +131,41 @@ def test_unsupported_and_invalid():
     with pytest.raises(capi.GabmError) as ei:
         capi.gabm_backward_table(ctx, to_dev(np.ones((1, T)))[0])
     assert ei.value.status == capi.GABM_EUNSUPPORTED
+
+
+def test_several_graphs_and_graph_replay(monkeypatch):
+    """Three graphs in one ctx, each following the oracle's run of its own instance; CUDA-
+    graph replay of the day loops equals eager launches bitwise."""
+    pops = [synth.population_small(n=n, seed=40 + i) for i, n in enumerate((3000, 777, 4500))]
+    G, T, n_seed = len(pops), 26, 12
+    rng = np.random.default_rng(41)
+    R = rng.uniform(2.2, 3.2, (G, T)).astype(np.float32)
+    m = rng.uniform(0.01, 0.05, (G, T)).astype(np.float32)
+    S = np.repeat(synth.SUSCEPTIBILITY[None, :], G, axis=0).astype(np.float32)
+    md, mo = _models(PMF, 3)
+    refs = [DU.forward(pops[g], mo, R[g], m[g], S[g], n_seed=n_seed, inst=g) for g in range(G)]
+    gD = np.stack([O.mse(refs[g]["D"], synth.target_curve(T, pops[g].n, seed=g, level=5e-5))[1] for g in range(G)])
+    Rd, md_, Sd, gDd = to_dev(R, m, S, gD)
+    out = []
+    for graphs in ("1", "0"):
+        monkeypatch.setenv("GABM_CUDA_GRAPHS", graphs)
+        ctx = capi.gabm_create(pops, md)
+        D, _ = capi.gabm_forward(ctx, T, Rd, md_, Sd, [n_seed] * G)
+        out.append([capi.gabm_get_state(ctx)[0], D.cpu().numpy()] +
+                   [x.cpu().numpy() for x in capi.gabm_backward(ctx, gDd)])
+    for a, b in zip(*out):
+        assert np.array_equal(a, b)
+    e, D, dR, dm, dS = out[0]
+    off = np.concatenate([[0], np.cumsum([p.n for p in pops])])
+    checked = 0
+    for g in range(G):
+        if refs[g]["margin"] <= EXACT_MARGIN:
+            continue
+        assert np.array_equal(e[off[g]:off[g + 1]], refs[g]["e_final"]), g
+        assert np.array_equal(D[g], refs[g]["D"]), g
+        ref = DU.backward(pops[g], mo, R[g], m[g], S[g], refs[g]["e_final"], gD[g], inst=g)
+        check_adjoint(dR[g], ref["dR"], f"dR[{g}]")
+        check_adjoint(dm[g], ref["dm"], f"dm[{g}]")
+        check_adjoint(dS[g], ref["dS"], f"dS[{g}]")
+        checked += 1
+    assert checked >= 2
