@@ -78,6 +78,20 @@ def test_create_rejects_bad_models(lib):
     _expect(capi.GABM_EINVAL, [pop], _md(lambda_policy=7))
     _expect(capi.GABM_EINVAL, [pop], _md(), sets=0)
     _expect(capi.GABM_EINVAL, [], _md())
+    # progression variants: the sampled R/M split (tau_IM) and stochastic I-stage durations (p_IR)
+    c11 = synth.infectiousness_table(4, 7)
+    _expect(capi.GABM_EINVAL, [pop], _md(tau_IM=-2))
+    _expect(capi.GABM_EINVAL, [pop], _md(tau_IM=40, c=np.r_[0.0, np.full(43, 0.02)].astype(np.float32)))
+    pmf = np.full(7, 1 / 7, np.float32)
+    _expect(capi.GABM_EINVAL, [pop], _md(p_IR=np.r_[pmf[:6], -1.0].astype(np.float32)))
+    _expect(capi.GABM_EINVAL, [pop], _md(p_IR=np.zeros(7, np.float32)))
+    for kw, sets in ((dict(tau_IM=9, c=synth.infectiousness_table(4, 9), relax_mode=capi.GABM_SOFT), 1),
+                     (dict(tau_IM=9, c=synth.infectiousness_table(4, 9)), 2),
+                     (dict(p_IR=pmf, lambda_policy=capi.GABM_RECOMPUTE), 1),
+                     (dict(p_IR=pmf, tau_IM=5, c=c11), 1)):
+        _expect(capi.GABM_EUNSUPPORTED, [pop], _md(**kw), sets=sets)
+    with pytest.raises(ValueError):
+        capi.gabm_create([pop], _md(tau_IM=9))   # c must have tau_EI + max(tau_IR, tau_IM) = 13 entries
     # parameter sets per graph: up to 64; without the lambda store only on symmetric weights
     _expect(capi.GABM_EUNSUPPORTED, [pop], _md(), sets=65)
     _expect(capi.GABM_EUNSUPPORTED, [synth.random_directed(64, 4.0, seed=3)],
