@@ -135,6 +135,14 @@ typedef struct {
                            * where the expected deaths m_t newRM(t) count it.  The adjoint takes
                            * each row's drawn window.  Same restrictions as tau_IM > 0, and not
                            * together with it (GABM_EUNSUPPORTED).  Read during gabm_create only. */
+    int tau_RS;           /* 0: no reinfection (A4 of App. A).  > 0: SIRS reinfection, A4 relaxed --
+                           * an agent returns to S tau_RS days after entering RM (tau_EI + tau_IR +
+                           * tau_RS days after its exposure) and can be exposed again; the state is
+                           * the last exposure day, and every exposure is recorded for the
+                           * backward.  D_t = m_t newRM(t) counts every I -> RM transition.  Needs
+                           * GABM_HARD_ST, sets_per_graph = 1, GABM_STORE_LAMBDA, a one-hop graph,
+                           * tau_IM = 0 and p_IR = NULL; gabm_set_state and the table adjoint return
+                           * GABM_EUNSUPPORTED. */
 } gabm_model_desc;
 
 /* Build a ctx: validates and copies the graphs (GABM_EINVAL on bad data, before

@@ -15,8 +15,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libgabm.so")
-SOURCES = ["capi.cu", "forward.cu", "backward.cu", "batched.cu", "batched_bwd.cu", "twohop.cu", "noalloc.cu"]
-HEADERS = ["gabm_internal.cuh", "rowsum.cuh", "batched_common.cuh"]
+SOURCES = ["capi.cu", "forward.cu", "backward.cu", "batched.cu", "batched_bwd.cu", "twohop.cu", "sirs.cu", "noalloc.cu"]
+HEADERS = ["gabm_internal.cuh", "rowsum.cuh", "batched_common.cuh", "sirs.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr"]

@@ -55,7 +55,7 @@ class _ModelDesc(ctypes.Structure):
     _fields_ = [("tau_EI", ctypes.c_int), ("tau_IR", ctypes.c_int), ("c", ctypes.c_void_p),
                 ("gumbel_tau", ctypes.c_float), ("relax_mode", ctypes.c_int),
                 ("lambda_policy", ctypes.c_int), ("seed", ctypes.c_uint64), ("agent_order", ctypes.c_int),
-                ("tau_IM", ctypes.c_int), ("p_IR", ctypes.c_void_p)]
+                ("tau_IM", ctypes.c_int), ("p_IR", ctypes.c_void_p), ("tau_RS", ctypes.c_int)]
 
 
 class _Schedule(ctypes.Structure):
@@ -194,6 +194,7 @@ class ModelDesc:
     agent_order: int = GABM_ORDER_BFS
     tau_IM: int = 0          # > 0: the sampled R/M split (c then has tau_EI + max(tau_IR, tau_IM) entries)
     p_IR: np.ndarray = None  # [tau_IR] pmf of a per-agent I-stage duration 1..tau_IR, or None
+    tau_RS: int = 0          # > 0: SIRS reinfection, back to S tau_RS days after entering RM
 
     @property
     def L(self) -> int:
@@ -243,7 +244,7 @@ def _model_struct(model: ModelDesc, c: np.ndarray) -> _ModelDesc:
             raise ValueError(f"p_IR must have tau_IR = {model.tau_IR} entries, got {p.size}")
     md = _ModelDesc(int(model.tau_EI), int(model.tau_IR), _ptr(c, np.float32), float(model.gumbel_tau),
                     int(model.relax_mode), int(model.lambda_policy), int(model.seed), int(model.agent_order),
-                    int(model.tau_IM), _ptr(p, np.float32))
+                    int(model.tau_IM), _ptr(p, np.float32), int(model.tau_RS))
     md._keep = p   # alive for as long as the descriptor
     return md
 

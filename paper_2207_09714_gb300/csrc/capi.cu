@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "gabm_internal.cuh"
+#include "sirs.cuh"
 
 using namespace gabm;
 
@@ -43,6 +44,13 @@ struct gabm_ctx {
     bool fate = false;
     double *Pm = nullptr;                // [Tcap][ntiles] fate-draw shares of dL/dm by draw day
     DurRef dur{};                        // stochastic I-stage durations (dur.n > 0)
+    bool sirs = false;                   // SIRS reinfection (tau_RS > 0)
+    int tau_RS = 0, cycle = 0;           // days in RM before S again; L + tau_RS
+    int sirs_H = 0;                      // history entries per row
+    int16_t *sirs_hist = nullptr;        // [n_rows][sirs_H] exposure days
+    uint8_t *sirs_cnt = nullptr;         // [n_rows]
+    float *sirs_Gh = nullptr;            // [n_rows][sirs_H] G at each exposure
+    int grid_sirs_f = 0, grid_sirs_b = 0;
     float c[kMaxL] = {0};
     uint64_t seed = 0;
     int policy = GABM_STORE_LAMBDA;
@@ -230,6 +238,7 @@ gabm_status validate_model(const gabm_model_desc *md) {
     if (!md) return fail(nullptr, GABM_EINVAL, "model descriptor is NULL");
     if (md->tau_EI < 1 || md->tau_IR < 1) return fail(nullptr, GABM_EINVAL, "tau_EI and tau_IR must be >= 1");
     if (md->tau_IM < 0) return fail(nullptr, GABM_EINVAL, "tau_IM must be >= 0 (0: a single RM exit)");
+    if (md->tau_RS < 0) return fail(nullptr, GABM_EINVAL, "tau_RS must be >= 0 (0: no return to S)");
     if (md->p_IR) {
         double sum = 0.0;
         for (int j = 0; j < md->tau_IR && j < kMaxL; ++j) {
@@ -682,8 +691,108 @@ gabm_status backward_days_batched(gabm_ctx *c, int T, cudaStream_t s) {
     return GABM_OK;
 }
 
+// SIRS reinfection: the forward from the seeded state, recording every exposure.
+gabm_status forward_days_sirs(gabm_ctx *c, int t0, int T, cudaStream_t s) {
+    if (t0 != 0) return fail(c, GABM_EUNSUPPORTED, "SIRS reinfection runs from the seeded state (day 0)");
+    LAUNCH(launch_sirs_hist_init(c->e, c->n_rows, c->sirs_H, c->sirs_hist, c->sirs_cnt, s));
+    if (T > 0) LAUNCH(launch_infectious_bits(c->e, 0, 1, c->L, c->ntiles, c->bits, (size_t)c->ntiles, s));
+    SirsFwdArgs a;
+    a.m = sell_view(c, false);
+    a.age = c->age;
+    a.gr = graph_ref(c);
+    a.e = c->e;
+    a.hist = c->sirs_hist;
+    a.cnt = c->sirs_cnt;
+    a.H = c->sirs_H;
+    a.R = c->R;
+    a.S = c->S;
+    a.ldP = c->Tcap;
+    a.counts = c->counts;
+    a.newRM = c->newRM;
+    a.ntiles = c->ntiles;
+    a.tau_EI = c->tau_EI;
+    a.L = c->L;
+    a.cycle = c->cycle;
+    a.seed = c->seed;
+    for (int k = 0; k < kMaxL; ++k) a.c[k] = k < c->L ? c->c[k] : 0.f;
+    for (int t = 0; t < T; ++t) {
+        a.t = t;
+        a.lam_out = c->lam + (size_t)t * c->n_rows;
+        a.bits_cur = c->bits + (size_t)t * c->ntiles;
+        a.bits_next = c->bits + (size_t)(t + 1) * c->ntiles;
+        prof_begin(c, 0);
+        LAUNCH(launch_fwd_day_sirs(a, c->grid_sirs_f, s));
+        prof_end(c, 0);
+    }
+    return GABM_OK;
+}
+
+// SIRS reinfection: the reverse sweep over the recorded exposure histories.
+gabm_status backward_days_sirs(gabm_ctx *c, int T, cudaStream_t s) {
+    const int ld = c->Tcap;
+    SirsBwdArgs a;
+    a.m = sell_view(c, true);
+    a.age = c->age;
+    a.gr = graph_ref(c);
+    a.E = c->e;
+    a.hist = c->sirs_hist;
+    a.cnt = c->sirs_cnt;
+    a.H = c->sirs_H;
+    a.Gh = c->sirs_Gh;
+    a.ring = c->ring;
+    a.ring_stride = (size_t)c->n_rows;
+    a.R = c->R;
+    a.m_t = c->m;
+    a.S = c->S;
+    a.gD = c->gD;
+    a.ldP = ld;
+    a.newRM = c->newRM_b;
+    a.sig = c->sig;
+    a.emax = c->emax;
+    a.ld_sig = ld + 1;
+    a.ntiles = c->ntiles;
+    a.T = T;
+    a.tau_EI = c->tau_EI;
+    a.L = c->L;
+    a.cycle = c->cycle;
+    a.seed = c->seed;
+    for (int k = 0; k < kMaxL; ++k) a.c[k] = k < c->L ? c->c[k] : 0.f;
+    const int Lm1 = c->L - 1;
+    for (int t = T - 1; t >= 0; --t) {
+        a.t = t;
+        a.lam_t = c->lam + (size_t)t * c->n_rows;
+        a.r_next = c->r + (size_t)((t + 1) & 1) * c->n_rows;
+        a.r_cur = c->r + (size_t)(t & 1) * c->n_rows;
+        a.P_t = c->P + (size_t)t * c->ntiles * kAges;
+        for (int k = 0; k < kMaxL; ++k) a.ring_slot[k] = (k >= 1 && k < c->L) ? (t + k) % Lm1 : 0;
+        prof_begin(c, 1);
+        LAUNCH(launch_bwd_day_sirs(a, c->grid_sirs_b, s));
+        prof_end(c, 1);
+    }
+    LAUNCH(launch_bwd_reduce(c->P, c->ntiles, ld, c->d_tile0, c->d_ntiles, T, c->I, c->sig, ld + 1, c->Q, s));
+    return GABM_OK;
+}
+
+// History capacity of SIRS reinfection for a horizon of T days: a seed's exposure plus
+// exposures at least `cycle` days apart.
+gabm_status ensure_sirs(gabm_ctx *c, int T) {
+    const int H = (T + c->tau_EI) / c->cycle + 2;
+    if (H <= c->sirs_H) return GABM_OK;
+    CK(cudaStreamSynchronize(c->stream));
+    dfree(c, c->sirs_hist); dfree(c, c->sirs_cnt); dfree(c, c->sirs_Gh);
+    c->sirs_H = 0;
+    TRY(dalloc(c, &c->sirs_hist, (size_t)c->n_rows * H));
+    TRY(dalloc(c, &c->sirs_cnt, (size_t)c->n_rows));
+    TRY(dalloc(c, &c->sirs_Gh, (size_t)c->n_rows * H));
+    c->sirs_H = H;
+    c->T_last = -1;
+    c->buffer_generation++;
+    return GABM_OK;
+}
+
 // Day loop of the forward, one set per graph (parameters staged, seeding done).
 gabm_status forward_days_plain(gabm_ctx *c, int t0, int T, cudaStream_t s) {
+    if (c->sirs) return forward_days_sirs(c, t0, T, s);
     const int ld = c->Tcap;
     FwdDayArgs a;
     a.m = sell_view(c, false);
@@ -729,6 +838,7 @@ gabm_status forward_days_plain(gabm_ctx *c, int t0, int T, cudaStream_t s) {
 
 // Reverse sweep, one set per graph (gD staged; r and counters cleared).
 gabm_status backward_days_plain(gabm_ctx *c, int T, cudaStream_t s) {
+    if (c->sirs) return backward_days_sirs(c, T, s);
     const int ld = c->Tcap;
     BwdDayArgs a;
     const int mode = c->soft ? kBwdSoft
@@ -972,7 +1082,7 @@ void apply_schedule(gabm_ctx *c) {
         c->grid_fwd = c->num_sms * occupancy_fwd_b(c->Bp, c->spl_fwd, c->kahan_b);
         c->grid_bwd = c->num_sms * occupancy_bwd_b(c->bwd_chunk, c->spl_bwd, c->kahan_b);
     } else {
-        if (c->fate || c->dur.n > 0) c->smem_bits = false;   // these forwards read the bitmap from global memory
+        if (c->fate || c->dur.n > 0 || c->sirs) c->smem_bits = false;   // these forwards read the bitmap from global memory
         const int bps = c->smem_bits ? occupancy_fwd(c->ntiles, true) : 0;
         if (c->smem_bits && bps <= 0) c->smem_bits = false;
         c->grid_fwd = c->num_sms * (c->smem_bits ? bps : occupancy_fwd(c->ntiles, false));
@@ -990,6 +1100,8 @@ void apply_schedule(gabm_ctx *c) {
     if (c->grid_bwd > max_grid) c->grid_bwd = max_grid;
     if (c->grid_bwd_dc > max_grid) c->grid_bwd_dc = max_grid;
     if (c->grid_bwd_fate > max_grid) c->grid_bwd_fate = max_grid;
+    c->grid_sirs_f = std::min(max_grid, c->num_sms * occupancy_sirs(false));
+    c->grid_sirs_b = std::min(max_grid, c->num_sms * occupancy_sirs(true));
     for (auto &g : c->loop_graph) drop_graph(g);   // captured launches carry the old schedule
 }
 
@@ -1080,6 +1192,9 @@ static gabm_status create_on_device(const HostLayout &H, const gabm_model_desc *
     c->L_R = model->tau_EI + model->tau_IR;
     c->L_M = model->tau_EI + model->tau_IM;
     c->L = model->tau_EI + std::max(model->tau_IR, model->tau_IM);
+    c->sirs = model->tau_RS > 0;
+    c->tau_RS = model->tau_RS;
+    c->cycle = c->L + model->tau_RS;
     c->dur = DurRef{};
     if (model->p_IR) {   // running sums of the duration pmf, in order, in FP64
         c->dur.n = model->tau_IR;
@@ -1261,6 +1376,10 @@ gabm_status gabm_create(const gabm_graph_desc *graphs, int num_graphs, int sets_
                     "need GABM_HARD_ST, sets_per_graph = 1 and GABM_STORE_LAMBDA in this build");
     if (model->tau_IM > 0 && model->p_IR)
         return fail(nullptr, GABM_EUNSUPPORTED, "tau_IM > 0 with p_IR is not built");
+    if (model->tau_RS > 0 && (model->relax_mode != GABM_HARD_ST || sets_per_graph > 1 ||
+                              model->lambda_policy != GABM_STORE_LAMBDA || model->tau_IM > 0 || model->p_IR))
+        return fail(nullptr, GABM_EUNSUPPORTED, "SIRS reinfection (tau_RS > 0) needs GABM_HARD_ST, sets_per_graph = 1, "
+                    "GABM_STORE_LAMBDA, tau_IM = 0 and p_IR = NULL in this build");
 
     // ---- host side: validate, concatenate, transpose ----
     std::vector<HostGraph> hg((size_t)num_graphs);
@@ -1399,7 +1518,7 @@ gabm_status gabm_create_bipartite(const gabm_bipartite_desc *graphs, int num_gra
     if (!graphs || num_graphs < 1 || num_graphs > 65535) return fail(nullptr, GABM_EINVAL, "need 1..65535 graphs");
     TRY(validate_model(model));
     if (model->relax_mode != GABM_HARD_ST || model->lambda_policy != GABM_STORE_LAMBDA || model->tau_IM > 0 ||
-        model->p_IR)
+        model->p_IR || model->tau_RS > 0)
         return fail(nullptr, GABM_EUNSUPPORTED, "agent-location graphs need GABM_HARD_ST, GABM_STORE_LAMBDA, "
                     "tau_IM = 0 and p_IR = NULL in this build");
     int sigma = 1024;
@@ -1645,6 +1764,7 @@ gabm_status gabm_forward(gabm_ctx *ctx, int T, const float *R, const float *m, c
         }
     }
     TRY(ensure_days(c, T));
+    if (c->sirs) TRY(ensure_sirs(c, T));
     const int ld = c->Tcap;
     cudaStream_t s = c->stream;
     CK(cudaMemcpy2DAsync(c->R, ld * sizeof(float), R, T * sizeof(float), T * sizeof(float), c->I, h2d_kind(mem_space), s));
@@ -1710,7 +1830,7 @@ gabm_status gabm_backward_table(gabm_ctx *ctx, const double *gD, double *dR, dou
     if (!dc) return fail(ctx, GABM_EINVAL, "dc is required");
     if (ctx->batched && ctx->policy != GABM_STORE_LAMBDA)
         return fail(ctx, GABM_EUNSUPPORTED, "the table adjoint of several sets per graph needs GABM_STORE_LAMBDA in this build");
-    if (ctx->fate || ctx->dur.n > 0)
+    if (ctx->fate || ctx->dur.n > 0 || ctx->sirs)
         return fail(ctx, GABM_EUNSUPPORTED, "the table adjoint of the sampled R/M split or stochastic durations is not built");
     return backward_impl(ctx, gD, dR, dm, dS_age, dc, mem_space);
 }
@@ -1787,6 +1907,9 @@ gabm_status gabm_set_state(gabm_ctx *ctx, int day, const int16_t *e_in, int mem_
     TRY(check_ms(c, mem_space));
     if (!e_in) return fail(c, GABM_EINVAL, "e_in is NULL");
     if (c->soft) return fail(c, GABM_EUNSUPPORTED, "GABM_SOFT has masses, not exposure days");
+    if (c->sirs)
+        return fail(c, GABM_EUNSUPPORTED, "SIRS reinfection: the last exposure days do not fix the trajectory "
+                    "(a set state would need the exposure histories)");
     if (day < 0 || day > GABM_MAX_DAYS) return fail(c, GABM_EINVAL, "day %d outside 0..%d", day, GABM_MAX_DAYS);
     std::vector<int16_t> h((size_t)c->n_total * c->B);
     if (mem_space == GABM_HOST) {
@@ -1890,7 +2013,7 @@ gabm_status gabm_set_schedule(gabm_ctx *ctx, const gabm_schedule *sched) {
         c->spl_bwd = sched->bwd_sets_per_lane;
         c->bwd_chunk = chunk;
     } else {
-        if (sched->fwd_smem_bitmap && (c->soft || c->two_hop || c->fate || c->dur.n > 0 ||
+        if (sched->fwd_smem_bitmap && (c->soft || c->two_hop || c->fate || c->dur.n > 0 || c->sirs ||
                                        occupancy_fwd(c->ntiles, true) <= 0))
             return fail(c, GABM_EINVAL, "the infectious bitmap (%d words) does not fit in shared memory", c->ntiles);
         c->smem_bits = sched->fwd_smem_bitmap != 0;
@@ -1917,7 +2040,7 @@ gabm_status gabm_autotune(gabm_ctx *ctx, int repetitions) {
             if (batch_config_ok(c->Bp, spl)) fc.push_back(gabm_schedule{spl, cur.bwd_sets_per_lane, 0, cur.bwd_sets_per_launch});
     } else {
         fc.push_back(gabm_schedule{0, 0, 0, 0});
-        if (!c->soft && !c->two_hop && !c->fate && c->dur.n == 0 && occupancy_fwd(c->ntiles, true) > 0)
+        if (!c->soft && !c->two_hop && !c->fate && c->dur.n == 0 && !c->sirs && occupancy_fwd(c->ntiles, true) > 0)
             fc.push_back(gabm_schedule{0, 0, 1, 0});
     }
     cudaEvent_t ev[2];
