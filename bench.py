@@ -470,6 +470,7 @@ def bench_twohop(stream, dist, steps=5, n=1_000_000):
 TAU_IM = 10   # I->M days of the sampled R/M split workload (the paper gives no value)
 # I-stage duration pmf of the stochastic-duration workload (1..9 days; mean 5.7)
 P_IR = np.array([0.02, 0.05, 0.13, 0.2, 0.2, 0.15, 0.12, 0.08, 0.05], np.float32)
+TAU_RS = 10   # days in RM before S again in the SIRS-reinfection workload (the paper gives no value)
 
 
 def bench_progression_variant(pop, stream, S, y_np, dist, peak, peak_kind, variant, steps=5):
@@ -486,10 +487,14 @@ def bench_progression_variant(pop, stream, S, y_np, dist, peak, peak_kind, varia
         md = capi.ModelDesc(TAU_EI, TAU_IR, synth.infectiousness_table(TAU_EI, max(TAU_IR, TAU_IM)), seed=0,
                             tau_IM=TAU_IM)
         what = f"sampled R/M split: tau_EI {TAU_EI}, tau_IR {TAU_IR}, tau_IM {TAU_IM}"
-    else:
+    elif variant == "durations":
         L = TAU_EI + P_IR.size
         md = capi.ModelDesc(TAU_EI, P_IR.size, synth.infectiousness_table(TAU_EI, P_IR.size), seed=0, p_IR=P_IR)
         what = f"stochastic I-stage durations: tau_EI {TAU_EI}, I days ~ pmf {P_IR.round(2).tolist()} over 1..{P_IR.size}"
+    else:
+        L = TAU_EI + TAU_IR
+        md = capi.ModelDesc(TAU_EI, TAU_IR, synth.infectiousness_table(TAU_EI, TAU_IR), seed=0, tau_RS=TAU_RS)
+        what = f"SIRS reinfection: tau_EI {TAU_EI}, tau_IR {TAU_IR}, back to S after tau_RS {TAU_RS}"
     with torch.cuda.stream(stream):
         ctx = capi.gabm_create([pop], md, stream=stream)
         R = torch.full((1, DAYS), R0, dtype=torch.float32, device="cuda")
@@ -522,6 +527,15 @@ def bench_progression_variant(pop, stream, S, y_np, dist, peak, peak_kind, varia
         capi.gabm_set_profiling(ctx, False)
         E = capi.gabm_get_state(ctx)[0]
         D = capi.gabm_forward(ctx, DAYS, R, m, S, [N_SEED])[0].cpu().numpy()[0]
+    out = {"workload": f"{what}, on the bench graph, m = {MORTALITY}, {DAYS} days, forward + MSE + backward",
+           "ms_per_step": ms, "steps": steps, "value": pop.n * DAYS / (ms / 1e3), "unit": "agent-days/s",
+           "deaths": float(D.sum())}
+    if variant == "sirs":
+        # the final state does not fix who was susceptible on each day under reinfection,
+        # so the base model's byte count does not apply; launch times only
+        out.update({"fwd_day": {"avg_launch_ms": f_ms / f_n}, "bwd_day": {"avg_launch_ms": b_ms / b_n},
+                    "agents_last_exposed_after_day_0_share": float(np.mean((E >= 0) & (E != 32767)))})
+        return out
     n_rows = ((pop.n + 31) // 32) * 32
     fwd_b, bwd_b, _, _ = trajectory_bytes(E, pop.degrees().astype(np.float64), DAYS, L, n_rows, True)
     f_gbs = fwd_b.sum() * steps / (f_ms / 1e3) / 1e9
@@ -772,6 +786,10 @@ def main():
     batched = None
     if not args.no_batched:
         batched = bench_batched(args, stream, peak, peak_kind)
+    try:   # the last GPU section: a failure here is reported in its own key
+        sirs = bench_progression_variant(pop, stream, S, y_np, dist, peak, peak_kind, "sirs")
+    except Exception as exc:
+        sirs = {"error": f"{type(exc).__name__}: {exc}"}
     if rank != 0:
         return
     cpu = None
@@ -801,6 +819,7 @@ def main():
         "agent_location": twohop,
         "rm_split": rm_split,
         "stochastic_durations": durations,
+        "sirs_reinfection": sirs,
         "batched": batched,
     }
     print(json.dumps(line), flush=True)
