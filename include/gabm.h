@@ -248,7 +248,8 @@ gabm_status gabm_get_state(gabm_ctx *ctx, int16_t *e_out, int mem_space);
  * seeding; a gabm_forward with T == day only records its parameters, after
  * which gabm_backward (GABM_RECOMPUTE, one set per graph) replays the trajectory e
  * encodes.  With several sets per graph a backward needs a forward over days 0..T-1
- * (GABM_ESTATE after a forward from a set state at day > 0).
+ * (GABM_ESTATE after a forward from a set state at day > 0).  GABM_EUNSUPPORTED under
+ * SIRS reinfection (tau_RS > 0), whose trajectory the last exposure days do not fix.
  * Values must be GABM_NEVER or in [-GABM_MAX_L, day). */
 gabm_status gabm_set_state(gabm_ctx *ctx, int day, const int16_t *e_in, int mem_space);
 

@@ -92,6 +92,12 @@ def test_create_rejects_bad_models(lib):
         _expect(capi.GABM_EUNSUPPORTED, [pop], _md(**kw), sets=sets)
     with pytest.raises(ValueError):
         capi.gabm_create([pop], _md(tau_IM=9))   # c must have tau_EI + max(tau_IR, tau_IM) = 13 entries
+    # SIRS reinfection (tau_RS)
+    _expect(capi.GABM_EINVAL, [pop], _md(tau_RS=-1))
+    for kw, sets in ((dict(tau_RS=5, relax_mode=capi.GABM_SOFT), 1), (dict(tau_RS=5), 3),
+                     (dict(tau_RS=5, lambda_policy=capi.GABM_RECOMPUTE), 1), (dict(tau_RS=5, p_IR=pmf), 1),
+                     (dict(tau_RS=5, tau_IM=9, c=synth.infectiousness_table(4, 9)), 1)):
+        _expect(capi.GABM_EUNSUPPORTED, [pop], _md(**kw), sets=sets)
     # parameter sets per graph: up to 64; without the lambda store only on symmetric weights
     _expect(capi.GABM_EUNSUPPORTED, [pop], _md(), sets=65)
     _expect(capi.GABM_EUNSUPPORTED, [synth.random_directed(64, 4.0, seed=3)],
