@@ -69,16 +69,20 @@ def _infectiousness(md, e, t):
     return x
 
 
-def forward(pop, md: SirsModel, R, m, S_age, n_seed: int = 0, inst: int = 0):
-    """Hard forward of days 0..T-1 from the seeded state.  Returns e_final (last exposure
+def forward(pop, md: SirsModel, R, m, S_age, n_seed: int = 0, inst: int = 0, e0=None):
+    """Hard forward of days 0..T-1 from the seeded state (or the day-0 state e0: exposure
+    days before day 0, or NEVER).  Returns e_final (last exposure
     days), exposures (list of (day, agent) in order), e_hist [T+1, n] (the state at the
     start of each day), D, newRM, counts [T, 4] (S, E, I, RM) and margin."""
     R = np.asarray(R, np.float32); m = np.asarray(m, np.float32); S = np.asarray(S_age, np.float32)
     T = R.size
     n = pop.n
     ids = np.arange(n, dtype=np.uint32)
-    e = np.full(n, NEVER, np.int64)
-    e[select_seeds(n, md.seed, inst, n_seed)] = -md.tau_EI
+    if e0 is None:
+        e = np.full(n, NEVER, np.int64)
+        e[select_seeds(n, md.seed, inst, n_seed)] = -md.tau_EI
+    else:
+        e = np.asarray(e0, np.int64).copy()
     A = _csr(pop)
     Dbar = float(np.sum(np.asarray(pop.w, np.float64))) / n
     age = np.asarray(pop.age, np.int64)
