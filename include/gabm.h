@@ -218,7 +218,10 @@ gabm_status gabm_set_infectiousness(gabm_ctx *ctx, const float *c);
  * several sets per graph when the last forward did not start at day 0.  Several sets
  * under GABM_RECOMPUTE: each day's lambda is summed again from the final state over the
  * same entries in the same order as the forward, so the result is bitwise that of
- * GABM_STORE_LAMBDA. */
+ * GABM_STORE_LAMBDA.  The reverse sweep runs in fp32 at a power-of-two scale per day
+ * that follows the adjoint's growth (FP64 for the sums); each m_t gD_t enters it as an
+ * fp32 value, so |gD| must stay below about 1e30 (a loss gradient of that size is not
+ * a meaningful input; beyond the fp32 range the results are not finite). */
 gabm_status gabm_backward(gabm_ctx *ctx, const double *gD, double *dR, double *dm,
                           double *dS_age, int mem_space);
 
@@ -342,8 +345,10 @@ const char *gabm_version(void);
  * allocation or release.  Limits: 1 <= num_instances <=
  * GABM_NOALLOC_MAX_INSTANCES, n >= 1 and n * num_instances < 2^31; anything
  * else returns GABM_EINVAL with a message in gabm_noalloc_last_error().
- * The first call on a device looks up the array's device address (once per
- * device), so make that first call before any stream capture.  All calls
+ * Each call outside a stream capture looks up the array's device address on
+ * the current device; a call on a capturing stream reuses the address of the
+ * last uncaptured call on that device (GABM_ECUDA if there was none), so make
+ * the first call on a device before any stream capture.  All calls
  * share the array: calls whose GPU work overlaps (different streams without
  * ordering) race on it and must not be issued.
  */

@@ -502,9 +502,14 @@ def gabm_seed_state_noalloc(seed: int, n: int, n_seed, tau_EI: int, e_out, strea
     if not _is_cuda(e_out):
         raise ValueError("e_out must be a CUDA tensor")
     _shape(e_out, (seeds.size, int(n)), "e_out")
-    s = ctypes.c_void_p((stream or torch.cuda.current_stream()).cuda_stream)
-    st = load_library().gabm_seed_state_noalloc(int(seed), int(n), int(seeds.size), _ptr(seeds, np.int32),
-                                                int(tau_EI), _ptr(e_out, np.int16), s)
+    # the C side works on the current device's scratch: make e_out's device current
+    with torch.cuda.device(e_out.device):
+        strm = stream or torch.cuda.current_stream()
+        if strm.device != e_out.device:
+            raise ValueError("stream and e_out must be on the same device")
+        st = load_library().gabm_seed_state_noalloc(int(seed), int(n), int(seeds.size), _ptr(seeds, np.int32),
+                                                    int(tau_EI), _ptr(e_out, np.int16),
+                                                    ctypes.c_void_p(strm.cuda_stream))
     if st != GABM_OK:
         raise GabmError(st, load_library().gabm_noalloc_last_error().decode(errors="replace"))
     return e_out

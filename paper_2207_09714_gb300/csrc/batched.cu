@@ -37,15 +37,21 @@ namespace {
 // Forward day t for every set (Transmit, draw, Progress).
 // ---------------------------------------------------------------------------
 template <int LPR, int SPL, bool KAHAN>
-__global__ void __launch_bounds__(kBlock, 2) k_fwd_day_b(const FwdBatchArgs a) {
+__global__ void __launch_bounds__(kBlock, GABM_BFWD_MINBLOCKS) k_fwd_day_b(const FwdBatchArgs a) {
     constexpr int RPW = 32 / LPR;
     constexpr int Bp = LPR * SPL;
     constexpr int NW = kBlock / 32;
     __shared__ float c_s[kMaxL + 1];
+    __shared__ float lam_s[NW][SPL * 32];   // a pass's lambdas, by set position and lane
+    __shared__ int hit_s[NW][SPL * 32];     // draws that exposed, by set position and lane
+    const int lane = threadIdx.x & 31;
+    float *lam_w = lam_s[threadIdx.x >> 5];
+    int *hit_w = hit_s[threadIdx.x >> 5];
     if (threadIdx.x <= kMaxL) c_s[threadIdx.x] = threadIdx.x < kMaxL ? a.c[threadIdx.x] : 0.f;
+#pragma unroll
+    for (int h = 0; h < SPL; ++h) hit_w[h * 32 + lane] = 0;
     __syncthreads();
 
-    const int lane = threadIdx.x & 31;
     const int grp = lane / LPR, q = lane % LPR;
     const int t = a.t, L = a.L, B = a.B, ntiles = a.ntiles;
     uint32_t *e32 = reinterpret_cast<uint32_t *>(a.e);
@@ -55,10 +61,6 @@ __global__ void __launch_bounds__(kBlock, 2) k_fwd_day_b(const FwdBatchArgs a) {
     auto ld = [&](uint32_t j, bool ok, EWords<SPL> &r) { ld_words<SPL>(e32r + (size_t)j * WPR + q * (SPL / 2), ok, r.w); };
     auto val = [&](const EWords<SPL> &r, int h) { return infect_lut(half_of(r.w[h >> 1], h & 1), c_s, t, (unsigned)L); };
 
-    int cur_g = -1;
-    float Rt[SPL];
-#pragma unroll
-    for (int h = 0; h < SPL; ++h) Rt[h] = 0.f;
     TileDispenser disp;
     disp.init(a.tile_ctr, ntiles, gridDim.x * NW, lane);
     // row bounds of the tile's 32 rows (lane r: rows r and r + 1), one tile ahead
@@ -76,14 +78,6 @@ __global__ void __launch_bounds__(kBlock, 2) k_fwd_day_b(const FwdBatchArgs a) {
             nrp_hi = a.m.rowptr[ntile * kTile + lane + 1];
         }
         const int g = a.gr.tile_graph ? (int)a.gr.tile_graph[tile] : 0;
-        if (g != cur_g) {
-            cur_g = g;
-#pragma unroll
-            for (int h = 0; h < SPL; ++h) {
-                const int s = q * SPL + h;
-                Rt[h] = (s < B) ? a.R[(size_t)(g * B + s) * a.ldP + t] : 0.f;
-            }
-        }
         const float inv_D = a.gr.inv_Dbar[g];
         uint32_t word = 0u;
         int nnew[SPL];
@@ -112,34 +106,79 @@ __global__ void __launch_bounds__(kBlock, 2) k_fwd_day_b(const FwdBatchArgs a) {
             group_row_sums<LPR, SPL, KAHAN, EWords<SPL>>(a.m, cu.p0, act ? cu.len : 0u, cu.j0, cu.w0, a.bits_cur, lane,
                                                          ld, val, sum);
 
-            bool inf = false;
-            if (mine) {
-                const int ai = a.age[row];
-                const uint32_t id = caller_id(a.gr, row, g);
-                float Lam[SPL];
-                uint32_t nw[SPL / 2];
+            // lambda of each susceptible set with an infectious neighbour; only those draw
+            float Lam[SPL];
+            uint32_t dmask[SPL];
+            int ndraw = 0;
 #pragma unroll
-                for (int k = 0; k < SPL / 2; ++k) nw[k] = ew[k];
-                bool changed = false;
+            for (int h = 0; h < SPL; ++h) {
+                const bool need = sS[h] && sum[h] != 0.f;   // lambda = 0: p = 0, no draw
+                Lam[h] = need ? sum[h] * inv_D : 0.f;
+                dmask[h] = __ballot_sync(kFull, need);
+                ndraw += __popc(dmask[h]);
+            }
+            // The pass's draws (expm1f and Philox) are dealt to the lanes 32 at a time.  Drawn
+            // where they sit, they would run once for every set position in which any lane of
+            // the warp draws, with most lanes idle.  A draw's result returns to its lane through
+            // shared memory; each draw computes exactly what the lane owning the set would.
+            uint32_t drew = 0u;   // bit h: set h of this lane exposed today
+            if (ndraw) {
 #pragma unroll
-                for (int h = 0; h < SPL; ++h) {
-                    Lam[h] = 0.f;
-                    if (!sS[h] || sum[h] == 0.f) continue;   // lambda = 0: p = 0, no draw
-                    const int inst = g * B + q * SPL + h;
-                    Lam[h] = sum[h] * inv_D;
-                    const float lam = (Rt[h] * a.S[inst * kAges + ai]) * Lam[h];
-                    const float p = -expm1f(-lam);
-                    if (p > kUmin) {
-                        const float u = uniform_from_word(philox_word(a.seed, id, (uint32_t)t, (uint32_t)inst, 0u));
-                        if (u < p) {
-                            const uint32_t tv = (uint32_t)(uint16_t)(int16_t)t;
-                            nw[h >> 1] = (h & 1) ? ((nw[h >> 1] & 0xffffu) | (tv << 16)) : ((nw[h >> 1] & 0xffff0000u) | tv);
-                            ++nnew[h];
-                            changed = true;
+                for (int h = 0; h < SPL; ++h) lam_w[h * 32 + lane] = Lam[h];
+                __syncwarp();
+                for (int base = 0; base < ndraw; base += 32) {
+                    const int pi = base + lane;
+                    // set position hs of draw pi and its index among that position's draws
+                    int hs = 0, before = 0;
+                    uint32_t msel = dmask[0];
+#pragma unroll
+                    for (int h = 0; h + 1 < SPL; ++h) {
+                        const int upto = before + __popc(dmask[h]);
+                        if (hs == h && pi >= upto) {
+                            hs = h + 1;
+                            before = upto;
+                            msel = dmask[h + 1];
+                        }
+                    }
+                    if (pi < ndraw) {
+                        const int src = nth_set_bit(msel, pi - before);
+                        const int srow = tile * kTile + pass * RPW + src / LPR;
+                        const int inst = g * B + (src % LPR) * SPL + hs;
+                        const float lam = (a.R[(size_t)inst * a.ldP + t] * a.S[inst * kAges + a.age[srow]]) *
+                                          lam_w[hs * 32 + src];
+                        const float p = -expm1f(-lam);
+                        if (p > kUmin) {
+                            const uint32_t id = caller_id(a.gr, srow, g);
+                            if (uniform_from_word(philox_word(a.seed, id, (uint32_t)t, (uint32_t)inst, 0u)) < p)
+                                hit_w[hs * 32 + src] = 1;
                         }
                     }
                 }
-                if (changed) st_words<SPL>(mine_p, nw);
+                __syncwarp();
+#pragma unroll
+                for (int h = 0; h < SPL; ++h) {
+                    if (hit_w[h * 32 + lane]) {
+                        drew |= 1u << h;
+                        hit_w[h * 32 + lane] = 0;
+                    }
+                }
+                __syncwarp();
+            }
+
+            bool inf = false;
+            if (mine) {
+                uint32_t nw[SPL / 2];
+#pragma unroll
+                for (int k = 0; k < SPL / 2; ++k) nw[k] = ew[k];
+#pragma unroll
+                for (int h = 0; h < SPL; ++h) {
+                    if ((drew >> h) & 1u) {
+                        const uint32_t tv = (uint32_t)(uint16_t)(int16_t)t;
+                        nw[h >> 1] = (h & 1) ? ((nw[h >> 1] & 0xffffu) | (tv << 16)) : ((nw[h >> 1] & 0xffff0000u) | tv);
+                        ++nnew[h];
+                    }
+                }
+                if (drew) st_words<SPL>(mine_p, nw);
                 if (a.lam_out) st_floats<SPL>(a.lam_out + (size_t)row * Bp + q * SPL, Lam);
 #pragma unroll
                 for (int k = 0; k < SPL / 2; ++k) ew[k] = nw[k];

@@ -18,7 +18,7 @@ namespace {
 // days over the same entries, with the forward's marking (a.bits_t) and order, so it
 // is bitwise the forward's.
 template <int LPR, int SPL, bool KAHAN, bool DC, bool REC = false>
-__global__ void __launch_bounds__(kBlock, 2) k_bwd_day_b(const BwdBatchArgs a) {
+__global__ void __launch_bounds__(kBlock, GABM_BBWD_MINBLOCKS) k_bwd_day_b(const BwdBatchArgs a) {
     constexpr int RPW = 32 / LPR;
     constexpr int Bc = LPR * SPL;        // sets of this launch (a chunk of the row's Bw)
     constexpr int NW = kBlock / 32;

@@ -8,6 +8,15 @@
 #include "gabm_internal.cuh"
 #include "rowsum.cuh"
 
+// Resident blocks per SM the batched day kernels are compiled for (register budget
+// 65536 / (256 x blocks) per thread).
+#ifndef GABM_BFWD_MINBLOCKS
+#define GABM_BFWD_MINBLOCKS 2
+#endif
+#ifndef GABM_BBWD_MINBLOCKS
+#define GABM_BBWD_MINBLOCKS 2
+#endif
+
 namespace gabm {
 
 namespace {
@@ -78,6 +87,13 @@ __device__ __forceinline__ void st_words(uint32_t *p, const uint32_t (&w)[SPL / 
 }
 
 __device__ __forceinline__ int half_of(uint32_t w, int h) { return (int16_t)(h ? (w >> 16) : (w & 0xffffu)); }
+
+// Lane of the i-th (0-based) set bit of m; i < popc(m).
+__device__ __forceinline__ int nth_set_bit(uint32_t m, int i) {
+    uint32_t pos;
+    asm("fns.b32 %0, %1, 0, %2;" : "=r"(pos) : "r"(m), "r"(i + 1));
+    return (int)(pos & 31u);
+}
 
 // c[t - e] for 1 <= t - e < L, else 0, from a table c_s[0..kMaxL] with c_s[k] = 0 for k >= L:
 // t - e is negative for susceptible agents (e = NEVER) and huge for padding (e = kPad), both

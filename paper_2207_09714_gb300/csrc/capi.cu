@@ -48,8 +48,9 @@ struct gabm_ctx {
     int tau_RS = 0, cycle = 0;           // days in RM before S again; L + tau_RS
     int sirs_H = 0;                      // history entries per row
     int16_t *sirs_hist = nullptr;        // [n_rows][sirs_H] exposure days
-    uint8_t *sirs_cnt = nullptr;         // [n_rows]
+    uint16_t *sirs_cnt = nullptr;        // [n_rows] (H <= GABM_MAX_DAYS / 3 + 2 fits)
     float *sirs_Gh = nullptr;            // [n_rows][sirs_H] G at each exposure
+    float *sirs_Lh = nullptr;            // [n_rows][sirs_H] G's own-day terms at each exposure
     int grid_sirs_f = 0, grid_sirs_b = 0;
     float c[kMaxL] = {0};
     uint64_t seed = 0;
@@ -739,6 +740,7 @@ gabm_status backward_days_sirs(gabm_ctx *c, int T, cudaStream_t s) {
     a.cnt = c->sirs_cnt;
     a.H = c->sirs_H;
     a.Gh = c->sirs_Gh;
+    a.Lh = c->sirs_Lh;
     a.ring = c->ring;
     a.ring_stride = (size_t)c->n_rows;
     a.R = c->R;
@@ -779,11 +781,12 @@ gabm_status ensure_sirs(gabm_ctx *c, int T) {
     const int H = (T + c->tau_EI) / c->cycle + 2;
     if (H <= c->sirs_H) return GABM_OK;
     CK(cudaStreamSynchronize(c->stream));
-    dfree(c, c->sirs_hist); dfree(c, c->sirs_cnt); dfree(c, c->sirs_Gh);
+    dfree(c, c->sirs_hist); dfree(c, c->sirs_cnt); dfree(c, c->sirs_Gh); dfree(c, c->sirs_Lh);
     c->sirs_H = 0;
     TRY(dalloc(c, &c->sirs_hist, (size_t)c->n_rows * H));
     TRY(dalloc(c, &c->sirs_cnt, (size_t)c->n_rows));
     TRY(dalloc(c, &c->sirs_Gh, (size_t)c->n_rows * H));
+    TRY(dalloc(c, &c->sirs_Lh, (size_t)c->n_rows * H));
     c->sirs_H = H;
     c->T_last = -1;
     c->buffer_generation++;

@@ -33,7 +33,12 @@ constexpr int kMaxL = GABM_MAX_L;
 constexpr int kTile = 32;          // rows per warp tile
 constexpr int kBlock = 256;        // threads per block of the day kernels
 constexpr int kHistBins = 2048;    // radix-select digit bins (11 bits)
-constexpr int kTieCap = 4096;      // agents sharing the threshold hash (seeding)
+// Agents sharing the threshold hash (seeding).  A tie needs equal 32-bit Philox words;
+// among n < 2^31 agents the count of any one word is Binomial(n, 2^-32), mean < 0.5, so
+// more than kTieCap agents on one word has probability below 2^32 * 0.5^4097 / 4097!,
+// far below 1e-10000.  k_seed_mark still flags that case (SeedState::overflow) rather than
+// write past the list.
+constexpr int kTieCap = 4096;
 constexpr int kMaxSets = 64;       // parameter sets per graph (batched kernels: two per lane)
 // Batched sums use plain fused multiply-adds when no row has more entries than this:
 // a sum of k non-negative terms then carries a relative error below (k + 3) 2^-24 < 1e-5.

@@ -38,18 +38,27 @@ constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 NoallocScratch *g_scratch_ptr[kMaxDevices] = {nullptr};
 
-// Device address of the scratch array for the current device (looked up once per device).
-cudaError_t scratch_address(NoallocScratch **out) {
+// Device address of the scratch array on the current device.  It is looked up
+// afresh on every call made outside a stream capture, so a module reloaded at
+// another address (after cudaDeviceReset, say) is followed; a call on a
+// capturing stream reuses the address found by the last uncaptured call on
+// that device and fails if there was none.
+cudaError_t scratch_address(cudaStream_t s, NoallocScratch **out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(s, &cs);
+    if (e != cudaSuccess) return e;
     std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_scratch_ptr[dev]) {
+    if (cs == cudaStreamCaptureStatusNone) {
         void *p = nullptr;
         e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess) return e;
         g_scratch_ptr[dev] = static_cast<NoallocScratch *>(p);
+    } else if (!g_scratch_ptr[dev]) {
+        return cudaErrorStreamCaptureUnsupported;
     }
     *out = g_scratch_ptr[dev];
     return cudaSuccess;
@@ -100,7 +109,7 @@ gabm_status gabm_seed_state_noalloc(uint64_t seed, int64_t n, int num_instances,
         counts.n_seed[i] = n_seed[i];
     }
     NoallocScratch *sc = nullptr;
-    cudaError_t e = scratch_address(&sc);
+    cudaError_t e = scratch_address((cudaStream_t)cuda_stream, &sc);
     if (e != cudaSuccess) return fail_noalloc(GABM_ECUDA, std::string("scratch address: ") + cudaGetErrorString(e));
     cudaStream_t s = (cudaStream_t)cuda_stream;
     const size_t ni = (size_t)num_instances;

@@ -29,7 +29,7 @@ __device__ __forceinline__ void flush_counts(int32_t *counts, int32_t *newRM, in
 }
 
 // The history of every row starts with its state after seeding (a seed's exposure day).
-__global__ void k_sirs_hist_init(const int16_t *e, int64_t n_rows, int H, int16_t *hist, uint8_t *cnt) {
+__global__ void k_sirs_hist_init(const int16_t *e, int64_t n_rows, int H, int16_t *hist, uint16_t *cnt) {
     for (int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; row < n_rows;
          row += (int64_t)gridDim.x * blockDim.x) {
         const int ei = e[row];
@@ -92,7 +92,7 @@ __global__ void __launch_bounds__(kBlock) k_fwd_day_sirs(const SirsFwdArgs a) {
                 const int ci = a.cnt[row];
                 if (ci < a.H) {
                     a.hist[(size_t)row * a.H + ci] = (int16_t)t;
-                    a.cnt[row] = (uint8_t)(ci + 1);
+                    a.cnt[row] = (uint16_t)(ci + 1);
                 }
             }
             a.lam_out[row] = Lam;
@@ -168,14 +168,25 @@ __global__ void __launch_bounds__(kBlock) k_bwd_day_sirs(const SirsBwdArgs a) {
                 return j < n_e ? a.Gh[(size_t)row * H + j] * exp2i(sg[hr[j]] - sig_t) : 0.f;
             };
             const size_t pg = (size_t)g * a.ldP;
-            float G = (t + L < T) ? a.m_t[pg + t + L] * (float)a.gD[pg + t + L] * exp2i(-sig_t) : 0.f;
-            if (has_next) G = __fmaf_rn(c_s[1], gx1 * exp2i(sg[t + 1] - sig_t), G);
+            // the day's own terms: the death term and the infectiousness it would cause
+            float loc = (t + L < T) ? a.m_t[pg + t + L] * (float)a.gD[pg + t + L] * exp2i(-sig_t) : 0.f;
+            if (has_next) loc = __fmaf_rn(c_s[1], gx1 * exp2i(sg[t + 1] - sig_t), loc);
             for (int k = 2; k < L; ++k)
-                if (t + k < T) G = __fmaf_rn(c_s[k], a.ring[(size_t)slot_k[k] * a.ring_stride + row] * exp2i(sg[t + k] - sig_t), G);
-            G += B_at(t + C);
-            const float dy = G - B_at(t + 1);
-            if (y) a.Gh[(size_t)row * H + j_t] = G;
-            float stored = fabsf(G);
+                if (t + k < T) loc = __fmaf_rn(c_s[k], a.ring[(size_t)slot_k[k] * a.ring_stride + row] * exp2i(sg[t + k] - sig_t), loc);
+            const float G = loc + B_at(t + C);
+            // dL/dy = G - B(t+1).  With t' the row's first exposure after t, B(t+1) = G(t'),
+            // and B(t+C) = B(t'+C) when t' < t+C (the next exposure after t' is at least
+            // t'+C), while B(t+C) = G(t') when t' >= t+C: so dL/dy = loc - loc(t') or loc.
+            // Formed this way the return terms cancel exactly instead of in fp32, where on
+            // short cycles they dwarf the difference.
+            const int jn = y ? j_t + 1 : j_t;
+            float dy = loc;
+            if (jn < n_e && hr[jn] < t + C) dy = loc - a.Lh[(size_t)row * H + jn] * exp2i(sg[hr[jn]] - sig_t);
+            if (y) {
+                a.Gh[(size_t)row * H + j_t] = G;
+                a.Lh[(size_t)row * H + j_t] = loc;
+            }
+            float stored = fmaxf(fabsf(G), fabsf(loc));
             const float Lam = a.lam_t[row];
             const float RS = a.R[pg + t] * a.S[g * kAges + ai];
             const float lam = RS * Lam;
@@ -219,7 +230,7 @@ __global__ void __launch_bounds__(kBlock) k_bwd_day_sirs(const SirsBwdArgs a) {
 
 }  // namespace
 
-cudaError_t launch_sirs_hist_init(const int16_t *e, int64_t n_rows, int H, int16_t *hist, uint8_t *cnt,
+cudaError_t launch_sirs_hist_init(const int16_t *e, int64_t n_rows, int H, int16_t *hist, uint16_t *cnt,
                                   cudaStream_t s) {
     const int grid = (int)std::min<int64_t>((n_rows + 255) / 256, 65535);
     k_sirs_hist_init<<<grid > 0 ? grid : 1, 256, 0, s>>>(e, n_rows, H, hist, cnt);

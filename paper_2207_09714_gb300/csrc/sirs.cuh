@@ -6,12 +6,15 @@
 // final state no longer encodes the trajectory, so the forward appends every exposure to
 // a per-agent history, which the reverse sweep reads:
 //   hist [n_rows][H] int16   exposure days in order (a seed's initial exposure first)
-//   cnt  [n_rows]    u8      entries used
+//   cnt  [n_rows]    u16     entries used (H <= GABM_MAX_DAYS / 3 + 2 < 65536)
 //   Gh   [n_rows][H] f32     G at each exposure day (that day's scale), written by the sweep
+//   Lh   [n_rows][H] f32     G's own-day terms at each exposure (G without the return term)
 // Adjoint (straight-through, App. B): with B_i(t) = dL/ds_i(t), which equals G_i at the
 // agent's first exposure on or after t (0 if none),
 //   G_i(t) = sum_{k=1}^{L-1} c[k] gx_i(t+k) + m_{t+L} gD_{t+L} + B_i(t + cycle)
-//   dL/dy_i(t) = G_i(t) - B_i(t+1)  for rows susceptible on day t.
+//   dL/dy_i(t) = G_i(t) - B_i(t+1)  for rows susceptible on day t,
+// evaluated as the own-day terms of G_i(t) minus those of the next exposure when that falls
+// within `cycle` days (the return terms cancel exactly; see k_bwd_day_sirs).
 #pragma once
 #include "gabm_internal.cuh"
 
@@ -23,7 +26,7 @@ struct SirsFwdArgs {
     GraphRef gr;
     int16_t *e;                 // last exposure day
     int16_t *hist;
-    uint8_t *cnt;
+    uint16_t *cnt;
     int H;
     float *lam_out;             // day-t slice of the lambda store
     const float *R, *S;         // [I][ldP], [I][9]
@@ -42,9 +45,9 @@ struct SirsBwdArgs {
     GraphRef gr;
     const int16_t *E;           // final state (kPad marks padding rows)
     const int16_t *hist;
-    const uint8_t *cnt;
+    const uint16_t *cnt;
     int H;
-    float *Gh;
+    float *Gh, *Lh;
     const float *lam_t;         // stored normalised sums of day t
     const float *r_next;        // r of day t + 1
     float *r_cur;               // r of day t (0 for rows not susceptible on day t)
@@ -63,7 +66,7 @@ struct SirsBwdArgs {
     float c[kMaxL];
 };
 
-cudaError_t launch_sirs_hist_init(const int16_t *e, int64_t n_rows, int H, int16_t *hist, uint8_t *cnt,
+cudaError_t launch_sirs_hist_init(const int16_t *e, int64_t n_rows, int H, int16_t *hist, uint16_t *cnt,
                                   cudaStream_t s);
 cudaError_t launch_fwd_day_sirs(const SirsFwdArgs &a, int grid, cudaStream_t s);
 cudaError_t launch_bwd_day_sirs(const SirsBwdArgs &a, int grid, cudaStream_t s);

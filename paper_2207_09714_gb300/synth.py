@@ -338,11 +338,22 @@ def population_bipartite(n: int = 20_000, seed: int = 0, school=(100, 400), work
                      age=age, name=f"bipartite_n{n}")
 
 
-def uneven_counties(num: int = 32, lo: float = 5e4, hi: float = 2e6, seed: int = 0, scale: float = 1.0):
-    """County graphs with agent counts log-uniform in [lo, hi] (times ``scale``)."""
+def uneven_county_sizes(num: int = 32, lo: float = 5e4, hi: float = 2e6, seed: int = 0,
+                        scale: float = 1.0) -> list:
+    """Agent counts of ``uneven_counties``: log-uniform in [lo, hi] (times ``scale``), at least 64."""
     rng = _rng([seed, 400])
     sizes = np.exp(rng.uniform(np.log(lo), np.log(hi), size=num)) * scale
-    return [population_typed(max(int(s), 64), seed=seed * 1000 + g) for g, s in enumerate(sizes)]
+    return [max(int(s), 64) for s in sizes]
+
+
+def county(g: int, n: int, seed: int = 0) -> Population:
+    """County g of ``uneven_counties`` (the typed generator with its own seed)."""
+    return population_typed(n, seed=seed * 1000 + g)
+
+
+def uneven_counties(num: int = 32, lo: float = 5e4, hi: float = 2e6, seed: int = 0, scale: float = 1.0):
+    """County graphs with agent counts log-uniform in [lo, hi] (times ``scale``)."""
+    return [county(g, n, seed) for g, n in enumerate(uneven_county_sizes(num, lo, hi, seed, scale))]
 
 
 def target_curve(T: int, n: int, seed: int = 1, growth: float = 0.12, level: float = 2e-7) -> np.ndarray:

@@ -10,7 +10,7 @@ import pytest
 import oracle as O
 from paper_2207_09714_gb300 import capi, synth
 
-from helpers import EXACT_MARGIN, check_adjoint, ensure_built, model, to_dev, torch_cuda
+from helpers import EXACT_MARGIN, NEVER, check_adjoint, ensure_built, model, to_dev, torch_cuda
 
 pytestmark = pytest.mark.gpu
 
@@ -232,19 +232,35 @@ def test_full_size_replay_adjoint(full_size_adjoint):
 
 
 def test_full_size_store_policy_pipeline(full_size_adjoint):
-    """The benchmark's own call sequence (store policy, device buffers) at full size."""
+    """The benchmark's own call sequence (store policy, device buffers) at full size.
+
+    At 1M agents x 60 days some draw lies within the kernel's fp32 error of its
+    threshold on most seeds, so the GPU may take another trajectory than the oracle's
+    run after such a near-tie (the lockstep tests hold each day's decisions to the
+    flip rule).  The check is therefore made on the GPU's own trajectory, whatever it
+    is: its deaths equal m_t times the exits that its final state implies, its loss
+    gradient equals the oracle's MSE gradient of those deaths, and its adjoint equals
+    the oracle's adjoint of that trajectory."""
     pop, T, R, m, S, ref, y, loss, gD, g = full_size_adjoint
+    L = 11
     ctx = capi.gabm_create([pop], model(seed=0))
     Rd, md_, Sd, yd = to_dev(R[None, :], m[None, :], S[None, :], y[None, :])
     D, _ = capi.gabm_forward(ctx, T, Rd, md_, Sd, [20])
-    same = np.array_equal(capi.gabm_get_state(ctx)[0], ref["e_final"])
-    _, gDd = capi.gabm_mse_loss(ctx, yd)
+    E = capi.gabm_get_state(ctx)[0].astype(np.int64)
+    exits = np.bincount(E[(E != NEVER) & (E + L >= 0) & (E + L < T)] + L, minlength=T)
+    D_ref = m.astype(np.float64) * exits
+    assert np.array_equal(D.cpu().numpy()[0], D_ref)
+    loss_gpu, gDd = capi.gabm_mse_loss(ctx, yd)
+    loss_ref, gD_ref = O.mse(D_ref, y)
+    assert abs(float(loss_gpu.cpu().numpy().ravel()[0]) - loss_ref) <= 1e-12 * abs(loss_ref)
+    assert np.allclose(gDd.cpu().numpy()[0], gD_ref, rtol=1e-12, atol=0)
     dR, dm, dS = [x.cpu().numpy()[0] for x in capi.gabm_backward(ctx, gDd)]
-    assert np.all(np.isfinite(dR)) and np.all(np.isfinite(dS))
-    if same:
-        check_adjoint(dR, g["dR"], "dR")
-        check_adjoint(dm, g["dm"], "dm")
-        check_adjoint(dS, g["dS"], "dS")
+    md_o = O.Model(4, 7, synth.infectiousness_table(), seed=0)
+    g_own = O.backward_hard(pop, md_o, R, m, S, E.astype(np.int16), gDd.cpu().numpy()[0])
+    check_adjoint(dR, g_own["dR"], "dR")
+    check_adjoint(dm, g_own["dm"], "dm")
+    check_adjoint(dS, g_own["dS"], "dS")
+    assert np.abs(g_own["dR"]).max() > 0
 
 
 def test_long_horizon_adjoint_beyond_fp32_range():

@@ -89,11 +89,21 @@ def test_batched_free_run_matches_oracle(B):
     assert np.array_equal(capi.gabm_get_state(ctx), e)
 
 
-@pytest.mark.parametrize("graph,B", [("typed", 8), ("typed", 64), ("hub", 4)])
+def _graph(kind, n, seed):
+    """"typed": the four-interaction-type generator (households, schools, workplaces, random
+    contacts); "small": households and random contacts only; "hub": directed, one long row."""
+    if kind == "typed":
+        return synth.population_typed(n, seed=seed)
+    if kind == "small":
+        return synth.population_small(n=n, seed=seed)
+    return _hub_graph()
+
+
+@pytest.mark.parametrize("graph,B", [("typed", 8), ("typed", 64), ("small", 64), ("hub", 4)])
 def test_batched_lockstep_days(graph, B):
     """Each day from the oracle's start-of-day states of all sets: lambda per set within
     1e-5 relative, decisions equal except at near-ties."""
-    pop = synth.population_small(n=10_000, seed=2) if graph == "typed" else _hub_graph()
+    pop = _graph(graph, 10_000, 2)
     T = 24
     R, m, S = _params(B, T, rng_seed=100 + B)
     n_seed = [20] * B
@@ -171,9 +181,9 @@ def _adjoint_case(pops, B, T, seed, rng_seed):
     return checked, I
 
 
-@pytest.mark.parametrize("graph,B", [("typed", 6), ("typed", 64), ("hub", 5)])
+@pytest.mark.parametrize("graph,B", [("typed", 6), ("typed", 64), ("small", 64), ("hub", 5)])
 def test_batched_adjoint_matches_oracle(graph, B):
-    pop = synth.population_small(n=4000, seed=8) if graph == "typed" else _hub_graph()
+    pop = _graph(graph, 4000, 8)
     checked, I = _adjoint_case([pop], B, T=22, seed=9, rng_seed=40 + B)
     assert checked >= max(1, I // 2)
 
@@ -204,7 +214,7 @@ def _assert_same(a, b, what):
         assert np.array_equal(a[k], b[k]), (what, k)
 
 
-@pytest.mark.parametrize("B", [3, 8, 64])
+@pytest.mark.parametrize("B", [3, 8, 20, 64])
 def test_schedules_are_bitwise_equal(B):
     """Every sets-per-lane schedule sums each set in entry order and each tile's rows in
     ascending order: identical trajectories, lambdas and adjoints."""
@@ -213,7 +223,7 @@ def test_schedules_are_bitwise_equal(B):
     R, m, S = _params(B, T, rng_seed=300 + B)
     y = np.stack([synth.target_curve(T, pop.n, seed=b, level=5e-5) for b in range(B)])
     ctx = capi.gabm_create([pop], model(seed=21), sets_per_graph=B)
-    Bp = 4 if B == 3 else B
+    Bp = 1 << (B - 1).bit_length()
     ref = None
     for spl in (2, 4, 8):
         if spl > Bp:

@@ -101,18 +101,34 @@ def test_adam_calibration_lowers_the_loss():
     assert min(losses[-5:]) < 0.2 * losses[0], losses[::5]
 
 
+def _outputs64(net, x):
+    """DeepCalibration's outputs before its float32 cast: R [1, T], m [1, T], c [L] in FP64."""
+    theta = net.net(x)
+    return theta[:, net.week, 0], theta[:, net.week, 1], calibrate.table_from(net.log_T, net.log_iota, net.is_E)
+
+
 def test_deep_calibration_gradient_matches_oracle():
     """DC-GradABM: the CalibNN weights' gradients through the simulator equal the network's
-    vector-Jacobian product with the oracle's dL/dR_t, dL/dm_t and dL/dc."""
+    vector-Jacobian product J^T g with the oracle's g = (dL/dR_t, dL/dm_t, dL/dc).
+
+    The network runs in FP64 (on the host), so the only fp32 arithmetic between the two
+    sides is the simulator's.  Each weight gradient is a sum over the entries of g; with
+    every entry of g held to 1e-3 relative, the bar that follows for the sum is
+    1e-3 * (|J|^T |g|) elementwise, which is 1e-3 relative wherever the sum does not cancel.
+    The two sides run the network's FP64 backward in different orders (one pass over the
+    graph against rows of J): a weight whose gradient is zero in exact arithmetic (the
+    attention keys' bias, which the softmax cancels) carries FP64 rounding of the other
+    terms, below 1e-12 of the largest gradient; that is added to the bar."""
     torch = torch_cuda()
     torch.manual_seed(0)
     pop = synth.population_small(n=6000, seed=4)
     T, n_seed = 21, 20
     S = synth.SUSCEPTIBILITY.astype(np.float32)
-    x = torch.as_tensor(calibrate.synthetic_features(np.full((1, T), 2.5), t_N=14, F=5, seed=1), device="cuda")
-    net = calibrate.DeepCalibration(5, T, R_bounds=(2.0, 3.5), m_bounds=(0.005, 0.05), hidden=16).cuda()
+    x = torch.as_tensor(calibrate.synthetic_features(np.full((1, T), 2.5), t_N=14, F=5, seed=1),
+                        dtype=torch.float64)
+    net = calibrate.DeepCalibration(5, T, R_bounds=(2.0, 3.5), m_bounds=(0.005, 0.05), hidden=16).double()
     R, m, c = net(x)
-    R_np, m_np, c_np = R.detach().cpu().numpy()[0], m.detach().cpu().numpy()[0], c.detach().cpu().numpy()
+    R_np, m_np, c_np = R.detach().numpy()[0], m.detach().numpy()[0], c.detach().numpy()
     for seed in range(30):
         md_o = O.Model(4, 7, c_np, seed=seed)
         f = O.forward_hard(pop, md_o, R_np, m_np, S, n_seed=n_seed)
@@ -124,20 +140,26 @@ def test_deep_calibration_gradient_matches_oracle():
     gD = np.cumsum((2.0 * (C - y_cum) / T)[::-1])[::-1]
     g = O.backward_hard(pop, md_o, R_np, m_np, S, f["e_final"], gD)
     params = [p for p in net.parameters() if p.requires_grad]
-    ref = torch.autograd.grad([R, m, c], params,
-                              grad_outputs=[torch.as_tensor(g["dR"][None, :], dtype=torch.float32, device="cuda"),
-                                            torch.as_tensor(g["dm"][None, :], dtype=torch.float32, device="cuda"),
-                                            torch.as_tensor(g["dc"], dtype=torch.float32, device="cuda")],
-                              retain_graph=True)
+    # the Jacobian J [outputs, weights] of the network's FP64 outputs, one row per output
+    outs = torch.cat([o.reshape(-1) for o in _outputs64(net, x)])
+    g_vec = np.concatenate([g["dR"], g["dm"], g["dc"]])
+    assert outs.numel() == g_vec.size
+    J = np.stack([np.concatenate([(gr if gr is not None else torch.zeros_like(p)).numpy().ravel()
+                                  for gr, p in zip(torch.autograd.grad(outs[k], params, retain_graph=True,
+                                                                       allow_unused=True), params)])
+                  for k in range(outs.numel())])
+    flat_ref = J.T @ g_vec
+    bound = np.abs(J).T @ np.abs(g_vec) + 1e-9 * np.abs(flat_ref).max()   # 1e-3 x this: see above
     ctx = capi.gabm_create([pop], model(seed=seed))
     (Sd,) = to_dev(S[None, :])
-    D = calibrate.TableFunction.apply(ctx, R, m, Sd, c, [n_seed])
+    D = calibrate.TableFunction.apply(ctx, R.cuda(), m.cuda(), Sd, c.cuda(), [n_seed])
     assert np.array_equal(capi.gabm_get_state(ctx)[0], f["e_final"])
     calibrate.cumulative_mse(D, torch.as_tensor(y_cum[None, :], device="cuda")).backward()
-    flat_gpu = np.concatenate([p.grad.detach().double().cpu().numpy().ravel() for p in params])
-    flat_ref = np.concatenate([r.detach().double().cpu().numpy().ravel() for r in ref])
+    flat_gpu = np.concatenate([p.grad.detach().numpy().ravel() for p in params])
     assert np.abs(flat_ref).max() > 0
-    check_adjoint(flat_gpu, flat_ref, "CalibNN weights")
+    check_adjoint(flat_gpu, flat_ref, "CalibNN weights", bound=bound)
+    # most weights are not cancellation-dominated: there the bar is the plain relative one
+    assert np.mean(np.abs(flat_ref) >= 0.1 * bound) > 0.5
 
 
 def test_joint_deep_calibration_lowers_the_loss():

@@ -145,3 +145,39 @@ def test_unsupported():
     with pytest.raises(capi.GabmError) as ei:
         capi.gabm_backward_table(ctx, to_dev(np.ones((1, T)))[0])
     assert ei.value.status == capi.GABM_EUNSUPPORTED
+
+
+def test_more_than_255_exposures_per_agent():
+    """A 3-day cycle (tau_EI = tau_IR = tau_RS = 1) over 900 days: agents are exposed up
+    to ~300 times, so each row's history holds more entries than an 8-bit count can
+    number.  State, counts, D and the adjoint follow the oracle.  Each susceptible day's
+    dL/dy is a difference of two adjoints that share the return term of every later
+    exposure; the sweep cancels that term exactly (in fp32 it would swamp the
+    difference on a cycle this short)."""
+    pop = synth.population_small(n=300, seed=3)
+    T, n_seed = 900, 30
+    c = np.array([0.0, 1.0], np.float32)
+    Rv = np.full(T, 5.0, np.float32)
+    mv = np.full(T, 0.02, np.float32)
+    S = synth.SUSCEPTIBILITY.astype(np.float32)
+    for seed in range(40):
+        mo = SI.SirsModel(1, 1, 1, c, seed=seed)
+        f = SI.forward(pop, mo, Rv, mv, S, n_seed=n_seed)
+        if f["margin"] > EXACT_MARGIN:
+            break
+    assert f["margin"] > EXACT_MARGIN
+    assert (f["e_hist"][1:] != f["e_hist"][:-1]).sum(0).max() > 255
+    _, gD = O.mse(f["D"], synth.target_curve(T, pop.n, seed=5, growth=0.0, level=5e-3))
+    g = SI.backward(pop, mo, Rv, mv, S, f["e_hist"], gD)
+    assert np.abs(g["dR"]).max() > 0
+    ctx = capi.gabm_create([pop], capi.ModelDesc(tau_EI=1, tau_IR=1, c=c, seed=seed, tau_RS=1))
+    Rd, md_, Sd = to_dev(Rv[None, :], mv[None, :], S[None, :])
+    D, counts = capi.gabm_forward(ctx, T, Rd, md_, Sd, [n_seed], want_counts=True)
+    assert np.array_equal(capi.gabm_get_state(ctx)[0].astype(np.int64), f["e_final"])
+    assert np.array_equal(counts.cpu().numpy()[0], f["counts"])
+    assert np.array_equal(D.cpu().numpy()[0], f["D"])
+    (gDd,) = to_dev(gD[None, :])
+    dR, dm, dS = [x.cpu().numpy()[0] for x in capi.gabm_backward(ctx, gDd)]
+    check_adjoint(dR, g["dR"], "dR")
+    check_adjoint(dm, g["dm"], "dm")
+    check_adjoint(dS, g["dS"], "dS")
