@@ -155,9 +155,37 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def trajectory_bytes(E, deg, T, L, n_rows, policy_store):
+def frontier_counts(pop, E, T, L):
+    """Per day t of the trajectory fixed by the final exposure days E (caller order): the
+    susceptible rows with an in-neighbour infectious on day t (the rows the forward sums),
+    their entries, and the out-entries of the rows infectious on day t + 1 (the flags the
+    day's launch pushes for tomorrow)."""
+    E = np.asarray(E).astype(np.int64)
+    NEVER = 32767
+    deg = np.diff(pop.rowptr.astype(np.int64))
+    col = pop.col.astype(np.int64)
+    rows = np.repeat(np.arange(pop.n, dtype=np.int64), deg)
+    sf_rows = np.zeros(T)
+    sf_nnz = np.zeros(T)
+    push = np.zeros(T)
+    for t in range(T):
+        inf = (E != NEVER) & (t - E >= 1) & (t - E < L)
+        flag = np.zeros(pop.n, bool)
+        flag[rows[inf[col]]] = True
+        sf = flag & (E >= t)
+        sf_rows[t] = sf.sum()
+        sf_nnz[t] = deg[sf].sum()
+        inf1 = (E != NEVER) & (t + 1 - E >= 1) & (t + 1 - E < L)
+        push[t] = deg[inf1].sum()
+    return sf_rows, sf_nnz, push
+
+
+def trajectory_bytes(E, deg, T, L, n_rows, policy_store, frontier=None):
     """Algorithmic (compulsory) HBM bytes of every forward and backward day launch, from
-    the final exposure days E (which determine each day's state)."""
+    the final exposure days E (which determine each day's state).  With ``frontier`` (from
+    frontier_counts) the forward reads only the entries of susceptible rows with an
+    infectious in-neighbour, plus every row's state, flag and length and the pushes of
+    tomorrow's flags; without it, every susceptible row's entries."""
     E = E.astype(np.int64)
     NEVER = 32767
     seed = (E != NEVER) & (E < 0)
@@ -171,7 +199,13 @@ def trajectory_bytes(E, deg, T, L, n_rows, policy_store):
     S_cnt = np.cumsum(hist_n[::-1])[::-1][:T]
     S_nnz = np.cumsum(hist_e[::-1])[::-1][:T]
     new = np.bincount(E[live & ~never], minlength=T)[:T]
-    fwd = 8.0 * S_nnz + 4.0 * S_cnt + 1.0 * S_cnt + 2.0 * n_rows + 2.0 * new
+    if frontier is None:
+        fwd = 8.0 * S_nnz + 4.0 * S_cnt + 1.0 * S_cnt + 2.0 * n_rows + 2.0 * new
+    else:
+        sf_rows, sf_nnz, push = frontier
+        # entries (col + w) and age + caller id of the summed rows; state, flag read and
+        # clear, row length of every row; tomorrow's flags: out-entries read, one byte each
+        fwd = 8.0 * sf_nnz + 5.0 * sf_rows + 8.0 * n_rows + 2.0 * new + 5.0 * push
     if policy_store:
         fwd += 4.0 * S_cnt
     # backward: rows needing the transpose gather on day t are live with Ec >= t + 2 - L
@@ -201,8 +235,11 @@ def trajectory_bytes(E, deg, T, L, n_rows, policy_store):
 def batched_trajectory_bytes(E, deg, T, L, n, B, l2_bytes):
     """Algorithmic HBM bytes of the batched day launches (B sets sharing one graph) from the
     final exposure days E [B, n] of every set: rows are read once for all sets, per-set
-    state once per set; a gathered per-agent array that fits in half of L2 costs nothing
-    per edge, else its B values per edge."""
+    state once per set.  The backward's coefficient gather costs nothing per edge when
+    the array fits in half of L2, else its B values per edge (every entry of a row that
+    needs the transpose gather reads them).  The forward's exposure-day gathers are not
+    charged: they are made for the marked neighbours only (infectious in some set), a
+    data-dependent share of the entries, and their DRAM cost is what ncu measures."""
     E = E.astype(np.int64)
     NEVER = 32767
     seed = (E != NEVER) & (E < 0)
@@ -217,7 +254,7 @@ def batched_trajectory_bytes(E, deg, T, L, n, B, l2_bytes):
     hist_s = np.bincount(np.clip(flat, 0, T), minlength=T + 1)
     S_t = np.cumsum(hist_s[::-1])[::-1]              # sum over sets of susceptible agents on day t
     new = np.bincount(E[(E != NEVER) & (E >= 0)], minlength=T)[:T]
-    gath_f = 0.0 if n * B * 2 <= l2_bytes / 2 else 2.0 * B
+    gath_f = 0.0
     gath_b = 0.0 if n * B * 4 <= l2_bytes / 2 else 4.0 * B
     fwd = np.zeros(T)
     bwd = np.zeros(T)
@@ -364,42 +401,45 @@ def workload_config(pop, policy: str) -> dict:
 
 
 def run_reference(args, world, rank):
-    """The FP64 CPU oracle as it stands, on a bounded sample of the workload."""
+    """The FP64 CPU oracle as it stands (OpenMP over the host cores) on the same workload
+    and config as the GPU arm: each step is one forward + MSE + backward of the 1M-agent,
+    60-day workload (about 6 s on 16 cores).  Warm-up is capped at one step: the oracle has
+    no caches or compilation to warm, and each step is a full workload."""
     if rank != 0:
         return
     import oracle as O
     from paper_2207_09714_gb300 import synth
-    n_sample = 250_000
-    pop = synth.population_typed(n_sample, seed=0)
+    pop = synth.population_typed(N_AGENTS, seed=0)
     c = synth.infectiousness_table(TAU_EI, TAU_IR)
     R = np.full(DAYS, R0, np.float32)
     m = np.full(DAYS, MORTALITY, np.float32)
     S = synth.SUSCEPTIBILITY.astype(np.float32)
     y = synth.target_curve(DAYS, pop.n)
     md = O.Model(TAU_EI, TAU_IR, c, seed=0)
+    O.build()
 
     def step():
         f = O.forward_hard(pop, md, R, m, S, n_seed=N_SEED)
         _, gD = O.mse(f["D"], y)
         O.backward_hard(pop, md, R, m, S, f["e_final"], gD)
 
-    for _ in range(args.warmup):
+    warm = min(args.warmup, 1)
+    for _ in range(warm):
         step()
     t0 = time.perf_counter()
     for _ in range(args.steps):
         step()
     dt = (time.perf_counter() - t0) / max(args.steps, 1)
     value = pop.n * DAYS / dt
-    sample = (f"each step a bounded sample of the workload: {pop.n} agents of the same generator "
-              f"({pop.nnz} directed edges), {DAYS} days, forward + MSE + backward; value in agent-days/s "
-              f"of the sample")
+    sample = (f"each step the full workload: {pop.n} agents, {pop.nnz} directed edges, {DAYS} days, forward + MSE "
+              f"+ backward, FP64, {dt:.1f} s per step on {O.num_threads()} threads ({_cpu_model()})")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "agent-days/s", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+        "steps": args.steps, "warmup": warm, "ms_per_step": dt * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": workload_config(synth.population_typed(N_AGENTS, seed=0), args.policy),
+        "config": workload_config(pop, args.policy),
         "cpu_baseline": {"value": value, "unit": "agent-days/s", "cores": O.num_threads(), "kind": "oracle",
-                         "sample": sample},
+                         "sample": sample, "cpu_model": _cpu_model(), "nproc": os.cpu_count()},
         "e2e": {"value": value, "unit": "agent-days/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -422,7 +462,8 @@ def cpu_baseline(pop, c, y):
     dt = time.perf_counter() - t0
     return {"value": pop.n * DAYS / dt, "unit": "agent-days/s", "cores": O.num_threads(), "kind": "oracle",
             "sample": f"one forward + MSE + backward of the full workload ({pop.n} agents, {pop.nnz} directed "
-                      f"edges, {DAYS} days), FP64, {dt:.1f} s"}
+                      f"edges, {DAYS} days), FP64, {dt:.1f} s",
+            "cpu_model": _cpu_model(), "nproc": os.cpu_count()}
 
 
 def bench_twohop(stream, dist, steps=5, n=1_000_000):
@@ -537,7 +578,8 @@ def bench_progression_variant(pop, stream, S, y_np, dist, peak, peak_kind, varia
                     "agents_last_exposed_after_day_0_share": float(np.mean((E >= 0) & (E != 32767)))})
         return out
     n_rows = ((pop.n + 31) // 32) * 32
-    fwd_b, bwd_b, _, _ = trajectory_bytes(E, pop.degrees().astype(np.float64), DAYS, L, n_rows, True)
+    fwd_b, bwd_b, _, _ = trajectory_bytes(E, pop.degrees().astype(np.float64), DAYS, L, n_rows, True,
+                                          frontier=frontier_counts(pop, E, DAYS, L))
     f_gbs = fwd_b.sum() * steps / (f_ms / 1e3) / 1e9
     b_gbs = bwd_b.sum() * steps / (b_ms / 1e3) / 1e9
     return {"workload": f"{what}, on the bench graph, m = {MORTALITY}, {DAYS} days, forward + MSE + backward",
@@ -607,6 +649,318 @@ def bench_calibration(ctx, stream, S, y_np, dist, steps=5):
             "dc_calibnn_ms_per_step": ms_dc}
 
 
+# ---- the other configurations of the workload family -------------------------------
+CFG0_AGENTS, CFG0_DAYS = 10_000, 30
+CFG3_COUNTIES, CFG3_DAYS = 32, 90
+CFG4_AGENTS, CFG4_DAYS = 8_000_000, 120
+B1M_SETS, B1M_DAYS = 64, 60
+ORACLE_SAMPLE_DAYS = 8
+
+
+def _gen_population(kind, arg):
+    """Worker of the generator pool (spawned processes): one synthetic population."""
+    from paper_2207_09714_gb300 import synth
+    if kind == "powerlaw":
+        return synth.population_typed(arg, seed=0, powerlaw=True)
+    g, n = arg
+    return synth.county(g, n, seed=0)
+
+
+class Populations:
+    """The large populations of configs 3 and 4, generated by a pool of spawned processes
+    while the GPU sections before them run."""
+
+    def __init__(self, workers: int):
+        import multiprocessing as mp
+        from paper_2207_09714_gb300 import synth
+        self.sizes = synth.uneven_county_sizes(CFG3_COUNTIES, seed=0)
+        self.pool = mp.get_context("spawn").Pool(processes=workers)
+        self.big = self.pool.apply_async(_gen_population, ("powerlaw", CFG4_AGENTS))
+        order = sorted(range(len(self.sizes)), key=lambda g: -self.sizes[g])
+        self.counties = {g: self.pool.apply_async(_gen_population, ("county", (g, self.sizes[g]))) for g in order}
+
+    def powerlaw(self):
+        return self.big.get()
+
+    def county_list(self):
+        return [self.counties[g].get() for g in range(len(self.sizes))]
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
+def _padded_rows(pops):
+    return sum(((p.n + 31) // 32) * 32 for p in pops)
+
+
+def workload_bytes(pops, E, B, T, L, store, l2_bytes):
+    """Algorithmic bytes per forward and backward day launch of a ctx over ``pops`` (one
+    set per graph, or B sets on one graph) from its final state E [B, n_total], and the
+    paper-style full-pull count (every row, every day)."""
+    deg = np.concatenate([p.degrees().astype(np.float64) for p in pops])
+    NEVER = 32767
+    if B == 1:
+        n_rows = _padded_rows(pops)
+        off = np.concatenate([[0], np.cumsum([p.n for p in pops])])
+        parts = [frontier_counts(p, E[0][off[g]:off[g + 1]], T, L) for g, p in enumerate(pops)]
+        frontier = tuple(sum(pt[k] for pt in parts) for k in range(3))
+        fwd, bwd, _, _ = trajectory_bytes(E[0], deg, T, L, n_rows, store, frontier=frontier)
+        ffwd, fbwd, _, _ = trajectory_bytes(np.full(deg.size, NEVER, np.int16), deg, T, L, n_rows, store)
+    else:
+        n = pops[0].n
+        fwd, bwd = batched_trajectory_bytes(E, deg, T, L, n, B, l2_bytes)
+        ffwd, fbwd = batched_trajectory_bytes(np.full((B, n), NEVER, np.int16), deg, T, L, n, B, l2_bytes)
+    return fwd, bwd, ffwd, fbwd
+
+
+def bench_workload(name, what, pops, B, T, R_np, m_np, S_np, n_seed, y_np, policy, stream, peak, peak_kind,
+                   fwd_only=False, steps=3, warmup=3, autotune=True):
+    """One configuration through the library: the ctx, a warm-up, the autotuner, then
+    ``steps`` timed steps (forward, or forward + MSE + backward) with CUDA events on the ctx
+    stream (day loops replayed as CUDA graphs), one profiled step with events around every
+    day launch for the per-kernel rates, algorithmic and full-pull bytes, peak HBM."""
+    import torch
+    from paper_2207_09714_gb300 import capi, synth
+    c = synth.infectiousness_table(TAU_EI, TAU_IR)
+    L = TAU_EI + TAU_IR
+    I = len(pops) * B
+    with torch.cuda.stream(stream):
+        ctx = capi.gabm_create(pops, capi.ModelDesc(TAU_EI, TAU_IR, c, seed=0, lambda_policy=policy),
+                               sets_per_graph=B, stream=stream)
+    R = torch.from_numpy(np.ascontiguousarray(R_np, np.float32)).cuda()
+    m = torch.from_numpy(np.ascontiguousarray(m_np, np.float32)).cuda()
+    S = torch.from_numpy(np.ascontiguousarray(S_np, np.float32)).cuda()
+    y = torch.from_numpy(np.ascontiguousarray(y_np, np.float64)).cuda()
+    D = torch.empty((I, T), dtype=torch.float64, device="cuda")
+    loss = torch.empty((I,), dtype=torch.float64, device="cuda")
+    gD = torch.empty((I, T), dtype=torch.float64, device="cuda")
+    dR = torch.empty((I, T), dtype=torch.float64, device="cuda")
+    dm = torch.empty((I, T), dtype=torch.float64, device="cuda")
+    dS = torch.empty((I, 9), dtype=torch.float64, device="cuda")
+
+    def step():
+        capi.gabm_forward(ctx, T, R, m, S, n_seed, D=D)
+        if not fwd_only:
+            capi.gabm_mse_loss(ctx, y, loss=loss, gD=gD)
+            capi.gabm_backward(ctx, gD, dR=dR, dm=dm, dS_age=dS)
+
+    step()
+    schedule = capi.gabm_autotune(ctx, 1) if autotune else capi.gabm_get_schedule(ctx)
+    for _ in range(max(warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l0 = capi.gabm_launch_count(ctx)
+    e0.record(stream)
+    for _ in range(steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    launches = capi.gabm_launch_count(ctx) - l0
+    ms = e0.elapsed_time(e1) / steps
+    capi.gabm_set_profiling(ctx, True)
+    step()
+    torch.cuda.synchronize()
+    f_ms, f_n = capi.gabm_get_profile(ctx, 0)
+    b_ms, b_n = capi.gabm_get_profile(ctx, 1)
+    capi.gabm_set_profiling(ctx, False)
+    E = capi.gabm_get_state(ctx)
+    counts = capi.gabm_forward(ctx, T, R, m, S, n_seed, want_counts=True)[1]
+    torch.cuda.synchronize()
+    counts = counts.cpu().numpy()
+    _, peak_mem = capi.gabm_mem_stats(ctx)
+    del ctx
+    l2 = torch.cuda.get_device_properties(0).L2_cache_size
+    fwd_b, bwd_b, ffwd_b, fbwd_b = workload_bytes(pops, E, B, T, L, policy == capi.GABM_STORE_LAMBDA, l2)
+    n_tot = sum(p.n for p in pops)
+    nnz_tot = sum(p.nnz for p in pops)
+    units = B * n_tot * T
+    f_gbs = fwd_b.sum() / (f_ms / 1e3) / 1e9
+    out = {"workload": what, "n_agents": n_tot, "nnz": nnz_tot, "graphs": len(pops), "sets_per_graph": B,
+           "days": T, "lambda_policy": "store" if policy == capi.GABM_STORE_LAMBDA else "recompute",
+           "step": "forward" if fwd_only else "forward + MSE + backward",
+           "ms_per_step": ms, "steps": steps, "value": units / (ms / 1e3), "unit": "agent-days/s",
+           "edge_updates_per_s": B * nnz_tot * T / (ms / 1e3), "gpu_launches": launches,
+           "schedule": schedule, "peak_hbm_bytes": peak_mem,
+           "attack_rate_range": [float(1.0 - (counts[:, -1, 0] / np.repeat([p.n for p in pops], B)).max()),
+                                 float(1.0 - (counts[:, -1, 0] / np.repeat([p.n for p in pops], B)).min())],
+           "fwd_day": {"launches": f_n, "avg_launch_ms": f_ms / f_n, "alg_bytes_per_launch": fwd_b.sum() / T,
+                       "achieved_gbs": f_gbs, "frac": f_gbs / peak}}
+    full = ffwd_b.sum() if fwd_only else ffwd_b.sum() + fbwd_b.sum()
+    alg = fwd_b.sum() if fwd_only else fwd_b.sum() + bwd_b.sum()
+    kern_ms = f_ms if fwd_only else f_ms + b_ms
+    if not fwd_only:
+        b_gbs = bwd_b.sum() / (b_ms / 1e3) / 1e9
+        out["bwd_day"] = {"launches": b_n, "avg_launch_ms": b_ms / b_n, "alg_bytes_per_launch": bwd_b.sum() / T,
+                          "achieved_gbs": b_gbs, "frac": b_gbs / peak}
+    out["day_kernels"] = {"alg_bytes_per_step": alg, "ms_per_step": kern_ms,
+                          "achieved_gbs": alg / (kern_ms / 1e3) / 1e9, "frac": alg / (kern_ms / 1e3) / 1e9 / peak,
+                          "peak": peak, "peak_source": peak_kind}
+    out["full_pull"] = {"bytes_per_step": full, "gbs_at_step_time": full / (ms / 1e3) / 1e9,
+                        "note": "paper-style count: every row's edges and state on every day"}
+    return out
+
+
+def _cpu_model() -> str:
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu part")):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def oracle_sample(pops, B, T, days, R_np, m_np, S_np, n_seed, y_np, fwd_only, insts=None):
+    """The FP64 oracle (OpenMP over the host cores) on a bounded sample of a configuration:
+    the first ``days`` days of the instances ``insts`` (all by default), forward (+ MSE +
+    backward over those days).  Returns agent-days/s of the sample and its description."""
+    import oracle as O
+    from paper_2207_09714_gb300 import synth
+    md = O.Model(TAU_EI, TAU_IR, synth.infectiousness_table(TAU_EI, TAU_IR), seed=0)
+    insts = list(range(len(pops) * B)) if insts is None else insts
+    O.build()
+    units = 0
+    t0 = time.perf_counter()
+    for i in insts:
+        pop = pops[i // B]
+        f = O.forward_hard(pop, md, R_np[i, :days], m_np[i, :days], S_np[i], n_seed=n_seed[i], inst=i)
+        if not fwd_only:
+            _, gD = O.mse(f["D"], y_np[i, :days])
+            O.backward_hard(pop, md, R_np[i, :days], m_np[i, :days], S_np[i], f["e_final"], gD, inst=i)
+        units += pop.n * days
+    dt = time.perf_counter() - t0
+    return {"value": units / dt, "unit": "agent-days/s", "cores": O.num_threads(), "kind": "oracle",
+            "sample": f"{len(insts)} of {len(pops) * B} instances, days 0..{days - 1} of {T}, "
+                      f"{'forward' if fwd_only else 'forward + MSE + backward'}, FP64, {dt:.1f} s"
+                      + ("" if days == T else "; throughput of the first days, not extrapolated")}
+
+
+def _single_thread_oracle_cmd():
+    """Command of a child process that times the oracle single-threaded on the full main
+    workload (one forward + MSE + backward of 1M agents over 60 days) and prints JSON."""
+    code = (
+        "import json,time,numpy as np,oracle as O;"
+        "from paper_2207_09714_gb300 import synth;"
+        f"pop=synth.population_typed({N_AGENTS},seed=0);"
+        f"c=synth.infectiousness_table({TAU_EI},{TAU_IR});md=O.Model({TAU_EI},{TAU_IR},c,seed=0);"
+        f"R=np.full({DAYS},{R0},np.float32);m=np.full({DAYS},{MORTALITY},np.float32);"
+        "S=synth.SUSCEPTIBILITY.astype(np.float32);"
+        f"y=synth.target_curve({DAYS},pop.n);O.build();t0=time.perf_counter();"
+        f"f=O.forward_hard(pop,md,R,m,S,n_seed={N_SEED});_,gD=O.mse(f['D'],y);"
+        "O.backward_hard(pop,md,R,m,S,f['e_final'],gD);dt=time.perf_counter()-t0;"
+        f"print(json.dumps({{'seconds':dt,'threads':O.num_threads(),'value':pop.n*{DAYS}/dt}}))")
+    return [sys.executable, "-c", code]
+
+
+def run_configs(args, gen, pop1m, stream, peak, peak_kind):
+    """The other configurations, each in its own key (a failure is reported there):
+    10k agents forward only (30 days); 1M agents x 64 parameter sets (60 days); 32 uneven
+    counties (90 days); 8M agents with power-law contacts (120 days, recompute policy).
+    The single-threaded oracle runs in a child process meanwhile (after the generator
+    pool has finished, so that nothing else loads the host), and the OpenMP oracle on a
+    bounded sample of each configuration after the GPU sections."""
+    from paper_2207_09714_gb300 import capi, synth
+    out = {}
+    samples = {}
+    rng = np.random.default_rng(0)
+
+    def guarded(key, fn):
+        try:
+            out[key] = fn()
+        except Exception as exc:   # reported, the other sections still run
+            out[key] = {"error": f"{type(exc).__name__}: {exc}"}
+
+    # config 0: 10k agents, households + random contacts, forward only
+    p0 = synth.population_small(CFG0_AGENTS, seed=0)
+    R0v = np.full((1, CFG0_DAYS), R0, np.float32)
+    m0v = np.full((1, CFG0_DAYS), MORTALITY, np.float32)
+    S0v = synth.SUSCEPTIBILITY[None, :].astype(np.float32)
+    y0 = synth.target_curve(CFG0_DAYS, p0.n)[None, :]
+    guarded("c0_10k_forward_30d", lambda: bench_workload(
+        "c0", f"{p0.n} agents, households U{{1..6}} + random contacts (mean degree 10), {CFG0_DAYS} days, forward only",
+        [p0], 1, CFG0_DAYS, R0v, m0v, S0v, [N_SEED], y0, capi.GABM_STORE_LAMBDA, stream, peak, peak_kind,
+        fwd_only=True, steps=20))
+
+    # 1M agents x 64 parameter sets, 60 days (the main graph, the ensemble's parameter ranges)
+    Rb = np.repeat(rng.uniform(1.5, 4.0, (B1M_SETS, 1)), B1M_DAYS, axis=1).astype(np.float32)
+    mb = np.repeat(rng.uniform(0.005, 0.05, (B1M_SETS, 1)), B1M_DAYS, axis=1).astype(np.float32)
+    Sb = np.tile(synth.SUSCEPTIBILITY, (B1M_SETS, 1)).astype(np.float32)
+    yb = np.stack([synth.target_curve(B1M_DAYS, pop1m.n, seed=b) for b in range(B1M_SETS)])
+    guarded("batched_1M_x64_60d", lambda: bench_workload(
+        "b1m", f"one shared {pop1m.n}-agent typed contact graph, {B1M_SETS} parameter sets (R ~ U[1.5, 4.0], "
+               f"m ~ U[0.005, 0.05]), {B1M_DAYS} days, forward + MSE + backward of every set",
+        [pop1m], B1M_SETS, B1M_DAYS, Rb, mb, Sb, [N_SEED] * B1M_SETS, yb, capi.GABM_STORE_LAMBDA, stream, peak,
+        peak_kind, steps=3))
+
+    counties = gen.county_list()
+    p4 = gen.powerlaw()
+    gen.close()
+    single = None
+    if not args.no_cpu_baseline:
+        single = subprocess.Popen(_single_thread_oracle_cmd(), stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                                  text=True, cwd=ROOT, env=dict(os.environ, OMP_NUM_THREADS="1"))
+
+    # config 3: 32 uneven counties, each with its own parameters, 90 days
+    G = len(counties)
+    R3 = (rng.uniform(1.8, 3.2, (G, 1)) * rng.uniform(0.9, 1.1, (G, CFG3_DAYS))).astype(np.float32)
+    m3 = np.repeat(rng.uniform(0.005, 0.05, (G, 1)), CFG3_DAYS, axis=1).astype(np.float32)
+    S3 = (synth.SUSCEPTIBILITY[None, :] * rng.uniform(0.8, 1.2, (G, 9))).astype(np.float32)
+    y3 = np.stack([synth.target_curve(CFG3_DAYS, p.n, seed=g) for g, p in enumerate(counties)])
+    guarded("c3_32_counties_90d", lambda: bench_workload(
+        "c3", f"{G} county graphs of the typed generator, agent counts log-uniform in [5e4, 2e6] "
+              f"(sum {sum(p.n for p in counties)}), own parameters each, {CFG3_DAYS} days, autotuned, "
+              f"forward + MSE + backward", counties, 1, CFG3_DAYS, R3, m3, S3, [N_SEED] * G, y3,
+        capi.GABM_STORE_LAMBDA, stream, peak, peak_kind, steps=3))
+
+    # config 4: 8M agents, power-law random contacts, 120 days, recompute policy
+    R4 = np.full((1, CFG4_DAYS), R0, np.float32)
+    m4 = np.full((1, CFG4_DAYS), MORTALITY, np.float32)
+    S4 = synth.SUSCEPTIBILITY[None, :].astype(np.float32)
+    y4 = synth.target_curve(CFG4_DAYS, p4.n)[None, :]
+    guarded("c4_8M_powerlaw_120d", lambda: bench_workload(
+        "c4", f"{p4.n} agents, typed generator with Chung-Lu power-law contacts (exponent 2.5, degrees up to "
+              f"2000), {CFG4_DAYS} days, recompute policy (lambda recomputed from the final exposure days), "
+              f"forward + MSE + backward", [p4], 1, CFG4_DAYS, R4, m4, S4, [N_SEED], y4, capi.GABM_RECOMPUTE,
+        stream, peak, peak_kind, steps=3))
+
+    if single is not None:
+        try:
+            so, _ = single.communicate(timeout=900)
+            st = json.loads(so.strip().splitlines()[-1])
+            out["_single_thread"] = {"value": st["value"], "unit": "agent-days/s", "cores": st["threads"],
+                                     "kind": "oracle",
+                                     "sample": f"one forward + MSE + backward of the full main workload, one thread, "
+                                               f"{st['seconds']:.1f} s (child process, run while the GPU sections "
+                                               f"ran)"}
+        except Exception as exc:
+            single.kill()
+            out["_single_thread"] = {"error": f"{type(exc).__name__}: {exc}"}
+        try:   # the OpenMP oracle on bounded samples of each configuration
+            samples["c0_10k_forward_30d"] = oracle_sample([p0], 1, CFG0_DAYS, CFG0_DAYS, R0v, m0v, S0v, [N_SEED],
+                                                          y0, True)
+            samples["batched_1M_x64_60d"] = oracle_sample([pop1m], B1M_SETS, B1M_DAYS, B1M_DAYS, Rb, mb, Sb,
+                                                          [N_SEED] * B1M_SETS, yb, False, insts=[0])
+            samples["c3_32_counties_90d"] = oracle_sample(counties, 1, CFG3_DAYS, ORACLE_SAMPLE_DAYS, R3, m3, S3,
+                                                          [N_SEED] * G, y3, False)
+            samples["c4_8M_powerlaw_120d"] = oracle_sample([p4], 1, CFG4_DAYS, ORACLE_SAMPLE_DAYS, R4, m4, S4,
+                                                           [N_SEED], y4, False)
+        except Exception as exc:
+            samples["error"] = f"{type(exc).__name__}: {exc}"
+        out["_oracle_samples"] = samples
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -619,6 +973,8 @@ def main():
     ap.add_argument("--batched-only", action="store_true",
                     help="run only the batched ensemble; its result is the printed line")
     ap.add_argument("--no-plain", action="store_true", help="skip the per-set plain comparator")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the other configurations (10k forward, 1M x 64 sets, 32 counties, 8M power-law)")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -630,6 +986,9 @@ def main():
             dist.init_process_group("gloo")
         run_reference(args, world, rank)
         return
+
+    extra = world == 1 and not args.no_configs and not args.batched_only
+    gen = Populations(workers=max(1, min(8, (os.cpu_count() or 2) // 2))) if extra else None
 
     import torch
     from paper_2207_09714_gb300 import build as gbuild
@@ -730,8 +1089,9 @@ def main():
     E = capi.gabm_get_state(ctx)[0]
     deg = pop.degrees().astype(np.float64)
     n_rows = ((pop.n + 31) // 32) * 32
+    frontier = frontier_counts(pop, E, DAYS, TAU_EI + TAU_IR)
     fwd_b, bwd_b, S_cnt, S_nnz = trajectory_bytes(E, deg, DAYS, TAU_EI + TAU_IR, n_rows,
-                                                  policy == capi.GABM_STORE_LAMBDA)
+                                                  policy == capi.GABM_STORE_LAMBDA, frontier=frontier)
     fwd_gbs = fwd_b.sum() * args.steps / (fwd_ms_k / 1e3) / 1e9 if fwd_ms_k > 0 else None
     bwd_gbs = bwd_b.sum() * args.steps / (bwd_ms_k / 1e3) / 1e9 if bwd_ms_k > 0 else None
     peak, peak_kind = _peaks()
@@ -786,15 +1146,24 @@ def main():
     batched = None
     if not args.no_batched:
         batched = bench_batched(args, stream, peak, peak_kind)
-    try:   # the last GPU section: a failure here is reported in its own key
+    try:   # a failure here is reported in its own key
         sirs = bench_progression_variant(pop, stream, S, y_np, dist, peak, peak_kind, "sirs")
     except Exception as exc:
         sirs = {"error": f"{type(exc).__name__}: {exc}"}
+    configs = run_configs(args, gen, pop, stream, peak, peak_kind) if extra else None
     if rank != 0:
         return
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         cpu = cpu_baseline(pop, c, y_np[0])
+        if configs is not None:
+            cpu["single_thread"] = configs.pop("_single_thread", None)
+            cpu["per_config"] = configs.pop("_oracle_samples", None)
+    if configs is not None:
+        configs.pop("_single_thread", None)
+        configs.pop("_oracle_samples", None)
+    full_fwd, full_bwd = (trajectory_bytes(np.full(pop.n, 32767, np.int16), deg, DAYS, TAU_EI + TAU_IR, n_rows,
+                                           policy == capi.GABM_STORE_LAMBDA)[:2])
     line = {
         "metric": METRIC, "value": value, "unit": "agent-days/s", "n_gpus": world, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -804,6 +1173,7 @@ def main():
         "ms_per_step_profiled": ms_per_step_profiled,
         "edge_updates_per_s": world * pop.nnz * DAYS / (ms_per_step / 1e3),
         "sus_edges_per_day_mean": float(S_nnz.mean()),
+        "summed_edges_per_day_mean": float(frontier[1].mean()),
         "roofline": {"bound": "hbm", "kernel": dominant, "achieved": dom_gbs, "peak": peak, "unit": "GB/s",
                      "frac": (dom_gbs / peak) if dom_gbs else None, "traffic": traffic,
                      "peak_source": peak_kind,
@@ -821,6 +1191,11 @@ def main():
         "stochastic_durations": durations,
         "sirs_reinfection": sirs,
         "batched": batched,
+        "full_pull": {"bytes_per_step": float(full_fwd.sum() + full_bwd.sum()),
+                      "gbs_at_step_time": float(full_fwd.sum() + full_bwd.sum()) / (ms_per_step / 1e3) / 1e9,
+                      "frac": float(full_fwd.sum() + full_bwd.sum()) / (ms_per_step / 1e3) / 1e9 / peak,
+                      "note": "paper-style count: every row's edges and state on every day, forward and backward"},
+        "configs": configs,
     }
     print(json.dumps(line), flush=True)
     if dist is not None:

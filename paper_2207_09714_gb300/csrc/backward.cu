@@ -68,8 +68,7 @@ __device__ __forceinline__ void dc_accumulate(double *dc_tile, int tile, bool ha
 // sums over the window L_i it would draw and takes the death term m gD of its own exit
 // day; the exits recounted for dm are at each row's drawn L_i.
 template <int MODE, bool DC, int EXIT = kExitBase>
-__global__ void __launch_bounds__(kBlock, (MODE == kBwdStore && !DC && EXIT == kExitBase) ? GABM_BWD_MINBLOCKS
-                                                                                           : GABM_MINBLOCKS)
+__global__ void __launch_bounds__(kBlock, (MODE == kBwdStore && !DC) ? GABM_BWD_MINBLOCKS : GABM_MINBLOCKS)
     k_bwd_day(const BwdDayArgs a) {
     constexpr bool FATE = EXIT == kExitFate;
     constexpr bool DUR = EXIT == kExitDur;

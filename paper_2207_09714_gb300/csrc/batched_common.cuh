@@ -11,7 +11,7 @@
 // Resident blocks per SM the batched day kernels are compiled for (register budget
 // 65536 / (256 x blocks) per thread).
 #ifndef GABM_BFWD_MINBLOCKS
-#define GABM_BFWD_MINBLOCKS 2
+#define GABM_BFWD_MINBLOCKS 3
 #endif
 #ifndef GABM_BBWD_MINBLOCKS
 #define GABM_BBWD_MINBLOCKS 2
@@ -126,12 +126,44 @@ __device__ __forceinline__ void load_pass_row(const Csr &m, const uint32_t *ew_p
     pr.w0 = ld_cs_if(m.w + pr.p0 + q, v);
 }
 
+// V marked entries of the current chunk, taken from mm in entry order (lowest lane
+// of the group first): their columns and weights broadcast from the lanes holding
+// them, every lane's gathers issued before any of their values is used, then the
+// sums.  Slots past the group's last marked entry carry weight 0 and load nothing.
+template <int V, int LPR, int SPL, bool KAHAN, class Raw, class Ld, class Val>
+__device__ __forceinline__ void gather_batch(unsigned &mm, uint32_t j, float w, Ld &ld, Val &val, float (&sum)[SPL],
+                                             float (&comp)[SPL]) {
+    uint32_t jv[V];
+    float wv[V];
+    bool ok[V];
+#pragma unroll
+    for (int u = 0; u < V; ++u) {
+        ok[u] = mm != 0u;
+        const int src = ok[u] ? __ffs(mm) - 1 : 0;
+        mm &= mm - 1u;
+        jv[u] = __shfl_sync(kFull, j, src, LPR);
+        const float ws = __shfl_sync(kFull, w, src, LPR);
+        wv[u] = ok[u] ? ws : 0.f;   // a zero weight leaves a plain sum unchanged
+    }
+    Raw rv[V];
+#pragma unroll
+    for (int u = 0; u < V; ++u) ld(jv[u], ok[u], rv[u]);
+#pragma unroll
+    for (int u = 0; u < V; ++u)
+#pragma unroll
+        for (int h = 0; h < SPL; ++h) acc_add<KAHAN>(sum[h], comp[h], wv[u], val(rv[u], h), ok[u]);
+}
+
 // For this lane's group row (entries [p0, p0 + len)), sum[h] = sum over the
 // entries whose column is marked in `bits` of w * x_h(j), in entry order, where
 // ld(j, ok, raw) gathers column j's values for this lane's sets (predicated by
 // ok) and val(raw, h) is set h's value.  (j0, w0) is the row's entry q, loaded
 // by the caller; each later chunk of LPR entries is in flight while the one
-// before it is used.  Called by all 32 lanes.
+// before it is used.  A chunk's marked entries go in batches of U gathers in
+// flight, and the rest (fewer than U, counted by the group with the most) in
+// batches of U/2, U/4, ..., 1: where few neighbours are marked, as early in an
+// epidemic, a batch no larger than needed is most of the saving.  Called by all
+// 32 lanes.
 template <int LPR, int SPL, bool KAHAN, class Raw, class Ld, class Val>
 __device__ __forceinline__ void group_row_sums(const Csr &m, uint32_t p0, uint32_t len, uint32_t j0, float w0,
                                                const uint32_t *__restrict__ bits, int lane, Ld ld, Val val,
@@ -156,27 +188,13 @@ __device__ __forceinline__ void group_row_sums(const Csr &m, uint32_t p0, uint32
         const bool mk = valid && marked(bits, j);
         unsigned mm = (__ballot_sync(kFull, mk) >> (grp * LPR)) & gmask;
         const int nmax = (int)__reduce_max_sync(kFull, (unsigned)__popc(mm));
-        for (int i0 = 0; i0 < nmax; i0 += U) {
-            uint32_t jv[U];
-            float wv[U];
-            bool ok[U];
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                ok[u] = mm != 0u;
-                const int src = ok[u] ? __ffs(mm) - 1 : 0;
-                mm &= mm - 1u;
-                jv[u] = __shfl_sync(kFull, j, src, LPR);
-                const float ws = __shfl_sync(kFull, w, src, LPR);
-                wv[u] = ok[u] ? ws : 0.f;   // a zero weight leaves a plain sum unchanged
-            }
-            Raw rv[U];
-#pragma unroll
-            for (int u = 0; u < U; ++u) ld(jv[u], ok[u], rv[u]);
-#pragma unroll
-            for (int u = 0; u < U; ++u)
-#pragma unroll
-                for (int h = 0; h < SPL; ++h) acc_add<KAHAN>(sum[h], comp[h], wv[u], val(rv[u], h), ok[u]);
-        }
+        int i0 = 0;
+        for (; i0 + U <= nmax; i0 += U) gather_batch<U, LPR, SPL, KAHAN, Raw>(mm, j, w, ld, val, sum, comp);
+        const int rest = nmax - i0;   // < U, warp-uniform
+        if constexpr (U >= 8)
+            if (rest & 4) gather_batch<4, LPR, SPL, KAHAN, Raw>(mm, j, w, ld, val, sum, comp);
+        if (rest & 2) gather_batch<2, LPR, SPL, KAHAN, Raw>(mm, j, w, ld, val, sum, comp);
+        if (rest & 1) gather_batch<1, LPR, SPL, KAHAN, Raw>(mm, j, w, ld, val, sum, comp);
     }
 }
 

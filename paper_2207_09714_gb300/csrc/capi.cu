@@ -49,6 +49,7 @@ struct gabm_ctx {
     int sirs_H = 0;                      // history entries per row
     int16_t *sirs_hist = nullptr;        // [n_rows][sirs_H] exposure days
     uint16_t *sirs_cnt = nullptr;        // [n_rows] (H <= GABM_MAX_DAYS / 3 + 2 fits)
+    uint8_t *flags = nullptr;            // [3][n_rows] rows with an infectious in-neighbour (day t mod 3)
     float *sirs_Gh = nullptr;            // [n_rows][sirs_H] G at each exposure
     float *sirs_Lh = nullptr;            // [n_rows][sirs_H] G's own-day terms at each exposure
     int grid_sirs_f = 0, grid_sirs_b = 0;
@@ -716,11 +717,22 @@ gabm_status forward_days_sirs(gabm_ctx *c, int t0, int T, cudaStream_t s) {
     a.cycle = c->cycle;
     a.seed = c->seed;
     for (int k = 0; k < kMaxL; ++k) a.c[k] = k < c->L ? c->c[k] : 0.f;
+    // rows with an infectious in-neighbour, in three rotating buffers (as forward_days_plain)
+    a.m_out = sell_view(c, true);
+    auto fbuf = [&](int d) { return c->flags + (size_t)(d % 3) * c->n_rows; };
+    if (c->flags && T > 0) {
+        CK(cudaMemsetAsync(fbuf(0), 0, (size_t)c->n_rows, s));
+        CK(cudaMemsetAsync(fbuf(1), 0, (size_t)c->n_rows, s));
+        LAUNCH(launch_flags_from_bits(c->bits, a.m_out, c->ntiles, fbuf(0), s));
+    }
     for (int t = 0; t < T; ++t) {
         a.t = t;
         a.lam_out = c->lam + (size_t)t * c->n_rows;
         a.bits_cur = c->bits + (size_t)t * c->ntiles;
         a.bits_next = c->bits + (size_t)(t + 1) * c->ntiles;
+        a.flag_cur = c->flags ? fbuf(t) : nullptr;
+        a.flag_next = c->flags ? fbuf(t + 1) : nullptr;
+        a.flag_clear = c->flags ? fbuf(t + 2) : nullptr;
         prof_begin(c, 0);
         LAUNCH(launch_fwd_day_sirs(a, c->grid_sirs_f, s));
         prof_end(c, 0);
@@ -821,11 +833,24 @@ gabm_status forward_days_plain(gabm_ctx *c, int t0, int T, cudaStream_t s) {
     else if (t0 < T)
         LAUNCH(launch_infectious_bits(c->e, t0, 1, c->L, c->ntiles, c->bits + (size_t)t0 * c->ntiles,
                                       (size_t)c->ntiles, s));
+    // Rows with an infectious in-neighbour, per day, in three rotating buffers: day t
+    // reads buffer t mod 3, fills t + 1 mod 3 and clears t + 2 mod 3.
+    const bool flagged = c->flags && !c->two_hop;
+    a.m_out = sell_view(c, true);
+    auto fbuf = [&](int d) { return c->flags + (size_t)(d % 3) * c->n_rows; };
+    if (flagged && t0 < T) {
+        CK(cudaMemsetAsync(fbuf(t0), 0, (size_t)c->n_rows, s));
+        CK(cudaMemsetAsync(fbuf(t0 + 1), 0, (size_t)c->n_rows, s));
+        LAUNCH(launch_flags_from_bits(c->bits + (size_t)t0 * c->ntiles, a.m_out, c->ntiles, fbuf(t0), s));
+    }
     for (int t = t0; t < T; ++t) {
         a.t = t;
         a.lam_out = c->policy == GABM_STORE_LAMBDA ? c->lam + (size_t)t * c->n_rows : nullptr;
         a.bits_cur = c->bits + (size_t)t * c->ntiles;
         a.bits_next = c->bits + (size_t)(t + 1) * c->ntiles;
+        a.flag_cur = flagged ? fbuf(t) : nullptr;
+        a.flag_next = flagged ? fbuf(t + 1) : nullptr;
+        a.flag_clear = flagged ? fbuf(t + 2) : nullptr;
         a.pull = nullptr;
         prof_begin(c, 0);
         if (c->two_hop) {   // location pressures of day t, then the agents' pull over their locations
@@ -1325,6 +1350,8 @@ static gabm_status create_on_device(const HostLayout &H, const gabm_model_desc *
     if (batched) {
         CTRY(dalloc(c, &c->rbits, (size_t)2 * ntiles * std::max(1, c->Bp / 2)));
         CTRY(dalloc(c, &c->hist0, (size_t)c->I * (c->L + 2)));
+    } else if (!c->soft) {
+        CTRY(dalloc(c, &c->flags, (size_t)3 * n_rows));
     }
     if (c->soft) {
         CTRY(dalloc(c, &c->s_soft, (size_t)n_rows));

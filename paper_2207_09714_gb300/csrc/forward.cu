@@ -88,14 +88,15 @@ __global__ void __launch_bounds__(NT, MINB) k_fwd_day(const FwdDayArgs a) {
     // tile ahead of use (and, when enabled, its slice prefetched into L2).
     BlockTiles disp;
     disp.init(ntiles, lane);
+    const uint8_t *flags = PULL ? nullptr : a.flag_cur;
     TileRows cur, nxt;
-    load_tile_rows(a.m, e, a.gr.tile_graph, ntiles, disp.get(), lane, cur);
-    load_tile_rows(a.m, e, a.gr.tile_graph, ntiles, disp.get(), lane, nxt);
+    load_tile_rows(a.m, e, a.gr.tile_graph, ntiles, disp.get(), lane, cur, flags);
+    load_tile_rows(a.m, e, a.gr.tile_graph, ntiles, disp.get(), lane, nxt, flags);
     prefetch_slice(a.m, cur.p0, cur.p1, lane);
     while (cur.tile < ntiles) {
         prefetch_slice(a.m, nxt.p0, nxt.p1, lane);
         TileRows nn;
-        load_tile_rows(a.m, e, a.gr.tile_graph, ntiles, disp.get(), lane, nn);
+        load_tile_rows(a.m, e, a.gr.tile_graph, ntiles, disp.get(), lane, nn, flags);
 
         const int g = cur.g, tile = cur.tile, ei = cur.e;
         if (g != cur_g) {
@@ -125,11 +126,14 @@ __global__ void __launch_bounds__(NT, MINB) k_fwd_day(const FwdDayArgs a) {
         }
         cS += isS;
 
+        // A susceptible row with no infectious in-neighbour has lambda = 0 exactly (no
+        // marked entry): it reads no entries and does not draw (u < p = 0 is false).
+        const bool act = isS && cur.flag;
         float sum[1];
-        row_sums<1>(a.m, cur.p0, cur.len, isS, lane, contrib, want, sum);
+        row_sums<1>(a.m, cur.p0, cur.len, act, lane, contrib, want, sum);
 
         int e_next = ei;
-        if (isS) {
+        if (act) {
             const float Lam = sum[0] * a.gr.inv_Dbar[g];
             const int inst = g;
             const float lam = (a.R[(size_t)inst * a.ldP + t] * a.S[inst * kAges + a.age[row]]) * Lam;
@@ -141,11 +145,18 @@ __global__ void __launch_bounds__(NT, MINB) k_fwd_day(const FwdDayArgs a) {
                 e_next = t;
             }
             if (a.lam_out) a.lam_out[row] = Lam;
+        } else if (isS && a.lam_out) {
+            a.lam_out[row] = 0.f;
         }
         // rows infectious tomorrow (susceptible and padding rows fall outside the window)
         const int kn = t + 1 - e_next;
-        const unsigned inf_next = __ballot_sync(0xffffffffu, (unsigned)(kn - 1) < (unsigned)(Lx - 1));
+        const bool inf = (unsigned)(kn - 1) < (unsigned)(Lx - 1);
+        const unsigned inf_next = __ballot_sync(0xffffffffu, inf);
         if (lane == 0) a.bits_next[tile] = inf_next;
+        if (!PULL && flags) {   // tomorrow's flags: the out-neighbours of tomorrow's infectious rows
+            push_flags(a.m_out, tile, lane, inf, a.flag_next);
+            a.flag_clear[row] = 0;
+        }
 
         cur = nxt;
         nxt = nn;
@@ -654,6 +665,20 @@ cudaError_t launch_seed_ties(const SeedArgs &a, int I, cudaStream_t s) {
 }
 
 constexpr int kBitsBlock = 768;   // one block of 24 warps per SM when the bitmap lives in shared memory
+
+__global__ void k_flags_from_bits(const uint32_t *bits_t, Sell m_out, int ntiles, uint8_t *flags) {
+    const int lane = threadIdx.x & 31;
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    for (int tile = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; tile < ntiles; tile += warps)
+        push_flags(m_out, tile, lane, (bits_t[tile] >> lane) & 1u, flags);
+}
+
+cudaError_t launch_flags_from_bits(const uint32_t *bits_t, Sell m_out, int ntiles, uint8_t *flags, cudaStream_t s) {
+    int grid = (ntiles + 7) / 8;
+    if (grid > 65535) grid = 65535;
+    k_flags_from_bits<<<grid > 0 ? grid : 1, 256, 0, s>>>(bits_t, m_out, ntiles, flags);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_fwd_day(const FwdDayArgs &a, int grid, bool smem_bits, cudaStream_t s) {
     if (a.fate.L_M > 0) {

@@ -168,6 +168,13 @@ struct FwdDayArgs {
     uint32_t *bits_next;        // [ntiles] the same for day t + 1 (written by this launch)
     const float *pull;          // agent-location graphs: location pressures P [locations] (m lists
                                 // each agent's locations), gathered in place of marked neighbours
+    // Rows with an infectious in-neighbour (one byte per row), or nullptr (every
+    // susceptible row sums): flag_cur for day t; the launch sets flag_next (day t + 1)
+    // for the out-neighbours of the rows infectious tomorrow, and clears its rows of
+    // flag_clear (the buffer day t + 1 will fill for day t + 2).
+    const uint8_t *flag_cur;
+    uint8_t *flag_next, *flag_clear;
+    Sell m_out;                 // out-edges (the in-edges when the weights are symmetric)
     int ntiles, t, tau_EI, L;   // L: the longest infectious window (the table's length)
     uint64_t seed;
     FateRef fate;               // sampled R/M split (fate.L_M > 0) or the single RM exit
@@ -391,6 +398,9 @@ cudaError_t launch_seed_scan(const SeedArgs &a, int I, cudaStream_t s);
 cudaError_t launch_seed_mark(const SeedArgs &a, int I, int grid_x, cudaStream_t s);
 cudaError_t launch_seed_ties(const SeedArgs &a, int I, cudaStream_t s);
 cudaError_t launch_fwd_day(const FwdDayArgs &a, int grid, bool smem_bits, cudaStream_t s);
+// Flags for day t of the rows with an in-neighbour infectious on day t (bits_t): every
+// out-neighbour of a marked row gets flag 1.  flags must be zero on entry.
+cudaError_t launch_flags_from_bits(const uint32_t *bits_t, Sell m_out, int ntiles, uint8_t *flags, cudaStream_t s);
 // bits[d][tile] for days t0 .. t0 + ndays - 1: rows with 1 <= t - e < L (infectious on day t).
 cudaError_t launch_infectious_bits_fate(const int16_t *e, GraphRef gr, FateRef f, int t, int ntiles, uint32_t *bits,
                                         cudaStream_t s);

@@ -146,15 +146,18 @@ struct TileRows {
     uint32_t len;     // entries of this lane's row
     uint32_t p0, p1;  // the tile's slice bounds
     int g;            // graph of the tile
+    bool flag;        // the row has an infectious in-neighbour today (true without flags)
 };
 
 __device__ __forceinline__ void load_tile_rows(const Sell &m, const int16_t *e, const uint16_t *tile_graph,
-                                               int ntiles, int tile, int lane, TileRows &tr) {
+                                               int ntiles, int tile, int lane, TileRows &tr,
+                                               const uint8_t *flags = nullptr) {
     tr.tile = tile;
     tr.e = kPad;
     tr.len = 0;
     tr.p0 = tr.p1 = 0;
     tr.g = 0;
+    tr.flag = true;
     if (tile < ntiles) {
         const int row = tile * kTile + lane;
         tr.e = e[row];
@@ -162,6 +165,25 @@ __device__ __forceinline__ void load_tile_rows(const Sell &m, const int16_t *e, 
         tr.p0 = m.slice_ptr[tile];
         tr.p1 = m.slice_ptr[tile + 1];
         tr.g = tile_graph ? (int)tile_graph[tile] : 0;
+        if (flags) tr.flag = flags[row] != 0;
+    }
+}
+
+// Sets flags[j] = 1 for every out-neighbour j of the tile rows whose lane has `push`
+// (one byte store each: every writer stores the same value, so the result does not
+// depend on their order).  The warp takes those rows one at a time, its lanes splitting
+// the row's entries (entry k of tile row r sits at slice_ptr[tile] + 32 k + r), so a
+// row costs a load round trip per 32 entries.  Called by all 32 lanes.
+__device__ __forceinline__ void push_flags(const Sell &m_out, int tile, int lane, bool push, uint8_t *flags) {
+    unsigned rows = __ballot_sync(0xffffffffu, push);
+    if (!rows) return;
+    const uint32_t base = m_out.slice_ptr[tile];
+    const uint32_t my_len = push ? m_out.row_len[tile * kTile + lane] : 0u;
+    while (rows) {
+        const int r = __ffs(rows) - 1;
+        rows &= rows - 1u;
+        const uint32_t len = __shfl_sync(0xffffffffu, my_len, r);
+        for (uint32_t k = (uint32_t)lane; k < len; k += 32u) flags[__ldg(m_out.col + base + 32u * k + (uint32_t)r)] = 1;
     }
 }
 

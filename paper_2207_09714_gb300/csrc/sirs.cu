@@ -1,6 +1,6 @@
 // sirs.cu -- forward and reverse day kernels of SIRS reinfection (see sirs.cuh).
 //
-// Each warp holds one 32-row tile at a time (tiles strided over the launch).  The sums
+// Each warp holds one 32-row tile at a time.  The sums
 // are those of the base model's kernels -- the same row_sums over the same SELL entries,
 // the same fused multiply-adds in the same order for G -- so with nobody returning
 // within the horizon the results are bitwise the base model's.
@@ -40,14 +40,16 @@ __global__ void k_sirs_hist_init(const int16_t *e, int64_t n_rows, int H, int16_
 }
 
 // Day t: rows susceptible on day t (never exposed, or at least `cycle` days past their
-// last exposure) draw; an exposure is appended to the row's history.
-__global__ void __launch_bounds__(kBlock) k_fwd_day_sirs(const SirsFwdArgs a) {
+// last exposure) draw; an exposure is appended to the row's history.  Each block takes a
+// contiguous range of tiles (neighbours stay in its SM's L1), each warp's next tile is
+// read one tile ahead, and a susceptible row with no infectious in-neighbour (flag_cur)
+// reads no entries: its lambda is 0 exactly.
+__global__ void __launch_bounds__(kBlock, 3) k_fwd_day_sirs(const SirsFwdArgs a) {
     __shared__ float c_s[kMaxL];
     if (threadIdx.x < kMaxL) c_s[threadIdx.x] = a.c[threadIdx.x];
     __syncthreads();
     const int lane = threadIdx.x & 31;
-    const int nwarps = gridDim.x * (kBlock / 32);
-    const int t = a.t, L = a.L;
+    const int t = a.t, L = a.L, ntiles = a.ntiles;
     const uint32_t *bits = a.bits_cur;
     const int16_t *e = a.e;
     // neighbours marked infectious today (never written by this launch) contribute
@@ -58,15 +60,22 @@ __global__ void __launch_bounds__(kBlock) k_fwd_day_sirs(const SirsFwdArgs a) {
     };
     const bool want[1] = {true};
     int cur_g = -1, cS = 0, cE = 0, cI = 0, cR = 0, cN = 0;
-    for (int tile = blockIdx.x * (kBlock / 32) + (threadIdx.x >> 5); tile < a.ntiles; tile += nwarps) {
-        const int g = a.gr.tile_graph ? (int)a.gr.tile_graph[tile] : 0;
+    BlockTiles disp;
+    disp.init(ntiles, lane);
+    TileRows cur, nxt;
+    load_tile_rows(a.m, e, a.gr.tile_graph, ntiles, disp.get(), lane, cur, a.flag_cur);
+    load_tile_rows(a.m, e, a.gr.tile_graph, ntiles, disp.get(), lane, nxt, a.flag_cur);
+    while (cur.tile < ntiles) {
+        TileRows nn;
+        load_tile_rows(a.m, e, a.gr.tile_graph, ntiles, disp.get(), lane, nn, a.flag_cur);
+        const int g = cur.g, tile = cur.tile;
         if (g != cur_g) {
             if (cur_g >= 0) flush_counts(a.counts, a.newRM, a.ldP, cur_g, t, cS, cE, cI, cR, cN, lane);
             cur_g = g;
             cS = cE = cI = cR = cN = 0;
         }
         const int row = tile * kTile + lane;
-        const int ei = e[row];
+        const int ei = cur.e;
         const bool agent = ei != kPad;
         const int k = t - ei;
         const bool isS = agent && (ei == kNever || k >= a.cycle);
@@ -75,10 +84,11 @@ __global__ void __launch_bounds__(kBlock) k_fwd_day_sirs(const SirsFwdArgs a) {
             cN += (k == L);
         }
         cS += isS;
+        const bool act = isS && cur.flag;
         float sum[1];
-        row_sums<1>(a.m, a.m.slice_ptr[tile], a.m.row_len[row], isS, lane, contrib, want, sum);
+        row_sums<1>(a.m, cur.p0, cur.len, act, lane, contrib, want, sum);
         int e_next = ei;
-        if (isS) {
+        if (act) {
             const float Lam = sum[0] * a.gr.inv_Dbar[g];
             const float lam = (a.R[(size_t)g * a.ldP + t] * a.S[g * kAges + a.age[row]]) * Lam;
             const float p = -expm1f(-lam);
@@ -96,18 +106,34 @@ __global__ void __launch_bounds__(kBlock) k_fwd_day_sirs(const SirsFwdArgs a) {
                 }
             }
             a.lam_out[row] = Lam;
+        } else if (isS) {
+            a.lam_out[row] = 0.f;
         }
         const int kn = t + 1 - e_next;
-        const unsigned inf_next = __ballot_sync(0xffffffffu, (unsigned)(kn - 1) < (unsigned)(L - 1));
+        const bool inf = (unsigned)(kn - 1) < (unsigned)(L - 1);
+        const unsigned inf_next = __ballot_sync(0xffffffffu, inf);
         if (lane == 0) a.bits_next[tile] = inf_next;
+        if (a.flag_cur) {   // tomorrow's flags: the out-neighbours of tomorrow's infectious rows
+            push_flags(a.m_out, tile, lane, inf, a.flag_next);
+            a.flag_clear[row] = 0;
+        }
+        cur = nxt;
+        nxt = nn;
     }
     if (cur_g >= 0) flush_counts(a.counts, a.newRM, a.ldP, cur_g, t, cS, cE, cI, cR, cN, lane);
+}
+
+// The next tile's row data for the reverse sweep (one tile ahead of use).
+__device__ __forceinline__ TileRows nn_next(const SirsBwdArgs &a, BlockTiles &disp, int lane) {
+    TileRows nn;
+    load_tile_rows(a.m, a.E, a.gr.tile_graph, a.ntiles, disp.get(), lane, nn);
+    return nn;
 }
 
 // Reverse day t: gx(t+1) of every agent into the ring, then for rows susceptible on
 // day t the adjoint of the draw, with the return terms B(t+1) and B(t+cycle) read from
 // the G stored at the row's later exposures.
-__global__ void __launch_bounds__(kBlock) k_bwd_day_sirs(const SirsBwdArgs a) {
+__global__ void __launch_bounds__(kBlock, 3) k_bwd_day_sirs(const SirsBwdArgs a) {
     __shared__ float c_s[kMaxL];
     __shared__ int slot_k[kMaxL];
     if (threadIdx.x < kMaxL) {
@@ -116,7 +142,6 @@ __global__ void __launch_bounds__(kBlock) k_bwd_day_sirs(const SirsBwdArgs a) {
     }
     __syncthreads();
     const int lane = threadIdx.x & 31;
-    const int nwarps = gridDim.x * (kBlock / 32);
     const int t = a.t, T = a.T, L = a.L, C = a.cycle, H = a.H;
     const bool has_next = t + 1 < T;
     const float *__restrict__ r_next = a.r_next;
@@ -124,8 +149,14 @@ __global__ void __launch_bounds__(kBlock) k_bwd_day_sirs(const SirsBwdArgs a) {
     const bool want[1] = {true};
     int cur_g = -1, cN = 0;
     unsigned emax_w = 0u;
-    for (int tile = blockIdx.x * (kBlock / 32) + (threadIdx.x >> 5); tile < a.ntiles; tile += nwarps) {
-        const int g = a.gr.tile_graph ? (int)a.gr.tile_graph[tile] : 0;
+    BlockTiles disp;
+    disp.init(a.ntiles, lane);
+    TileRows cur, nxt;
+    load_tile_rows(a.m, a.E, a.gr.tile_graph, a.ntiles, disp.get(), lane, cur);
+    load_tile_rows(a.m, a.E, a.gr.tile_graph, a.ntiles, disp.get(), lane, nxt);
+    for (; cur.tile < a.ntiles; cur = nxt, nxt = nn_next(a, disp, lane)) {
+        const int tile = cur.tile;
+        const int g = cur.g;
         if (g != cur_g) {
             if (cur_g >= 0) {
                 const int sN = __reduce_add_sync(0xffffffffu, cN);
@@ -141,7 +172,7 @@ __global__ void __launch_bounds__(kBlock) k_bwd_day_sirs(const SirsBwdArgs a) {
         if (lane == 0 && tile * kTile == a.gr.row0[g]) a.sig[(size_t)g * a.ld_sig + t] = sig_t;
 
         const int row = tile * kTile + lane;
-        const bool agent = a.E[row] != kPad;
+        const bool agent = cur.e != kPad;
         const int n_e = min((int)a.cnt[row], H);
         const int16_t *hr = a.hist + (size_t)row * H;
         int j_t = 0;   // exposures before day t
@@ -153,7 +184,7 @@ __global__ void __launch_bounds__(kBlock) k_bwd_day_sirs(const SirsBwdArgs a) {
 
         const bool act = has_next && agent;
         float sum[1];
-        row_sums<1>(a.m, a.m.slice_ptr[tile], a.m.row_len[row], act, lane, contrib, want, sum);
+        row_sums<1>(a.m, cur.p0, cur.len, act, lane, contrib, want, sum);
         const float gx1 = sum[0];
         if (act) a.ring[(size_t)slot_k[1] * a.ring_stride + row] = gx1;
 

@@ -34,6 +34,9 @@ struct SirsFwdArgs {
     int32_t *counts, *newRM;    // [I][ldP][4], [I][ldP]
     const uint32_t *bits_cur;   // rows infectious on day t
     uint32_t *bits_next;        // the same for day t + 1 (written here)
+    const uint8_t *flag_cur;    // rows with an infectious in-neighbour on day t (or nullptr: all)
+    uint8_t *flag_next, *flag_clear;   // day t + 1's flags (set here), day t + 2's (cleared here)
+    Sell m_out;                 // out-edges
     int ntiles, t, tau_EI, L, cycle;
     uint64_t seed;
     float c[kMaxL];
