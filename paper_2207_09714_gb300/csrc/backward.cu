@@ -98,12 +98,14 @@ __global__ void __launch_bounds__(kBlock, (MODE == kBwdStore && !DC) ? GABM_BWD_
     const uint32_t *bits = a.bits_t;
     // contribution 0: w * r_j(t+1) (transpose gather); contribution 1 (recompute):
     // w * c[t - E_j] for neighbours marked infectious on day t
-    auto contrib = [&](uint32_t j, float w, bool valid, float (&out)[NARR]) {
+    auto contrib = [&](uint32_t j, float w, bool valid, float (&out)[NARR], bool (&take)[NARR]) {
         out[0] = w * ld_if(r_next + j, valid);
+        take[0] = valid;
         if constexpr (NARR == 2) {
             const bool mk = valid && marked(bits, j);
             const int Ej = ld_if(E + j, mk, kNever);
             out[1] = mk ? w * infectiousness(Ej, c_s, t, L) : 0.f;
+            take[1] = mk;
         }
     };
 
@@ -349,10 +351,11 @@ __global__ void __launch_bounds__(kBlock) k_lam_day(Sell m, const int16_t *E, co
     __syncthreads();
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int nwarps = gridDim.x * (kBlock / 32);
-    auto contrib = [&](uint32_t j, float w, bool valid, float (&out)[1]) {
+    auto contrib = [&](uint32_t j, float w, bool valid, float (&out)[1], bool (&take)[1]) {
         const bool mk = valid && marked(bits, j);
         const int Ej = ld_if(E + j, mk, kNever);
         out[0] = mk ? w * infectiousness(Ej, c_s, t, L) : 0.f;
+        take[0] = mk;
     };
     const bool want[1] = {true};
     for (int tile = blockIdx.x * (kBlock / 32) + wib; tile < ntiles; tile += nwarps) {
@@ -376,7 +379,10 @@ __global__ void __launch_bounds__(kBlock) k_dc_seeds(Sell m, const int16_t *E, c
                                                      double *dc_tile) {
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int nwarps = gridDim.x * (kBlock / 32);
-    auto contrib = [&](uint32_t j, float w, bool valid, float (&out)[1]) { out[0] = w * ld_if(r0 + j, valid); };
+    auto contrib = [&](uint32_t j, float w, bool valid, float (&out)[1], bool (&take)[1]) {
+        out[0] = w * ld_if(r0 + j, valid);
+        take[0] = valid;
+    };
     const bool want[1] = {true};
     for (int tile = blockIdx.x * (kBlock / 32) + wib; tile < ntiles; tile += nwarps) {
         const int row = tile * kTile + lane;
@@ -404,7 +410,10 @@ __global__ void __launch_bounds__(kBlock) k_fate_seeds(Sell m, const int16_t *E,
     const int L = Lm1 + 1;
     const int Lmin = min(f.L_R, f.L_M);
     const double sgn = f.L_M > f.L_R ? 1.0 : -1.0;
-    auto contrib = [&](uint32_t j, float w, bool valid, float (&out)[1]) { out[0] = w * ld_if(r0 + j, valid); };
+    auto contrib = [&](uint32_t j, float w, bool valid, float (&out)[1], bool (&take)[1]) {
+        out[0] = w * ld_if(r0 + j, valid);
+        take[0] = valid;
+    };
     const bool want[1] = {true};
     for (int tile = blockIdx.x * (kBlock / 32) + wib; tile < ntiles; tile += nwarps) {
         const int row = tile * kTile + lane;

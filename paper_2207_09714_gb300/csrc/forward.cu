@@ -70,13 +70,15 @@ __global__ void __launch_bounds__(NT, MINB) k_fwd_day(const FwdDayArgs a) {
     const int16_t *e = a.e;
     const uint32_t *bits = a.bits_cur;
     // only neighbours marked infectious today contribute; their exposure day is gathered
-    auto contrib = [&](uint32_t j, float w, bool valid, float (&out)[1]) {
+    auto contrib = [&](uint32_t j, float w, bool valid, float (&out)[1], bool (&take)[1]) {
         if constexpr (PULL) {
             out[0] = w * ld_if(a.pull + j, valid);
+            take[0] = valid;
         } else {
             const bool mk = valid && (SMEM_BITS ? ((bits_s[j >> 5] >> (j & 31u)) & 1u) : marked(bits, j));
             const int ej = ld_if(e + j, mk, kNever);
             out[0] = mk ? w * infectiousness(ej, c_s, t, L) : 0.f;
+            take[0] = mk;
         }
     };
     const bool want[1] = {true};
@@ -130,7 +132,17 @@ __global__ void __launch_bounds__(NT, MINB) k_fwd_day(const FwdDayArgs a) {
         // marked entry): it reads no entries and does not draw (u < p = 0 is false).
         const bool act = isS && cur.flag;
         float sum[1];
-        row_sums<1>(a.m, cur.p0, cur.len, act, lane, contrib, want, sum);
+        const unsigned amask = __ballot_sync(0xffffffffu, act);
+        if (flags && __popc(amask) <= GABM_COOP_ROWS) {   // few summing rows: one at a time, warp-wide
+            float cs = 0.f;
+            sum[0] = 0.f;
+            for (unsigned rows = amask; rows; rows &= rows - 1u) {
+                const int r = __ffs(rows) - 1;
+                warp_row_sum(a.m, cur.p0, __shfl_sync(0xffffffffu, cur.len, r), r, lane, contrib, sum[0], cs);
+            }
+        } else {
+            row_sums<1>(a.m, cur.p0, cur.len, act, lane, contrib, want, sum);
+        }
 
         int e_next = ei;
         if (act) {
@@ -227,7 +239,10 @@ __global__ void __launch_bounds__(kBlock, GABM_MINBLOCKS) k_fwd_day_soft(const S
     const int lane = threadIdx.x & 31;
     const int t = a.t, L = a.L, ntiles = a.ntiles;
     const float *__restrict__ x_cur = a.x_cur;
-    auto contrib = [&](uint32_t j, float w, bool valid, float (&out)[1]) { out[0] = w * ld_if(x_cur + j, valid); };
+    auto contrib = [&](uint32_t j, float w, bool valid, float (&out)[1], bool (&take)[1]) {
+        out[0] = w * ld_if(x_cur + j, valid);
+        take[0] = valid;
+    };
     const bool want[1] = {true};
     const size_t n_rows = (size_t)ntiles * kTile;
     const int slot_t = t % L;   // holds n(t - L) before this launch overwrites it with n(t)

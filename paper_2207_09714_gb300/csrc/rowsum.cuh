@@ -222,11 +222,15 @@ __device__ __forceinline__ int ld_if(const int16_t *p, bool pred, int dflt) {
 }
 
 // For this lane's row (when act), sum[a] = the sum of contribution a over the
-// row's entries in entry order, with compensated summation; f(j, w, valid, out)
-// writes the NARR contributions of the entry with column j and weight w (it is
-// also called for invalid entries -- padding, other rows' tails -- and must then
-// touch no memory beyond the slice), and want[a] says whether sum a is taken
-// for this row.  Called by all 32 lanes; the batch runs without branches.
+// row's entries in entry order, with compensated summation; f(j, w, valid, out, take)
+// writes the NARR contributions of the entry with column j and weight w and whether
+// each is added (it is also called for invalid entries -- padding, other rows'
+// tails -- and must then touch no memory beyond the slice and take nothing), and
+// want[a] says whether sum a is taken for this row.  A sum of marked neighbours'
+// infectiousness takes the marked entries only: the compensated sum of a row is then
+// a function of its marked entries in entry order, however they are visited
+// (row_sums here, or a warp walking one row).  Called by all 32 lanes; the batch runs
+// without branches.
 template <int NARR, class F>
 __device__ __forceinline__ void row_sums(const Sell &m, uint32_t p0, uint32_t len, bool act, int lane, F f,
                                          const bool (&want)[NARR], float (&sum)[NARR]) {
@@ -260,9 +264,10 @@ __device__ __forceinline__ void row_sums(const Sell &m, uint32_t p0, uint32_t le
             const uint32_t k = k0 + (uint32_t)u;
             const bool valid = act && k < len;
             float out[NARR];
-            f(jv[u], wv[u], valid, out);
+            bool take[NARR];
+            f(jv[u], wv[u], valid, out, take);
 #pragma unroll
-            for (int a = 0; a < NARR; ++a) kahan_add_if(sum[a], comp[a], out[a], valid && want[a]);
+            for (int a = 0; a < NARR; ++a) kahan_add_if(sum[a], comp[a], out[a], take[a] && want[a]);
         }
     };
     if (GABM_PIPE) {
@@ -283,6 +288,39 @@ __device__ __forceinline__ void row_sums(const Sell &m, uint32_t p0, uint32_t le
             float wv[kUnroll];
             load_batch(k0, jv, wv);
             use_batch(k0, jv, wv);
+        }
+    }
+}
+
+// Tiles with at most this many summing rows have them summed one row at a time by the
+// whole warp (warp_row_sum) instead of lane by lane over the tile's longest row.
+#ifndef GABM_COOP_ROWS
+#define GABM_COOP_ROWS 8
+#endif
+
+// The sum of one row's taken contributions by the whole warp: the row of tile lane r
+// (entries [0, len) at p0 + 32 k + r), the result in lane r's sum / comp.  The lanes
+// load 32 entries at a time and evaluate f as row_sums does; lane r then adds the taken
+// ones in entry order with the same compensated addition, so the value is row_sums'.
+// Called by all 32 lanes.
+template <class F>
+__device__ __forceinline__ void warp_row_sum(const Sell &m, uint32_t p0, uint32_t len, int r, int lane, F f,
+                                             float &sum, float &comp) {
+    for (uint32_t k0 = 0; k0 < len; k0 += 32u) {
+        const uint32_t k = k0 + (uint32_t)lane;
+        const bool valid = k < len;
+        const uint32_t idx = p0 + k * 32u + (uint32_t)r;
+        const uint32_t j = ld_cs_if(m.col + idx, valid);
+        const float w = ld_cs_if(m.w + idx, valid);
+        float out[1];
+        bool take[1];
+        f(j, w, valid, out, take);
+        unsigned mm = __ballot_sync(0xffffffffu, take[0]);
+        while (mm) {
+            const int src = __ffs(mm) - 1;
+            mm &= mm - 1u;
+            const float v = __shfl_sync(0xffffffffu, out[0], src);
+            if (lane == r) kahan_add(sum, comp, v);
         }
     }
 }

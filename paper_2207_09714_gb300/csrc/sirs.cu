@@ -53,10 +53,11 @@ __global__ void __launch_bounds__(kBlock, 3) k_fwd_day_sirs(const SirsFwdArgs a)
     const uint32_t *bits = a.bits_cur;
     const int16_t *e = a.e;
     // neighbours marked infectious today (never written by this launch) contribute
-    auto contrib = [&](uint32_t j, float w, bool valid, float (&out)[1]) {
+    auto contrib = [&](uint32_t j, float w, bool valid, float (&out)[1], bool (&take)[1]) {
         const bool mk = valid && marked(bits, j);
         const int ej = ld_if(e + j, mk, kNever);
         out[0] = mk ? w * infectiousness(ej, c_s, t, L) : 0.f;
+        take[0] = mk;
     };
     const bool want[1] = {true};
     int cur_g = -1, cS = 0, cE = 0, cI = 0, cR = 0, cN = 0;
@@ -86,7 +87,17 @@ __global__ void __launch_bounds__(kBlock, 3) k_fwd_day_sirs(const SirsFwdArgs a)
         cS += isS;
         const bool act = isS && cur.flag;
         float sum[1];
-        row_sums<1>(a.m, cur.p0, cur.len, act, lane, contrib, want, sum);
+        const unsigned amask = __ballot_sync(0xffffffffu, act);
+        if (a.flag_cur && __popc(amask) <= GABM_COOP_ROWS) {   // few summing rows: one at a time, warp-wide
+            float cs = 0.f;
+            sum[0] = 0.f;
+            for (unsigned rows = amask; rows; rows &= rows - 1u) {
+                const int r = __ffs(rows) - 1;
+                warp_row_sum(a.m, cur.p0, __shfl_sync(0xffffffffu, cur.len, r), r, lane, contrib, sum[0], cs);
+            }
+        } else {
+            row_sums<1>(a.m, cur.p0, cur.len, act, lane, contrib, want, sum);
+        }
         int e_next = ei;
         if (act) {
             const float Lam = sum[0] * a.gr.inv_Dbar[g];
@@ -145,7 +156,10 @@ __global__ void __launch_bounds__(kBlock, 3) k_bwd_day_sirs(const SirsBwdArgs a)
     const int t = a.t, T = a.T, L = a.L, C = a.cycle, H = a.H;
     const bool has_next = t + 1 < T;
     const float *__restrict__ r_next = a.r_next;
-    auto contrib = [&](uint32_t j, float w, bool valid, float (&out)[1]) { out[0] = w * ld_if(r_next + j, valid); };
+    auto contrib = [&](uint32_t j, float w, bool valid, float (&out)[1], bool (&take)[1]) {
+        out[0] = w * ld_if(r_next + j, valid);
+        take[0] = valid;
+    };
     const bool want[1] = {true};
     int cur_g = -1, cN = 0;
     unsigned emax_w = 0u;

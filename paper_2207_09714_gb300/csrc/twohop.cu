@@ -28,13 +28,15 @@ __global__ void __launch_bounds__(kBlock) k_loc_sum(Sell ml, int nloc_tiles, con
     if (threadIdx.x < kMaxL) c_s[threadIdx.x] = c[threadIdx.x];
     __syncthreads();
     const int lane = threadIdx.x & 31;
-    auto contrib = [&](uint32_t j, float w, bool valid, float (&o)[1]) {
+    auto contrib = [&](uint32_t j, float w, bool valid, float (&o)[1], bool (&take)[1]) {
         if constexpr (FWD) {
             const bool mk = valid && marked(bits, j);
             const int ej = ld_if(e + j, mk, kNever);
             o[0] = mk ? w * infectiousness(ej, c_s, t, L) : 0.f;
+            take[0] = mk;
         } else {
             o[0] = w * ld_if(r + j, valid);
+            take[0] = valid;
         }
     };
     const bool want[1] = {true};
