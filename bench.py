@@ -87,6 +87,23 @@ def _ncu_traffic(kernel: str, sha: str, workload: str):
     return None
 
 
+_SRC = {"k_fwd_day": ["forward.cu", "rowsum.cuh", "gabm_internal.cuh"],
+        "k_bwd_day": ["backward.cu", "rowsum.cuh", "gabm_internal.cuh"],
+        "k_fwd_day_b": ["batched.cu", "batched_common.cuh", "rowsum.cuh", "gabm_internal.cuh"],
+        "k_bwd_day_b": ["batched_bwd.cu", "batched_common.cuh", "rowsum.cuh", "gabm_internal.cuh"]}
+
+
+def dram_rate(kernel: str, workload: str, ms_per_launch: float, peak: float):
+    """The ncu-measured DRAM bytes per launch of ``kernel`` on ``workload`` (profiles/
+    ncu_traffic.txt, current source only) and the rate and fraction of the peak they
+    give at the live per-launch duration; None without a matching capture."""
+    tr = _ncu_traffic(kernel, _kernel_source_sha(_SRC[kernel]), workload)
+    if tr is None or not ms_per_launch:
+        return None
+    gbs = tr / (ms_per_launch / 1e3) / 1e9
+    return {"traffic_bytes_per_launch": tr, "dram_gbs": gbs, "dram_frac": gbs / peak}
+
+
 class ClockSampler:
     """nvidia-smi clocks / throttle reasons sampled every 100 ms while running.  Entering
     waits until the sampler is up, so its samples cover the region it brackets."""
@@ -340,6 +357,9 @@ def bench_batched(args, stream, peak, peak_kind):
     src = ["batched_bwd.cu" if dom == "k_bwd_day_b" else "batched.cu", "batched_common.cuh", "rowsum.cuh",
            "gabm_internal.cuh"]
     traffic = _ncu_traffic(dom, _kernel_source_sha(src), f"typed500k_B{B}_T{T}_store")
+    wl = f"typed500k_B{B}_T{T}_store"
+    f_dr = dram_rate("k_fwd_day_b", wl, f_ms / f_n, peak)
+    b_dr = dram_rate("k_bwd_day_b", wl, b_ms / b_n, peak)
     result = {
         "workload": f"one shared {pop.n}-agent typed contact graph, {B} parameter sets (R ~ U[1.5, 4.0], "
                     f"m ~ U[0.005, 0.05]), {T} days, forward + MSE + backward of every set",
@@ -357,6 +377,11 @@ def bench_batched(args, stream, peak, peak_kind):
                                  "alg_bytes_per_launch": bwd_b.sum() / T},
                      "fwd_plus_bwd_frac": both_gbs / peak},
     }
+    result["roofline"]["fwd_day"]["dram"] = f_dr
+    result["roofline"]["bwd_day"]["dram"] = b_dr
+    if f_dr and b_dr:
+        tot = f_dr["traffic_bytes_per_launch"] * f_n + b_dr["traffic_bytes_per_launch"] * b_n
+        result["roofline"]["fwd_plus_bwd_dram_frac"] = tot / ((f_ms + b_ms) / 1e3) / 1e9 / peak
     if args.no_plain:
         return result
 
@@ -797,6 +822,16 @@ def bench_workload(name, what, pops, B, T, R_np, m_np, S_np, n_seed, y_np, polic
     out["day_kernels"] = {"alg_bytes_per_step": alg, "ms_per_step": kern_ms,
                           "achieved_gbs": alg / (kern_ms / 1e3) / 1e9, "frac": alg / (kern_ms / 1e3) / 1e9 / peak,
                           "peak": peak, "peak_source": peak_kind}
+    if B > 1 and len(pops) == 1 and policy == capi.GABM_STORE_LAMBDA:
+        wl = f"typed{pops[0].n // 1000}k_B{B}_T{T}_store".replace("1000k", "1M")
+        f_dr = dram_rate("k_fwd_day_b", wl, f_ms / f_n, peak)
+        b_dr = None if fwd_only else dram_rate("k_bwd_day_b", wl, b_ms / b_n, peak)
+        out["fwd_day"]["dram"] = f_dr
+        if not fwd_only:
+            out["bwd_day"]["dram"] = b_dr
+        if f_dr and b_dr:
+            tot = f_dr["traffic_bytes_per_launch"] * f_n + b_dr["traffic_bytes_per_launch"] * b_n
+            out["day_kernels"]["dram_frac"] = tot / (kern_ms / 1e3) / 1e9 / peak
     out["full_pull"] = {"bytes_per_step": full, "gbs_at_step_time": full / (ms / 1e3) / 1e9,
                         "note": "paper-style count: every row's edges and state on every day"}
     return out
@@ -863,7 +898,11 @@ def _single_thread_oracle_cmd():
     return [sys.executable, "-c", code]
 
 
-def run_configs(args, gen, pop1m, stream, peak, peak_kind):
+CONFIG_KEYS = {"c0": "c0_10k_forward_30d", "b1m": "batched_1M_x64_60d", "c3": "c3_32_counties_90d",
+               "c4": "c4_8M_powerlaw_120d"}
+
+
+def run_configs(args, gen, pop1m, stream, peak, peak_kind, only=None):
     """The other configurations, each in its own key (a failure is reported there):
     10k agents forward only (30 days); 1M agents x 64 parameter sets (60 days); 32 uneven
     counties (90 days); 8M agents with power-law contacts (120 days, recompute policy).
@@ -876,6 +915,8 @@ def run_configs(args, gen, pop1m, stream, peak, peak_kind):
     rng = np.random.default_rng(0)
 
     def guarded(key, fn):
+        if only is not None and CONFIG_KEYS[only] != key:
+            return
         try:
             out[key] = fn()
         except Exception as exc:   # reported, the other sections still run
@@ -896,27 +937,35 @@ def run_configs(args, gen, pop1m, stream, peak, peak_kind):
     Rb = np.repeat(rng.uniform(1.5, 4.0, (B1M_SETS, 1)), B1M_DAYS, axis=1).astype(np.float32)
     mb = np.repeat(rng.uniform(0.005, 0.05, (B1M_SETS, 1)), B1M_DAYS, axis=1).astype(np.float32)
     Sb = np.tile(synth.SUSCEPTIBILITY, (B1M_SETS, 1)).astype(np.float32)
-    yb = np.stack([synth.target_curve(B1M_DAYS, pop1m.n, seed=b) for b in range(B1M_SETS)])
+    yb = np.stack([synth.target_curve(B1M_DAYS, N_AGENTS, seed=b) for b in range(B1M_SETS)])
     guarded("batched_1M_x64_60d", lambda: bench_workload(
         "b1m", f"one shared {pop1m.n}-agent typed contact graph, {B1M_SETS} parameter sets (R ~ U[1.5, 4.0], "
                f"m ~ U[0.005, 0.05]), {B1M_DAYS} days, forward + MSE + backward of every set",
         [pop1m], B1M_SETS, B1M_DAYS, Rb, mb, Sb, [N_SEED] * B1M_SETS, yb, capi.GABM_STORE_LAMBDA, stream, peak,
         peak_kind, steps=3))
 
-    counties = gen.county_list()
-    p4 = gen.powerlaw()
-    gen.close()
+    if only in ("c0", "b1m"):
+        return out
+    if gen is not None:
+        counties = gen.county_list() if only in (None, "c3") else []
+        p4 = gen.powerlaw() if only in (None, "c4") else None
+        gen.close()
+    else:
+        counties = ([synth.county(g, n) for g, n in enumerate(synth.uneven_county_sizes(CFG3_COUNTIES, seed=0))]
+                    if only in (None, "c3") else [])
+        p4 = synth.population_typed(CFG4_AGENTS, seed=0, powerlaw=True) if only in (None, "c4") else None
     single = None
-    if not args.no_cpu_baseline:
+    if not args.no_cpu_baseline and only is None:
         single = subprocess.Popen(_single_thread_oracle_cmd(), stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
                                   text=True, cwd=ROOT, env=dict(os.environ, OMP_NUM_THREADS="1"))
 
     # config 3: 32 uneven counties, each with its own parameters, 90 days
-    G = len(counties)
+    G = max(len(counties), 1)
     R3 = (rng.uniform(1.8, 3.2, (G, 1)) * rng.uniform(0.9, 1.1, (G, CFG3_DAYS))).astype(np.float32)
     m3 = np.repeat(rng.uniform(0.005, 0.05, (G, 1)), CFG3_DAYS, axis=1).astype(np.float32)
     S3 = (synth.SUSCEPTIBILITY[None, :] * rng.uniform(0.8, 1.2, (G, 9))).astype(np.float32)
-    y3 = np.stack([synth.target_curve(CFG3_DAYS, p.n, seed=g) for g, p in enumerate(counties)])
+    y3 = (np.stack([synth.target_curve(CFG3_DAYS, p.n, seed=g) for g, p in enumerate(counties)]) if counties
+          else np.zeros((1, CFG3_DAYS)))
     guarded("c3_32_counties_90d", lambda: bench_workload(
         "c3", f"{G} county graphs of the typed generator, agent counts log-uniform in [5e4, 2e6] "
               f"(sum {sum(p.n for p in counties)}), own parameters each, {CFG3_DAYS} days, autotuned, "
@@ -927,7 +976,7 @@ def run_configs(args, gen, pop1m, stream, peak, peak_kind):
     R4 = np.full((1, CFG4_DAYS), R0, np.float32)
     m4 = np.full((1, CFG4_DAYS), MORTALITY, np.float32)
     S4 = synth.SUSCEPTIBILITY[None, :].astype(np.float32)
-    y4 = synth.target_curve(CFG4_DAYS, p4.n)[None, :]
+    y4 = synth.target_curve(CFG4_DAYS, p4.n if p4 is not None else CFG4_AGENTS)[None, :]
     guarded("c4_8M_powerlaw_120d", lambda: bench_workload(
         "c4", f"{p4.n} agents, typed generator with Chung-Lu power-law contacts (exponent 2.5, degrees up to "
               f"2000), {CFG4_DAYS} days, recompute policy (lambda recomputed from the final exposure days), "
@@ -975,6 +1024,9 @@ def main():
     ap.add_argument("--no-plain", action="store_true", help="skip the per-set plain comparator")
     ap.add_argument("--no-configs", action="store_true",
                     help="skip the other configurations (10k forward, 1M x 64 sets, 32 counties, 8M power-law)")
+    ap.add_argument("--only", choices=sorted(CONFIG_KEYS),
+                    help="run only this configuration (c0: 10k forward, b1m: 1M x 64 sets, c3: 32 counties, "
+                         "c4: 8M power-law) and print its result as the JSON line")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -1000,6 +1052,15 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     gbuild.build()
+    if args.only:
+        stream = torch.cuda.Stream()
+        peak, peak_kind = _peaks()
+        pop1m = synth.population_typed(N_AGENTS, seed=0) if args.only == "b1m" else None
+        with ClockSampler(local) as clk:
+            res = run_configs(args, None, pop1m, stream, peak, peak_kind, only=args.only)[CONFIG_KEYS[args.only]]
+        if rank == 0:
+            print(json.dumps({"only": CONFIG_KEYS[args.only], "clocks": clk.summary(), **res}), flush=True)
+        return
     if args.batched_only:
         stream = torch.cuda.Stream()
         peak, peak_kind = _peaks()
@@ -1100,6 +1161,8 @@ def main():
           ["forward.cu", "rowsum.cuh", "gabm_internal.cuh"]
     workload_tag = f"typed1M_T{DAYS}_{args.policy}"
     traffic = _ncu_traffic(dominant, _kernel_source_sha(src), workload_tag)
+    fwd_dr = dram_rate("k_fwd_day", workload_tag, fwd_ms_k / fwd_n if fwd_n else 0.0, peak)
+    bwd_dr = dram_rate("k_bwd_day", workload_tag, bwd_ms_k / bwd_n if bwd_n else 0.0, peak)
     dom_gbs = bwd_gbs if dominant == "k_bwd_day" else fwd_gbs
     dom_bytes = (bwd_b.sum() if dominant == "k_bwd_day" else fwd_b.sum()) / DAYS
     dom_ms = (bwd_ms_k / bwd_n) if dominant == "k_bwd_day" else (fwd_ms_k / fwd_n)
@@ -1178,8 +1241,10 @@ def main():
                      "frac": (dom_gbs / peak) if dom_gbs else None, "traffic": traffic,
                      "peak_source": peak_kind,
                      "alg_bytes_per_launch": dom_bytes, "avg_launch_ms": dom_ms,
-                     "fwd_day": {"achieved": fwd_gbs, "launches": fwd_n, "ms_total": fwd_ms_k},
-                     "bwd_day": {"achieved": bwd_gbs, "launches": bwd_n, "ms_total": bwd_ms_k}},
+                     "dram_frac": (bwd_dr if dominant == "k_bwd_day" else fwd_dr or {}).get("dram_frac")
+                     if (bwd_dr if dominant == "k_bwd_day" else fwd_dr) else None,
+                     "fwd_day": {"achieved": fwd_gbs, "launches": fwd_n, "ms_total": fwd_ms_k, "dram": fwd_dr},
+                     "bwd_day": {"achieved": bwd_gbs, "launches": bwd_n, "ms_total": bwd_ms_k, "dram": bwd_dr}},
         "e2e": {"value": e2e_value, "unit": "agent-days/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
         "clocks": clk.summary(),

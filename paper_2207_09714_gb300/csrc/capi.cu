@@ -17,6 +17,10 @@
 
 using namespace gabm;
 
+#ifndef GABM_DAY_WAVES
+#define GABM_DAY_WAVES 1
+#endif
+
 namespace {
 
 thread_local std::string g_create_error;
@@ -360,6 +364,44 @@ void sort_windows_by_degree(const HostGraph &h, std::vector<uint32_t> &order, in
         std::stable_sort(order.begin() + w0, order.begin() + w1, [&](uint32_t a, uint32_t b) {
             return (h.rowptr[a + 1] - h.rowptr[a]) > (h.rowptr[b + 1] - h.rowptr[b]);
         });
+    }
+}
+
+// Rows much longer than the rest (hubs of a power-law contact graph) cost a SELL tile
+// its longest row in every lane's loop.  Rows of more than kLongRow entries therefore
+// leave their degree window: they are sorted by length and put, 32 to a tile, at evenly
+// spaced window boundaries of the order, so that each such tile holds rows of similar
+// length and the heavy tiles spread over the launch's tile ranges.
+constexpr uint64_t kLongRow = 128;
+
+void group_long_rows(const HostGraph &h, std::vector<uint32_t> &order, int sigma) {
+    auto len = [&](uint32_t a) { return h.rowptr[a + 1] - h.rowptr[a]; };
+    std::vector<uint32_t> rest, lng;
+    rest.reserve(order.size());
+    for (uint32_t a : order) (len(a) > kLongRow ? lng : rest).push_back(a);
+    if (lng.empty()) return;
+    std::stable_sort(lng.begin(), lng.end(), [&](uint32_t a, uint32_t b) { return len(a) > len(b); });
+    const size_t groups = (lng.size() + kTile - 1) / kTile;
+    const size_t win = (size_t)std::max(sigma, kTile);
+    const size_t nwin = rest.size() / win;   // whole windows of the other rows
+    order.clear();
+    size_t r = 0, gi = 0;
+    for (size_t wi = 0; wi <= nwin; ++wi) {
+        // group gi goes after window floor((gi + 1) * nwin / (groups + 1))
+        while (gi < groups && (wi == nwin || (gi + 1) * nwin / (groups + 1) <= wi)) {
+            const size_t b = gi * kTile, e = std::min(lng.size(), b + kTile);
+            order.insert(order.end(), lng.begin() + (long)b, lng.begin() + (long)e);
+            ++gi;
+            if (e - b < (size_t)kTile) break;   // a partial group only at the very end
+        }
+        const size_t r1 = (wi == nwin) ? rest.size() : std::min(rest.size(), r + win);
+        order.insert(order.end(), rest.begin() + (long)r, rest.begin() + (long)r1);
+        r = r1;
+    }
+    while (gi < groups) {   // a partial last group (it completes no window)
+        const size_t b = gi * kTile, e = std::min(lng.size(), b + kTile);
+        order.insert(order.end(), lng.begin() + (long)b, lng.begin() + (long)e);
+        ++gi;
     }
 }
 
@@ -1113,8 +1155,11 @@ void apply_schedule(gabm_ctx *c) {
         if (c->fate || c->dur.n > 0 || c->sirs) c->smem_bits = false;   // these forwards read the bitmap from global memory
         const int bps = c->smem_bits ? occupancy_fwd(c->ntiles, true) : 0;
         if (c->smem_bits && bps <= 0) c->smem_bits = false;
-        c->grid_fwd = c->num_sms * (c->smem_bits ? bps : occupancy_fwd(c->ntiles, false));
-        c->grid_bwd = c->num_sms * occupancy_bwd(mode);
+        // GABM_DAY_WAVES waves of blocks, each block a contiguous range of tiles: blocks that
+        // finish early leave their SM to the next wave's blocks
+        const int waves = std::max(1, GABM_DAY_WAVES);
+        c->grid_fwd = c->num_sms * (c->smem_bits ? bps : occupancy_fwd(c->ntiles, false) * waves);
+        c->grid_bwd = c->num_sms * occupancy_bwd(mode) * waves;
         c->grid_bwd_dc = c->num_sms * occupancy_bwd(mode, true);
         c->grid_bwd_fate = c->num_sms * occupancy_bwd(mode, false, c->fate ? kExitFate : kExitDur);
     }
@@ -1447,6 +1492,7 @@ gabm_status gabm_create(const gabm_graph_desc *graphs, int num_graphs, int sets_
             for (int64_t i = 0; i < hg[g].n; ++i) orders[g][i] = (uint32_t)i;
         }
         sort_windows_by_degree(hg[g], orders[g], sigma);
+        if (sets_per_graph == 1) group_long_rows(hg[g], orders[g], sigma);
         hg[g] = permute_graph(hg[g], orders[g]);
     }
     if (n_rows >= ((int64_t)1 << 31) - 64) return fail(nullptr, GABM_EUNSUPPORTED, "total rows >= 2^31");

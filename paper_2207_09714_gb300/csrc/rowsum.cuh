@@ -295,7 +295,7 @@ __device__ __forceinline__ void row_sums(const Sell &m, uint32_t p0, uint32_t le
 // Tiles with at most this many summing rows have them summed one row at a time by the
 // whole warp (warp_row_sum) instead of lane by lane over the tile's longest row.
 #ifndef GABM_COOP_ROWS
-#define GABM_COOP_ROWS 8
+#define GABM_COOP_ROWS 4
 #endif
 
 // The sum of one row's taken contributions by the whole warp: the row of tile lane r
