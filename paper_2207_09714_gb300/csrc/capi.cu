@@ -879,6 +879,7 @@ gabm_status forward_days_plain(gabm_ctx *c, int t0, int T, cudaStream_t s) {
     // reads buffer t mod 3, fills t + 1 mod 3 and clears t + 2 mod 3.
     const bool flagged = c->flags && !c->two_hop;
     a.m_out = sell_view(c, true);
+    a.t_first = t0;
     auto fbuf = [&](int d) { return c->flags + (size_t)(d % 3) * c->n_rows; };
     if (flagged && t0 < T) {
         CK(cudaMemsetAsync(fbuf(t0), 0, (size_t)c->n_rows, s));

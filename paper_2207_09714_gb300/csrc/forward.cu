@@ -18,6 +18,12 @@
 #include "gabm_internal.cuh"
 #include "rowsum.cuh"
 
+// The share (percent) of a graph's agents in E or I on the previous day from which the
+// one-set forward gathers every entry's exposure day instead of testing the day's bitmap.
+#ifndef GABM_DENSE_MARKS_PCT
+#define GABM_DENSE_MARKS_PCT 25
+#endif
+
 namespace gabm {
 
 namespace {
@@ -69,15 +75,22 @@ __global__ void __launch_bounds__(NT, MINB) k_fwd_day(const FwdDayArgs a) {
     const int t = a.t, L = a.L, tau_EI = a.tau_EI, ntiles = a.ntiles;
     const int16_t *e = a.e;
     const uint32_t *bits = a.bits_cur;
-    // only neighbours marked infectious today contribute; their exposure day is gathered
+    // Only neighbours infectious today contribute; their exposure day is gathered.  While
+    // few rows are infectious the day's bitmap spares the gathers of the others; once many
+    // are (use_bits false, base model only), every entry's exposure day is gathered and
+    // tested directly, which selects the same entries (an exposure during the day gives
+    // c[0] = 0) at one scattered load per entry instead of two.
+    bool use_bits = true;
     auto contrib = [&](uint32_t j, float w, bool valid, float (&out)[1], bool (&take)[1]) {
         if constexpr (PULL) {
             out[0] = w * ld_if(a.pull + j, valid);
             take[0] = valid;
         } else {
-            const bool mk = valid && (SMEM_BITS ? ((bits_s[j >> 5] >> (j & 31u)) & 1u) : marked(bits, j));
-            const int ej = ld_if(e + j, mk, kNever);
-            out[0] = mk ? w * infectiousness(ej, c_s, t, L) : 0.f;
+            const bool pre = valid && (!use_bits || (SMEM_BITS ? ((bits_s[j >> 5] >> (j & 31u)) & 1u) : marked(bits, j)));
+            const int ej = ld_if(e + j, pre, kNever);
+            const int k = t - ej;
+            const bool mk = pre && (unsigned)(k - 1) < (unsigned)(L - 1);
+            out[0] = mk ? w * c_s[k] : 0.f;
             take[0] = mk;
         }
     };
@@ -105,6 +118,11 @@ __global__ void __launch_bounds__(NT, MINB) k_fwd_day(const FwdDayArgs a) {
             if (cur_g >= 0) flush_counts_warp(a.counts, a.newRM, a.ldP, cur_g, t, cS, cE, cI, cR, cN, lane);
             cur_g = g;
             cS = cE = cI = cR = cN = 0;
+            if (!PULL && EXIT == kExitBase && t > a.t_first) {   // the graph's E + I share yesterday
+                const int32_t *cp = a.counts + ((size_t)g * a.ldP + t - 1) * 4;
+                const int32_t ei_cnt = cp[1] + cp[2], all = cp[0] + cp[1] + cp[2] + cp[3];
+                use_bits = (int64_t)ei_cnt * 100 < (int64_t)GABM_DENSE_MARKS_PCT * all;
+            }
         }
         const int row = tile * kTile + lane;
         const bool isS = (ei == kNever);

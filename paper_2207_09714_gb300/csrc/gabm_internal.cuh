@@ -175,6 +175,7 @@ struct FwdDayArgs {
     const uint8_t *flag_cur;
     uint8_t *flag_next, *flag_clear;
     Sell m_out;                 // out-edges (the in-edges when the weights are symmetric)
+    int t_first;                // first day of this forward (counts of earlier days are not its own)
     int ntiles, t, tau_EI, L;   // L: the longest infectious window (the table's length)
     uint64_t seed;
     FateRef fate;               // sampled R/M split (fate.L_M > 0) or the single RM exit
