@@ -304,9 +304,9 @@ __device__ __forceinline__ void row_sums(const Sell &m, uint32_t p0, uint32_t le
 // ones in entry order with the same compensated addition, so the value is row_sums'.
 // Called by all 32 lanes.
 template <class F>
-__device__ __forceinline__ void warp_row_sum(const Sell &m, uint32_t p0, uint32_t len, int r, int lane, F f,
-                                             float &sum, float &comp) {
-    for (uint32_t k0 = 0; k0 < len; k0 += 32u) {
+__device__ __forceinline__ void warp_row_sum_from(const Sell &m, uint32_t p0, uint32_t len, uint32_t k_first, int r,
+                                                  int lane, F f, float &sum, float &comp) {
+    for (uint32_t k0 = k_first; k0 < len; k0 += 32u) {
         const uint32_t k = k0 + (uint32_t)lane;
         const bool valid = k < len;
         const uint32_t idx = p0 + k * 32u + (uint32_t)r;
@@ -323,6 +323,61 @@ __device__ __forceinline__ void warp_row_sum(const Sell &m, uint32_t p0, uint32_
             if (lane == r) kahan_add(sum, comp, v);
         }
     }
+}
+
+template <class F>
+__device__ __forceinline__ void warp_row_sum(const Sell &m, uint32_t p0, uint32_t len, int r, int lane, F f,
+                                             float &sum, float &comp) {
+    warp_row_sum_from(m, p0, len, 0u, r, lane, f, sum, comp);
+}
+
+// warp_row_sum for up to GABM_COOP_ROWS rows of a tile at once (the rows of `amask`), so
+// that their loads overlap: the first 32 entries of every row are loaded, tested and
+// gathered together, then each row's lane adds its taken contributions in entry order;
+// entries past the first 32 go through warp_row_sum.  Each row's value is row_sums'.
+// sum / comp: this lane's row (lanes without a row keep 0).  Called by all 32 lanes.
+template <class F>
+__device__ __forceinline__ void few_row_sums(const Sell &m, uint32_t p0, uint32_t my_len, unsigned amask, int lane,
+                                             F f, float &sum, float &comp) {
+    constexpr int K = GABM_COOP_ROWS;
+    int r[K];
+    uint32_t len[K], j[K];
+    float w[K], out[K];
+    bool take[K];
+    unsigned mm = amask;
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+        r[i] = mm ? __ffs(mm) - 1 : -1;
+        mm &= mm - 1u;
+        len[i] = __shfl_sync(0xffffffffu, my_len, r[i] < 0 ? 0 : r[i]);
+        if (r[i] < 0) len[i] = 0u;
+        const bool valid = (uint32_t)lane < len[i];
+        const uint32_t idx = p0 + (uint32_t)lane * 32u + (uint32_t)(r[i] < 0 ? 0 : r[i]);
+        j[i] = ld_cs_if(m.col + idx, valid);
+        w[i] = ld_cs_if(m.w + idx, valid);
+    }
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+        float o[1];
+        bool tk[1];
+        f(j[i], w[i], (uint32_t)lane < len[i], o, tk);
+        out[i] = o[0];
+        take[i] = tk[0];
+    }
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+        unsigned tm = __ballot_sync(0xffffffffu, take[i]);
+        while (tm) {
+            const int src = __ffs(tm) - 1;
+            tm &= tm - 1u;
+            const float v = __shfl_sync(0xffffffffu, out[i], src);
+            if (lane == r[i]) kahan_add(sum, comp, v);
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < K; ++i)
+        if (__shfl_sync(0xffffffffu, len[i], 0) > 32u)   // len[i] is warp-uniform
+            warp_row_sum_from(m, p0, len[i], 32u, r[i], lane, f, sum, comp);
 }
 
 }  // namespace gabm

@@ -88,13 +88,10 @@ __global__ void __launch_bounds__(kBlock, 3) k_fwd_day_sirs(const SirsFwdArgs a)
         const bool act = isS && cur.flag;
         float sum[1];
         const unsigned amask = __ballot_sync(0xffffffffu, act);
-        if (a.flag_cur && __popc(amask) <= GABM_COOP_ROWS) {   // few summing rows: one at a time, warp-wide
+        if (a.flag_cur && __popc(amask) <= GABM_COOP_ROWS) {   // few summing rows: warp-wide, together
             float cs = 0.f;
             sum[0] = 0.f;
-            for (unsigned rows = amask; rows; rows &= rows - 1u) {
-                const int r = __ffs(rows) - 1;
-                warp_row_sum(a.m, cur.p0, __shfl_sync(0xffffffffu, cur.len, r), r, lane, contrib, sum[0], cs);
-            }
+            if (amask) few_row_sums(a.m, cur.p0, cur.len, amask, lane, contrib, sum[0], cs);
         } else {
             row_sums<1>(a.m, cur.p0, cur.len, act, lane, contrib, want, sum);
         }
