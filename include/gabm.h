@@ -68,10 +68,15 @@ enum { GABM_STORE_LAMBDA = 0, GABM_RECOMPUTE = 1 };
 /* Device layout of the agents.  GABM_ORDER_BFS relabels the agents of each
  * graph in breadth-first order of the contact graph so that an agent's
  * neighbours sit close together in memory (gathers hit fewer cache lines).
- * Results do not depend on it beyond fp32 summation order: the Philox draws
- * and every input and output stay keyed by the caller's agent ids, and the
- * aggregation is permutation invariant (Sec. 2.3, App. A). */
-enum { GABM_ORDER_INPUT = 0, GABM_ORDER_BFS = 1 };
+ * GABM_ORDER_COMMUNITY lays out densely connected groups (found by label
+ * propagation over the contacts) as consecutive rows, groups in breadth-first
+ * order: on contact graphs made of cliques (households, schools, workplaces)
+ * with random contacts on top, more of an agent's neighbours sit nearby than in
+ * breadth-first order.  It costs a few passes over the edges at creation.
+ * Results do not depend on the layout beyond fp32 summation order: the Philox
+ * draws and every input and output stay keyed by the caller's agent ids, and
+ * the aggregation is permutation invariant (Sec. 2.3, App. A). */
+enum { GABM_ORDER_INPUT = 0, GABM_ORDER_BFS = 1, GABM_ORDER_COMMUNITY = 2 };
 
 #define GABM_NEVER 32767     /* exposure day of a susceptible agent */
 #define GABM_NUM_AGES 9      /* age bins 0-10, 11-20, ..., 71-80, 80+ (Sec. 3.1) */
@@ -112,7 +117,7 @@ typedef struct {
                            * return GABM_EUNSUPPORTED and gabm_forward's counts must be NULL. */
     int lambda_policy;    /* GABM_STORE_LAMBDA or GABM_RECOMPUTE */
     uint64_t seed;        /* Philox key */
-    int agent_order;      /* GABM_ORDER_INPUT or GABM_ORDER_BFS (device layout only) */
+    int agent_order;      /* GABM_ORDER_INPUT, _BFS or _COMMUNITY (device layout only) */
     int tau_IM;           /* 0: the single RM exit at L with expected deaths D_t = m_t newRM(t)
                            * (Sec. 3.1 Aggregate).  > 0: the sampled R/M split -- the mortality
                            * stage M with its own I->M time (Sec. 3.1 lists tau_IM in theta_P):
@@ -182,6 +187,15 @@ typedef struct {
  * GABM_STORE_LAMBDA (GABM_EUNSUPPORTED otherwise). */
 gabm_status gabm_create_bipartite(const gabm_bipartite_desc *graphs, int num_graphs,
                                   const gabm_model_desc *model, void *cuda_stream, gabm_ctx **out);
+
+/* The device order gabm_create gives one graph's agents, computed on the host (no GPU
+ * work for host arrays): order_out[r] (n entries, caller-allocated host memory) is the
+ * caller's id of device row r -- the agent order (GABM_ORDER_*), then degree windows of
+ * 1024 rows, then, when sets_per_graph == 1, rows of more than 128 entries grouped 32 to
+ * a tile.  Always a permutation of 0..n-1.  GABM_EINVAL on a bad graph (gabm_create's
+ * checks), an unknown order, sets_per_graph < 1 or a NULL order_out. */
+gabm_status gabm_agent_layout(const gabm_graph_desc *graph, int agent_order, int sets_per_graph,
+                              uint32_t *order_out);
 
 /* Forward over days t0..T-1 (Sec. 3.1, Eq. 1-3, K = T steps).  t0 = 0 after
  * create (seeding from n_seed), or the day given to the last gabm_set_state.

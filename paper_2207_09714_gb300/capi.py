@@ -26,7 +26,7 @@ GABM_ETIMEOUT, GABM_ECANCELLED, GABM_EUNSUPPORTED = 5, 6, 7
 GABM_DEVICE, GABM_HOST = 0, 1
 GABM_HARD_ST, GABM_SOFT = 0, 1
 GABM_STORE_LAMBDA, GABM_RECOMPUTE = 0, 1
-GABM_ORDER_INPUT, GABM_ORDER_BFS = 0, 1
+GABM_ORDER_INPUT, GABM_ORDER_BFS, GABM_ORDER_COMMUNITY = 0, 1, 2
 GABM_NEVER = 32767
 GABM_NUM_AGES = 9
 STATUS_NAMES = {0: "GABM_OK", 1: "GABM_EINVAL", 2: "GABM_ENOMEM", 3: "GABM_ECUDA", 4: "GABM_ESTATE",
@@ -107,12 +107,13 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         L.gabm_get_schedule.argtypes = [P, ctypes.POINTER(_Schedule)]
         L.gabm_set_schedule.argtypes = [P, ctypes.POINTER(_Schedule)]
         L.gabm_autotune.argtypes = [P, i32]
+        L.gabm_agent_layout.argtypes = [ctypes.POINTER(_GraphDesc), i32, i32, P]
         for name in ("gabm_create", "gabm_create_bipartite", "gabm_forward", "gabm_mse_loss", "gabm_backward", "gabm_backward_table",
                      "gabm_set_infectiousness",
                      "gabm_get_state",
                      "gabm_set_state", "gabm_get_lambda", "gabm_mem_stats", "gabm_set_profiling",
                      "gabm_get_profile", "gabm_philox", "gabm_get_schedule", "gabm_set_schedule",
-                     "gabm_autotune"):
+                     "gabm_autotune", "gabm_agent_layout"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
         return L
@@ -191,7 +192,7 @@ class ModelDesc:
     lambda_policy: int = GABM_STORE_LAMBDA
     gumbel_tau: float = 1.0
     relax_mode: int = GABM_HARD_ST
-    agent_order: int = GABM_ORDER_BFS
+    agent_order: int = GABM_ORDER_COMMUNITY
     tau_IM: int = 0          # > 0: the sampled R/M split (c then has tau_EI + max(tau_IR, tau_IM) entries)
     p_IR: np.ndarray = None  # [tau_IR] pmf of a per-agent I-stage duration 1..tau_IR, or None
     tau_RS: int = 0          # > 0: SIRS reinfection, back to S tau_RS days after entering RM
@@ -277,6 +278,21 @@ def gabm_create_bipartite(graphs, model: ModelDesc, stream=None) -> GabmCtx:
     st = L.gabm_create_bipartite(descs, len(graphs), ctypes.byref(md), s, ctypes.byref(out))
     _check(st, None)
     return GabmCtx(out, graphs, 1, model, device, stream)
+
+
+def gabm_agent_layout(graph, agent_order: int = GABM_ORDER_COMMUNITY, sets_per_graph: int = 1) -> np.ndarray:
+    """The device order gabm_create gives one graph's agents (host arrays, host work only):
+    order[r] = the caller's id of device row r."""
+    rowptr = np.ascontiguousarray(graph.rowptr, np.uint64)
+    col = np.ascontiguousarray(graph.col, np.uint32)
+    w = np.ascontiguousarray(graph.w, np.float32)
+    age = np.ascontiguousarray(graph.age, np.uint8)
+    desc = _GraphDesc(int(graph.n), int(col.shape[0]), _ptr(rowptr, np.uint64), _ptr(col, np.uint32),
+                      _ptr(w, np.float32), _ptr(age, np.uint8), GABM_HOST)
+    out = np.empty(int(graph.n), np.uint32)
+    _check(load_library().gabm_agent_layout(ctypes.byref(desc), int(agent_order), int(sets_per_graph),
+                                            out.ctypes.data_as(ctypes.c_void_p)), None)
+    return out
 
 
 def gabm_create(graphs, model: ModelDesc, sets_per_graph: int = 1, stream=None) -> GabmCtx:
@@ -463,6 +479,45 @@ def gabm_autotune(ctx: GabmCtx, repetitions: int = 1) -> dict:
     """Time every schedule on the last forward's workload, keep the fastest; returns it."""
     _check(load_library().gabm_autotune(ctx.handle, int(repetitions)), ctx.handle)
     return gabm_get_schedule(ctx)
+
+
+def gabm_create_order_tuned(graphs, model: ModelDesc, R, m, S_age, n_seed, sets_per_graph: int = 1,
+                            stream=None, orders=(GABM_ORDER_COMMUNITY, GABM_ORDER_BFS), repetitions: int = 2):
+    """gabm_create with the device layout of the agents chosen by timing: a ctx is built for
+    each agent order in `orders` (the model's own agent_order is ignored), each runs this
+    workload's forward (R, m, S_age as gabm_forward takes them, n_seed per instance) and a
+    backward with dL/dD = 1 once untimed and then `repetitions` times under CUDA events on
+    the ctx stream; the fastest ctx is returned and the others are destroyed.  Results do
+    not depend on the order beyond fp32 summation order (ids stay the caller's), so the
+    choice is free.  Returns (ctx, {order: ms per forward + backward})."""
+    import dataclasses
+    import torch
+    T = int(R.shape[-1])
+    best, best_ms, times = None, None, {}
+    for order in orders:
+        ctx = gabm_create(graphs, dataclasses.replace(model, agent_order=int(order)), sets_per_graph, stream)
+        s = ctx.stream
+        if not hasattr(s, "cuda_stream"):
+            s = torch.cuda.ExternalStream(int(s)) if s is not None else torch.cuda.current_stream()
+        gD = None
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for rep in range(1 + repetitions):
+            if rep == 1:
+                e0.record(s)
+            D, _ = gabm_forward(ctx, T, R, m, S_age, n_seed)
+            if gD is None:
+                gD = torch.ones_like(D)
+            gabm_backward(ctx, gD)
+        e1.record(s)
+        e1.synchronize()
+        times[int(order)] = e0.elapsed_time(e1) / repetitions
+        if best is None or times[int(order)] < best_ms:
+            if best is not None:
+                gabm_destroy(best)
+            best, best_ms = ctx, times[int(order)]
+        else:
+            gabm_destroy(ctx)
+    return best, times
 
 
 def gabm_launch_count(ctx: GabmCtx) -> int:

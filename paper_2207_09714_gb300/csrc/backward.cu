@@ -169,6 +169,15 @@ __global__ void __launch_bounds__(kBlock, (MODE == kBwdStore && !DC) ? GABM_BWD_
         const int kd = t + 1 - Ei;
         const bool dc_row = DC && !SOFT && has_next && agent && !never && kd >= 1 && kd <= L - 1;
 
+        // the epilogue's row loads that do not depend on the sums go out before them, so
+        // that their latency overlaps the entry stream; A was stored on day E_i (soft:
+        // dL/ds on day t+1) at that day's scale
+        const bool readA = SOFT || (!never && Ei != t);
+        const float A_ld = ld_if(a.A + row, isS && readA);
+        float lam_ld = 0.f;
+        if constexpr (MODE != kBwdFused) lam_ld = ld_if(a.lam_t + row, isS);
+        const int age_ld = isS ? (int)a.age[row] : 0;
+
         float sum[NARR];
         {
             const bool act = (MODE == kBwdFused) ? (needA || isS || dc_row) : (needA || dc_row);
@@ -207,16 +216,13 @@ __global__ void __launch_bounds__(kBlock, (MODE == kBwdStore && !DC) ? GABM_BWD_
         float v = 0.f, pm = 0.f;
         int ai = 0;
         if (isS) {
-            ai = a.age[row];
+            ai = age_ld;
             const int inst = g;
             const size_t pi = (size_t)inst * a.ldP;
-            // loads that do not depend on G first, then the ring in batches of 8 slots; A was
-            // stored on day E_i (soft: dL/ds on day t+1) at that day's scale
-            const bool readA = SOFT || (!never && Ei != t);
-            const float Apre = readA ? a.A[row] * (SOFT ? fac_s[wib][1] : exp2i(sg[Ei] - sig_t)) : 0.f;
+            const float Apre = readA ? A_ld * (SOFT ? fac_s[wib][1] : exp2i(sg[Ei] - sig_t)) : 0.f;
             float Lam;
             if constexpr (MODE == kBwdFused) Lam = sum[NARR - 1] * a.gr.inv_Dbar[g];
-            else Lam = a.lam_t[row];
+            else Lam = lam_ld;
             // R/M split: the fate an exposure today would draw on day t + tau_EI
             bool phi = false;
             float vf = 0.5f;

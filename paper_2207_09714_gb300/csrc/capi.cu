@@ -266,7 +266,8 @@ gabm_status validate_model(const gabm_model_desc *md) {
     if (!(md->gumbel_tau == 1.0f)) return fail(nullptr, GABM_EUNSUPPORTED, "only gumbel_tau = 1 is implemented");
     if (md->lambda_policy != GABM_STORE_LAMBDA && md->lambda_policy != GABM_RECOMPUTE)
         return fail(nullptr, GABM_EINVAL, "unknown lambda_policy %d", md->lambda_policy);
-    if (md->agent_order != GABM_ORDER_INPUT && md->agent_order != GABM_ORDER_BFS)
+    if (md->agent_order != GABM_ORDER_INPUT && md->agent_order != GABM_ORDER_BFS &&
+        md->agent_order != GABM_ORDER_COMMUNITY)
         return fail(nullptr, GABM_EINVAL, "unknown agent_order %d", md->agent_order);
     return GABM_OK;
 }
@@ -350,6 +351,59 @@ std::vector<uint32_t> bfs_order(const HostGraph &h) {
             }
         }
     }
+    return order;
+}
+
+// Community order: agents of one densely connected group (a school, a workplace) become
+// consecutive rows, which breadth-first order does not give on a small-world contact
+// graph (a group's members are reached over many paths, long before the first of them is
+// expanded).  A few sweeps of label propagation find the groups: every agent, visited in
+// breadth-first order, takes the label most frequent among its in-neighbours (ties broken
+// by a seeded reservoir draw), labels updated in place.  Groups are then laid out at the
+// breadth-first position of their first member, and members in breadth-first order.
+std::vector<uint32_t> community_order(const HostGraph &h, int sweeps) {
+    const int64_t n = h.n;
+    std::vector<uint32_t> bfs = bfs_order(h);
+    std::vector<uint32_t> lab((size_t)n);
+    for (int64_t i = 0; i < n; ++i) lab[i] = (uint32_t)i;
+    std::vector<uint32_t> nl;
+    uint64_t rng = 0x243F6A8885A308D3ull;   // fixed: the layout is a function of the graph
+    for (int sw = 0; sw < sweeps; ++sw) {
+        for (int64_t q = 0; q < n; ++q) {
+            const uint32_t v = bfs[q];
+            const uint64_t p0 = h.rowptr[v], p1 = h.rowptr[v + 1];
+            if (p0 == p1) continue;
+            nl.resize(p1 - p0);
+            for (uint64_t p = p0; p < p1; ++p) nl[p - p0] = lab[h.col[p]];
+            std::sort(nl.begin(), nl.end());
+            uint32_t best = lab[v];
+            size_t best_c = 0, ties = 0;
+            for (size_t i = 0; i < nl.size();) {
+                size_t j = i;
+                while (j < nl.size() && nl[j] == nl[i]) ++j;
+                const size_t c = j - i;
+                if (c > best_c) {
+                    best_c = c;
+                    best = nl[i];
+                    ties = 1;
+                } else if (c == best_c) {   // keep each tied label with probability 1 / ties
+                    ++ties;
+                    rng = rng * 6364136223846793005ull + 1442695040888963407ull;
+                    if ((rng >> 33) % ties == 0) best = nl[i];
+                }
+                i = j;
+            }
+            lab[v] = best;
+        }
+    }
+    std::vector<uint64_t> bpos((size_t)n), first((size_t)n, (uint64_t)n);
+    for (int64_t q = 0; q < n; ++q) bpos[bfs[q]] = (uint64_t)q;
+    for (int64_t v = 0; v < n; ++v) first[lab[v]] = std::min(first[lab[v]], bpos[v]);
+    std::vector<uint64_t> key((size_t)n);
+    for (int64_t v = 0; v < n; ++v) key[v] = first[lab[v]] * (uint64_t)n + bpos[v];   // unique: bpos is
+    std::vector<uint32_t> order((size_t)n);
+    for (int64_t i = 0; i < n; ++i) order[i] = (uint32_t)i;
+    std::sort(order.begin(), order.end(), [&](uint32_t a, uint32_t b) { return key[a] < key[b]; });
     return order;
 }
 
@@ -445,6 +499,31 @@ bool build_sell(const std::vector<uint32_t> &rowptr, const std::vector<uint32_t>
 }
 
 // Relabel a graph: new row k is old agent order[k]; each row's entries sorted by new column.
+// The device order of one graph's agents (order[r] = the caller's id of row r): the agent
+// order, then degree windows of sigma rows (GABM_SELL_SIGMA, default 1024), then, with one
+// set per graph, the long rows grouped.
+int sell_sigma() {
+    int sigma = 1024;
+    if (const char *f = getenv("GABM_SELL_SIGMA")) sigma = std::max(1, atoi(f));
+    return sigma;
+}
+
+std::vector<uint32_t> layout_order(const HostGraph &h, int agent_order, int sets_per_graph) {
+    const int sigma = sell_sigma();
+    std::vector<uint32_t> order;
+    if (agent_order == GABM_ORDER_BFS) {
+        order = bfs_order(h);
+    } else if (agent_order == GABM_ORDER_COMMUNITY) {
+        order = community_order(h, 3);
+    } else {
+        order.resize((size_t)h.n);
+        for (int64_t i = 0; i < h.n; ++i) order[i] = (uint32_t)i;
+    }
+    sort_windows_by_degree(h, order, sigma);
+    if (sets_per_graph == 1) group_long_rows(h, order, sigma);
+    return order;
+}
+
 HostGraph permute_graph(const HostGraph &h, const std::vector<uint32_t> &order) {
     HostGraph o;
     o.n = h.n;
@@ -1197,6 +1276,20 @@ const char *gabm_version(void) { return "gabm-gb300 0.1 (sm_103a)"; }
 
 const char *gabm_last_error(const gabm_ctx *ctx) { return ctx ? ctx->err.c_str() : g_create_error.c_str(); }
 
+gabm_status gabm_agent_layout(const gabm_graph_desc *graph, int agent_order, int sets_per_graph,
+                              uint32_t *order_out) {
+    if (!graph) return fail(nullptr, GABM_EINVAL, "graph is NULL");
+    if (!order_out) return fail(nullptr, GABM_EINVAL, "order_out is NULL");
+    if (sets_per_graph < 1) return fail(nullptr, GABM_EINVAL, "sets_per_graph must be >= 1");
+    if (agent_order != GABM_ORDER_INPUT && agent_order != GABM_ORDER_BFS && agent_order != GABM_ORDER_COMMUNITY)
+        return fail(nullptr, GABM_EINVAL, "unknown agent_order %d", agent_order);
+    HostGraph h;
+    TRY(fetch_graph(*graph, 0, h));
+    const std::vector<uint32_t> order = layout_order(h, agent_order, sets_per_graph);
+    if (!order.empty()) memcpy(order_out, order.data(), sizeof(uint32_t) * order.size());
+    return GABM_OK;
+}
+
 // Host-side layout of a ctx's graphs, ready for upload (built by gabm_create and
 // gabm_create_bipartite).
 struct HostLayout {
@@ -1480,20 +1573,11 @@ gabm_status gabm_create(const gabm_graph_desc *graphs, int num_graphs, int sets_
         for (int64_t p = 0; p < hg[g].nnz; ++p) s += (double)hg[g].w[p];
         Dbar[g] = hg[g].n > 0 ? s / (double)hg[g].n : 0.0;
     }
-    // device layout: optionally relabel each graph's agents (D-bar above uses the caller's order)
+    // device layout: relabel each graph's agents (D-bar above uses the caller's order)
     std::vector<std::vector<uint32_t>> orders((size_t)num_graphs);
     const bool reorder = true;
-    int sigma = 1024;
-    if (const char *f = getenv("GABM_SELL_SIGMA")) sigma = std::max(1, atoi(f));
     for (int g = 0; g < num_graphs; ++g) {
-        if (model->agent_order == GABM_ORDER_BFS) {
-            orders[g] = bfs_order(hg[g]);
-        } else {
-            orders[g].resize((size_t)hg[g].n);
-            for (int64_t i = 0; i < hg[g].n; ++i) orders[g][i] = (uint32_t)i;
-        }
-        sort_windows_by_degree(hg[g], orders[g], sigma);
-        if (sets_per_graph == 1) group_long_rows(hg[g], orders[g], sigma);
+        orders[g] = layout_order(hg[g], model->agent_order, sets_per_graph);
         hg[g] = permute_graph(hg[g], orders[g]);
     }
     if (n_rows >= ((int64_t)1 << 31) - 64) return fail(nullptr, GABM_EUNSUPPORTED, "total rows >= 2^31");
@@ -1582,7 +1666,7 @@ gabm_status gabm_create(const gabm_graph_desc *graphs, int num_graphs, int sets_
     H.nnz_pad = nnz_pad;
     H.ntiles = ntiles;
     H.n_total = n_total;
-    H.sigma = sigma;
+    H.sigma = sell_sigma();
     H.num_graphs = num_graphs;
     return create_on_device(H, model, sets_per_graph, cuda_stream, out);
 }

@@ -149,6 +149,9 @@ __global__ void __launch_bounds__(NT, MINB) k_fwd_day(const FwdDayArgs a) {
         // A susceptible row with no infectious in-neighbour has lambda = 0 exactly (no
         // marked entry): it reads no entries and does not draw (u < p = 0 is false).
         const bool act = isS && cur.flag;
+        // the draw's row loads go out before the sums, so that their latency overlaps them
+        const int age_ld = act ? (int)a.age[row] : 0;
+        const uint32_t id_ld = act ? caller_id(a.gr, row, g) : 0u;
         float sum[1];
         const unsigned amask = __ballot_sync(0xffffffffu, act);
         if (flags && __popc(amask) <= GABM_COOP_ROWS) {   // few summing rows: warp-wide, together
@@ -163,9 +166,9 @@ __global__ void __launch_bounds__(NT, MINB) k_fwd_day(const FwdDayArgs a) {
         if (act) {
             const float Lam = sum[0] * a.gr.inv_Dbar[g];
             const int inst = g;
-            const float lam = (a.R[(size_t)inst * a.ldP + t] * a.S[inst * kAges + a.age[row]]) * Lam;
+            const float lam = (a.R[(size_t)inst * a.ldP + t] * a.S[inst * kAges + age_ld]) * Lam;
             const float p = -expm1f(-lam);
-            const uint32_t id = caller_id(a.gr, row, g);
+            const uint32_t id = id_ld;
             const float u = uniform_from_word(philox_word(a.seed, id, (uint32_t)t, (uint32_t)inst, 0u));
             if (u < p) {
                 a.e[row] = (int16_t)t;

@@ -40,7 +40,7 @@ def torch_cuda():
     return torch
 
 
-def model(c=None, tau_EI=4, tau_IR=7, seed=0, policy=capi.GABM_STORE_LAMBDA, order=capi.GABM_ORDER_BFS):
+def model(c=None, tau_EI=4, tau_IR=7, seed=0, policy=capi.GABM_STORE_LAMBDA, order=capi.GABM_ORDER_COMMUNITY):
     if c is None:
         c = synth.infectiousness_table(tau_EI, tau_IR)
     return capi.ModelDesc(tau_EI=tau_EI, tau_IR=tau_IR, c=np.asarray(c, np.float32), seed=seed,

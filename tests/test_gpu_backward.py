@@ -34,7 +34,7 @@ def _setup(pop, T, seed, n_seed, R=2.5, m=0.02, rng_seed=0, inst=0):
     return Rv, mv, S, md_o, ref, y, loss, gD, g
 
 
-def _replay(pop, T, Rv, mv, S, seed, E, gD, order=capi.GABM_ORDER_BFS):
+def _replay(pop, T, Rv, mv, S, seed, E, gD, order=capi.GABM_ORDER_COMMUNITY):
     ctx = capi.gabm_create([pop], model(seed=seed, policy=capi.GABM_RECOMPUTE, order=order))
     capi.gabm_set_state(ctx, T, E[None, :])
     Rd, md_, Sd = to_dev(Rv[None, :], mv[None, :], S[None, :])
@@ -55,7 +55,7 @@ def test_replay_adjoint_10k():
     assert np.abs(g["dR"]).max() > 0 and np.abs(g["dS"]).max() > 0
 
 
-@pytest.mark.parametrize("order", [capi.GABM_ORDER_INPUT, capi.GABM_ORDER_BFS])
+@pytest.mark.parametrize("order", [capi.GABM_ORDER_INPUT, capi.GABM_ORDER_BFS, capi.GABM_ORDER_COMMUNITY])
 def test_replay_adjoint_agent_orders(order):
     pop = synth.population_small(n=4099, seed=3)
     T = 28

@@ -154,9 +154,9 @@ def test_layout_and_bitmap_variants_are_bitwise_equal(knobs, monkeypatch):
     assert np.array_equal(capi.gabm_get_state(base)[0], e0)
 
 
-@pytest.mark.parametrize("order", [capi.GABM_ORDER_INPUT, capi.GABM_ORDER_BFS])
+@pytest.mark.parametrize("order", [capi.GABM_ORDER_INPUT, capi.GABM_ORDER_BFS, capi.GABM_ORDER_COMMUNITY])
 def test_agent_orders_agree(order):
-    """Either device layout of the agents gives the oracle's day steps (ids stay the caller's)."""
+    """Every device layout of the agents gives the oracle's day steps (ids stay the caller's)."""
     pop = synth.population_small(n=3001, seed=7)
     T = 20
     R, m, S = _params(T, R=3.0)
@@ -173,6 +173,24 @@ def test_agent_orders_agree(order):
     D, counts = capi.gabm_forward(ctx, T, Rd, md_, Sd, [9], want_counts=True)
     assert np.array_equal(np.sort(np.flatnonzero(capi.gabm_get_state(ctx)[0] == -4)),
                           np.sort(O.select_seeds(pop.n, 2, 0, 9)))
+
+
+def test_order_tuned_creation_keeps_the_fastest_layout():
+    """gabm_create_order_tuned times every candidate layout and returns one that runs the
+    workload exactly as a ctx created directly with that layout."""
+    pop = synth.population_typed(20_000, seed=3)
+    T = 15
+    R, m, S = _params(T, R=3.0)
+    Rd, md_, Sd = to_dev(R, m, S)
+    ctx, times = capi.gabm_create_order_tuned([pop], model(seed=4), Rd, md_, Sd, [12])
+    assert set(times) == {capi.GABM_ORDER_COMMUNITY, capi.GABM_ORDER_BFS}
+    assert all(v > 0 for v in times.values())
+    chosen = min(times, key=times.get)
+    ref = capi.gabm_create([pop], model(seed=4, order=chosen))
+    D0, _ = capi.gabm_forward(ctx, T, Rd, md_, Sd, [12])
+    D1, _ = capi.gabm_forward(ref, T, Rd, md_, Sd, [12])
+    assert np.array_equal(D0.cpu().numpy(), D1.cpu().numpy())
+    assert np.array_equal(capi.gabm_get_state(ctx)[0], capi.gabm_get_state(ref)[0])
 
 
 def test_directed_graph_and_hubs():
