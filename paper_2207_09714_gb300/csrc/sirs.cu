@@ -193,7 +193,13 @@ __global__ void __launch_bounds__(kBlock, 3) k_bwd_day_sirs(const SirsBwdArgs a)
         const bool isS = agent && (e_t == kNever || t - e_t >= C);
         cN += (agent && e_t != kNever && t - e_t == L);
 
-        const bool act = has_next && agent;
+        // gx(t+1) is used by the G of the row's susceptible days in [t + 2 - L, t]; a row
+        // with none lies, the whole window, inside one exposure's stretch (e, e + C) of not
+        // being susceptible, e in [t - C + 1, lo - 1], and skips the gather
+        const int lo = max(0, t + 2 - L);
+        bool covered = false;
+        for (int j = 0; j < j_t; ++j) covered |= (hr[j] >= t - C + 1 && hr[j] <= lo - 1);
+        const bool act = has_next && agent && !covered;
         float sum[1];
         row_sums<1>(a.m, cur.p0, cur.len, act, lane, contrib, want, sum);
         const float gx1 = sum[0];
