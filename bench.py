@@ -87,10 +87,11 @@ def _ncu_traffic(kernel: str, sha: str, workload: str):
     return None
 
 
-_SRC = {"k_fwd_day": ["forward.cu", "rowsum.cuh", "gabm_internal.cuh"],
-        "k_bwd_day": ["backward.cu", "rowsum.cuh", "gabm_internal.cuh"],
-        "k_fwd_day_b": ["batched.cu", "batched_common.cuh", "rowsum.cuh", "gabm_internal.cuh"],
-        "k_bwd_day_b": ["batched_bwd.cu", "batched_common.cuh", "rowsum.cuh", "gabm_internal.cuh"]}
+# a kernel's sources and capi.cu, which builds the device layout its traffic depends on
+_SRC = {"k_fwd_day": ["forward.cu", "rowsum.cuh", "gabm_internal.cuh", "capi.cu"],
+        "k_bwd_day": ["backward.cu", "rowsum.cuh", "gabm_internal.cuh", "capi.cu"],
+        "k_fwd_day_b": ["batched.cu", "batched_common.cuh", "rowsum.cuh", "gabm_internal.cuh", "capi.cu"],
+        "k_bwd_day_b": ["batched_bwd.cu", "batched_common.cuh", "rowsum.cuh", "gabm_internal.cuh", "capi.cu"]}
 
 
 def dram_rate(kernel: str, workload: str, ms_per_launch: float, peak: float):
