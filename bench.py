@@ -217,6 +217,7 @@ def trajectory_bytes(E, deg, T, L, n_rows, policy_store, frontier=None):
     S_cnt = np.cumsum(hist_n[::-1])[::-1][:T]
     S_nnz = np.cumsum(hist_e[::-1])[::-1][:T]
     new = np.bincount(E[live & ~never], minlength=T)[:T]
+    n_never = int(np.count_nonzero(live & never))
     if frontier is None:
         fwd = 8.0 * S_nnz + 4.0 * S_cnt + 1.0 * S_cnt + 2.0 * n_rows + 2.0 * new
     else:
@@ -240,9 +241,13 @@ def trajectory_bytes(E, deg, T, L, n_rows, policy_store, frontier=None):
         else:
             nA, eA = nS, eS
         ring_reads = max(0, min(L - 1, T - 1 - t) - 1)      # slots k = 2..L-1 inside the horizon
-        b = 8.0 * eA + 4.0 * nA + 2.0 * n_rows + 1.0 * nS
+        # entries (col + w) of the gathering rows; state and row length of every row; age
+        # of the susceptible rows
+        b = 8.0 * eA + 6.0 * n_rows + 1.0 * nS
         b += 4.0 * ring_reads * nS + (4.0 * nA if t + 1 < T else 0.0)   # ring reads and write
-        b += 4.0 * nS + 4.0 * nS                                     # A read/write, r write
+        # A read by the susceptible rows exposed later (not today, not never), written by
+        # today's exposures; r written by every susceptible row
+        b += 4.0 * (nS - n_never - new[t]) + 4.0 * new[t] + 4.0 * nS
         if policy_store:
             b += 4.0 * nS
         b += 72.0 * (n_rows // 32)                                   # per-tile partial sums
