@@ -301,8 +301,8 @@ def bench_batched(args, stream, peak, peak_kind):
     import torch
     from paper_2207_09714_gb300 import capi, synth
     from paper_2207_09714_gb300.autograd import GabmFunction
-    B, T = BATCH_SETS, BATCH_DAYS
-    pop = synth.population_typed(BATCH_AGENTS, seed=0)
+    B, T = BATCH_SETS, args.batched_days
+    pop = synth.population_typed(args.batched_agents, seed=0)
     c = synth.infectiousness_table(TAU_EI, TAU_IR)
     rng = np.random.default_rng(0)
     R_np = np.repeat(rng.uniform(1.5, 4.0, (B, 1)), T, axis=1).astype(np.float32)
@@ -327,7 +327,12 @@ def bench_batched(args, stream, peak, peak_kind):
         capi.gabm_backward(ctx, gD, dR=dR, dm=dm, dS_age=dS)
 
     step()
-    schedule = capi.gabm_autotune(ctx, 1)
+    if args.batched_schedule:   # a fixed schedule (profiling runs): no autotuner launches
+        spl_f, spl_b, smem, chunk = (int(x) for x in args.batched_schedule.split(","))
+        capi.gabm_set_schedule(ctx, spl_f, spl_b, smem, chunk)
+        schedule = capi.gabm_get_schedule(ctx)
+    else:
+        schedule = capi.gabm_autotune(ctx, 1)
     steps = max(args.steps // 2, 2)
     for _ in range(max(args.warmup, 3)):
         step()
@@ -362,8 +367,8 @@ def bench_batched(args, stream, peak, peak_kind):
     dom = "k_bwd_day_b" if b_ms >= f_ms else "k_fwd_day_b"
     src = ["batched_bwd.cu" if dom == "k_bwd_day_b" else "batched.cu", "batched_common.cuh", "rowsum.cuh",
            "gabm_internal.cuh"]
-    traffic = _ncu_traffic(dom, _kernel_source_sha(src), f"typed500k_B{B}_T{T}_store")
-    wl = f"typed500k_B{B}_T{T}_store"
+    wl = f"typed{pop.n // 1000}k_B{B}_T{T}_store"
+    traffic = _ncu_traffic(dom, _kernel_source_sha(src), wl)
     f_dr = dram_rate("k_fwd_day_b", wl, f_ms / f_n, peak)
     b_dr = dram_rate("k_bwd_day_b", wl, b_ms / b_n, peak)
     result = {
@@ -1028,6 +1033,12 @@ def main():
     ap.add_argument("--batched-only", action="store_true",
                     help="run only the batched ensemble; its result is the printed line")
     ap.add_argument("--no-plain", action="store_true", help="skip the per-set plain comparator")
+    ap.add_argument("--batched-agents", type=int, default=BATCH_AGENTS,
+                    help="agents of the batched ensemble's graph (smaller cases for profiling)")
+    ap.add_argument("--batched-days", type=int, default=BATCH_DAYS, help="days of the batched ensemble")
+    ap.add_argument("--batched-schedule", default="",
+                    help="fwd_sets_per_lane,bwd_sets_per_lane,fwd_smem_bitmap,bwd_sets_per_launch for the "
+                         "batched ensemble instead of the autotuner's choice")
     ap.add_argument("--no-configs", action="store_true",
                     help="skip the other configurations (10k forward, 1M x 64 sets, 32 counties, 8M power-law)")
     ap.add_argument("--only", choices=sorted(CONFIG_KEYS),
