@@ -74,6 +74,7 @@ __global__ void __launch_bounds__(kBlock, (MODE == kBwdStore && !DC) ? GABM_BWD_
     constexpr bool DUR = EXIT == kExitDur;
     constexpr int NARR = (MODE == kBwdFused) ? 2 : 1;
     constexpr bool SOFT = MODE == kBwdSoft;
+    constexpr int RB = 8;   // ring slots loaded together in the epilogue (16: 4% slower)
     __shared__ float c_s[kMaxL];
     __shared__ int slot_k[kMaxL];
     __shared__ int32_t red_s[kBlock / 32][2];
@@ -184,7 +185,11 @@ __global__ void __launch_bounds__(kBlock, (MODE == kBwdStore && !DC) ? GABM_BWD_
             bool want[NARR];
             want[0] = needA || dc_row;
             if constexpr (NARR == 2) want[1] = isS;
-            row_sums<NARR>(a.m, cur.p0, cur.len, act, lane, contrib, want, sum);
+            if constexpr (NARR == 1)   // every valid entry's w r_j(t+1) is taken
+                row_sums<1>(a.m, cur.p0, cur.len, act, lane, contrib, want, sum,
+                            [&](uint32_t j, float w) { return w * r_next[j]; });
+            else
+                row_sums<NARR>(a.m, cur.p0, cur.len, act, lane, contrib, want, sum);
         }
         float gx_mine = sum[0];
         if (a.self_q) gx_mine = __fmaf_rn(-a.self_q[row], a.self_r[row], gx_mine);
@@ -245,16 +250,16 @@ __global__ void __launch_bounds__(kBlock, (MODE == kBwdStore && !DC) ? GABM_BWD_
             float G = (FATE && !phi) ? 0.f : gtail;
             float H = gtail;
             if (has_next) G = __fmaf_rn(c_s[1], gx_mine * fac_s[wib][1], G);
-            for (int k0 = 2; k0 < L; k0 += 8) {
-                float rv[8];
+            for (int k0 = 2; k0 < L; k0 += RB) {
+                float rv[RB];
 #pragma unroll
-                for (int u = 0; u < 8; ++u) {
+                for (int u = 0; u < RB; ++u) {
                     const int k = k0 + u;
                     const bool ok = k < L && t + k < T;
                     rv[u] = ld_if(a.ring + (size_t)slot_k[ok ? k : 0] * a.ring_stride + row, ok);
                 }
 #pragma unroll
-                for (int u = 0; u < 8; ++u) {
+                for (int u = 0; u < RB; ++u) {
                     const int k = k0 + u;
                     if (k < L && t + k < T) {
                         const float gk = rv[u] * fac_s[wib][k];
@@ -301,22 +306,11 @@ __global__ void __launch_bounds__(kBlock, (MODE == kBwdStore && !DC) ? GABM_BWD_
         }
 
         // per-tile sums of gl * Lam by age bin (fp32 over 32 rows, FP64 from here on)
+        static_assert(kAges <= 16, "age bins fit the warp's bin sums");
         const unsigned smask = __ballot_sync(0xffffffffu, isS);
-        double outv = 0.0;
-        if (smask) {
-            float vb[kAges];
-#pragma unroll
-            for (int b = 0; b < kAges; ++b) vb[b] = (isS && ai == b) ? v : 0.f;
-#pragma unroll
-            for (int b = 0; b < kAges; ++b)
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) vb[b] += __shfl_xor_sync(0xffffffffu, vb[b], o);
-            float mine = 0.f;
-#pragma unroll
-            for (int b = 0; b < kAges; ++b) if (lane == b) mine = vb[b];
-            outv = (double)mine;
-        }
-        if (lane < kAges) a.P_t[(size_t)tile * kAges + lane] = outv;
+        float mine = 0.f;   // lanes 2b, 2b + 1: bin b
+        if (smask) mine = warp_bin_sums16(isS ? v : 0.f, ai, lane);
+        if (!(lane & 1) && (lane >> 1) < kAges) a.P_t[(size_t)tile * kAges + (lane >> 1)] = (double)mine;
         if constexpr (FATE) {
             // dL/dm of day t + tau_EI from this tile's exposures today (fixed tree, FP64 out)
 #pragma unroll

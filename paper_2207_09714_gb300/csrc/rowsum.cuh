@@ -10,6 +10,8 @@
 // so that a slice holds rows of similar length (little padding).
 #pragma once
 
+#include <type_traits>
+
 #include "gabm_internal.cuh"
 
 namespace gabm {
@@ -139,6 +141,28 @@ __device__ __forceinline__ void prefetch_slice(const Sell &m, uint32_t p0, uint3
     }
 }
 
+// Warp sums of v by bin (bins 0..15; lanes with nothing to add pass v = 0): a
+// reduce-scatter over the lanes, each step keeping half of a lane's bins and receiving
+// the same half from the partner lane, 16 shuffles for all 16 bins (a butterfly per bin
+// would take 80).  On return lanes 2b and 2b + 1 hold bin b's sum.  The addition tree is
+// fixed, so the sums do not depend on anything but the inputs.  Called by all 32 lanes.
+__device__ __forceinline__ float warp_bin_sums16(float v, int bin, int lane) {
+    float x[16];
+#pragma unroll
+    for (int b = 0; b < 16; ++b) x[b] = (bin == b) ? v : 0.f;
+#pragma unroll
+    for (int h = 8, o = 16; h >= 1; h >>= 1, o >>= 1) {
+        const bool hi = (lane & o) != 0;
+#pragma unroll
+        for (int i = 0; i < h; ++i) {
+            const float send = hi ? x[i] : x[i + h];
+            const float keep = hi ? x[i + h] : x[i];
+            x[i] = __fadd_rn(keep, __shfl_xor_sync(0xffffffffu, send, o));
+        }
+    }
+    return __fadd_rn(x[0], __shfl_xor_sync(0xffffffffu, x[0], 1));
+}
+
 // Row data of one tile, loaded one tile ahead of use.
 struct TileRows {
     int tile;
@@ -231,9 +255,14 @@ __device__ __forceinline__ int ld_if(const int16_t *p, bool pred, int dflt) {
 // a function of its marked entries in entry order, however they are visited
 // (row_sums here, or a warp walking one row).  Called by all 32 lanes; the batch runs
 // without branches.
-template <int NARR, class F>
+// No all-taken contribution: every batch goes through f.
+struct NoFull {};
+
+template <int NARR, class F, class FF = NoFull>
 __device__ __forceinline__ void row_sums(const Sell &m, uint32_t p0, uint32_t len, bool act, int lane, F f,
-                                         const bool (&want)[NARR], float (&sum)[NARR]) {
+                                         const bool (&want)[NARR], float (&sum)[NARR], FF ff = NoFull{}) {
+    constexpr bool HAS_FULL = !std::is_same<FF, NoFull>::value;
+    static_assert(!HAS_FULL || NARR == 1, "the all-taken path sums one contribution");
     float comp[NARR];
 #pragma unroll
     for (int a = 0; a < NARR; ++a) { sum[a] = 0.f; comp[a] = 0.f; }
@@ -242,7 +271,25 @@ __device__ __forceinline__ void row_sums(const Sell &m, uint32_t p0, uint32_t le
     // Mostly-active slices are read whole (padding and inactive rows included: every
     // entry below kmax lies inside the slice); sparse ones with predicated loads.
     const bool dense = __popc(amask) >= 24;
+    // Batches wholly below every lane's row length (all lanes summing) have every entry
+    // valid: with ff (the contribution of a valid entry when every valid entry is taken,
+    // ff(j, w) = what f gives) they run without predicates or selects; the operations
+    // and their order are those of the predicated path, so the sums are bitwise equal.
+    uint32_t kfull = 0u;
+    if constexpr (HAS_FULL) {
+        const unsigned fmask = __ballot_sync(0xffffffffu, act && want[0]);
+        kfull = __reduce_min_sync(0xffffffffu, (fmask == 0xffffffffu) ? len : 0u);
+    }
     auto load_batch = [&](uint32_t k0, uint32_t (&jv)[kUnroll], float (&wv)[kUnroll]) {
+        if (HAS_FULL && dense && k0 + (uint32_t)kUnroll <= kmax) {   // inside the slice: no predicates
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u) {
+                const uint32_t idx = p0 + (k0 + (uint32_t)u) * 32u + (uint32_t)lane;
+                jv[u] = __ldcs(m.col + idx);
+                wv[u] = __ldcs(m.w + idx);
+            }
+            return;
+        }
 #pragma unroll
         for (int u = 0; u < kUnroll; ++u) {
             const uint32_t k = k0 + (uint32_t)u;
@@ -259,6 +306,13 @@ __device__ __forceinline__ void row_sums(const Sell &m, uint32_t p0, uint32_t le
         }
     };
     auto use_batch = [&](uint32_t k0, const uint32_t (&jv)[kUnroll], const float (&wv)[kUnroll]) {
+        if constexpr (HAS_FULL) {
+            if (k0 + (uint32_t)kUnroll <= kfull) {
+#pragma unroll
+                for (int u = 0; u < kUnroll; ++u) kahan_add(sum[0], comp[0], ff(jv[u], wv[u]));
+                return;
+            }
+        }
 #pragma unroll
         for (int u = 0; u < kUnroll; ++u) {
             const uint32_t k = k0 + (uint32_t)u;

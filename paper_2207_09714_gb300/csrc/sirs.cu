@@ -201,7 +201,8 @@ __global__ void __launch_bounds__(kBlock, 3) k_bwd_day_sirs(const SirsBwdArgs a)
         for (int j = 0; j < j_t; ++j) covered |= (hr[j] >= t - C + 1 && hr[j] <= lo - 1);
         const bool act = has_next && agent && !covered;
         float sum[1];
-        row_sums<1>(a.m, cur.p0, cur.len, act, lane, contrib, want, sum);
+        row_sums<1>(a.m, cur.p0, cur.len, act, lane, contrib, want, sum,
+                    [&](uint32_t j, float w) { return w * r_next[j]; });
         const float gx1 = sum[0];
         if (act) a.ring[(size_t)slot_k[1] * a.ring_stride + row] = gx1;
 
@@ -253,21 +254,9 @@ __global__ void __launch_bounds__(kBlock, 3) k_bwd_day_sirs(const SirsBwdArgs a)
         a.r_cur[row] = rc;   // 0 for rows not susceptible today (r of a later day may sit there)
 
         const unsigned smask = __ballot_sync(0xffffffffu, isS);
-        double outv = 0.0;
-        if (smask) {
-            float vb[kAges];
-#pragma unroll
-            for (int b = 0; b < kAges; ++b) vb[b] = (isS && ai == b) ? v : 0.f;
-#pragma unroll
-            for (int b = 0; b < kAges; ++b)
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) vb[b] += __shfl_xor_sync(0xffffffffu, vb[b], o);
-            float mine = 0.f;
-#pragma unroll
-            for (int b = 0; b < kAges; ++b) if (lane == b) mine = vb[b];
-            outv = (double)mine;
-        }
-        if (lane < kAges) a.P_t[(size_t)tile * kAges + lane] = outv;
+        float mine = 0.f;   // lanes 2b, 2b + 1: bin b (the base kernel's tree)
+        if (smask) mine = warp_bin_sums16(isS ? v : 0.f, ai, lane);
+        if (!(lane & 1) && (lane >> 1) < kAges) a.P_t[(size_t)tile * kAges + (lane >> 1)] = (double)mine;
     }
     if (cur_g >= 0) {
         const int sN = __reduce_add_sync(0xffffffffu, cN);
