@@ -236,10 +236,8 @@ def trajectory_bytes(E, deg, T, L, n_rows, policy_store, frontier=None):
     bwd = np.zeros(T)
     for t in range(T):
         nS, eS = S_cnt[t], S_nnz[t]
-        if t + 1 < T:
-            nA, eA = ge(max(t + 2 - L, 0))
-        else:
-            nA, eA = nS, eS
+        # the last reverse day has no gx(t+1) to gather
+        nA, eA = ge(max(t + 2 - L, 0)) if t + 1 < T else (0, 0.0)
         ring_reads = max(0, min(L - 1, T - 1 - t) - 1)      # slots k = 2..L-1 inside the horizon
         # entries (col + w) of the gathering rows; state and row length of every row; age
         # of the susceptible rows
